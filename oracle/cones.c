@@ -1,0 +1,328 @@
+/*
+ * cones.c -- oracle projections onto (diagonally rescaled) disciplined cones.
+ *
+ * TEST INFRASTRUCTURE ONLY (see pdcs_oracle.h).  Plain FP64 loops.
+ *
+ *  - orc_proj_soc      : Theorem 1 (Sec. 3, eq. bisection-soc; proof App. A.1),
+ *                        the four cases in the printed order, case 4 by bisection;
+ *                        the first entry of the case-4 result is taken from the
+ *                        active constraint ||Dhat^{-1} y|| = s (eq. kkt_sys_fixed_2).
+ *  - orc_proj_rsoc     : rotated SOC as an orthogonal transform of the SOC
+ *                        (Sec. 2 notes the equivalence; App. B.2 uses the map
+ *                        ((w+r)/sqrt2, (w-r)/sqrt2)).
+ *  - orc_proj_exp      : Theorem 3 (App. A.2, eqs. h_rho, sp_rd, lrho_urho,
+ *                        vpvd_defn), cases 1-3 in closed form, case 4 by
+ *                        bisection of h on the interval (l_rho, u_rho).
+ *  - orc_proj_exp_dual : Remark after Theorem 3 (dual cone via Moreau).
+ *
+ * Readings where the paper is silent on floating point:
+ *  - membership tests of K_exp / K_exp^* are done in log form
+ *    (log t - log s >= r/s, and 1 + log t - log(-r) >= s/r) so they never overflow;
+ *  - case 4 of Theorem 3 searches over the logarithm of the offset of rho from an
+ *    endpoint of (l_rho, u_rho): rho = a3 - e^L (interval (-inf, a3)),
+ *    rho = a4 + e^L (interval (a4, inf)), and for the finite interval each half
+ *    from its own endpoint.  Offsets enter s~ = r0 (rho - a4) and r~ = s0 (a3 - rho)
+ *    exactly (App. A.2, eq. tilde_defs), and the sign of h is decided in log
+ *    form, so roots within 1e-16 |rho| of an endpoint and rho > 709 stay exact;
+ *  - every bisection runs until the midpoint equals an endpoint (FP64 limit).
+ */
+#include "pdcs_oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Second-order cone, Theorem 1.                                             */
+/* ------------------------------------------------------------------------ */
+
+/* f(lambda) of eq. (bisection-soc) / (kkt_sys_fixed_3):
+ *   sum_i ( dhat_i^{-1} x_i / (1 + 2 lambda dhat_i^{-2}) )^2 - t^2 / (1 - 2 lambda)^2 */
+static double soc_f(double lam, double t, const double* x, const double* dhat, int64_t n) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double di = dhat[i];
+        double q = (x[i] / di) / (1.0 + 2.0 * lam / (di * di));
+        s += q * q;
+    }
+    double w = 1.0 - 2.0 * lam;
+    return s - (t * t) / (w * w);
+}
+
+void orc_proj_soc(double t, const double* x, const double* d, int64_t n, double* out_t, double* out_x) {
+    double* dhat = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) dhat[i] = d[i + 1] / d[0]; /* dhat_i = d_{i+1} / d_1 */
+    double nDx = 0.0, nDinvx = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = dhat[i] * x[i], b = x[i] / dhat[i];
+        nDx += a * a;
+        nDinvx += b * b;
+    }
+    nDx = sqrt(nDx);
+    nDinvx = sqrt(nDinvx);
+
+    if (t <= 0.0 && nDx <= -t) { /* case 1: -(t,x) in the polar cone */
+        *out_t = 0.0;
+        for (int64_t i = 0; i < n; ++i) out_x[i] = 0.0;
+    } else if (nDinvx <= t) { /* case 2: already in the cone */
+        *out_t = t;
+        for (int64_t i = 0; i < n; ++i) out_x[i] = x[i];
+    } else if (t == 0.0) { /* case 3: lambda = 1/2 in closed form */
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double di = dhat[i];
+            double q = x[i] / (di + 1.0 / di);
+            s += q * q;
+            out_x[i] = x[i] / (1.0 + 1.0 / (di * di));
+        }
+        *out_t = sqrt(s);
+    } else { /* case 4: root of f on (0, 1/2) for t > 0, on (1/2, inf) for t < 0 */
+        double lo, hi;
+        int sign_lo;
+        if (t > 0.0) {
+            lo = 0.0;
+            hi = 0.5;
+            sign_lo = 1; /* f(0+) > 0 since ||Dhat^{-1} x|| > t */
+        } else {
+            lo = 0.5;
+            hi = 1.0;
+            sign_lo = -1; /* f(1/2+) = -inf */
+            while (soc_f(hi, t, x, dhat, n) <= 0.0) hi *= 2.0; /* lambda^2 f -> (||Dhat x||^2 - t^2)/4 > 0 */
+        }
+        for (int it = 0; it < 5000; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (!(mid > lo && mid < hi)) break;
+            double fm = soc_f(mid, t, x, dhat, n);
+            int sm = (fm > 0.0) - (fm < 0.0);
+            if (sm == 0) { lo = hi = mid; break; }
+            if (sm == sign_lo) lo = mid; else hi = mid;
+        }
+        double lam = 0.5 * (lo + hi);
+        /* y = (I + 2 lambda Dhat^{-2})^{-1} x; s from the active cone constraint
+         * ||Dhat^{-1} y|| = s of eq. kkt_sys_fixed_2, which equals t / (1 - 2 lambda)
+         * at the root but does not cancel when lambda is close to 1/2. */
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            out_x[i] = x[i] / (1.0 + 2.0 * lam / (dhat[i] * dhat[i]));
+            double q = out_x[i] / dhat[i];
+            s += q * q;
+        }
+        *out_t = sqrt(s);
+    }
+    free(dhat);
+}
+
+/* Rotated SOC {(x, y, z): ||z||^2 <= 2 x y, x, y >= 0} = Q K_soc with
+ * Q = [[1, 1], [1, -1]] / sqrt2 (+) I, orthogonal and symmetric.  With equal
+ * scales on the first two coordinates D Q = Q D, so
+ * Proj_{D K_rsoc}(v) = Q Proj_{D K_soc}(Q v). */
+void orc_proj_rsoc(const double* v, const double* d, int64_t dim, double* out) {
+    double* w = (double*)malloc(sizeof(double) * (size_t)dim);
+    double* p = (double*)malloc(sizeof(double) * (size_t)dim);
+    w[0] = (v[0] + v[1]) * M_SQRT1_2;
+    w[1] = (v[0] - v[1]) * M_SQRT1_2;
+    for (int64_t i = 2; i < dim; ++i) w[i] = v[i];
+    orc_proj_soc(w[0], w + 1, d, dim - 1, &p[0], p + 1);
+    out[0] = (p[0] + p[1]) * M_SQRT1_2;
+    out[1] = (p[0] - p[1]) * M_SQRT1_2;
+    for (int64_t i = 2; i < dim; ++i) out[i] = p[i];
+    free(w);
+    free(p);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exponential cone, Theorem 3 and the Remark (App. A.2).                     */
+/* ------------------------------------------------------------------------ */
+
+/* (r, s, t) in K_exp (eq. exp_cone), tested in log form. */
+static int in_kexp(double r, double s, double t) {
+    if (s > 0.0) return t > 0.0 && (log(t) - log(s)) >= r / s;
+    if (s == 0.0) return t >= 0.0 && r <= 0.0;
+    return 0;
+}
+
+/* (r, s, t) in K_exp^* (eq. exp_cone_dual), tested in log form. */
+static int in_kexp_dual(double r, double s, double t) {
+    if (r < 0.0) return t > 0.0 && (1.0 + log(t) - log(-r)) >= s / r;
+    if (r == 0.0) return s >= 0.0 && t >= 0.0;
+    return 0;
+}
+
+static double lse(double a, double b) { /* log(e^a + e^b) */
+    if (a == -INFINITY) return b;
+    if (b == -INFINITY) return a;
+    double mx = a > b ? a : b, mn = a > b ? b : a;
+    return mx + log1p(exp(mn - mx));
+}
+
+typedef struct {
+    double r0, s0, t0, dr, ds, dt, tau, a3, a4, ldt;
+    int anchor;  /* 3: rho measured from a3, 4: from a4 */
+    double dir;  /* rho = anchor + dir * delta */
+    double w34;  /* a3 - a4 */
+    int kind;    /* 1: r0 > 0, s0 > 0;  2: r0 <= 0, s0 > 0;  3: r0 > 0, s0 <= 0 */
+} exp_ctx;
+
+/* rho, s_p and r_d (eq. sp_rd) at offset delta from the anchor endpoint,
+ * using s_p = s~ / (d_r d~), r_d = d_s r~ / d~ (App. A.2, eq. tilde_defs). */
+static void exp_eval(const exp_ctx* e, double delta, double* rho, double* sp, double* rd) {
+    double st, rt, rh;
+    if (e->anchor == 4) {
+        rh = e->a4 + e->dir * delta;
+        st = e->r0 * (e->dir * delta);                 /* r0 (rho - a4) */
+        if (e->kind == 1) rt = e->s0 * (e->w34 - e->dir * delta); /* s0 (a3 - rho) */
+        else rt = e->tau * e->r0 - rh * e->s0;          /* both terms >= 0 here */
+    } else {
+        rh = e->a3 + e->dir * delta;
+        rt = e->s0 * (-e->dir * delta);                /* s0 (a3 - rho) */
+        if (e->kind == 1) st = e->r0 * (e->w34 + e->dir * delta); /* r0 (rho - a4) */
+        else st = e->s0 * e->tau - e->r0 + e->r0 * rh;  /* both terms >= 0 here */
+    }
+    double dt_ = rh * (rh - 1.0) + e->tau * e->tau;    /* d~ = rho(rho - 1) + tau^2 */
+    *rho = rh;
+    *sp = st / (e->dr * dt_);
+    *rd = e->ds * rt / dt_;
+}
+
+/* sign of h(rho) = d_t e^rho s_p - d_t^{-1} e^{-rho} r_d - t0 (eq. h_rho), decided in logs. */
+static int exp_hsign(const exp_ctx* e, double L) {
+    double rho, sp, rd;
+    exp_eval(e, exp(L), &rho, &sp, &rd);
+    double A = sp > 0.0 ? e->ldt + rho + log(sp) : -INFINITY;
+    double B = rd > 0.0 ? -e->ldt - rho + log(rd) : -INFINITY;
+    double lhs, rhs;
+    if (e->t0 >= 0.0) {
+        lhs = A;
+        rhs = e->t0 > 0.0 ? lse(B, log(e->t0)) : B;
+    } else {
+        lhs = lse(A, log(-e->t0));
+        rhs = B;
+    }
+    return (lhs > rhs) - (lhs < rhs);
+}
+
+/* bisection over L in (lo, hi) with sign(h) at the lo end equal to sign_lo */
+static double exp_bisect(const exp_ctx* e, double lo, double hi, int sign_lo) {
+    for (int it = 0; it < 5000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        int s = exp_hsign(e, mid);
+        if (s == 0) return mid;
+        if (s == sign_lo) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+void orc_proj_exp(const double* v0, const double* d, double* out) {
+    double r0 = v0[0], s0 = v0[1], t0 = v0[2];
+    double dr = d[0], ds = d[1], dt = d[2];
+    /* case 1: v0 in D K_exp */
+    if (in_kexp(r0 / dr, s0 / ds, t0 / dt)) { out[0] = r0; out[1] = s0; out[2] = t0; return; }
+    /* case 2: v0 in -D^{-1} K_exp^*, i.e. -D v0 in K_exp^* */
+    if (in_kexp_dual(-dr * r0, -ds * s0, -dt * t0)) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
+    /* case 3: r0 <= 0 and s0 <= 0 */
+    if (r0 <= 0.0 && s0 <= 0.0) { out[0] = r0; out[1] = 0.0; out[2] = t0 > 0.0 ? t0 : 0.0; return; }
+    /* case 4: root of h on (l_rho, u_rho), eq. lrho_urho */
+    exp_ctx e;
+    e.r0 = r0; e.s0 = s0; e.t0 = t0; e.dr = dr; e.ds = ds; e.dt = dt;
+    e.tau = ds / dr;
+    e.ldt = log(dt);
+    e.a3 = (s0 > 0.0) ? (r0 * ds) / (s0 * dr) : 0.0;
+    e.a4 = (r0 > 0.0) ? 1.0 - (s0 * ds) / (r0 * dr) : 0.0;
+    e.w34 = e.a3 - e.a4;
+    double L;
+    if (r0 > 0.0 && s0 > 0.0) {
+        e.kind = 1;
+        double W = fabs(e.w34);
+        if (!(W > 0.0)) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
+        double Lh = log(0.5 * W);
+        /* sign at the midpoint, measured from a4 */
+        e.anchor = 4;
+        e.dir = e.w34 > 0.0 ? 1.0 : -1.0;
+        int sm = exp_hsign(&e, Lh);
+        if (sm == 0) {
+            L = Lh;
+        } else if (sm > 0) { /* h(a4) < 0 < h(mid): root in the half next to a4 */
+            L = exp_bisect(&e, Lh - 800.0, Lh, -1);
+        } else {             /* h(mid) < 0 < h(a3): root in the half next to a3 */
+            e.anchor = 3;
+            e.dir = -e.dir;
+            L = exp_bisect(&e, Lh - 800.0, Lh, +1);
+        }
+    } else if (s0 > 0.0) { /* r0 <= 0: interval (-inf, a3), rho = a3 - delta */
+        e.kind = 2;
+        e.anchor = 3;
+        e.dir = -1.0;
+        double hi = 0.0;
+        while (exp_hsign(&e, hi) > 0 && hi < 60.0) hi = 2.0 * hi + 1.0; /* h -> -inf as rho -> -inf */
+        L = exp_bisect(&e, hi - 800.0, hi, +1);
+    } else { /* r0 > 0, s0 <= 0: interval (a4, inf), rho = a4 + delta */
+        e.kind = 3;
+        e.anchor = 4;
+        e.dir = 1.0;
+        double hi = 0.0;
+        while (exp_hsign(&e, hi) < 0 && hi < 60.0) hi = 2.0 * hi + 1.0; /* h -> +inf as rho -> +inf */
+        L = exp_bisect(&e, hi - 800.0, hi, -1);
+    }
+    double rho, sp, rd;
+    exp_eval(&e, exp(L), &rho, &sp, &rd);
+    if (!(sp > 0.0)) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
+    /* eq. vpvd_defn: v_p = (d_r rho, d_s, d_t e^rho) s_p, the t entry formed in logs */
+    out[0] = dr * rho * sp;
+    out[1] = ds * sp;
+    out[2] = exp(e.ldt + rho + log(sp));
+}
+
+/* Remark (App. A.2): Proj_{D K_exp^*}(v0) = v0 + Proj_{D^{-1} K_exp}(-v0). */
+void orc_proj_exp_dual(const double* v0, const double* d, double* out) {
+    double nv[3] = {-v0[0], -v0[1], -v0[2]};
+    double di[3] = {1.0 / d[0], 1.0 / d[1], 1.0 / d[2]};
+    double p[3];
+    orc_proj_exp(nv, di, p);
+    for (int i = 0; i < 3; ++i) out[i] = v0[i] + p[i];
+}
+
+/* Blockwise projection, eq. multi_cone_proj.  dual == 0: onto D C.
+ * dual == 1: onto (D C)^* = D^{-1} C^*, where zero^* = R, nonneg, SOC and RSOC
+ * are self-dual and exp^* is handled by the Remark. */
+void orc_proj_cones(const double* v, const double* d, int64_t m, const int32_t* types,
+                    const int64_t* dims, int64_t n_cones, int dual, double* out) {
+    (void)m;
+    int64_t o = 0;
+    for (int64_t k = 0; k < n_cones; ++k) {
+        int64_t dim = dims[k];
+        const double* vv = v + o;
+        const double* dd = d + o;
+        double* oo = out + o;
+        double* dinv = NULL;
+        if (dual && (types[k] == ORC_SOC || types[k] == ORC_RSOC)) {
+            dinv = (double*)malloc(sizeof(double) * (size_t)dim);
+            for (int64_t i = 0; i < dim; ++i) dinv[i] = 1.0 / dd[i];
+        }
+        switch (types[k]) {
+            case ORC_ZERO:
+                for (int64_t i = 0; i < dim; ++i) oo[i] = dual ? vv[i] : 0.0;
+                break;
+            case ORC_NONNEG:
+                for (int64_t i = 0; i < dim; ++i) oo[i] = vv[i] > 0.0 ? vv[i] : 0.0;
+                break;
+            case ORC_SOC:
+                orc_proj_soc(vv[0], vv + 1, dual ? dinv : dd, dim - 1, &oo[0], oo + 1);
+                break;
+            case ORC_RSOC:
+                orc_proj_rsoc(vv, dual ? dinv : dd, dim, oo);
+                break;
+            case ORC_EXP:
+                if (dual) {
+                    double dinv3[3] = {1.0 / dd[0], 1.0 / dd[1], 1.0 / dd[2]};
+                    orc_proj_exp_dual(vv, dinv3, oo);
+                } else {
+                    orc_proj_exp(vv, dd, oo);
+                }
+                break;
+            default:
+                break;
+        }
+        free(dinv);
+        o += dim;
+    }
+}

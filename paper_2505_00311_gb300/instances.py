@@ -1,0 +1,181 @@
+"""Seeded synthetic conic programs with a known optimal primal-dual pair.
+
+This module only draws inputs; it holds none of the solver's arithmetic and is
+shared by the tests, the benchmark and the smoke check.  Every generator uses
+numpy's PCG64 through ``np.random.default_rng(seed)``.
+
+Known-optimum construction (used for the mixed-cone programs):
+pick x* >= 0 and lambda* >= 0 with complementary supports, and per cone a
+complementary slack/dual pair s* in C, y* in C* with <s*, y*> = 0:
+  - zero rows:    s* = 0, y* ~ N(0, 1);
+  - nonneg rows:  half with s* > 0, y* = 0; half with s* = 0, y* > 0;
+  - SOC blocks:   a third on the boundary, s* = a (1, u), y* = b (1, -u), ||u|| = 1;
+                  a third with s* interior, y* = 0; a third with y* interior, s* = 0;
+  - exp blocks:   s* = a (rho, 1, e^rho), y* = b (-1, rho - 1, e^-rho) (orthogonal for
+                  every rho, as in the proof of Theorem 3), or one side interior and
+                  the other zero.
+Then c = K'y* + lambda* and h = K x* - s*; with l = 0, u = +inf every KKT
+residual of (x*, y*) vanishes and the optimal value is c'x* = h'y*.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+ZERO, NONNEG, SOC, RSOC, EXP = 0, 1, 2, 3, 4
+
+
+def _unique_cols(rng, row_ptr, n):
+    """Uniform column indices without repeats inside a row, sorted per row."""
+    m = row_ptr.size - 1
+    nnz = int(row_ptr[-1])
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(row_ptr))
+    cols = rng.integers(0, n, size=nnz, dtype=np.int64)
+    for _ in range(64):
+        key = rows * n + cols
+        order = np.argsort(key, kind="stable")
+        cols = cols[order]
+        key = key[order]
+        dup = np.zeros(nnz, dtype=bool)
+        dup[1:] = key[1:] == key[:-1]
+        if not dup.any():
+            break
+        cols[dup] = rng.integers(0, n, size=int(dup.sum()), dtype=np.int64)
+    return cols.astype(np.int32)
+
+
+def _soc_pair(rng, dim):
+    """(s*, y*) for one SOC block of size dim (dim >= 2)."""
+    kind = rng.integers(0, 3)
+    s = np.zeros(dim)
+    y = np.zeros(dim)
+    if kind == 0:  # both on the boundary, orthogonal
+        u = rng.standard_normal(dim - 1)
+        u /= np.linalg.norm(u)
+        a, b = rng.uniform(0.5, 1.5, 2)
+        s[0], s[1:] = a, a * u
+        y[0], y[1:] = b, -b * u
+    elif kind == 1:  # s* interior
+        w = rng.standard_normal(dim - 1)
+        s[0], s[1:] = np.linalg.norm(w) + rng.uniform(0.1, 1.0), w
+    else:  # y* interior
+        w = rng.standard_normal(dim - 1)
+        y[0], y[1:] = np.linalg.norm(w) + rng.uniform(0.1, 1.0), w
+    return s, y
+
+
+def _exp_pair(rng):
+    kind = rng.integers(0, 3)
+    if kind == 0:
+        rho = rng.uniform(-2.0, 2.0)
+        a, b = rng.uniform(0.5, 1.5, 2)
+        return a * np.array([rho, 1.0, np.exp(rho)]), b * np.array([-1.0, rho - 1.0, np.exp(-rho)])
+    if kind == 1:  # s* interior of K_exp: s > 0, t > s exp(r / s)
+        r, s_ = rng.uniform(-1.0, 1.0), rng.uniform(0.5, 1.5)
+        t = s_ * np.exp(r / s_) * (1.0 + rng.uniform(0.1, 1.0))
+        return np.array([r, s_, t]), np.zeros(3)
+    r, s_ = -rng.uniform(0.5, 1.5), rng.uniform(-1.0, 1.0)  # y* interior of K_exp^*
+    t = (-r / np.e) * np.exp(s_ / r) * (1.0 + rng.uniform(0.1, 1.0))
+    return np.zeros(3), np.array([r, s_, t])
+
+
+def _finish(rng, m, n, row_ptr, cols, vals, cone_types, cone_dims, name):
+    """Draw (x*, lambda*, s*, y*) and set c, h so that (x*, y*) is optimal."""
+    K = sp.csr_matrix((vals, cols, row_ptr), shape=(m, n))
+    x = np.zeros(n)
+    lam = np.zeros(n)
+    pos = rng.random(n) < 0.5
+    x[pos] = rng.uniform(0.1, 1.0, int(pos.sum()))
+    lam[~pos] = rng.uniform(0.1, 1.0, int((~pos).sum()))
+    s = np.zeros(m)
+    y = np.zeros(m)
+    o = 0
+    for t, d in zip(cone_types, cone_dims):
+        d = int(d)
+        if t == ZERO:
+            y[o:o + d] = rng.standard_normal(d)
+        elif t == NONNEG:
+            half = rng.random(d) < 0.5
+            s[o:o + d][half] = rng.uniform(0.1, 1.0, int(half.sum()))
+            y[o:o + d][~half] = rng.uniform(0.1, 1.0, int((~half).sum()))
+        elif t == SOC:
+            if d == 1:
+                s[o] = rng.uniform(0.1, 1.0)
+            else:
+                s[o:o + d], y[o:o + d] = _soc_pair(rng, d)
+        elif t == EXP:
+            s[o:o + 3], y[o:o + 3] = _exp_pair(rng)
+        else:
+            raise ValueError("unsupported cone in the known-optimum construction")
+        o += d
+    c = K.T @ y + lam
+    h = K @ x - s
+    return {
+        "name": name, "m": m, "n": n, "row_ptr": row_ptr, "col": cols, "val": vals,
+        "c": c, "h": h, "lb": None, "ub": None,
+        "cone_types": np.asarray(cone_types, dtype=np.int32),
+        "cone_dims": np.asarray(cone_dims, dtype=np.int64),
+        "x_star": x, "y_star": y, "s_star": s, "lambda_star": lam, "obj_star": float(c @ x),
+    }
+
+
+def small_socp(seed: int = 0, n: int = 2000, m: int = 1000, row_nnz: int = 20,
+               n_nonneg: int = 500, n_soc: int = 50, soc_dim: int = 10):
+    """Random sparse SOCP: n = 2,000, m = 1,000, 20 nonzeros per row (uniform columns,
+    N(0,1) values), C = 500 nonnegative rows + 50 SOC(10), x >= 0, known optimum."""
+    assert n_nonneg + n_soc * soc_dim == m
+    rng = np.random.default_rng(seed)
+    row_ptr = np.arange(m + 1, dtype=np.int64) * row_nnz
+    cols = _unique_cols(rng, row_ptr, n)
+    vals = rng.standard_normal(row_ptr[-1])
+    types = [NONNEG] + [SOC] * n_soc
+    dims = [n_nonneg] + [soc_dim] * n_soc
+    return _finish(rng, m, n, row_ptr, cols, vals, types, dims, "small_socp")
+
+
+def mixed_cone(seed: int = 1, n: int = 1_000_000, m: int = 500_000, nnz: int = 10_000_000,
+               n_nonneg: int = 200_000, soc_rows: int = 200_000, n_exp: int = 20_000,
+               soc_dim_range=(4, 64), scalar_chunk: int = 1000):
+    """Large mixed-cone LP/SOCP/exp program: row degrees clip(round(LogNormal(2.5, 1)), 2, 200)
+    rescaled to ~nnz in total, N(0,1) values, 200k nonnegative rows, SOC blocks of
+    dimension U{4..64} filling 200k rows, 20k exponential cones, the remaining rows zero
+    cones; block order shuffled; known optimum."""
+    n_zero = m - n_nonneg - soc_rows - 3 * n_exp
+    assert n_zero >= 0
+    rng = np.random.default_rng(seed)
+    deg = np.clip(np.round(rng.lognormal(2.5, 1.0, m)), 2, 200)
+    deg = np.clip(np.round(deg * (nnz / deg.sum())), 2, 200).astype(np.int64)
+    deg = np.minimum(deg, n)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(deg, out=row_ptr[1:])
+    cols = _unique_cols(rng, row_ptr, n)
+    vals = rng.standard_normal(int(row_ptr[-1]))
+    soc_dims = []
+    left = soc_rows
+    lo, hi = soc_dim_range
+    while left > 0:
+        d = int(rng.integers(lo, hi + 1))
+        if left - d < lo and left - d != 0:
+            d = left
+        soc_dims.append(d)
+        left -= d
+    blocks = []
+    for k in range(0, n_zero, scalar_chunk):
+        blocks.append((ZERO, min(scalar_chunk, n_zero - k)))
+    for k in range(0, n_nonneg, scalar_chunk):
+        blocks.append((NONNEG, min(scalar_chunk, n_nonneg - k)))
+    blocks += [(SOC, d) for d in soc_dims]
+    blocks += [(EXP, 3)] * n_exp
+    order = rng.permutation(len(blocks))
+    types = [blocks[i][0] for i in order]
+    dims = [blocks[i][1] for i in order]
+    return _finish(rng, m, n, row_ptr, cols, vals, types, dims, "mixed_cone")
+
+
+def scaled_mixed_cone(seed: int = 1, scale: float = 0.01):
+    """The mixed-cone program at a fraction of its size (same recipe)."""
+    n = int(1_000_000 * scale)
+    m = int(500_000 * scale)
+    return mixed_cone(seed=seed, n=n, m=m, nnz=int(10_000_000 * scale),
+                      n_nonneg=int(200_000 * scale), soc_rows=int(200_000 * scale),
+                      n_exp=int(20_000 * scale), scalar_chunk=max(1, int(1000 * scale)))

@@ -1,0 +1,443 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these re-types an oracle formula: the projections are checked against
+the textbook SOC projection, against Moreau pairs built from their definition
+(Lemma moreau_decomp with the boundary points used in the proofs of Theorems 1
+and 3), against brute-force minimisation on tiny inputs, and the solver is
+checked against hand-worked PDHG steps, a fixed point at a known optimum and
+the known optimal value.
+"""
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+import oracle
+from paper_2505_00311_gb300 import instances as I
+
+RNG = np.random.default_rng(1234)
+
+
+# ---------------------------------------------------------------------------
+# second-order cone (Theorem 1)
+# ---------------------------------------------------------------------------
+def textbook_soc(v):
+    """Projection onto the unscaled SOC (Parikh & Boyd, cited in Sec. 2)."""
+    t, x = v[0], v[1:]
+    nx = np.linalg.norm(x)
+    if nx <= t:
+        return v.copy()
+    if nx <= -t:
+        return np.zeros_like(v)
+    a = 0.5 * (t + nx)
+    return np.concatenate([[a], a * x / nx])
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3, 10, 64])
+def test_soc_identity_scaling_is_textbook(dim):
+    for _ in range(200):
+        v = RNG.standard_normal(dim) * RNG.choice([1e-3, 1.0, 1e3])
+        got = oracle.proj_soc(v)
+        np.testing.assert_allclose(got, textbook_soc(v), rtol=1e-13, atol=1e-13 * np.linalg.norm(v))
+
+
+def _soc_pair(dim, scale_spread):
+    d = np.exp(RNG.normal(0, scale_spread, dim))
+    u = RNG.standard_normal(dim - 1)
+    u /= np.linalg.norm(u)
+    a, b = np.exp(RNG.normal(0, 1, 2))
+    w = np.concatenate([[1.0], u])
+    wp = np.concatenate([[1.0], -u])
+    vp = a * d * w           # a D (1, u) on the boundary of D K_soc
+    vd = -b * wp / d         # -b D^{-1} (1, -u) on the boundary of -D^{-1} K_soc, <vp, vd> = 0
+    return vp + vd, vp, d
+
+
+@pytest.mark.parametrize("dim", [2, 3, 5, 17, 64])
+@pytest.mark.parametrize("spread", [0.0, 0.3, 1.5])
+def test_soc_recovers_constructed_moreau_pair(dim, spread):
+    for _ in range(100):
+        v0, vp, d = _soc_pair(dim, spread)
+        got = oracle.proj_soc(v0, d)
+        np.testing.assert_allclose(got, vp, rtol=0, atol=2e-13 * np.linalg.norm(v0))
+
+
+def soc_certificate(v0, p, d):
+    """Moreau certificate for D K_soc: p in D K_soc, v0 - p in -(D K_soc)^* = -D^{-1} K_soc, orthogonal."""
+    w = p / d
+    q = (p - v0) * d
+    scale = np.linalg.norm(v0) + 1e-300
+    assert np.linalg.norm(w[1:]) <= w[0] + 1e-12 * np.linalg.norm(w) + 1e-300
+    assert np.linalg.norm(q[1:]) <= q[0] + 1e-12 * np.linalg.norm(q) + 1e-300
+    assert abs(np.dot(p, v0 - p)) <= 1e-12 * scale * scale
+
+
+@pytest.mark.parametrize("dim", [2, 4, 33])
+def test_soc_moreau_certificate_random(dim):
+    for _ in range(300):
+        v0 = RNG.standard_normal(dim) * np.exp(RNG.normal(0, 2))
+        d = np.exp(RNG.normal(0, 1.0, dim))
+        soc_certificate(v0, oracle.proj_soc(v0, d), d)
+
+
+def test_soc_special_cases():
+    d = np.array([2.0, 0.5, 3.0])
+    assert np.all(oracle.proj_soc(np.zeros(3), d) == 0)
+    # t = 0, x != 0 (case 3) still gives a valid certificate
+    v0 = np.array([0.0, 1.0, -2.0])
+    soc_certificate(v0, oracle.proj_soc(v0, d), d)
+    # deep inside the polar cone -> 0
+    assert np.all(oracle.proj_soc(np.array([-10.0, 0.1, 0.1]), d) == 0)
+
+
+def test_soc_bruteforce_tiny():
+    """3-d rescaled SOC: scan the boundary D (s, s cos th, s sin th), s >= 0 (best s in
+    closed form for each angle), refine the best angle, and compare with the oracle."""
+    from scipy.optimize import minimize_scalar
+    for _ in range(30):
+        v0 = RNG.standard_normal(3) * 2
+        d = np.exp(RNG.normal(0, 0.7, 3))
+
+        def best_on_ray(th):
+            w = d * np.array([1.0, np.cos(th), np.sin(th)])
+            s = max(0.0, (w @ v0) / (w @ w))
+            return np.sum((s * w - v0) ** 2), s * w
+
+        grid = np.linspace(0, 2 * np.pi, 4001)
+        vals = [best_on_ray(t)[0] for t in grid]
+        i = int(np.argmin(vals))
+        step = grid[1] - grid[0]
+        r = minimize_scalar(lambda t: best_on_ray(t)[0], bounds=(grid[i] - step, grid[i] + step), method="bounded",
+                            options={"xatol": 1e-13})
+        fbest, pbest = best_on_ray(r.x)
+        inside = np.linalg.norm(v0[1:] / d[1:]) <= v0[0] / d[0]
+        got = oracle.proj_soc(v0, d)
+        if inside:
+            np.testing.assert_array_equal(got, v0)
+            continue
+        assert np.sum((got - v0) ** 2) <= fbest * (1 + 1e-12) + 1e-15
+        np.testing.assert_allclose(got, pbest, atol=1e-6 * (1 + np.linalg.norm(v0)))
+
+
+# ---------------------------------------------------------------------------
+# rotated second-order cone
+# ---------------------------------------------------------------------------
+def in_rsoc(w, tol):
+    x, y, z = w[0], w[1], w[2:]
+    return x >= -tol and y >= -tol and z @ z <= 2 * x * y + tol
+
+
+@pytest.mark.parametrize("dim", [2, 3, 12])
+def test_rsoc_moreau_certificate(dim):
+    for _ in range(300):
+        v0 = RNG.standard_normal(dim) * 2
+        d = np.exp(RNG.normal(0, 0.8, dim))
+        d[1] = d[0]
+        p = oracle.proj_rsoc(v0, d)
+        s = np.linalg.norm(v0) ** 2 + 1e-300
+        assert in_rsoc(p / d, 1e-11 * s)
+        assert in_rsoc((p - v0) * d, 1e-11 * s)  # v0 - p in -D^{-1} K_rsoc (self-dual)
+        assert abs(np.dot(p, v0 - p)) <= 1e-12 * s
+
+
+def test_rsoc_fixes_its_points_and_the_lasso_map():
+    # (x, y, z) with ||z||^2 = 2xy lies on the boundary and is its own projection
+    z = np.array([0.3, -0.4])
+    x, y = 0.5, (z @ z) / (2 * 0.5)
+    v = np.array([x, y, *z])
+    np.testing.assert_allclose(oracle.proj_rsoc(v), v, atol=1e-15)
+    # App. B.2: ||y||^2 <= 2 r  <=>  ((1+r)/sqrt2, (1-r)/sqrt2, y) in K_soc, i.e. (1, r, y) in K_rsoc
+    r = 0.7
+    yy = np.array([0.5, 0.9])
+    inside = yy @ yy <= 2 * r
+    w = np.array([(1 + r) / np.sqrt(2), (1 - r) / np.sqrt(2), *yy])
+    assert inside == (np.linalg.norm(w[1:]) <= w[0])
+    assert inside == in_rsoc(np.array([1.0, r, *yy]), 0.0)
+
+
+# ---------------------------------------------------------------------------
+# exponential cone (Theorem 3 and the Remark)
+# ---------------------------------------------------------------------------
+def exp_pair(rho, sp, rd, d):
+    """Boundary pair of the proof of Theorem 3 (eq. vpvd_defn): orthogonal for every rho."""
+    dr, ds, dt = d
+    vp = sp * np.array([dr * rho, ds, dt * np.exp(rho)])
+    vd = rd * np.array([1 / dr, (1 - rho) / ds, -np.exp(-rho) / dt])
+    return vp, vd
+
+
+@pytest.mark.parametrize("spread", [0.0, 0.5, 2.0])
+def test_exp_recovers_constructed_moreau_pair(spread):
+    for _ in range(400):
+        d = np.exp(RNG.normal(0, spread, 3))
+        rho = RNG.uniform(-8, 8)
+        sp, rd = np.exp(RNG.normal(0, 1.5, 2))
+        vp, vd = exp_pair(rho, sp, rd, d)
+        v0 = vp + vd
+        got = oracle.proj_exp(v0, d)
+        np.testing.assert_allclose(got, vp, rtol=0, atol=1e-12 * np.linalg.norm(v0))
+
+
+def test_exp_stressed_roots_near_the_endpoints():
+    """Roots within ~1e-16 |rho| of an endpoint and rho well beyond 709."""
+    cases = [
+        (120.0, 1e-40, 1.0), (300.0, 1e-120, 2.0), (800.0, 1e-300, 1.0),
+        (-120.0, 1.0, 1e-40), (-600.0, 2.0, 1e-250), (0.5, 1e-8, 1e-8),
+    ]
+    for rho, sp, rd in cases:
+        for d in [np.ones(3), np.array([0.3, 2.5, 1.7])]:
+            vp, vd = exp_pair(rho, sp, rd, d)
+            if not np.all(np.isfinite(vp)) or not np.all(np.isfinite(vd)):
+                continue
+            v0 = vp + vd
+            got = oracle.proj_exp(v0, d)
+            assert np.all(np.isfinite(got))
+            np.testing.assert_allclose(got, vp, rtol=0, atol=1e-12 * np.linalg.norm(v0))
+            # the projection itself is accurate relative to its own size in the r and s entries
+            if np.abs(vp[:2]).max() > 1e-200:
+                np.testing.assert_allclose(got[:2], vp[:2], rtol=1e-9, atol=1e-300)
+
+
+def _in_kexp_exact(w):
+    r, s, t = w
+    if s > 0:
+        return t > 0 and np.log(t) - np.log(s) >= r / s
+    return s == 0 and t >= 0 and r <= 0
+
+
+def _in_kexp_dual_exact(w):
+    r, s, t = w
+    if r < 0:
+        return t > 0 and 1 + np.log(t) - np.log(-r) >= s / r
+    return r == 0 and s >= 0 and t >= 0
+
+
+def in_kexp(w, eps):
+    """w lies within eps of K_exp: w + eps (0, 1, 2) is in K_exp ((0, 1, 2) is interior, norm < 3)."""
+    return _in_kexp_exact(np.asarray(w) + eps * np.array([0.0, 1.0, 2.0]))
+
+
+def in_kexp_dual(w, eps):
+    """w lies within eps of K_exp^*: w + eps (-1, 0, 1) is in K_exp^* ((-1, 0, 1) is interior)."""
+    return _in_kexp_dual_exact(np.asarray(w) + eps * np.array([-1.0, 0.0, 1.0]))
+
+
+def test_exp_moreau_certificate_random():
+    for _ in range(3000):
+        v0 = RNG.standard_normal(3) * np.exp(RNG.normal(0, 1.5))
+        d = np.exp(RNG.normal(0, 1.0, 3))
+        p = oracle.proj_exp(v0, d)
+        q = v0 - p
+        s = np.linalg.norm(v0)
+        eps = 1e-12 * s * max(d.max(), 1 / d.min())
+        assert in_kexp(p / d, eps)
+        assert in_kexp_dual(-q * d, eps)
+        assert abs(p @ q) <= 1e-12 * s * s
+
+
+def test_exp_simple_cases():
+    d = np.array([0.5, 2.0, 3.0])
+    # case 1: in D K_exp
+    v = d * np.array([0.3, 1.0, 2.0 * np.exp(0.3)])
+    np.testing.assert_array_equal(oracle.proj_exp(v, d), v)
+    # case 2: in the polar cone -D^{-1} K_exp^*
+    v = -np.array([-1.0, 0.2, 3.0 * np.exp(0.2 / -1.0 - 1.0) * 1.0]) / d
+    assert np.all(oracle.proj_exp(v, d) == 0)
+    # case 3: r0 <= 0, s0 <= 0 -> (r0, 0, t0^+)
+    for t0 in [2.0, -2.0]:
+        v = np.array([-1.0, -0.5, t0])
+        np.testing.assert_array_equal(oracle.proj_exp(v, d), [-1.0, 0.0, max(t0, 0.0)])
+
+
+def test_exp_bruteforce_tiny():
+    for _ in range(20):
+        d = np.exp(RNG.normal(0, 0.5, 3))
+        v0 = RNG.standard_normal(3)
+        got = oracle.proj_exp(v0, d)
+        if np.linalg.norm(got) < 1e-9 or np.allclose(got, v0):
+            continue
+
+        def dist(q):  # boundary point D (r, s, s e^{r/s}), s = e^q[1]
+            s = np.exp(q[1])
+            w = d * np.array([q[0], s, s * np.exp(q[0] / s)])
+            return np.sum((w - v0) ** 2)
+
+        s0 = max(got[1] / d[1], 1e-6)
+        r = minimize(dist, [got[0] / d[0], np.log(s0)], method="Nelder-Mead",
+                     options={"xatol": 1e-12, "fatol": 1e-16, "maxiter": 4000})
+        assert np.sum((got - v0) ** 2) <= r.fun + 1e-10
+
+
+def test_exp_dual_by_remark_certificate():
+    for _ in range(1000):
+        v0 = RNG.standard_normal(3) * 2
+        d = np.exp(RNG.normal(0, 1.0, 3))
+        p = oracle.proj_exp_dual(v0, d)   # onto D K_exp^*
+        q = v0 - p                        # must lie in -(D K^*)^* = -D^{-1} K_exp
+        s = np.linalg.norm(v0)
+        eps = 1e-12 * s * max(d.max(), 1 / d.min())
+        assert in_kexp_dual(p / d, eps)
+        assert in_kexp(-q * d, eps)
+        assert abs(p @ q) <= 1e-12 * s * s
+
+
+def test_proj_cones_blockwise():
+    types = [oracle.ZERO, oracle.NONNEG, oracle.SOC, oracle.EXP, oracle.RSOC]
+    dims = [2, 3, 4, 3, 3]
+    v = RNG.standard_normal(sum(dims))
+    d = np.exp(RNG.normal(0, 0.5, v.size))
+    d[12] = d[13]
+    p = oracle.proj_cones(v, types, dims, d)
+    np.testing.assert_array_equal(p[:2], 0)
+    np.testing.assert_array_equal(p[2:5], np.maximum(v[2:5], 0))
+    np.testing.assert_array_equal(p[5:9], oracle.proj_soc(v[5:9], d[5:9]))
+    np.testing.assert_array_equal(p[9:12], oracle.proj_exp(v[9:12], d[9:12]))
+    np.testing.assert_array_equal(p[12:], oracle.proj_rsoc(v[12:], d[12:]))
+    q = oracle.proj_cones(v, types, dims, d, dual=True)
+    np.testing.assert_array_equal(q[:2], v[:2])                        # zero^* = R
+    np.testing.assert_array_equal(q[2:5], np.maximum(v[2:5], 0))
+    np.testing.assert_allclose(q[9:12], oracle.proj_exp_dual(v[9:12], 1 / d[9:12]), rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# KKT errors (eq. PDCS_terminate_tolerance)
+# ---------------------------------------------------------------------------
+def tiny_lp():
+    # min x1 + x2  s.t.  x1 + x2 - 1 >= 0,  x >= 0;  optimum 1
+    return {"m": 1, "n": 2, "row_ptr": np.array([0, 2]), "col": np.array([0, 1]), "val": np.array([1.0, 1.0]),
+            "c": np.array([1.0, 1.0]), "h": np.array([1.0]), "lb": None, "ub": None,
+            "cone_types": np.array([oracle.NONNEG]), "cone_dims": np.array([1])}
+
+
+def test_kkt_hand_worked_values():
+    k = oracle.kkt(tiny_lp(), np.array([0.25, 0.25]), np.array([2.0]))
+    # K x - h = -0.5 -> residual 0.5 over 1 + max(1, 0.5, 0) = 2
+    assert k["err_p"] == pytest.approx(0.25, rel=1e-15)
+    # lambda = c - K'y = (-1, -1), Lambda = R+ -> residual 1 over 1 + max(1, 2) = 3
+    assert k["err_d"] == pytest.approx(1 / 3, rel=1e-15)
+    # pobj 0.5, dobj = h'y + l'mu^+ = 2 -> 1.5 / (1 + 2)
+    assert k["err_gap"] == pytest.approx(0.5, rel=1e-15)
+    k = oracle.kkt(tiny_lp(), np.array([0.5, 0.5]), np.array([1.0]))
+    assert k["err_p"] == 0 and k["err_d"] == 0 and k["err_gap"] == 0
+
+
+def test_kkt_with_box_bounds_hand_worked():
+    p = tiny_lp()
+    p["lb"] = np.array([-np.inf, 0.0])
+    p["ub"] = np.array([2.0, np.inf])
+    # lambda = c - K'y = (1 - 3, 1 - 3) = (-2, -2); Lambda_1 = R^- (only u finite), Lambda_2 = R^+
+    k = oracle.kkt(p, np.array([1.0, 0.0]), np.array([3.0]))
+    assert k["err_d"] == pytest.approx(2 / (1 + 3), rel=1e-15)
+    # dual objective: h'y + u1 * mu1 (mu1 = -2) = 3 - 4 = -1; primal 1 -> gap 2 / (1 + 1)
+    assert k["dobj"] == pytest.approx(-1.0, rel=1e-15)
+    assert k["err_gap"] == pytest.approx(1.0, rel=1e-15)
+
+
+def test_kkt_vanishes_at_known_optimum_and_detects_perturbations():
+    p = I.small_socp(0)
+    k = oracle.kkt(p, p["x_star"], p["y_star"])
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) < 1e-13
+    assert k["pobj"] == pytest.approx(p["obj_star"], rel=1e-13)
+    x = p["x_star"].copy()
+    x[3] += 0.1
+    assert oracle.kkt(p, x, p["y_star"])["err_p"] > 1e-4
+    y = p["y_star"].copy()
+    y[7] += 0.1
+    assert oracle.kkt(p, p["x_star"], y)["err_d"] > 1e-4
+
+
+def test_kkt_vanishes_at_known_optimum_mixed_cones():
+    p = I.scaled_mixed_cone(1, 0.01)
+    k = oracle.kkt(p, p["x_star"], p["y_star"])
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# solver
+# ---------------------------------------------------------------------------
+def one_row_lp():
+    # min x  s.t.  x - 1 >= 0, x >= 0
+    return {"m": 1, "n": 1, "row_ptr": np.array([0, 1]), "col": np.array([0]), "val": np.array([1.0]),
+            "c": np.array([1.0]), "h": np.array([1.0]), "lb": None, "ub": None,
+            "cone_types": np.array([oracle.NONNEG]), "cone_dims": np.array([1])}
+
+
+def test_first_pdhg_steps_hand_worked():
+    """eq. PDHG + Algorithm 1 on min x s.t. x >= 1, no rescaling, from z = 0.
+    eta_0 = 1 / max|K| = 1 and omega_0 = ||c|| / ||h|| = 1, so tau = sigma = 1:
+      xhat = max(0 - (1 - 0), 0) = 0,  yhat = max(0 + (1 - K(0)), 0) = 1;
+      dx = 0 so the step is accepted and the next eta is (1 + 2^-0.6) * 1;
+      Halpern with k = 0: z^1 = 1/2 (2 zhat - z) + 1/2 z^0 = zhat = (0, 1).
+    Second evaluation with tau = sigma = 1 + 2^-0.6:
+      xhat = max(0 - tau (1 - 1), 0) = 0,  yhat = 1 + sigma (1 - 0)."""
+    s = oracle.Solver(one_row_lp(), rescale=oracle.RESCALE_NONE)
+    s.run(1)
+    x, y, xh, yh = s.iterate()
+    assert xh[0] == 0.0 and yh[0] == 1.0
+    assert x[0] == 0.0 and y[0] == 1.0
+    eta1 = 1.0 + 2.0 ** -0.6
+    assert s.scalars()["eta"] == pytest.approx(eta1, rel=1e-15)
+    s.run(1)
+    x, y, xh, yh = s.iterate()
+    assert xh[0] == 0.0
+    assert yh[0] == pytest.approx(1.0 + eta1, rel=1e-15)
+
+
+@pytest.mark.parametrize("rescale", [oracle.RESCALE_NONE, oracle.RESCALE_COORD])
+def test_known_optimum_is_a_fixed_point(rescale):
+    p = I.small_socp(0)
+    s = oracle.Solver(p, rescale=rescale, step_mode=oracle.STEP_CONSTANT)
+    s.set_start(p["x_star"], p["y_star"])
+    s.run(1)
+    x, y, xh, yh = s.iterate()
+    np.testing.assert_allclose(xh, p["x_star"], atol=1e-12)
+    np.testing.assert_allclose(yh, p["y_star"], atol=1e-12)
+
+
+def test_solver_reaches_known_optimum():
+    p = I.small_socp(0)
+    s = oracle.Solver(p)
+    st = s.run(50_000, tol=1e-6)
+    assert st == oracle.CONVERGED
+    x, y = s.solution()
+    k = oracle.kkt(p, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1e-6
+    assert abs(k["pobj"] - p["obj_star"]) <= 1e-5 * (1 + abs(p["obj_star"]))
+    assert np.all(x >= 0)
+
+
+@pytest.mark.parametrize("mode", [oracle.RESCALE_NONE, oracle.RESCALE_BLOCK])
+def test_solution_independent_of_scaling(mode):
+    p = I.small_socp(0, n=200, m=100, row_nnz=8, n_nonneg=50, n_soc=5, soc_dim=10)
+    s = oracle.Solver(p, rescale=mode)
+    assert s.run(200_000, tol=1e-7) == oracle.CONVERGED
+    x, y = s.solution()
+    k = oracle.kkt(p, x, y)
+    assert abs(k["pobj"] - p["obj_star"]) <= 1e-6 * (1 + abs(p["obj_star"]))
+
+
+def test_plain_pdhg_converges_on_small_lp():
+    p = I.small_socp(3, n=60, m=30, row_nnz=5, n_nonneg=30, n_soc=0, soc_dim=1)
+    s = oracle.Solver(p, rescale=oracle.RESCALE_NONE, step_mode=oracle.STEP_PLAIN)
+    s.run(200_000, tol=1e-5)
+    x, y = s.solution()
+    k = oracle.kkt(p, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1e-5
+    # plain PDHG uses 0.9 / ||K||_2 (App. D); the power estimate matches the SVD
+    from scipy.sparse import csr_matrix
+    K = csr_matrix((p["val"], p["col"], p["row_ptr"]), shape=(p["m"], p["n"])).toarray()
+    true = np.linalg.norm(K, 2)
+    assert 0.99 * true <= s.norm2() <= true * (1 + 1e-12)  # power iteration approaches from below
+
+
+def test_ruiz_equilibrates():
+    p = I.small_socp(0)
+    s = oracle.Solver(p, pock_chambolle=0, ruiz_iters=30)
+    dr, dc = s.scaling()
+    from scipy.sparse import csr_matrix
+    K = csr_matrix((p["val"], p["col"], p["row_ptr"]), shape=(p["m"], p["n"]))
+    Ks = abs(csr_matrix(np.diag(dr)) @ K @ csr_matrix(np.diag(dc)))
+    assert np.allclose(Ks.max(axis=1).toarray().ravel(), 1.0, atol=1e-3)
+    assert np.allclose(Ks.max(axis=0).toarray().ravel(), 1.0, atol=1e-3)
+    s0 = oracle.Solver(p, rescale=oracle.RESCALE_NONE)
+    dr0, dc0 = s0.scaling()
+    assert np.all(dr0 == 1) and np.all(dc0 == 1)
