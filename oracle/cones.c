@@ -18,12 +18,16 @@
  * Readings where the paper is silent on floating point:
  *  - membership tests of K_exp / K_exp^* are done in log form
  *    (log t - log s >= r/s, and 1 + log t - log(-r) >= s/r) so they never overflow;
- *  - case 4 of Theorem 3 searches over the logarithm of the offset of rho from an
- *    endpoint of (l_rho, u_rho): rho = a3 - e^L (interval (-inf, a3)),
+ *  - case 4 of Theorem 3 searches over the logarithm L of the offset of rho from
+ *    an endpoint of (l_rho, u_rho): rho = a3 - e^L (interval (-inf, a3)),
  *    rho = a4 + e^L (interval (a4, inf)), and for the finite interval each half
- *    from its own endpoint.  Offsets enter s~ = r0 (rho - a4) and r~ = s0 (a3 - rho)
- *    exactly (App. A.2, eq. tilde_defs), and the sign of h is decided in log
- *    form, so roots within 1e-16 |rho| of an endpoint and rho > 709 stay exact;
+ *    from its own endpoint.  The vanishing factor of s~ = r0 (rho - a4) or
+ *    r~ = s0 (a3 - rho) (App. A.2, eq. tilde_defs) enters as log r0 + L or
+ *    log s0 + L, the sign of h is decided in log form, and the lower end of the
+ *    search grows until h shows its endpoint sign, so roots within 1e-16 |rho| of
+ *    an endpoint, offsets below the smallest double and rho > 709 are handled;
+ *  - the result takes, per coordinate, the smaller of v_p and v_d from its formula
+ *    (eq. vpvd_defn) and the other from v0 = v_p + v_d (eq. diagonal_moreau);
  *  - every bisection runs until the midpoint equals an endpoint (FP64 limit).
  */
 #include "pdcs_oracle.h"
@@ -157,38 +161,50 @@ static double lse(double a, double b) { /* log(e^a + e^b) */
 typedef struct {
     double r0, s0, t0, dr, ds, dt, tau, a3, a4, ldt;
     int anchor;  /* 3: rho measured from a3, 4: from a4 */
-    double dir;  /* rho = anchor + dir * delta */
+    double dir;  /* rho = anchor + dir * delta, delta = e^L */
     double w34;  /* a3 - a4 */
     int kind;    /* 1: r0 > 0, s0 > 0;  2: r0 <= 0, s0 > 0;  3: r0 > 0, s0 <= 0 */
 } exp_ctx;
 
-/* rho, s_p and r_d (eq. sp_rd) at offset delta from the anchor endpoint,
- * using s_p = s~ / (d_r d~), r_d = d_s r~ / d~ (App. A.2, eq. tilde_defs). */
-static void exp_eval(const exp_ctx* e, double delta, double* rho, double* sp, double* rd) {
-    double st, rt, rh;
+/* rho and the logarithms of s_p, r_d (eq. sp_rd) at log-offset L from the anchor,
+ * using s_p = s~ / (d_r d~), r_d = d_s r~ / d~ (App. A.2, eq. tilde_defs).  The
+ * quantity that vanishes at the anchor enters as a logarithm (log r0 + L for
+ * s~ = r0 (rho - a4) near a4, log s0 + L for r~ = s0 (a3 - rho) near a3), so an
+ * offset below the smallest double still carries its value.  A non-positive
+ * s_p or r_d (possible only by rounding at the interval ends) gives -inf. */
+static void exp_eval(const exp_ctx* e, double L, double* rho, double* lsp, double* lrd) {
+    double delta = exp(L);
+    double rh, lst, lrt;
+    int sst, srt; /* signs of s~ and r~ */
     if (e->anchor == 4) {
         rh = e->a4 + e->dir * delta;
-        st = e->r0 * (e->dir * delta);                 /* r0 (rho - a4) */
-        if (e->kind == 1) rt = e->s0 * (e->w34 - e->dir * delta); /* s0 (a3 - rho) */
-        else rt = e->tau * e->r0 - rh * e->s0;          /* both terms >= 0 here */
+        lst = log(e->r0) + L;
+        sst = e->dir > 0.0 ? 1 : -1;
+        double rt = (e->kind == 1) ? e->s0 * (e->w34 - e->dir * delta) : e->tau * e->r0 - rh * e->s0;
+        lrt = log(fabs(rt));
+        srt = (rt > 0.0) - (rt < 0.0);
     } else {
         rh = e->a3 + e->dir * delta;
-        rt = e->s0 * (-e->dir * delta);                /* s0 (a3 - rho) */
-        if (e->kind == 1) st = e->r0 * (e->w34 + e->dir * delta); /* r0 (rho - a4) */
-        else st = e->s0 * e->tau - e->r0 + e->r0 * rh;  /* both terms >= 0 here */
+        lrt = log(e->s0) + L;
+        srt = e->dir < 0.0 ? 1 : -1;
+        double st = (e->kind == 1) ? e->r0 * (e->w34 + e->dir * delta) : e->s0 * e->tau - e->r0 + e->r0 * rh;
+        lst = log(fabs(st));
+        sst = (st > 0.0) - (st < 0.0);
     }
-    double dt_ = rh * (rh - 1.0) + e->tau * e->tau;    /* d~ = rho(rho - 1) + tau^2 */
+    double dt_ = rh * (rh - 1.0) + e->tau * e->tau; /* d~ = rho (rho - 1) + tau^2 */
+    int sdt = (dt_ > 0.0) - (dt_ < 0.0);
+    double ldt_ = log(fabs(dt_));
     *rho = rh;
-    *sp = st / (e->dr * dt_);
-    *rd = e->ds * rt / dt_;
+    *lsp = (sst != 0 && sst == sdt) ? lst - log(e->dr) - ldt_ : -INFINITY;
+    *lrd = (srt != 0 && srt == sdt) ? log(e->ds) + lrt - ldt_ : -INFINITY;
 }
 
 /* sign of h(rho) = d_t e^rho s_p - d_t^{-1} e^{-rho} r_d - t0 (eq. h_rho), decided in logs. */
 static int exp_hsign(const exp_ctx* e, double L) {
-    double rho, sp, rd;
-    exp_eval(e, exp(L), &rho, &sp, &rd);
-    double A = sp > 0.0 ? e->ldt + rho + log(sp) : -INFINITY;
-    double B = rd > 0.0 ? -e->ldt - rho + log(rd) : -INFINITY;
+    double rho, lsp, lrd;
+    exp_eval(e, L, &rho, &lsp, &lrd);
+    double A = e->ldt + rho + lsp;  /* log of d_t e^rho s_p */
+    double B = -e->ldt - rho + lrd; /* log of d_t^{-1} e^-rho r_d */
     double lhs, rhs;
     if (e->t0 >= 0.0) {
         lhs = A;
@@ -210,6 +226,18 @@ static double exp_bisect(const exp_ctx* e, double lo, double hi, int sign_lo) {
         if (s == sign_lo) lo = mid; else hi = mid;
     }
     return 0.5 * (lo + hi);
+}
+
+/* lower end of the search: h keeps the sign it has at the anchor for small enough
+ * offsets; step down from hi by 1, 2, 4, ... until that sign shows. */
+static double exp_lower(const exp_ctx* e, double hi, int sign_lo) {
+    double step = 1.0;
+    for (int it = 0; it < 1100; ++it) {
+        double lo = hi - step;
+        if (exp_hsign(e, lo) == sign_lo || lo == -INFINITY) return lo;
+        step *= 2.0;
+    }
+    return -INFINITY;
 }
 
 void orc_proj_exp(const double* v0, const double* d, double* out) {
@@ -242,11 +270,11 @@ void orc_proj_exp(const double* v0, const double* d, double* out) {
         if (sm == 0) {
             L = Lh;
         } else if (sm > 0) { /* h(a4) < 0 < h(mid): root in the half next to a4 */
-            L = exp_bisect(&e, Lh - 800.0, Lh, -1);
+            L = exp_bisect(&e, exp_lower(&e, Lh, -1), Lh, -1);
         } else {             /* h(mid) < 0 < h(a3): root in the half next to a3 */
             e.anchor = 3;
             e.dir = -e.dir;
-            L = exp_bisect(&e, Lh - 800.0, Lh, +1);
+            L = exp_bisect(&e, exp_lower(&e, Lh, +1), Lh, +1);
         }
     } else if (s0 > 0.0) { /* r0 <= 0: interval (-inf, a3), rho = a3 - delta */
         e.kind = 2;
@@ -254,22 +282,26 @@ void orc_proj_exp(const double* v0, const double* d, double* out) {
         e.dir = -1.0;
         double hi = 0.0;
         while (exp_hsign(&e, hi) > 0 && hi < 60.0) hi = 2.0 * hi + 1.0; /* h -> -inf as rho -> -inf */
-        L = exp_bisect(&e, hi - 800.0, hi, +1);
+        L = exp_bisect(&e, exp_lower(&e, hi, +1), hi, +1);
     } else { /* r0 > 0, s0 <= 0: interval (a4, inf), rho = a4 + delta */
         e.kind = 3;
         e.anchor = 4;
         e.dir = 1.0;
         double hi = 0.0;
         while (exp_hsign(&e, hi) < 0 && hi < 60.0) hi = 2.0 * hi + 1.0; /* h -> +inf as rho -> +inf */
-        L = exp_bisect(&e, hi - 800.0, hi, -1);
+        L = exp_bisect(&e, exp_lower(&e, hi, -1), hi, -1);
     }
-    double rho, sp, rd;
-    exp_eval(&e, exp(L), &rho, &sp, &rd);
-    if (!(sp > 0.0)) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
-    /* eq. vpvd_defn: v_p = (d_r rho, d_s, d_t e^rho) s_p, the t entry formed in logs */
-    out[0] = dr * rho * sp;
-    out[1] = ds * sp;
-    out[2] = exp(e.ldt + rho + log(sp));
+    double rho, lsp, lrd;
+    exp_eval(&e, L, &rho, &lsp, &lrd);
+    /* eq. vpvd_defn: v_p = (d_r rho, d_s, d_t e^rho) s_p and
+     * v_d = (d_r^{-1}, (1 - rho) d_s^{-1}, -d_t^{-1} e^-rho) r_d, with v_p + v_d = v0
+     * (eq. diagonal_moreau).  Per coordinate the part of smaller magnitude is taken
+     * from its formula and v_p from v0 - v_d when v_d is the larger part, so both
+     * parts keep an absolute error of a few ulps of |v0|. */
+    double sp = exp(lsp), rd = exp(lrd);
+    double vp[3] = {dr * rho * sp, ds * sp, exp(e.ldt + rho + lsp)};
+    double vd[3] = {rd / dr, (1.0 - rho) * rd / ds, -exp(-e.ldt - rho + lrd)};
+    for (int k = 0; k < 3; ++k) out[k] = fabs(vp[k]) <= fabs(vd[k]) ? vp[k] : v0[k] - vd[k];
 }
 
 /* Remark (App. A.2): Proj_{D K_exp^*}(v0) = v0 + Proj_{D^{-1} K_exp}(-v0). */

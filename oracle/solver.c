@@ -366,10 +366,25 @@ void orc_destroy(orc_solver* S) {
     free(S);
 }
 
+/* Algorithm 1 "Require": z^{0,0} = zbar^{0,0} = (x, y); a new start also begins a
+ * new restart period (empty average, k = 0, counters cleared). */
 void orc_set_start(orc_solver* S, const double* x, const double* y, double omega) {
-    for (int64_t j = 0; j < S->n; ++j) S->x[j] = S->x0[j] = x ? x[j] / S->dc[j] : 0.0;
-    for (int64_t i = 0; i < S->m; ++i) S->y[i] = S->y0[i] = y ? y[i] / S->dr[i] : 0.0;
+    for (int64_t j = 0; j < S->n; ++j) {
+        S->x[j] = S->x0[j] = x ? x[j] / S->dc[j] : 0.0;
+        S->xsum[j] = 0.0;
+    }
+    for (int64_t i = 0; i < S->m; ++i) {
+        S->y[i] = S->y0[i] = y ? y[i] / S->dr[i] : 0.0;
+        S->ysum[i] = 0.0;
+    }
     if (omega > 0.0) S->omega = omega;
+    S->wsum = 0.0;
+    S->k = 0;
+    S->attempts = 0;
+    S->accepted = 0;
+    S->restarts = 0;
+    S->status = ORC_RUNNING;
+    S->phi_prev = INFINITY;
     S->started = 0;
 }
 

@@ -197,6 +197,46 @@ def test_exp_stressed_roots_near_the_endpoints():
                 np.testing.assert_allclose(got[:2], vp[:2], rtol=1e-9, atol=1e-300)
 
 
+def test_exp_roots_beyond_the_double_range():
+    """|rho| far beyond 709 (|a4| or |a3| huge, e.g. r0 tiny and s0 < 0): the pair of
+    eq. vpvd_defn is written in log form; its exact projection underflows to
+    (0, 0, T) or (d_r rho s_p, d_s s_p, 0) in double precision."""
+    for rho in [1e3, 1e5, 1.4e11]:
+        for d in [np.ones(3), np.array([1.147, 0.533, 49.5])]:
+            T, rd = 389.6, 0.7
+            sp = np.exp(np.log(T / d[2]) - rho)  # underflows to 0
+            vp = np.array([d[0] * rho * sp, d[1] * sp, T])
+            vd = rd * np.array([1 / d[0], (1 - rho) / d[1], 0.0])  # e^-rho r_d / d_t underflows
+            v0 = vp + vd
+            got = oracle.proj_exp(v0, d)
+            np.testing.assert_allclose(got, vp, rtol=0, atol=1e-12 * np.linalg.norm(v0))
+    for rho in [-1e3, -1e5, -1e11]:
+        for d in [np.ones(3), np.array([0.3, 2.5, 1.7])]:
+            sp, T = 0.9, 2.0
+            rd = np.exp(np.log(T * d[2]) + rho)  # underflows to 0
+            vp = sp * np.array([d[0] * rho, d[1], 0.0])
+            vd = np.array([rd / d[0], (1 - rho) * rd / d[1], -T])
+            v0 = vp + vd
+            got = oracle.proj_exp(v0, d)
+            np.testing.assert_allclose(got, vp, rtol=0, atol=1e-12 * np.linalg.norm(v0))
+
+
+def test_exp_certificate_extreme_magnitudes():
+    """Moreau certificates with entries spread over many orders of magnitude."""
+    rng = np.random.default_rng(99)
+    for _ in range(4000):
+        v0 = rng.standard_normal(3) * np.exp(rng.normal(0, 3.0, 3) * 3)
+        d = np.exp(rng.normal(0, 1.5, 3))
+        p = oracle.proj_exp(v0, d)
+        assert np.all(np.isfinite(p))
+        q = v0 - p
+        s = np.linalg.norm(v0)
+        eps = 1e-12 * s * max(d.max(), 1 / d.min())
+        assert in_kexp(p / d, eps), (v0, d, p)
+        assert in_kexp_dual(-q * d, eps), (v0, d, p)
+        assert abs(p @ q) <= 1e-12 * s * s
+
+
 def _in_kexp_exact(w):
     r, s, t = w
     if s > 0:
