@@ -1,0 +1,165 @@
+/*
+ * pdcs.h -- C ABI of the GB300 (sm_103a) restarted primal-dual conic solver.
+ *
+ * Solves   min c'x   s.t.   K x - h in C,   l <= x <= u
+ * (the conic program of Sec. 2, eq. prob_cp, with no primal cone block), where
+ * C is a product of zero, nonnegative, second-order, rotated second-order and
+ * exponential cones listed in row order (eq. multi_cone_proj).  The dual is
+ * eq. dual_conic: y in C*, lambda = c - K'y in Lambda (eq. defn_Lambda1).
+ * The method is PDCS, Algorithm 1 of the paper: adaptive-step PDHG (eq. PDHG)
+ * on the diagonally rescaled program, reflected Halpern iteration, the
+ * step-weighted average, restarts and primal-weight updates, stopped by the
+ * relative KKT test of eq. PDCS_terminate_tolerance.
+ *
+ * Conventions for every entry point:
+ *   - all problem arrays passed to pdcs_create are HOST pointers; the library
+ *     copies them into device memory it owns, so the caller may free them as
+ *     soon as pdcs_create returns;
+ *   - result arrays (x: n, y: m, lambda: n) are HOST pointers written by the
+ *     library;
+ *   - indices are 0-based; the column indices of a row need not be sorted;
+ *   - every call returns a pdcs_status; pdcs_last_error() gives the text of the
+ *     last failure of a context; no call aborts, traps or prints;
+ *   - one context is used by one host thread at a time; all of its GPU work
+ *     runs on the CUDA stream given to pdcs_create (NULL: a stream the library
+ *     creates).
+ */
+#ifndef PDCS_H
+#define PDCS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Cone kinds (Sec. 1 notation): ZERO {0}^d; NONNEG R_+^d; SOC {(t, x): ||x|| <= t};
+ * RSOC {(x, y, z): ||z||^2 <= 2xy, x, y >= 0}; EXP the closure of
+ * {(r, s, t): s > 0, t >= s exp(r / s)} (dim must be 3). */
+typedef enum {
+    PDCS_CONE_ZERO = 0,
+    PDCS_CONE_NONNEG = 1,
+    PDCS_CONE_SOC = 2,
+    PDCS_CONE_RSOC = 3,
+    PDCS_CONE_EXP = 4
+} pdcs_cone_type;
+
+typedef struct {
+    int32_t type; /* pdcs_cone_type */
+    int64_t dim;  /* rows covered; SOC >= 1, RSOC >= 2, EXP == 3; the dims sum to m */
+} pdcs_cone;
+
+/* CSR matrix in host memory: row_ptr[m + 1] (row_ptr[0] == 0, nondecreasing),
+ * col[nnz] in [0, n), val[nnz] finite.  nnz must be below 2^31. */
+typedef struct {
+    int64_t m, n, nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const double* val;
+} pdcs_csr;
+
+typedef enum {
+    PDCS_OK = 0,                 /* call succeeded; for pdcs_solve: converged to tol */
+    PDCS_ERR_INVALID = 1,        /* an argument failed validation (nothing changed) */
+    PDCS_ERR_CUDA = 2,           /* a CUDA call failed (text in pdcs_last_error) */
+    PDCS_ERR_OOM = 3,            /* device allocation failed */
+    PDCS_ERR_NUMERIC = 4,        /* a NaN / Inf appeared in the iterates */
+    PDCS_ERR_DEVICE_TIMEOUT = 5, /* a bounded device wait gave up */
+    PDCS_MAX_ITER = 10,          /* max_iter PDHG evaluations done without reaching tol */
+    PDCS_TIME_LIMIT = 11         /* options.time_limit seconds passed without reaching tol */
+} pdcs_status;
+
+enum { PDCS_RESCALE_NONE = 0, PDCS_RESCALE_COORD = 1, PDCS_RESCALE_BLOCK = 2 };
+enum { PDCS_STEP_ADAPTIVE = 0, PDCS_STEP_CONSTANT = 1, PDCS_STEP_PLAIN = 2 };
+enum { PDCS_PRECISION_FP64 = 0, PDCS_PRECISION_FP32 = 1 };
+
+typedef struct {
+    int32_t rescale;        /* PDCS_RESCALE_*: diagonal rescaling (Sec. 3), default per coordinate */
+    int32_t ruiz_iters;     /* Ruiz passes (infinity norm), default 10 */
+    int32_t pock_chambolle; /* 1: one Pock-Chambolle pass (alpha = 1) after Ruiz, default 1 */
+    int32_t step_mode;      /* PDCS_STEP_*: adaptive (Algorithm 1), constant 0.998/||K||_2,
+                               or plain PDHG of App. D (0.9/||K||_2, no Halpern, no restarts) */
+    int32_t check_period;   /* restart / termination check every this many PDHG evaluations, default 64 */
+    double beta;            /* reflection parameter of ReflectedHalpern, default 1 */
+    int32_t power_iters;    /* power iterations for ||K||_2 (constant / plain modes), default 50 */
+    int32_t precision;      /* PDCS_PRECISION_*: FP32 iterates with FP64 checks and FP64 polish */
+    double fp32_switch_tol; /* FP32 mode: switch to FP64 once the relative KKT error is below this */
+    int32_t use_graphs;     /* 1: replay each check period as one CUDA graph, default 1 */
+    int32_t spmv_lanes;     /* lanes per CSR row in SpMV (1..32, power of 2); 0: autotune */
+    double time_limit;      /* seconds for pdcs_solve; 0: none */
+} pdcs_options;
+
+typedef struct {
+    int64_t attempts;  /* PDHG evaluations (accepted or rejected) so far */
+    int64_t accepted;  /* accepted steps so far */
+    int64_t restarts;  /* restarts so far */
+    double err_p, err_d, err_gap; /* relative KKT errors of the returned solution */
+    double pobj, dobj;            /* primal and dual objective values (original scaling) */
+    double eta, omega;            /* current step size and primal weight */
+    double setup_seconds;         /* time spent in pdcs_create */
+    double solve_seconds;         /* time spent in pdcs_solve calls so far */
+    int32_t status;               /* pdcs_status of the last pdcs_solve */
+    int32_t fp64_phase;           /* 1 once FP32 mode has switched to FP64 polishing */
+} pdcs_info;
+
+typedef struct pdcs_ctx pdcs_ctx;
+
+/* Fills *opt with the defaults listed above. */
+void pdcs_default_options(pdcs_options* opt);
+
+/* Builds a solver for one conic program.  K, c (n), h (m), cones are required;
+ * lb / ub (n) may be NULL, meaning l = 0 and u = +inf; entries may be -inf / +inf.
+ * Copies the data to the device, rescales it (Sec. 3 "diagonal rescaling"),
+ * builds K' as a second CSR, groups the rows by cone kind and allocates the
+ * iterate state.  cuda_stream: a cudaStream_t or NULL.  opt may be NULL.
+ * Errors: PDCS_ERR_INVALID (bad sizes, indices, cone list, NaN data, l > u),
+ * PDCS_ERR_OOM, PDCS_ERR_CUDA; *out is NULL then. */
+pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, const double* lb,
+                        const double* ub, const pdcs_cone* cones, int64_t n_cones,
+                        const pdcs_options* opt, void* cuda_stream, pdcs_ctx** out);
+
+/* Runs Algorithm 1 from the current state until the relative KKT errors of
+ * eq. PDCS_terminate_tolerance are all <= tol (checked every check_period
+ * evaluations) or max_iter more PDHG evaluations are done.  tol <= 0 disables
+ * the test and runs exactly max_iter evaluations.  Calls may be repeated; the
+ * state carries over.  info may be NULL.  Returns PDCS_OK on convergence,
+ * PDCS_MAX_ITER / PDCS_TIME_LIMIT otherwise, or an error. */
+pdcs_status pdcs_solve(pdcs_ctx* ctx, double tol, int64_t max_iter, pdcs_info* info);
+
+/* Copies the returned solution (projected onto the bounds and the dual cone) in
+ * the original scaling: x (n), y (m), lambda = c - K'y (n, may be NULL). */
+pdcs_status pdcs_get_solution(pdcs_ctx* ctx, double* x, double* y, double* lambda);
+
+/* Copies the current Halpern iterate z = (x, y) and the last PDHG output
+ * zhat = (xhat, yhat), original scaling.  Any pointer may be NULL. */
+pdcs_status pdcs_get_iterate(pdcs_ctx* ctx, double* x, double* y, double* xhat, double* yhat);
+
+/* Copies the diagonal scalings: dr (m, rows), dc (n, columns); K~ = diag(dr) K diag(dc). */
+pdcs_status pdcs_get_scaling(pdcs_ctx* ctx, double* dr, double* dc);
+
+/* Fills *info with the counters and the errors of the last check. */
+pdcs_status pdcs_get_info(pdcs_ctx* ctx, pdcs_info* info);
+
+/* Sets the starting point z^{0,0} = (x, y) (original scaling; NULL means 0) and,
+ * when omega > 0, the initial primal weight; resets the counters. */
+pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y, double omega);
+
+/* Text of the last error of ctx (or of the last failed pdcs_create when ctx is NULL). */
+const char* pdcs_last_error(const pdcs_ctx* ctx);
+
+/* Frees every device and host resource of ctx; NULL is a no-op. */
+void pdcs_destroy(pdcs_ctx* ctx);
+
+/* Blockwise projection of the DEVICE vector v (m rows) onto D C (dual == 0) or
+ * onto (D C)* = D^{-1} C* (dual == 1), D = diag(d) (DEVICE pointer, d > 0; NULL
+ * means D = I), written to the DEVICE vector out (may equal v).  The cone list
+ * is a HOST array as in pdcs_create; for RSOC blocks d must be equal on their
+ * first two rows.  SOC by Theorem 1, exp by Theorem 3, exp* by the Remark of
+ * App. A.2.  Runs on cuda_stream and returns once the work is queued.
+ * Errors: PDCS_ERR_INVALID, PDCS_ERR_CUDA. */
+pdcs_status pdcs_proj_cones_device(const double* v, const double* d, int64_t m, const pdcs_cone* cones,
+                                   int64_t n_cones, int32_t dual, double* out, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -160,6 +160,7 @@ static double lse(double a, double b) { /* log(e^a + e^b) */
 
 typedef struct {
     double r0, s0, t0, dr, ds, dt, tau, a3, a4, ldt;
+    double a4m1; /* a4 - 1 = -(s0 d_s) / (r0 d_r), exact near a4 = 1 */
     int anchor;  /* 3: rho measured from a3, 4: from a4 */
     double dir;  /* rho = anchor + dir * delta, delta = e^L */
     double w34;  /* a3 - a4 */
@@ -174,10 +175,11 @@ typedef struct {
  * s_p or r_d (possible only by rounding at the interval ends) gives -inf. */
 static void exp_eval(const exp_ctx* e, double L, double* rho, double* lsp, double* lrd) {
     double delta = exp(L);
-    double rh, lst, lrt;
+    double rh, rm1, lst, lrt; /* rm1 = rho - 1 from the exact offset */
     int sst, srt; /* signs of s~ and r~ */
     if (e->anchor == 4) {
         rh = e->a4 + e->dir * delta;
+        rm1 = e->a4m1 + e->dir * delta;
         lst = log(e->r0) + L;
         sst = e->dir > 0.0 ? 1 : -1;
         double rt = (e->kind == 1) ? e->s0 * (e->w34 - e->dir * delta) : e->tau * e->r0 - rh * e->s0;
@@ -185,13 +187,14 @@ static void exp_eval(const exp_ctx* e, double L, double* rho, double* lsp, doubl
         srt = (rt > 0.0) - (rt < 0.0);
     } else {
         rh = e->a3 + e->dir * delta;
+        rm1 = (e->a3 - 1.0) + e->dir * delta;
         lrt = log(e->s0) + L;
         srt = e->dir < 0.0 ? 1 : -1;
         double st = (e->kind == 1) ? e->r0 * (e->w34 + e->dir * delta) : e->s0 * e->tau - e->r0 + e->r0 * rh;
         lst = log(fabs(st));
         sst = (st > 0.0) - (st < 0.0);
     }
-    double dt_ = rh * (rh - 1.0) + e->tau * e->tau; /* d~ = rho (rho - 1) + tau^2 */
+    double dt_ = rh * rm1 + e->tau * e->tau; /* d~ = rho (rho - 1) + tau^2 */
     int sdt = (dt_ > 0.0) - (dt_ < 0.0);
     double ldt_ = log(fabs(dt_));
     *rho = rh;
@@ -256,6 +259,7 @@ void orc_proj_exp(const double* v0, const double* d, double* out) {
     e.ldt = log(dt);
     e.a3 = (s0 > 0.0) ? (r0 * ds) / (s0 * dr) : 0.0;
     e.a4 = (r0 > 0.0) ? 1.0 - (s0 * ds) / (r0 * dr) : 0.0;
+    e.a4m1 = (r0 > 0.0) ? -(s0 * ds) / (r0 * dr) : -1.0;
     e.w34 = e.a3 - e.a4;
     double L;
     if (r0 > 0.0 && s0 > 0.0) {
@@ -301,7 +305,10 @@ void orc_proj_exp(const double* v0, const double* d, double* out) {
     double sp = exp(lsp), rd = exp(lrd);
     double vp[3] = {dr * rho * sp, ds * sp, exp(e.ldt + rho + lsp)};
     double vd[3] = {rd / dr, (1.0 - rho) * rd / ds, -exp(-e.ldt - rho + lrd)};
-    for (int k = 0; k < 3; ++k) out[k] = fabs(vp[k]) <= fabs(vd[k]) ? vp[k] : v0[k] - vd[k];
+    for (int k = 0; k < 2; ++k) out[k] = fabs(vp[k]) <= fabs(vd[k]) ? vp[k] : v0[k] - vd[k];
+    /* t entry: h(rho) = 0 says e^A - e^B = t0, so the part of smaller magnitude is
+     * v_d (t0 >= 0) or v_p (t0 < 0) whatever the rounding of A and B */
+    out[2] = t0 >= 0.0 ? t0 - vd[2] : vp[2];
 }
 
 /* Remark (App. A.2): Proj_{D K_exp^*}(v0) = v0 + Proj_{D^{-1} K_exp}(-v0). */

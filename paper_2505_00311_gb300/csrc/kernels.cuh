@@ -1,0 +1,687 @@
+// kernels.cuh -- per-iteration and per-check kernels of the PDCS solver.
+//
+// One PDHG evaluation (eq. PDHG on the rescaled program) is four launches:
+//   primal_update  : applies the pending ReflectedHalpern update (Algorithm 1,
+//                    step 6) and the eta-weighted average (step 7) to x and to the
+//                    cached K'y, then xhat = Proj_[l,u](x - tau (c - K'y)) and
+//                    per-block partials of ||xhat - x||^2;
+//   spmv (K)       : K xhat into one of two buffers (the previous one is still
+//                    needed by the pending Halpern update of K x);
+//   dual_update    : the same pending update for y and the cached K x, then
+//                    v = y + sigma (h - 2 K xhat + K x), yhat = Proj_{Dr^{-1} C*}(v)
+//                    block by block (one thread per scalar row or exp cone, one
+//                    warp per SOC / RSOC), partials of ||dy||^2 and dy'(K xhat - K x)
+//                    (= dy' K dx, no extra product); its last block is the step
+//                    controller (AdaptiveStepPDHG);
+//   spmv (K')      : K' yhat, skipped when the step was rejected.
+// The cached products follow from linearity: K z^{k+1} = ha K zhat + hb K z^k + hc K z^0.
+#pragma once
+#include "common.cuh"
+#include "cone_math.cuh"
+#include "state.h"
+
+namespace pdcs {
+
+// Device view of one problem and its iterate state (passed by value).
+template <typename T>
+struct Dev {
+    int m, n;
+    // scaled matrix K~ (rows in internal order) and its transpose
+    const int* rp;
+    const int* ci;
+    const T* val;
+    const int* rpT;
+    const int* ciT;
+    const T* valT;
+    // scaled data
+    const T* c;
+    const T* h;
+    const T* l;
+    const T* u;
+    const double* dr;
+    const double* dc;
+    // iterate state
+    T *x, *xh, *x0, *kty, *ktyh, *kty0, *xsum;
+    T *y, *yh, *y0, *kx, *kxh0, *kxh1, *kx0, *ysum;
+    // cone layout (internal row order): [0, m_zero) zero rows, [m_zero, m_scalar)
+    // nonnegative rows, then SOC / RSOC blocks, then exp cones (3 rows each)
+    int m_zero, m_scalar;
+    int n_soc;
+    const int* soc_off;
+    const int* soc_dim;
+    const unsigned char* soc_rot;
+    double* soc_lam;
+    int exp_row0, n_exp;
+    double* exp_L;
+    // blocks of the cone-structured kernels
+    int nb_scal, nb_soc, nb_exp;
+    int nb_primal;
+    // reductions and control
+    double* part;
+    PartLayout pl;
+    Ctrl* ctrl;
+    // check buffers (always FP64): candidates, their products, scratch
+    double* xc;    // 2 n
+    double* yc;    // 2 m
+    double* kxc;   // 2 m
+    double* ktyc;  // 2 n
+    double* scr;   // 2 m scratch for projections of residuals
+    // original-scale data for the unscaled KKT (FP64)
+    const double* l_orig;
+    const double* u_orig;
+};
+
+// ---------------------------------------------------------------------------
+// SpMV: y = A x, CSR, G lanes per row, a warp covers 32 / G rows at a time.
+// sel: 0 -> write y0;  1 -> write y0 / y1 by the parity of ctrl->attempts.
+// skip: 0 never; 1 when not running; 2 when not running or the step was rejected.
+// ---------------------------------------------------------------------------
+template <typename T, typename TO, int G>
+__global__ void __launch_bounds__(kBlock) spmv_csr(int rows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                   const T* __restrict__ val, const T* __restrict__ x, TO* y0, TO* y1,
+                                                   const Ctrl* ctrl, int sel, int skip) {
+    if (skip) {
+        if (ctrl->status != kRunning) return;
+        if (skip == 2 && !ctrl->pending) return;
+    }
+    TO* y = (sel == 1 && (ctrl->attempts & 1)) ? y1 : y0;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / G, gl = lane % G;
+    constexpr int RPW = 32 / G;
+    const long long wglob = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long r0 = wglob * RPW; r0 < rows; r0 += nw * RPW) {
+        const long long r = r0 + g;
+        T acc = T(0);
+        if (r < rows) {
+            const int e = __ldg(rp + r + 1);
+            for (int p = __ldg(rp + r) + gl; p < e; p += G) acc += __ldg(val + p) * __ldg(x + __ldg(ci + p));
+        }
+        acc = group_sum<G>(acc);
+        if (r < rows && gl == 0) y[r] = (TO)acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// last-block helper: returns true in every thread of the block that finished last
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool last_block(Ctrl* C) {
+    __shared__ unsigned int s_ticket;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&C->ticket, 1u);
+    __syncthreads();
+    const bool last = s_ticket == gridDim.x - 1;
+    if (last) __threadfence();
+    return last;
+}
+
+// Deterministic sum of part[0..cnt) by one block (fixed per-thread strides + fixed tree).
+__device__ __forceinline__ double block_reduce_parts(const double* part, int cnt, double (*sm)[kWarpsPerBlock]) {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) v[0] += __ldcg(part + i);
+    block_sum<1>(v, sm);
+    return v[0];  // valid in thread 0
+}
+
+__device__ __forceinline__ double block_max_parts(const double* part, int cnt, double (*sm)[kWarpsPerBlock]) {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) v[0] = fmax(v[0], __ldcg(part + i));
+    block_max<1>(v, sm);
+    return v[0];
+}
+
+// ---------------------------------------------------------------------------
+// primal update
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) primal_update(Dev<T> D) {
+    Ctrl* C = D.ctrl;
+    if (C->status != kRunning) return;
+    __shared__ double sm[1][kWarpsPerBlock];
+    const bool pend = C->pending != 0;
+    const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw, tau = (T)C->tau;
+    double acc[1] = {0.0};
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
+        T x = D.x[j], kty = D.kty[j];
+        if (pend) {
+            x = ha * D.xh[j] + hb * x + hc * D.x0[j];
+            kty = ha * D.ktyh[j] + hb * kty + hc * D.kty0[j];
+            D.x[j] = x;
+            D.kty[j] = kty;
+            if (hw != T(0)) D.xsum[j] += hw * x;
+        }
+        T xh = fmin(fmax(x - tau * (D.c[j] - kty), D.l[j]), D.u[j]);
+        D.xh[j] = xh;
+        double dx = (double)xh - (double)x;
+        acc[0] += dx * dx;
+    }
+    block_sum<1>(acc, sm);
+    if (threadIdx.x == 0) D.part[D.pl.off_px + blockIdx.x] = acc[0];
+}
+
+// Halpern update of one dual row (returns the updated y; writes y, kx, ysum).
+template <typename T>
+__device__ __forceinline__ void dual_row_halpern(const Dev<T>& D, int i, bool pend, T ha, T hb, T hc, T hw,
+                                                 const T* kxh_prev, T& y, T& kx) {
+    y = D.y[i];
+    kx = D.kx[i];
+    if (pend) {
+        y = ha * D.yh[i] + hb * y + hc * D.y0[i];
+        kx = ha * kxh_prev[i] + hb * kx + hc * D.kx0[i];
+        D.y[i] = y;
+        D.kx[i] = kx;
+        if (hw != T(0)) D.ysum[i] += hw * y;
+    }
+}
+
+// AdaptiveStepPDHG decision and Algorithm 1 bookkeeping (run by the last block).
+template <typename T>
+__device__ void step_controller(const Dev<T>& D, double (*sm)[kWarpsPerBlock]) {
+    Ctrl* C = D.ctrl;
+    const double nx2 = block_reduce_parts(D.part + D.pl.off_px, D.pl.primal_blocks, sm);
+    const double ny2 = block_reduce_parts(D.part + D.pl.off_dy, D.pl.dual_blocks, sm);
+    const double itr = block_reduce_parts(D.part + D.pl.off_dy + D.pl.dual_blocks, D.pl.dual_blocks, sm);
+    if (threadIdx.x != 0) return;
+    C->ticket = 0;
+    C->attempts += 1;
+    if (!isfinite(nx2) || !isfinite(ny2) || !isfinite(itr)) {
+        C->status = kNumericError;
+        C->pending = 0;
+        return;
+    }
+    const double eta = C->eta, om = C->omega;
+    bool accept = true;
+    if (C->step_mode == 0) {
+        const double inter = fabs(itr);
+        const double move = om * nx2 + ny2 / om;
+        const double eta_max = inter > 0.0 ? move / (2.0 * inter) : INFINITY;
+        const double j1 = (double)C->attempts + 1.0;
+        const double t1 = (1.0 - pow(j1, -0.3)) * eta_max;
+        const double t2 = (1.0 + pow(j1, -0.6)) * eta;
+        accept = eta <= eta_max;
+        C->eta = fmin(t1, t2);
+    }
+    if (accept) {
+        C->pending = 1;
+        if (C->step_mode == 2) {  // plain PDHG: z <- zhat
+            C->ha = 1.0; C->hb = 0.0; C->hc = 0.0; C->hw = 0.0;
+        } else {
+            const double kk = (double)C->k;
+            const double a = (kk + 1.0) / (kk + 2.0), be = C->beta;
+            C->ha = a * (1.0 + be);
+            C->hb = -a * be;
+            C->hc = 1.0 / (kk + 2.0);
+            C->hw = eta;
+            C->wsum += eta;
+        }
+        C->k += 1;
+        C->accepted += 1;
+    } else {
+        C->pending = 0;
+    }
+    C->tau = C->eta / C->omega;
+    C->sigma = C->eta * C->omega;
+}
+
+// ---------------------------------------------------------------------------
+// dual update + projection + step controller
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
+    Ctrl* C = D.ctrl;
+    if (C->status != kRunning) return;
+    __shared__ double sm[2][kWarpsPerBlock];
+    const long long att = C->attempts;
+    const T* p = (att & 1) ? D.kxh1 : D.kxh0;
+    const T* pprev = (att & 1) ? D.kxh0 : D.kxh1;
+    const bool pend = C->pending != 0;
+    const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw, sigma = (T)C->sigma;
+    double acc[2] = {0.0, 0.0};
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (b < D.nb_scal) {
+        const int stride = D.nb_scal * blockDim.x;
+        for (int i = b * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
+            T y, kx;
+            dual_row_halpern(D, i, pend, ha, hb, hc, hw, pprev, y, kx);
+            const T pi = p[i];
+            const T v = y + sigma * (D.h[i] - T(2) * pi + kx);
+            const T yh = (i < D.m_zero) ? v : fmax(v, T(0));
+            D.yh[i] = yh;
+            const double dy = (double)yh - (double)y;
+            acc[0] += dy * dy;
+            acc[1] += dy * ((double)pi - (double)kx);
+        }
+    } else if (b < D.nb_scal + D.nb_soc) {
+        const int stride = D.nb_soc * kWarpsPerBlock;
+        for (int cidx = (b - D.nb_scal) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
+            const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
+            for (int i = lane; i < dim; i += 32) {
+                T y, kx;
+                dual_row_halpern(D, o + i, pend, ha, hb, hc, hw, pprev, y, kx);
+                D.yh[o + i] = y + sigma * (D.h[o + i] - T(2) * p[o + i] + kx);
+            }
+            __syncwarp();
+            if (D.soc_rot[cidx]) rsoc_project_warp<true>(D.yh + o, D.dr + o, dim, D.soc_lam + cidx);
+            else soc_project_warp<true>(D.yh + o, D.dr + o, dim, D.soc_lam + cidx);
+            for (int i = lane; i < dim; i += 32) {
+                const double dy = (double)D.yh[o + i] - (double)D.y[o + i];
+                acc[0] += dy * dy;
+                acc[1] += dy * ((double)p[o + i] - (double)D.kx[o + i]);
+            }
+            __syncwarp();
+        }
+    } else {
+        const int stride = D.nb_exp * blockDim.x;
+        for (int e = (b - D.nb_scal - D.nb_soc) * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
+            const int r = D.exp_row0 + 3 * e;
+            T y[3], kx[3];
+            double v[3], out[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                dual_row_halpern(D, r + q, pend, ha, hb, hc, hw, pprev, y[q], kx[q]);
+                v[q] = (double)(y[q] + sigma * (D.h[r + q] - T(2) * p[r + q] + kx[q]));
+            }
+            exp_dual_project(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], out, D.exp_L + e, nullptr);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const T yh = (T)out[q];
+                D.yh[r + q] = yh;
+                const double dy = (double)yh - (double)y[q];
+                acc[0] += dy * dy;
+                acc[1] += dy * ((double)p[r + q] - (double)kx[q]);
+            }
+        }
+    }
+    block_sum<2>(acc, sm);
+    if (threadIdx.x == 0) {
+        D.part[D.pl.off_dy + b] = acc[0];
+        D.part[D.pl.off_dy + D.pl.dual_blocks + b] = acc[1];
+    }
+    if (last_block(C)) step_controller(D, sm);
+}
+
+// ---------------------------------------------------------------------------
+// flush: apply a pending Halpern update without a PDHG step (before a check)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) flush_primal(Dev<T> D) {
+    Ctrl* C = D.ctrl;
+    if (C->status != kRunning || !C->pending) return;
+    const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw;
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
+        const T x = ha * D.xh[j] + hb * D.x[j] + hc * D.x0[j];
+        D.x[j] = x;
+        D.kty[j] = ha * D.ktyh[j] + hb * D.kty[j] + hc * D.kty0[j];
+        if (hw != T(0)) D.xsum[j] += hw * x;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) flush_dual(Dev<T> D) {
+    Ctrl* C = D.ctrl;
+    if (C->status != kRunning || !C->pending) return;
+    // the pending evaluation is attempts - 1; its K xhat sits in buffer (attempts - 1) & 1
+    const T* pprev = ((C->attempts - 1) & 1) ? D.kxh1 : D.kxh0;
+    const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.m; i += stride) {
+        T y, kx;
+        dual_row_halpern(D, i, true, ha, hb, hc, hw, pprev, y, kx);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// check: candidates (Algorithm 1 step 8), their KKT, restart controller
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int n_candidates(const Ctrl* C) {
+    return (C->check_mode == 1 || C->step_mode == 2 || !(C->wsum > 0.0)) ? 1 : 2;
+}
+
+// xc[q] = Proj_[l,u](source_q): q = 0 current z, q = 1 the average zsum / wsum
+template <typename T>
+__global__ void __launch_bounds__(kBlock) cand_primal(Dev<T> D) {
+    const Ctrl* C = D.ctrl;
+    if (C->status != kRunning) return;
+    const int q = blockIdx.y;
+    if (q >= n_candidates(C)) return;
+    const double iw = q ? 1.0 / C->wsum : 0.0;
+    double* out = D.xc + (size_t)q * D.n;
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
+        const double s = q ? (double)D.xsum[j] * iw : (double)D.x[j];
+        out[j] = fmin(fmax(s, (double)D.l[j]), (double)D.u[j]);
+    }
+}
+
+// yc[q] = Proj_{Dr^{-1} C*}(source_q), same block split as dual_update
+template <typename T>
+__global__ void __launch_bounds__(kBlock) cand_dual(Dev<T> D) {
+    const Ctrl* C = D.ctrl;
+    if (C->status != kRunning) return;
+    const int q = blockIdx.y;
+    if (q >= n_candidates(C)) return;
+    const double iw = q ? 1.0 / C->wsum : 0.0;
+    double* out = D.yc + (size_t)q * D.m;
+    const T* src = q ? D.ysum : D.y;
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    auto val = [&](int i) { return q ? (double)src[i] * iw : (double)src[i]; };
+    if (b < D.nb_scal) {
+        const int stride = D.nb_scal * blockDim.x;
+        for (int i = b * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
+            const double v = val(i);
+            out[i] = (i < D.m_zero) ? v : fmax(v, 0.0);
+        }
+    } else if (b < D.nb_scal + D.nb_soc) {
+        const int stride = D.nb_soc * kWarpsPerBlock;
+        for (int cidx = (b - D.nb_scal) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
+            const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
+            for (int i = lane; i < dim; i += 32) out[o + i] = val(o + i);
+            __syncwarp();
+            if (D.soc_rot[cidx]) rsoc_project_warp<true>(out + o, D.dr + o, dim, nullptr);
+            else soc_project_warp<true>(out + o, D.dr + o, dim, nullptr);
+        }
+    } else {
+        const int stride = D.nb_exp * blockDim.x;
+        for (int e = (b - D.nb_scal - D.nb_soc) * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
+            const int r = D.exp_row0 + 3 * e;
+            double o3[3];
+            exp_dual_project(val(r), val(r + 1), val(r + 2), D.dr[r], D.dr[r + 1], D.dr[r + 2], o3, nullptr, nullptr);
+            out[r] = o3[0];
+            out[r + 1] = o3[1];
+            out[r + 2] = o3[2];
+        }
+    }
+}
+
+// Primal-side KKT partials of candidate q = blockIdx.y (rows of K):
+//   kpRp2  : ||v - Proj_{Dr C}(v)||^2, v = K~ xc - h~       (restart metric, scaled)
+//   kpHy   : h~' yc                                          (dual objective part)
+//   kpDy2  : ||yc - y0||^2                                   (primal weight update)
+//   kpRmax : ||w - Proj_C(w)||_inf, w = K x - h = v / dr      (err_p numerator)
+//   kpKxmax: ||K x||_inf, kpPmax: ||Proj_C(K x - h)||_inf     (err_p denominator)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
+    const Ctrl* C = D.ctrl;
+    if (C->status != kRunning) return;
+    const int q = blockIdx.y;
+    if (q >= n_candidates(C)) return;
+    __shared__ double sm[3][kWarpsPerBlock];
+    const double* kx = D.kxc + (size_t)q * D.m;
+    const double* yc = D.yc + (size_t)q * D.m;
+    double* s1 = D.scr + (size_t)q * D.m;  // scratch: scaled residual point
+    double sums[3] = {0.0, 0.0, 0.0};      // rp2, hy, dy2
+    double mx[3] = {0.0, 0.0, 0.0};        // rmax, kxmax, pmax
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    auto common = [&](int i) {
+        sums[1] += (double)D.h[i] * yc[i];
+        const double dy = yc[i] - (double)D.y0[i];
+        sums[2] += dy * dy;
+        mx[1] = fmax(mx[1], fabs(kx[i] / D.dr[i]));
+    };
+    if (b < D.nb_scal) {
+        const int stride = D.nb_scal * blockDim.x;
+        for (int i = b * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
+            const double v = kx[i] - (double)D.h[i];
+            const double w = v / D.dr[i];
+            double rs, ru, pu;
+            if (i < D.m_zero) { rs = v; ru = w; pu = 0.0; }
+            else { rs = fmin(v, 0.0); ru = fmin(w, 0.0); pu = fmax(w, 0.0); }
+            sums[0] += rs * rs;
+            mx[0] = fmax(mx[0], fabs(ru));
+            mx[2] = fmax(mx[2], fabs(pu));
+            common(i);
+        }
+    } else if (b < D.nb_scal + D.nb_soc) {
+        const int stride = D.nb_soc * kWarpsPerBlock;
+        for (int cidx = (b - D.nb_scal) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
+            const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
+            const bool rot = D.soc_rot[cidx] != 0;
+            // scaled residual: project v onto Dr K
+            for (int i = lane; i < dim; i += 32) s1[o + i] = kx[o + i] - (double)D.h[o + i];
+            __syncwarp();
+            if (rot) rsoc_project_warp<false>(s1 + o, D.dr + o, dim, nullptr);
+            else soc_project_warp<false>(s1 + o, D.dr + o, dim, nullptr);
+            for (int i = lane; i < dim; i += 32) {
+                const double v = kx[o + i] - (double)D.h[o + i];
+                const double r = v - s1[o + i];
+                sums[0] += r * r;
+            }
+            __syncwarp();
+            // unscaled residual: project w = v / dr onto K (D = I)
+            for (int i = lane; i < dim; i += 32) s1[o + i] = (kx[o + i] - (double)D.h[o + i]) / D.dr[o + i];
+            __syncwarp();
+            if (rot) rsoc_project_warp<false>(s1 + o, nullptr, dim, nullptr);
+            else soc_project_warp<false>(s1 + o, nullptr, dim, nullptr);
+            for (int i = lane; i < dim; i += 32) {
+                const double w = (kx[o + i] - (double)D.h[o + i]) / D.dr[o + i];
+                mx[0] = fmax(mx[0], fabs(w - s1[o + i]));
+                mx[2] = fmax(mx[2], fabs(s1[o + i]));
+                common(o + i);
+            }
+            __syncwarp();
+        }
+    } else {
+        const int stride = D.nb_exp * blockDim.x;
+        for (int e = (b - D.nb_scal - D.nb_soc) * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
+            const int r = D.exp_row0 + 3 * e;
+            double v[3], w[3], ps[3], pu[3];
+            for (int k = 0; k < 3; ++k) {
+                v[k] = kx[r + k] - (double)D.h[r + k];
+                w[k] = v[k] / D.dr[r + k];
+            }
+            exp_project(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], ps, nullptr, nullptr);
+            exp_project(w[0], w[1], w[2], 1.0, 1.0, 1.0, pu, nullptr, nullptr);
+            for (int k = 0; k < 3; ++k) {
+                const double rs = v[k] - ps[k];
+                sums[0] += rs * rs;
+                mx[0] = fmax(mx[0], fabs(w[k] - pu[k]));
+                mx[2] = fmax(mx[2], fabs(pu[k]));
+                common(r + k);
+            }
+        }
+    }
+    block_sum<3>(sums, sm);
+    block_max<3>(mx, sm);
+    if (threadIdx.x == 0) {
+        const int nb = D.pl.kktp_blocks;
+        double* P = D.part + D.pl.off_kp + (size_t)q * kKktPN * nb;
+        P[kpRp2 * nb + b] = sums[0];
+        P[kpHy * nb + b] = sums[1];
+        P[kpDy2 * nb + b] = sums[2];
+        P[kpRmax * nb + b] = mx[0];
+        P[kpKxmax * nb + b] = mx[1];
+        P[kpPmax * nb + b] = mx[2];
+    }
+}
+
+// Proj onto Lambda_j (eq. defn_Lambda1) from the bound pattern of column j
+__device__ __forceinline__ double proj_lambda(double lam, double l, double u) {
+    const bool lf = isfinite(l), uf = isfinite(u);
+    if (!lf && !uf) return 0.0;
+    if (!lf) return fmin(lam, 0.0);
+    if (!uf) return fmax(lam, 0.0);
+    return lam;
+}
+
+// restart / termination controller, run by the last block of kkt_dual
+template <typename T>
+__device__ void check_controller(const Dev<T>& D, double (*sm)[kWarpsPerBlock]) {
+    Ctrl* C = D.ctrl;
+    const int nc = n_candidates(C);
+    double kp[2][kKktPN], kd[2][kKktDN];
+    for (int q = 0; q < nc; ++q) {
+        const int nbp = D.pl.kktp_blocks, nbd = D.pl.kktd_blocks;
+        const double* P = D.part + D.pl.off_kp + (size_t)q * kKktPN * nbp;
+        const double* Q = D.part + D.pl.off_kd + (size_t)q * kKktDN * nbd;
+        kp[q][kpRp2] = block_reduce_parts(P + kpRp2 * nbp, nbp, sm);
+        kp[q][kpHy] = block_reduce_parts(P + kpHy * nbp, nbp, sm);
+        kp[q][kpDy2] = block_reduce_parts(P + kpDy2 * nbp, nbp, sm);
+        kp[q][kpRmax] = block_max_parts(P + kpRmax * nbp, nbp, sm);
+        kp[q][kpKxmax] = block_max_parts(P + kpKxmax * nbp, nbp, sm);
+        kp[q][kpPmax] = block_max_parts(P + kpPmax * nbp, nbp, sm);
+        kd[q][kdRd2] = block_reduce_parts(Q + kdRd2 * nbd, nbd, sm);
+        kd[q][kdPobj] = block_reduce_parts(Q + kdPobj * nbd, nbd, sm);
+        kd[q][kdBterm] = block_reduce_parts(Q + kdBterm * nbd, nbd, sm);
+        kd[q][kdDx2] = block_reduce_parts(Q + kdDx2 * nbd, nbd, sm);
+        kd[q][kdDmax] = block_max_parts(Q + kdDmax * nbd, nbd, sm);
+        kd[q][kdKtymax] = block_max_parts(Q + kdKtymax * nbd, nbd, sm);
+    }
+    if (threadIdx.x != 0) return;
+    C->ticket = 0;
+    double err[2][3], comp[2][3], emax[2];
+    bool finite = true;
+    for (int q = 0; q < nc; ++q) {
+        const double pobj = kd[q][kdPobj];
+        const double dobj = kp[q][kpHy] + kd[q][kdBterm];
+        const double gap = fabs(pobj - dobj);
+        err[q][0] = kp[q][kpRmax] / (1.0 + fmax(C->hmax, fmax(kp[q][kpKxmax], kp[q][kpPmax])));
+        err[q][1] = kd[q][kdDmax] / (1.0 + fmax(C->cmax, kd[q][kdKtymax]));
+        err[q][2] = gap / (1.0 + fmax(fabs(pobj), fabs(dobj)));
+        comp[q][0] = kp[q][kpRp2];
+        comp[q][1] = kd[q][kdRd2];
+        comp[q][2] = gap;
+        emax[q] = fmax(err[q][0], fmax(err[q][1], err[q][2]));
+        finite = finite && isfinite(emax[q]) && isfinite(comp[q][0]) && isfinite(comp[q][1]);
+    }
+    C->restart_now = 0;
+    C->pending = 0;
+    C->n_cand = nc;
+    if (!finite) { C->status = kNumericError; return; }
+    // solution = the better candidate of this check (current first)
+    int sol = 0;
+    if (nc == 2 && emax[1] < emax[0]) sol = 1;
+    C->sol_cand = sol;
+    for (int k = 0; k < 3; ++k) C->err[k] = err[sol][k];
+    C->pobj = kd[sol][kdPobj];
+    C->dobj = kp[sol][kpHy] + kd[sol][kdBterm];
+    const double om = C->omega;
+    auto phi_of = [&](const double* cc, double w) { return sqrt(w * cc[0] + cc[1] / w + cc[2] * cc[2]); };
+    if (C->check_mode == 1) {  // initial evaluation of the anchor
+        for (int k = 0; k < 3; ++k) C->comp0[k] = comp[0][k];
+        C->phi0 = phi_of(comp[0], om);
+        C->phi_prev = INFINITY;
+        C->check_mode = 0;
+        return;
+    }
+    if (C->tol > 0.0) {
+        for (int q = 0; q < nc; ++q) {
+            if (err[q][0] <= C->tol && err[q][1] <= C->tol && err[q][2] <= C->tol) {
+                C->sol_cand = q;
+                for (int k = 0; k < 3; ++k) C->err[k] = err[q][k];
+                C->pobj = kd[q][kdPobj];
+                C->dobj = kp[q][kpHy] + kd[q][kdBterm];
+                C->status = kConverged;
+                return;
+            }
+        }
+    }
+    if (C->step_mode == 2) return;  // plain PDHG: no restarts
+    double phi[2];
+    for (int q = 0; q < nc; ++q) phi[q] = phi_of(comp[q], om);
+    const int best = (nc == 2 && phi[1] < phi[0]) ? 1 : 0;
+    const double pc = phi[best];
+    const bool restart = (pc <= 0.2 * C->phi0) || (pc <= 0.8 * C->phi0 && pc > C->phi_prev) ||
+                         ((double)C->k >= 0.36 * (double)C->accepted);
+    C->phi_prev = pc;
+    if (!restart) return;
+    const double dx = sqrt(kd[best][kdDx2]), dy = sqrt(kp[best][kpDy2]);
+    double w = om;
+    if (dx > 1e-10 && dy > 1e-10) w = exp(0.5 * log(dy / dx) + 0.5 * log(om));
+    C->omega = w;
+    C->tau = C->eta / w;
+    C->sigma = C->eta * w;
+    C->best = best;
+    C->restart_now = 1;
+    C->wsum = 0.0;
+    C->k = 0;
+    C->restarts += 1;
+    for (int k = 0; k < 3; ++k) C->comp0[k] = comp[best][k];
+    C->phi0 = phi_of(comp[best], w);
+    C->phi_prev = INFINITY;
+}
+
+// Dual-side KKT partials of candidate q (columns of K), then the controller.
+//   kdRd2  : ||lambda~ - Proj_Lambda(lambda~)||^2, lambda~ = c~ - K~' yc
+//   kdPobj : c~' xc;  kdBterm : sum l~ mu^+ - u~ mu^-, mu = Proj_Lambda(lambda~)
+//   kdDx2  : ||xc - x0||^2
+//   kdDmax : ||lambda - Proj_Lambda(lambda)||_inf (original scale), kdKtymax : ||K'y||_inf
+template <typename T>
+__global__ void __launch_bounds__(kBlock) kkt_dual(Dev<T> D) {
+    Ctrl* C = D.ctrl;
+    if (C->status != kRunning) return;
+    const int nc = n_candidates(C);
+    __shared__ double sm[4][kWarpsPerBlock];
+    for (int q = 0; q < nc; ++q) {
+        const double* xc = D.xc + (size_t)q * D.n;
+        const double* kty = D.ktyc + (size_t)q * D.n;
+        double sums[4] = {0.0, 0.0, 0.0, 0.0};
+        double mx[2] = {0.0, 0.0};
+        const int stride = gridDim.x * blockDim.x;
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
+            const double ls = (double)D.l[j], us = (double)D.u[j];
+            const double lam = (double)D.c[j] - kty[j];
+            const double mu = proj_lambda(lam, ls, us);
+            sums[0] += (lam - mu) * (lam - mu);
+            sums[1] += (double)D.c[j] * xc[j];
+            if (mu > 0.0) sums[2] += ls * mu;
+            if (mu < 0.0) sums[2] += us * mu;
+            const double dx = xc[j] - (double)D.x0[j];
+            sums[3] += dx * dx;
+            const double lu = lam / D.dc[j];
+            mx[0] = fmax(mx[0], fabs(lu - proj_lambda(lu, D.l_orig[j], D.u_orig[j])));
+            mx[1] = fmax(mx[1], fabs(kty[j] / D.dc[j]));
+        }
+        block_sum<4>(sums, sm);
+        block_max<2>(mx, sm);
+        if (threadIdx.x == 0) {
+            const int nb = D.pl.kktd_blocks;
+            double* Q = D.part + D.pl.off_kd + (size_t)q * kKktDN * nb;
+            Q[kdRd2 * nb + blockIdx.x] = sums[0];
+            Q[kdPobj * nb + blockIdx.x] = sums[1];
+            Q[kdBterm * nb + blockIdx.x] = sums[2];
+            Q[kdDx2 * nb + blockIdx.x] = sums[3];
+            Q[kdDmax * nb + blockIdx.x] = mx[0];
+            Q[kdKtymax * nb + blockIdx.x] = mx[1];
+        }
+    }
+    if (last_block(C)) check_controller(D, sm);
+}
+
+// restart: z^{t+1,0} <- candidate `best` (and its cached products), averages reset
+template <typename T>
+__global__ void __launch_bounds__(kBlock) restart_primal(Dev<T> D) {
+    const Ctrl* C = D.ctrl;
+    if (!C->restart_now) return;
+    const int q = C->best;
+    const double* xc = D.xc + (size_t)q * D.n;
+    const double* kt = D.ktyc + (size_t)q * D.n;
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
+        D.x[j] = D.x0[j] = (T)xc[j];
+        D.kty[j] = D.kty0[j] = (T)kt[j];
+        D.xsum[j] = T(0);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) restart_dual(Dev<T> D) {
+    const Ctrl* C = D.ctrl;
+    if (!C->restart_now) return;
+    const int q = C->best;
+    const double* yc = D.yc + (size_t)q * D.m;
+    const double* kx = D.kxc + (size_t)q * D.m;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.m; i += stride) {
+        D.y[i] = D.y0[i] = (T)yc[i];
+        D.kx[i] = D.kx0[i] = (T)kx[i];
+        D.ysum[i] = T(0);
+    }
+}
+
+}  // namespace pdcs

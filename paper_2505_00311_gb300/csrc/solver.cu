@@ -1,0 +1,787 @@
+// solver.cu -- host side of the PDCS library: pdcs_create (validation, row
+// grouping by cone kind, K' build, diagonal rescaling on the device), the
+// iteration schedule (one CUDA graph per check period) and the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pdcs.h"
+#include "common.cuh"
+#include "kernels.cuh"
+#include "setup_kernels.cuh"
+#include "state.h"
+
+using namespace pdcs;
+
+namespace {
+
+std::string g_create_error;  // text of the last failed pdcs_create
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int pow2_floor(int v) {
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+// Device memory arena: one cudaMalloc, buffers carved at 256-byte boundaries.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0, used = 0;
+    size_t plan = 0;
+    template <typename T>
+    void reserve(size_t count) { plan += ((count * sizeof(T) + 255) / 256) * 256; }
+    template <typename T>
+    T* take(size_t count) {
+        size_t bytes = ((count * sizeof(T) + 255) / 256) * 256;
+        T* p = reinterpret_cast<T*>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+}  // namespace
+
+struct pdcs_ctx {
+    pdcs_options opt;
+    int m = 0, n = 0;
+    long long nnz = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int sms = 152;
+
+    // row grouping: internal row r holds original row perm[r]
+    std::vector<int> perm;
+    int m_zero = 0, m_scalar = 0, n_soc = 0, exp_row0 = 0, n_exp = 0;
+
+    Arena arena;
+    // device buffers (FP64 path)
+    int *rp = nullptr, *ci = nullptr, *rpT = nullptr, *ciT = nullptr;
+    double *val0 = nullptr, *val0T = nullptr, *val = nullptr, *valT = nullptr;
+    double *c0 = nullptr, *h0 = nullptr, *l0 = nullptr, *u0 = nullptr;
+    double *cs = nullptr, *hs = nullptr, *ls = nullptr, *us = nullptr;
+    double *dr = nullptr, *dc = nullptr, *rn = nullptr, *cn = nullptr;
+    int *soc_off = nullptr, *soc_dim = nullptr;
+    unsigned char* soc_rot = nullptr;
+    int *tie_off = nullptr, *tie_len = nullptr;
+    int n_tie = 0;
+    double *soc_lam = nullptr, *exp_L = nullptr;
+    double* part = nullptr;
+    Ctrl* ctrl = nullptr;
+    double* scal = nullptr;  // small scalar scratch
+    Ctrl* h_ctrl = nullptr;  // pinned host mirror
+
+    Dev<double> D;
+    int G = 8, GT = 4;
+    int g_vec_n = 0, g_vec_m = 0, g_dual = 0, g_spmv_k = 0, g_spmv_kt = 0, g_kktd = 0;
+
+    cudaGraphExec_t graph = nullptr;
+    bool started = false;
+    double setup_seconds = 0.0, solve_seconds = 0.0;
+    double norm2 = 0.0;
+    int last_status = PDCS_OK;
+
+    ~pdcs_ctx() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (arena.base) cudaFree(arena.base);
+        if (h_ctrl) cudaFreeHost(h_ctrl);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            return e_ == cudaErrorMemoryAllocation ? PDCS_ERR_OOM : PDCS_ERR_CUDA;        \
+        }                                                                                 \
+    } while (0)
+
+namespace {
+
+template <typename T, typename TO>
+void launch_spmv(int G, int grid, cudaStream_t s, int rows, const int* rp, const int* ci, const T* val, const T* x,
+                 TO* y0, TO* y1, const Ctrl* ctrl, int sel, int skip) {
+    switch (G) {
+        case 1: spmv_csr<T, TO, 1><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
+        case 2: spmv_csr<T, TO, 2><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
+        case 4: spmv_csr<T, TO, 4><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
+        case 8: spmv_csr<T, TO, 8><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
+        case 16: spmv_csr<T, TO, 16><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
+        default: spmv_csr<T, TO, 32><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
+    }
+}
+
+int spmv_grid(int rows, int G, int sms) {
+    long long rows_per_block = (long long)kWarpsPerBlock * (32 / G);
+    long long g = (rows + rows_per_block - 1) / rows_per_block;
+    return (int)std::max(1LL, std::min(g, (long long)sms * 32));
+}
+
+int vec_grid(long long k, int sms) {
+    long long g = (k + kBlock - 1) / kBlock;
+    return (int)std::max(1LL, std::min(g, (long long)sms * 8));
+}
+
+int choose_lanes(long long nnz, long long rows) {
+    double avg = rows > 0 ? (double)nnz / (double)rows : 1.0;
+    int g = pow2_floor(std::max(1, (int)std::ceil(avg / 3.0)));
+    return std::min(32, std::max(2, g));
+}
+
+// one PDHG evaluation
+void enqueue_attempt(pdcs_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    Dev<double>& D = ctx->D;
+    primal_update<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
+    launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, ctx->m, D.rp, D.ci, D.val, D.xh, D.kxh0, D.kxh1, D.ctrl, 1, 1);
+    dual_update<double><<<ctx->g_dual, kBlock, 0, s>>>(D);
+    launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, ctx->n, D.rpT, D.ciT, D.valT, D.yh, D.ktyh, nullptr,
+                                D.ctrl, 0, 2);
+}
+
+// restart / termination check (or the initial evaluation of the anchor)
+void enqueue_check(pdcs_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    Dev<double>& D = ctx->D;
+    flush_primal<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
+    flush_dual<double><<<ctx->g_vec_m, kBlock, 0, s>>>(D);
+    cand_primal<double><<<dim3(ctx->g_vec_n, 2), kBlock, 0, s>>>(D);
+    cand_dual<double><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(D);
+    for (int q = 0; q < 2; ++q) {
+        launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, ctx->m, D.rp, D.ci, D.val, D.xc + (size_t)q * ctx->n,
+                                    D.kxc + (size_t)q * ctx->m, nullptr, D.ctrl, 0, 1);
+        launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, ctx->n, D.rpT, D.ciT, D.valT,
+                                    D.yc + (size_t)q * ctx->m, D.ktyc + (size_t)q * ctx->n, nullptr, D.ctrl, 0, 1);
+    }
+    kkt_primal<double><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(D);
+    kkt_dual<double><<<ctx->g_kktd, kBlock, 0, s>>>(D);
+    restart_primal<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
+    restart_dual<double><<<ctx->g_vec_m, kBlock, 0, s>>>(D);
+}
+
+__global__ void clear_pending(Ctrl* C) { C->pending = 0; }
+
+pdcs_status read_ctrl(pdcs_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->h_ctrl, ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PDCS_OK;
+}
+
+bool finite_all(const double* a, long long k) {
+    if (!a) return true;
+    for (long long i = 0; i < k; ++i)
+        if (std::isnan(a[i])) return false;
+    return true;
+}
+
+pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const double* h, const double* lb,
+                  const double* ub, const pdcs_cone* cones, int64_t n_cones) {
+    const int m = ctx->m, n = ctx->n;
+    const long long nnz = ctx->nnz;
+    // ---- row grouping: zero rows, nonnegative rows, SOC/RSOC blocks, exp cones
+    std::vector<int> zero_rows, nonneg_rows, soc_o, soc_d, exp_o;
+    std::vector<unsigned char> soc_r;
+    {
+        long long o = 0;
+        for (int64_t k = 0; k < n_cones; ++k) {
+            const int t = cones[k].type;
+            const long long d = cones[k].dim;
+            if (t == PDCS_CONE_ZERO) for (long long i = 0; i < d; ++i) zero_rows.push_back((int)(o + i));
+            else if (t == PDCS_CONE_NONNEG) for (long long i = 0; i < d; ++i) nonneg_rows.push_back((int)(o + i));
+            else if (t == PDCS_CONE_SOC || t == PDCS_CONE_RSOC) {
+                soc_o.push_back((int)o); soc_d.push_back((int)d); soc_r.push_back(t == PDCS_CONE_RSOC);
+            } else exp_o.push_back((int)o);
+            o += d;
+        }
+    }
+    ctx->perm.clear();
+    ctx->perm.reserve(m);
+    for (int r : zero_rows) ctx->perm.push_back(r);
+    for (int r : nonneg_rows) ctx->perm.push_back(r);
+    ctx->m_zero = (int)zero_rows.size();
+    ctx->m_scalar = (int)(zero_rows.size() + nonneg_rows.size());
+    std::vector<int> soc_off_i(soc_o.size());
+    for (size_t k = 0; k < soc_o.size(); ++k) {
+        soc_off_i[k] = (int)ctx->perm.size();
+        for (int i = 0; i < soc_d[k]; ++i) ctx->perm.push_back(soc_o[k] + i);
+    }
+    ctx->exp_row0 = (int)ctx->perm.size();
+    for (int o : exp_o) for (int i = 0; i < 3; ++i) ctx->perm.push_back(o + i);
+    ctx->n_soc = (int)soc_o.size();
+    ctx->n_exp = (int)exp_o.size();
+    // tie groups for the rescaling: RSOC first two rows (per coordinate), whole blocks (block mode)
+    std::vector<int> tie_o, tie_l;
+    if (ctx->opt.rescale != PDCS_RESCALE_NONE) {
+        for (int k = 0; k < ctx->n_soc; ++k) {
+            if (ctx->opt.rescale == PDCS_RESCALE_BLOCK) { tie_o.push_back(soc_off_i[k]); tie_l.push_back(soc_d[k]); }
+            else if (soc_r[k]) { tie_o.push_back(soc_off_i[k]); tie_l.push_back(2); }
+        }
+        if (ctx->opt.rescale == PDCS_RESCALE_BLOCK)
+            for (int e = 0; e < ctx->n_exp; ++e) { tie_o.push_back(ctx->exp_row0 + 3 * e); tie_l.push_back(3); }
+    }
+    ctx->n_tie = (int)tie_o.size();
+
+    // ---- internal K (rows permuted) and K' by counting sort (host, once)
+    std::vector<int> rp_i(m + 1), ci_i((size_t)nnz);
+    std::vector<double> v_i((size_t)nnz);
+    rp_i[0] = 0;
+    for (int r = 0; r < m; ++r) {
+        const int src = ctx->perm[r];
+        const long long b = K->row_ptr[src], e = K->row_ptr[src + 1];
+        const int dst = rp_i[r];
+        for (long long p = b; p < e; ++p) {
+            ci_i[dst + (p - b)] = K->col[p];
+            v_i[dst + (p - b)] = K->val[p];
+        }
+        rp_i[r + 1] = dst + (int)(e - b);
+    }
+    std::vector<int> rpT(n + 1, 0), ciT((size_t)nnz);
+    std::vector<double> vT((size_t)nnz);
+    for (long long p = 0; p < nnz; ++p) rpT[ci_i[p] + 1]++;
+    for (int j = 0; j < n; ++j) rpT[j + 1] += rpT[j];
+    {
+        std::vector<int> cur(rpT.begin(), rpT.end() - 1);
+        for (int r = 0; r < m; ++r)
+            for (int p = rp_i[r]; p < rp_i[r + 1]; ++p) {
+                const int q = cur[ci_i[p]]++;
+                ciT[q] = r;
+                vT[q] = v_i[p];
+            }
+    }
+    std::vector<double> h_i(m), l_h(n), u_h(n);
+    for (int r = 0; r < m; ++r) h_i[r] = h[ctx->perm[r]];
+    for (int j = 0; j < n; ++j) {
+        l_h[j] = lb ? lb[j] : 0.0;
+        u_h[j] = ub ? ub[j] : INFINITY;
+    }
+    double hmax = 0.0, cmax = 0.0;
+    for (int i = 0; i < m; ++i) hmax = std::max(hmax, std::fabs(h[i]));
+    for (int j = 0; j < n; ++j) cmax = std::max(cmax, std::fabs(c[j]));
+
+    // ---- device memory plan
+    ctx->G = ctx->opt.spmv_lanes > 0 ? ctx->opt.spmv_lanes : choose_lanes(nnz, m);
+    ctx->GT = ctx->opt.spmv_lanes > 0 ? ctx->opt.spmv_lanes : choose_lanes(nnz, n);
+    ctx->g_vec_n = vec_grid(n, ctx->sms);
+    ctx->g_vec_m = vec_grid(m, ctx->sms);
+    ctx->g_spmv_k = spmv_grid(m, ctx->G, ctx->sms);
+    ctx->g_spmv_kt = spmv_grid(n, ctx->GT, ctx->sms);
+    ctx->g_kktd = vec_grid(n, ctx->sms);
+    const int nb_scal = ctx->m_scalar > 0 ? vec_grid(ctx->m_scalar, ctx->sms) : 0;
+    const int nb_soc = ctx->n_soc > 0 ? (int)std::min<long long>((ctx->n_soc + kWarpsPerBlock - 1) / kWarpsPerBlock,
+                                                                 (long long)ctx->sms * 8)
+                                      : 0;
+    const int nb_exp = ctx->n_exp > 0 ? vec_grid(ctx->n_exp, ctx->sms) : 0;
+    ctx->g_dual = std::max(1, nb_scal + nb_soc + nb_exp);
+    PartLayout pl;
+    pl.primal_blocks = ctx->g_vec_n;
+    pl.dual_blocks = ctx->g_dual;
+    pl.kktp_blocks = ctx->g_dual;
+    pl.kktd_blocks = ctx->g_kktd;
+    pl.off_px = 0;
+    pl.off_dy = pl.off_px + pl.primal_blocks;
+    pl.off_kp = pl.off_dy + 2LL * pl.dual_blocks;
+    pl.off_kd = pl.off_kp + 2LL * kKktPN * pl.kktp_blocks;
+    pl.total = pl.off_kd + 2LL * kKktDN * pl.kktd_blocks;
+
+    Arena& A = ctx->arena;
+    A.reserve<int>(m + 1); A.reserve<int>(nnz); A.reserve<int>(n + 1); A.reserve<int>(nnz);
+    for (int k = 0; k < 4; ++k) A.reserve<double>(nnz);              // val0, val0T, val, valT
+    for (int k = 0; k < 4; ++k) A.reserve<double>(n);                // c0 l0 u0 + cs
+    A.reserve<double>(m); A.reserve<double>(m);                      // h0, hs
+    A.reserve<double>(n); A.reserve<double>(n);                      // ls us
+    A.reserve<double>(m); A.reserve<double>(n); A.reserve<double>(m); A.reserve<double>(n);  // dr dc rn cn
+    A.reserve<int>(ctx->n_soc + 1); A.reserve<int>(ctx->n_soc + 1); A.reserve<unsigned char>(ctx->n_soc + 1);
+    A.reserve<int>(ctx->n_tie + 1); A.reserve<int>(ctx->n_tie + 1);
+    A.reserve<double>(ctx->n_soc + 1); A.reserve<double>(ctx->n_exp + 1);
+    A.reserve<double>(pl.total);
+    A.reserve<Ctrl>(1);
+    A.reserve<double>(16);
+    for (int k = 0; k < 7; ++k) A.reserve<double>(n);  // x xh x0 kty ktyh kty0 xsum
+    for (int k = 0; k < 8; ++k) A.reserve<double>(m);  // y yh y0 kx kxh0 kxh1 kx0 ysum
+    A.reserve<double>(2LL * n); A.reserve<double>(2LL * m); A.reserve<double>(2LL * m); A.reserve<double>(2LL * n);
+    A.reserve<double>(2LL * m);  // scr
+    {
+        cudaError_t e = cudaMalloc(&A.base, A.plan);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("cudaMalloc of ") + std::to_string(A.plan) + " bytes: " + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? PDCS_ERR_OOM : PDCS_ERR_CUDA;
+        }
+        A.cap = A.plan;
+    }
+    ctx->rp = A.take<int>(m + 1); ctx->ci = A.take<int>(nnz);
+    ctx->rpT = A.take<int>(n + 1); ctx->ciT = A.take<int>(nnz);
+    ctx->val0 = A.take<double>(nnz); ctx->val0T = A.take<double>(nnz);
+    ctx->val = A.take<double>(nnz); ctx->valT = A.take<double>(nnz);
+    ctx->c0 = A.take<double>(n); ctx->l0 = A.take<double>(n); ctx->u0 = A.take<double>(n); ctx->cs = A.take<double>(n);
+    ctx->h0 = A.take<double>(m); ctx->hs = A.take<double>(m);
+    ctx->ls = A.take<double>(n); ctx->us = A.take<double>(n);
+    ctx->dr = A.take<double>(m); ctx->dc = A.take<double>(n); ctx->rn = A.take<double>(m); ctx->cn = A.take<double>(n);
+    ctx->soc_off = A.take<int>(ctx->n_soc + 1); ctx->soc_dim = A.take<int>(ctx->n_soc + 1);
+    ctx->soc_rot = A.take<unsigned char>(ctx->n_soc + 1);
+    ctx->tie_off = A.take<int>(ctx->n_tie + 1); ctx->tie_len = A.take<int>(ctx->n_tie + 1);
+    ctx->soc_lam = A.take<double>(ctx->n_soc + 1); ctx->exp_L = A.take<double>(ctx->n_exp + 1);
+    ctx->part = A.take<double>(pl.total);
+    ctx->ctrl = A.take<Ctrl>(1);
+    ctx->scal = A.take<double>(16);
+    Dev<double>& D = ctx->D;
+    D.x = A.take<double>(n); D.xh = A.take<double>(n); D.x0 = A.take<double>(n); D.kty = A.take<double>(n);
+    D.ktyh = A.take<double>(n); D.kty0 = A.take<double>(n); D.xsum = A.take<double>(n);
+    D.y = A.take<double>(m); D.yh = A.take<double>(m); D.y0 = A.take<double>(m); D.kx = A.take<double>(m);
+    D.kxh0 = A.take<double>(m); D.kxh1 = A.take<double>(m); D.kx0 = A.take<double>(m); D.ysum = A.take<double>(m);
+    D.xc = A.take<double>(2LL * n); D.yc = A.take<double>(2LL * m); D.kxc = A.take<double>(2LL * m);
+    D.ktyc = A.take<double>(2LL * n); D.scr = A.take<double>(2LL * m);
+
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemsetAsync(A.base, 0, A.used, s));
+    CK(cudaMemcpyAsync(ctx->rp, rp_i.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->ci, ci_i.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->rpT, rpT.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->ciT, ciT.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->val0, v_i.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->val0T, vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->c0, c, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->l0, l_h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->u0, u_h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->h0, h_i.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    if (ctx->n_soc) {
+        CK(cudaMemcpyAsync(ctx->soc_off, soc_off_i.data(), sizeof(int) * ctx->n_soc, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->soc_dim, soc_d.data(), sizeof(int) * ctx->n_soc, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->soc_rot, soc_r.data(), ctx->n_soc, cudaMemcpyHostToDevice, s));
+    }
+    if (ctx->n_tie) {
+        CK(cudaMemcpyAsync(ctx->tie_off, tie_o.data(), sizeof(int) * ctx->n_tie, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->tie_len, tie_l.data(), sizeof(int) * ctx->n_tie, cudaMemcpyHostToDevice, s));
+    }
+    // the host copies above are pageable: wait before the vectors go out of scope
+    CK(cudaStreamSynchronize(s));
+
+    // ---- diagonal rescaling: Ruiz (infinity norm) then Pock-Chambolle (alpha = 1)
+    std::vector<double> ones_m(m, 1.0), ones_n(n, 1.0);
+    CK(cudaMemcpyAsync(ctx->dr, ones_m.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->dc, ones_n.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    if (ctx->opt.rescale != PDCS_RESCALE_NONE) {
+        const int passes = ctx->opt.ruiz_iters + (ctx->opt.pock_chambolle ? 1 : 0);
+        const int gr = spmv_grid(m, 32, ctx->sms), gc = spmv_grid(n, 32, ctx->sms);
+        for (int it = 0; it < passes; ++it) {
+            const int kind = it >= ctx->opt.ruiz_iters ? 1 : 0;
+            scaled_row_norms<<<gr, kBlock, 0, s>>>(m, ctx->rp, ctx->ci, ctx->val0, ctx->dr, ctx->dc, 1, kind, ctx->rn);
+            scaled_row_norms<<<gc, kBlock, 0, s>>>(n, ctx->rpT, ctx->ciT, ctx->val0T, ctx->dc, ctx->dr, 0, kind, ctx->cn);
+            if (ctx->n_tie) tie_groups<<<(ctx->n_tie + 255) / 256, 256, 0, s>>>(ctx->n_tie, ctx->tie_off, ctx->tie_len, ctx->rn);
+            apply_norm<<<(m + 255) / 256, 256, 0, s>>>(m, ctx->rn, ctx->dr);
+            apply_norm<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->cn, ctx->dc);
+        }
+    }
+    {
+        const int gr = spmv_grid(m, 32, ctx->sms), gc = spmv_grid(n, 32, ctx->sms);
+        scale_values<<<gr, kBlock, 0, s>>>(m, ctx->rp, ctx->ci, ctx->val0, ctx->dr, ctx->dc, 1, ctx->val);
+        scale_values<<<gc, kBlock, 0, s>>>(n, ctx->rpT, ctx->ciT, ctx->val0T, ctx->dc, ctx->dr, 0, ctx->valT);
+        scale_cols<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->dc, ctx->c0, ctx->l0, ctx->u0, ctx->cs, ctx->ls, ctx->us);
+        scale_rows<<<(m + 255) / 256, 256, 0, s>>>(m, ctx->dr, ctx->h0, ctx->hs);
+        reduce_small<<<1, kBlock, 0, s>>>(n, ctx->cs, nullptr, 0, ctx->scal + 0);
+        reduce_small<<<1, kBlock, 0, s>>>(m, ctx->hs, nullptr, 0, ctx->scal + 1);
+        reduce_small<<<1, kBlock, 0, s>>>(nnz, ctx->val, nullptr, 1, ctx->scal + 2);
+        CK(cudaGetLastError());
+    }
+    double sc[3];
+    CK(cudaMemcpyAsync(sc, ctx->scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double nc = std::sqrt(sc[0]), nh = std::sqrt(sc[1]), amax = sc[2];
+
+    // ---- ||K~||_2 by power iteration (constant / plain step modes)
+    double eta = amax > 0.0 ? 1.0 / amax : 1.0;
+    double omega = (nc > 1e-10 && nh > 1e-10) ? nc / nh : 1.0;
+    if (ctx->opt.step_mode != PDCS_STEP_ADAPTIVE) {
+        double* v = D.xc;
+        double* w = D.kxc;
+        double* u = D.ktyc;
+        std::vector<double> v0(n, 1.0 / std::sqrt((double)n));
+        CK(cudaMemcpyAsync(v, v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        double est = 0.0;
+        for (int it = 0; it < ctx->opt.power_iters; ++it) {
+            launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, m, ctx->rp, ctx->ci, ctx->val, v, w, nullptr, nullptr, 0, 0);
+            launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, n, ctx->rpT, ctx->ciT, ctx->valT, w, u, nullptr, nullptr, 0, 0);
+            reduce_small<<<1, kBlock, 0, s>>>(n, u, nullptr, 0, ctx->scal + 3);
+            double ss;
+            CK(cudaMemcpyAsync(&ss, ctx->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const double nu = std::sqrt(ss);
+            if (!(nu > 0.0)) break;
+            est = std::sqrt(nu);
+            scale_by_inv<<<vec_grid(n, ctx->sms), kBlock, 0, s>>>(n, u, ctx->scal + 3, v);
+        }
+        ctx->norm2 = est;
+        const double nn = est > 0.0 ? est : 1.0;
+        eta = (ctx->opt.step_mode == PDCS_STEP_PLAIN ? 0.9 : 0.998) / nn;
+        if (ctx->opt.step_mode == PDCS_STEP_PLAIN) omega = 1.0;
+        CK(cudaMemsetAsync(D.xc, 0, sizeof(double) * 2 * n, s));
+        CK(cudaMemsetAsync(D.kxc, 0, sizeof(double) * 2 * m, s));
+        CK(cudaMemsetAsync(D.ktyc, 0, sizeof(double) * 2 * n, s));
+    }
+
+    // ---- device view
+    D.m = m; D.n = n;
+    D.rp = ctx->rp; D.ci = ctx->ci; D.val = ctx->val;
+    D.rpT = ctx->rpT; D.ciT = ctx->ciT; D.valT = ctx->valT;
+    D.c = ctx->cs; D.h = ctx->hs; D.l = ctx->ls; D.u = ctx->us; D.dr = ctx->dr; D.dc = ctx->dc;
+    D.m_zero = ctx->m_zero; D.m_scalar = ctx->m_scalar;
+    D.n_soc = ctx->n_soc; D.soc_off = ctx->soc_off; D.soc_dim = ctx->soc_dim; D.soc_rot = ctx->soc_rot;
+    D.soc_lam = ctx->soc_lam;
+    D.exp_row0 = ctx->exp_row0; D.n_exp = ctx->n_exp; D.exp_L = ctx->exp_L;
+    D.nb_scal = nb_scal; D.nb_soc = nb_soc; D.nb_exp = nb_exp; D.nb_primal = ctx->g_vec_n;
+    D.part = ctx->part; D.pl = pl; D.ctrl = ctx->ctrl;
+    D.l_orig = ctx->l0; D.u_orig = ctx->u0;
+
+    // ---- controller scalars
+    Ctrl C;
+    std::memset(&C, 0, sizeof(C));
+    C.eta = eta; C.omega = omega; C.tau = eta / omega; C.sigma = eta * omega;
+    C.beta = ctx->opt.beta;
+    C.phi_prev = INFINITY;
+    C.hmax = hmax; C.cmax = cmax;
+    C.step_mode = ctx->opt.step_mode;
+    C.status = kRunning;
+    *ctx->h_ctrl = C;
+    CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    std::vector<double> nanv(std::max(ctx->n_soc, ctx->n_exp) + 1, NAN);
+    CK(cudaMemcpyAsync(ctx->exp_L, nanv.data(), sizeof(double) * (ctx->n_exp + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->soc_lam, nanv.data(), sizeof(double) * (ctx->n_soc + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    return PDCS_OK;
+}
+
+pdcs_status capture_graph(pdcs_ctx* ctx) {
+    if (ctx->graph) return PDCS_OK;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    for (int a = 0; a < ctx->opt.check_period; ++a) enqueue_attempt(ctx);
+    enqueue_check(ctx);
+    CK(cudaStreamEndCapture(ctx->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->graph = nullptr;
+        ctx->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+        return PDCS_ERR_CUDA;
+    }
+    return PDCS_OK;
+}
+
+pdcs_status status_of(const Ctrl& C) {
+    if (C.status == kConverged) return PDCS_OK;
+    if (C.status == kNumericError) return PDCS_ERR_NUMERIC;
+    return PDCS_MAX_ITER;
+}
+
+void fill_info(pdcs_ctx* ctx, pdcs_info* info) {
+    const Ctrl& C = *ctx->h_ctrl;
+    info->attempts = C.attempts;
+    info->accepted = C.accepted;
+    info->restarts = C.restarts;
+    info->err_p = C.err[0];
+    info->err_d = C.err[1];
+    info->err_gap = C.err[2];
+    info->pobj = C.pobj;
+    info->dobj = C.dobj;
+    info->eta = C.eta;
+    info->omega = C.omega;
+    info->setup_seconds = ctx->setup_seconds;
+    info->solve_seconds = ctx->solve_seconds;
+    info->status = ctx->last_status;
+    info->fp64_phase = 1;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void pdcs_default_options(pdcs_options* o) {
+    if (!o) return;
+    o->rescale = PDCS_RESCALE_COORD;
+    o->ruiz_iters = 10;
+    o->pock_chambolle = 1;
+    o->step_mode = PDCS_STEP_ADAPTIVE;
+    o->check_period = 64;
+    o->beta = 1.0;
+    o->power_iters = 50;
+    o->precision = PDCS_PRECISION_FP64;
+    o->fp32_switch_tol = 1e-4;
+    o->use_graphs = 1;
+    o->spmv_lanes = 0;
+    o->time_limit = 0.0;
+}
+
+pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, const double* lb, const double* ub,
+                        const pdcs_cone* cones, int64_t n_cones, const pdcs_options* opt, void* cuda_stream,
+                        pdcs_ctx** out) {
+    const double t0 = now_s();
+    if (!out) { g_create_error = "out is NULL"; return PDCS_ERR_INVALID; }
+    *out = nullptr;
+    auto bad = [&](const std::string& s) { g_create_error = s; return PDCS_ERR_INVALID; };
+    if (!K || !c || !h || !cones) return bad("K, c, h and cones are required");
+    if (K->m < 1 || K->n < 1 || K->m > 0x7fffffff || K->n > 0x7fffffff) return bad("m and n must be in [1, 2^31)");
+    if (!K->row_ptr || (K->nnz > 0 && (!K->col || !K->val))) return bad("CSR arrays are NULL");
+    if (K->nnz < 0 || K->nnz >= 0x7fffffffLL) return bad("nnz must be in [0, 2^31)");
+    if (K->row_ptr[0] != 0 || K->row_ptr[K->m] != K->nnz) return bad("row_ptr[0] must be 0 and row_ptr[m] == nnz");
+    for (int64_t i = 0; i < K->m; ++i)
+        if (K->row_ptr[i + 1] < K->row_ptr[i]) return bad("row_ptr is not nondecreasing");
+    for (int64_t p = 0; p < K->nnz; ++p) {
+        if (K->col[p] < 0 || K->col[p] >= K->n) return bad("column index out of range");
+        if (!std::isfinite(K->val[p])) return bad("matrix value is NaN or Inf");
+    }
+    for (int64_t j = 0; j < K->n; ++j) if (!std::isfinite(c[j])) return bad("c has NaN or Inf");
+    for (int64_t i = 0; i < K->m; ++i) if (!std::isfinite(h[i])) return bad("h has NaN or Inf");
+    if (!finite_all(lb, K->n) || !finite_all(ub, K->n)) return bad("bounds contain NaN");
+    for (int64_t j = 0; j < K->n; ++j) {
+        const double l = lb ? lb[j] : 0.0, u = ub ? ub[j] : INFINITY;
+        if (l > u) return bad("lb > ub");
+        if (l == INFINITY || u == -INFINITY) return bad("infeasible infinite bound");
+    }
+    if (n_cones < 1) return bad("the cone list is empty");
+    long long tot = 0;
+    for (int64_t k = 0; k < n_cones; ++k) {
+        const int t = cones[k].type;
+        const long long d = cones[k].dim;
+        if (t < PDCS_CONE_ZERO || t > PDCS_CONE_EXP) return bad("unknown cone type");
+        if (d < 1 || (t == PDCS_CONE_EXP && d != 3) || (t == PDCS_CONE_RSOC && d < 2))
+            return bad("bad cone dimension");
+        tot += d;
+    }
+    if (tot != K->m) return bad("cone dimensions do not sum to m");
+    pdcs_options o;
+    pdcs_default_options(&o);
+    if (opt) o = *opt;
+    if (o.check_period < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || o.rescale < 0 || o.rescale > 2 ||
+        o.step_mode < 0 || o.step_mode > 2 || !(o.beta >= 0.0) || o.beta > 1.0)
+        return bad("invalid options");
+    if (o.precision != PDCS_PRECISION_FP64) return bad("only FP64 precision is available in this build");
+    if (o.spmv_lanes != 0 && (o.spmv_lanes > 32 || (o.spmv_lanes & (o.spmv_lanes - 1)) != 0))
+        return bad("spmv_lanes must be 0 or a power of two <= 32");
+
+    pdcs_ctx* ctx = new (std::nothrow) pdcs_ctx();
+    if (!ctx) return bad("host allocation failed");
+    ctx->opt = o;
+    ctx->m = (int)K->m;
+    ctx->n = (int)K->n;
+    ctx->nnz = K->nnz;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            ctx->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            ctx->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) {
+        g_create_error = std::string("CUDA setup: ") + cudaGetErrorString(e);
+        delete ctx;
+        return PDCS_ERR_CUDA;
+    }
+    pdcs_status st = build(ctx, K, c, h, lb, ub, cones, n_cones);
+    if (st != PDCS_OK) {
+        g_create_error = ctx->err;
+        delete ctx;
+        return st;
+    }
+    ctx->setup_seconds = now_s() - t0;
+    *out = ctx;
+    return PDCS_OK;
+}
+
+pdcs_status pdcs_solve(pdcs_ctx* ctx, double tol, int64_t max_iter, pdcs_info* info) {
+    if (!ctx) return PDCS_ERR_INVALID;
+    if (max_iter < 0) { ctx->err = "max_iter < 0"; return PDCS_ERR_INVALID; }
+    const double t0 = now_s();
+    pdcs_status st = read_ctrl(ctx);
+    if (st != PDCS_OK) return st;
+    if (ctx->h_ctrl->status != kRunning) {  // a converged solver stays converged
+        ctx->last_status = status_of(*ctx->h_ctrl);
+        if (info) fill_info(ctx, info);
+        return (pdcs_status)ctx->last_status;
+    }
+    CK(cudaMemcpyAsync(&ctx->ctrl->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (!ctx->started) {
+        const int one = 1;
+        CK(cudaMemcpyAsync(&ctx->ctrl->check_mode, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        enqueue_check(ctx);
+        CK(cudaGetLastError());
+        ctx->started = true;
+    }
+    if (ctx->opt.use_graphs) {
+        st = capture_graph(ctx);
+        if (st != PDCS_OK) return st;
+    }
+    const int period = ctx->opt.check_period;
+    long long done = ctx->h_ctrl->attempts;
+    long long remaining = max_iter;
+    pdcs_status result = PDCS_MAX_ITER;
+    while (remaining > 0) {
+        const long long to_b = period - (done % period);
+        if (remaining >= to_b) {
+            if (to_b == period && ctx->graph) {
+                CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+            } else {
+                for (long long a = 0; a < to_b; ++a) enqueue_attempt(ctx);
+                enqueue_check(ctx);
+            }
+            done += to_b;
+            remaining -= to_b;
+        } else {
+            for (long long a = 0; a < remaining; ++a) enqueue_attempt(ctx);
+            done += remaining;
+            remaining = 0;
+        }
+        CK(cudaGetLastError());
+        st = read_ctrl(ctx);
+        if (st != PDCS_OK) return st;
+        if (ctx->h_ctrl->status != kRunning) break;
+        if (ctx->opt.time_limit > 0.0 && now_s() - t0 > ctx->opt.time_limit) { result = PDCS_TIME_LIMIT; break; }
+    }
+    st = read_ctrl(ctx);
+    if (st != PDCS_OK) return st;
+    if (ctx->h_ctrl->status == kConverged) result = PDCS_OK;
+    else if (ctx->h_ctrl->status == kNumericError) result = PDCS_ERR_NUMERIC;
+    else if (result != PDCS_TIME_LIMIT) result = PDCS_MAX_ITER;
+    if (result == PDCS_ERR_NUMERIC) ctx->err = "NaN or Inf in the iterates";
+    ctx->solve_seconds += now_s() - t0;
+    ctx->last_status = result;
+    if (info) fill_info(ctx, info);
+    return result;
+}
+
+static pdcs_status unscale_out(pdcs_ctx* ctx, const double* dx, const double* dy, double* x, double* y) {
+    std::vector<double> hx(ctx->n), hy(ctx->m), hdc(ctx->n), hdr(ctx->m);
+    CK(cudaMemcpyAsync(hdc.data(), ctx->dc, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hdr.data(), ctx->dr, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+    if (x) CK(cudaMemcpyAsync(hx.data(), dx, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (y) CK(cudaMemcpyAsync(hy.data(), dy, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (x) for (int j = 0; j < ctx->n; ++j) x[j] = hx[j] * hdc[j];
+    if (y) for (int r = 0; r < ctx->m; ++r) y[ctx->perm[r]] = hy[r] * hdr[r];
+    return PDCS_OK;
+}
+
+pdcs_status pdcs_get_solution(pdcs_ctx* ctx, double* x, double* y, double* lambda) {
+    if (!ctx) return PDCS_ERR_INVALID;
+    if (!ctx->started) { ctx->err = "no solution before the first pdcs_solve"; return PDCS_ERR_INVALID; }
+    pdcs_status st = read_ctrl(ctx);
+    if (st != PDCS_OK) return st;
+    const int q = ctx->h_ctrl->sol_cand;
+    const double* dx = ctx->D.xc + (size_t)q * ctx->n;
+    const double* dy = ctx->D.yc + (size_t)q * ctx->m;
+    st = unscale_out(ctx, dx, dy, x, y);
+    if (st != PDCS_OK) return st;
+    if (lambda) {
+        std::vector<double> kt(ctx->n), cs(ctx->n), dc(ctx->n);
+        CK(cudaMemcpyAsync(kt.data(), ctx->D.ktyc + (size_t)q * ctx->n, sizeof(double) * ctx->n,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(cs.data(), ctx->cs, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(dc.data(), ctx->dc, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int j = 0; j < ctx->n; ++j) lambda[j] = (cs[j] - kt[j]) / dc[j];
+    }
+    return PDCS_OK;
+}
+
+pdcs_status pdcs_get_iterate(pdcs_ctx* ctx, double* x, double* y, double* xhat, double* yhat) {
+    if (!ctx) return PDCS_ERR_INVALID;
+    // materialise a pending Halpern update (same arithmetic as the next evaluation would apply)
+    flush_primal<double><<<ctx->g_vec_n, kBlock, 0, ctx->stream>>>(ctx->D);
+    flush_dual<double><<<ctx->g_vec_m, kBlock, 0, ctx->stream>>>(ctx->D);
+    clear_pending<<<1, 1, 0, ctx->stream>>>(ctx->ctrl);
+    CK(cudaGetLastError());
+    pdcs_status st = unscale_out(ctx, ctx->D.x, ctx->D.y, x, y);
+    if (st != PDCS_OK) return st;
+    return unscale_out(ctx, ctx->D.xh, ctx->D.yh, xhat, yhat);
+}
+
+pdcs_status pdcs_get_scaling(pdcs_ctx* ctx, double* dr, double* dc) {
+    if (!ctx) return PDCS_ERR_INVALID;
+    std::vector<double> hdr(ctx->m);
+    CK(cudaMemcpyAsync(hdr.data(), ctx->dr, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+    if (dc) CK(cudaMemcpyAsync(dc, ctx->dc, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (dr) for (int r = 0; r < ctx->m; ++r) dr[ctx->perm[r]] = hdr[r];
+    return PDCS_OK;
+}
+
+pdcs_status pdcs_get_info(pdcs_ctx* ctx, pdcs_info* info) {
+    if (!ctx || !info) return PDCS_ERR_INVALID;
+    pdcs_status st = read_ctrl(ctx);
+    if (st != PDCS_OK) return st;
+    fill_info(ctx, info);
+    return PDCS_OK;
+}
+
+pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y, double omega) {
+    if (!ctx) return PDCS_ERR_INVALID;
+    if (x) for (int j = 0; j < ctx->n; ++j) if (!std::isfinite(x[j])) { ctx->err = "x has NaN/Inf"; return PDCS_ERR_INVALID; }
+    if (y) for (int i = 0; i < ctx->m; ++i) if (!std::isfinite(y[i])) { ctx->err = "y has NaN/Inf"; return PDCS_ERR_INVALID; }
+    std::vector<double> hdc(ctx->n), hdr(ctx->m), xs(ctx->n, 0.0), ys(ctx->m, 0.0);
+    CK(cudaMemcpyAsync(hdc.data(), ctx->dc, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hdr.data(), ctx->dr, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (x) for (int j = 0; j < ctx->n; ++j) xs[j] = x[j] / hdc[j];
+    if (y) for (int r = 0; r < ctx->m; ++r) ys[r] = y[ctx->perm[r]] / hdr[r];
+    Dev<double>& D = ctx->D;
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(D.x, xs.data(), sizeof(double) * ctx->n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.x0, xs.data(), sizeof(double) * ctx->n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.y, ys.data(), sizeof(double) * ctx->m, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.y0, ys.data(), sizeof(double) * ctx->m, cudaMemcpyHostToDevice, s));
+    // cached products of the start: K x, K'y
+    launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, ctx->m, D.rp, D.ci, D.val, D.x, D.kx, nullptr, nullptr, 0, 0);
+    launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, ctx->n, D.rpT, D.ciT, D.valT, D.y, D.kty, nullptr, nullptr, 0, 0);
+    CK(cudaMemcpyAsync(D.kx0, D.kx, sizeof(double) * ctx->m, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(D.kty0, D.kty, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(D.xsum, 0, sizeof(double) * ctx->n, s));
+    CK(cudaMemsetAsync(D.ysum, 0, sizeof(double) * ctx->m, s));
+    CK(cudaStreamSynchronize(s));
+    pdcs_status st = read_ctrl(ctx);
+    if (st != PDCS_OK) return st;
+    Ctrl C = *ctx->h_ctrl;
+    if (omega > 0.0) C.omega = omega;
+    C.tau = C.eta / C.omega;
+    C.sigma = C.eta * C.omega;
+    C.pending = 0; C.wsum = 0.0; C.k = 0; C.accepted = 0; C.attempts = 0; C.restarts = 0;
+    C.status = kRunning; C.check_mode = 0; C.phi_prev = INFINITY;
+    *ctx->h_ctrl = C;
+    CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->started = false;
+    return PDCS_OK;
+}
+
+const char* pdcs_last_error(const pdcs_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void pdcs_destroy(pdcs_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+"""ctypes binding of the C ABI in ``include/pdcs.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libpdcs.so``; there is no
+fallback.  If the library has not been built, or no CUDA device is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpdcs.so")
+
+CONE_ZERO, CONE_NONNEG, CONE_SOC, CONE_RSOC, CONE_EXP = 0, 1, 2, 3, 4
+OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_DEVICE_TIMEOUT, MAX_ITER, TIME_LIMIT = 0, 1, 2, 3, 4, 5, 10, 11
+RESCALE_NONE, RESCALE_COORD, RESCALE_BLOCK = 0, 1, 2
+STEP_ADAPTIVE, STEP_CONSTANT, STEP_PLAIN = 0, 1, 2
+PRECISION_FP64, PRECISION_FP32 = 0, 1
+STATUS_NAMES = {0: "ok", 1: "invalid", 2: "cuda", 3: "oom", 4: "numeric", 5: "device_timeout", 10: "max_iter",
+                11: "time_limit"}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+class pdcs_csr(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", _i64p), ("col", _i32p), ("val", _dp)]
+
+
+class pdcs_cone(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("dim", ctypes.c_int64)]
+
+
+class pdcs_options(ctypes.Structure):
+    _fields_ = [("rescale", ctypes.c_int32), ("ruiz_iters", ctypes.c_int32), ("pock_chambolle", ctypes.c_int32),
+                ("step_mode", ctypes.c_int32), ("check_period", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("power_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("fp32_switch_tol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
+                ("spmv_lanes", ctypes.c_int32), ("time_limit", ctypes.c_double)]
+
+
+class pdcs_info(ctypes.Structure):
+    _fields_ = [("attempts", ctypes.c_int64), ("accepted", ctypes.c_int64), ("restarts", ctypes.c_int64),
+                ("err_p", ctypes.c_double), ("err_d", ctypes.c_double), ("err_gap", ctypes.c_double),
+                ("pobj", ctypes.c_double), ("dobj", ctypes.c_double), ("eta", ctypes.c_double),
+                ("omega", ctypes.c_double), ("setup_seconds", ctypes.c_double),
+                ("solve_seconds", ctypes.c_double), ("status", ctypes.c_int32), ("fp64_phase", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+# exported symbols and their signatures (kept in step with include/pdcs.h)
+SIGNATURES = {
+    "pdcs_default_options": (None, [ctypes.POINTER(pdcs_options)]),
+    "pdcs_create": (ctypes.c_int, [ctypes.POINTER(pdcs_csr), _dp, _dp, _dp, _dp, ctypes.POINTER(pdcs_cone),
+                                   ctypes.c_int64, ctypes.POINTER(pdcs_options), ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    "pdcs_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(pdcs_info)]),
+    "pdcs_get_solution": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp]),
+    "pdcs_get_iterate": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
+    "pdcs_get_scaling": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+    "pdcs_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pdcs_info)]),
+    "pdcs_set_warm_start": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_double]),
+    "pdcs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "pdcs_destroy": (None, [ctypes.c_void_p]),
+    "pdcs_proj_cones_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.POINTER(pdcs_cone), ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("CUDA library %s is missing: run paper_2505_00311_gb300.build.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+class PdcsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, t=_dp):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def pdcs_default_options(**kw):
+    o = pdcs_options()
+    lib().pdcs_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _cones(types, dims):
+    types = np.asarray(types)
+    dims = np.asarray(dims)
+    arr = (pdcs_cone * len(types))()
+    for i, (t, d) in enumerate(zip(types.tolist(), dims.tolist())):
+        arr[i].type = int(t)
+        arr[i].dim = int(d)
+    return arr
+
+
+def pdcs_last_error(ctx=None):
+    s = lib().pdcs_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def pdcs_create(prob, options=None, stream=None):
+    """Creates a solver for ``prob`` (dict with m, n, row_ptr, col, val, c, h, lb, ub,
+    cone_types, cone_dims; host arrays).  Returns the opaque context handle."""
+    rp = np.ascontiguousarray(prob["row_ptr"], dtype=np.int64)
+    ci = np.ascontiguousarray(prob["col"], dtype=np.int32)
+    val = _f64(prob["val"])
+    c = _f64(prob["c"])
+    h = _f64(prob["h"])
+    lb = None if prob.get("lb") is None else _f64(prob["lb"])
+    ub = None if prob.get("ub") is None else _f64(prob["ub"])
+    K = pdcs_csr(int(prob["m"]), int(prob["n"]), int(rp[-1]), _ptr(rp, _i64p), _ptr(ci, _i32p), _ptr(val))
+    cones = _cones(prob["cone_types"], prob["cone_dims"])
+    opt = options if options is not None else pdcs_default_options()
+    out = ctypes.c_void_p()
+    st = lib().pdcs_create(ctypes.byref(K), _ptr(c), _ptr(h), _ptr(lb), _ptr(ub), cones, len(cones),
+                           ctypes.byref(opt), stream, ctypes.byref(out))
+    if st != OK:
+        raise PdcsError(st, pdcs_last_error(None))
+    return out.value
+
+
+def pdcs_solve(ctx, tol, max_iter):
+    info = pdcs_info()
+    st = lib().pdcs_solve(ctx, float(tol), int(max_iter), ctypes.byref(info))
+    if st not in (OK, MAX_ITER, TIME_LIMIT):
+        raise PdcsError(st, pdcs_last_error(ctx))
+    return st, info.as_dict()
+
+
+def pdcs_get_solution(ctx, m, n, want_lambda=False):
+    x, y = np.empty(n), np.empty(m)
+    lam = np.empty(n) if want_lambda else None
+    st = lib().pdcs_get_solution(ctx, _ptr(x), _ptr(y), _ptr(lam))
+    if st != OK:
+        raise PdcsError(st, pdcs_last_error(ctx))
+    return (x, y, lam) if want_lambda else (x, y)
+
+
+def pdcs_get_iterate(ctx, m, n):
+    x, y, xh, yh = np.empty(n), np.empty(m), np.empty(n), np.empty(m)
+    st = lib().pdcs_get_iterate(ctx, _ptr(x), _ptr(y), _ptr(xh), _ptr(yh))
+    if st != OK:
+        raise PdcsError(st, pdcs_last_error(ctx))
+    return x, y, xh, yh
+
+
+def pdcs_get_scaling(ctx, m, n):
+    dr, dc = np.empty(m), np.empty(n)
+    st = lib().pdcs_get_scaling(ctx, _ptr(dr), _ptr(dc))
+    if st != OK:
+        raise PdcsError(st, pdcs_last_error(ctx))
+    return dr, dc
+
+
+def pdcs_get_info(ctx):
+    info = pdcs_info()
+    st = lib().pdcs_get_info(ctx, ctypes.byref(info))
+    if st != OK:
+        raise PdcsError(st, pdcs_last_error(ctx))
+    return info.as_dict()
+
+
+def pdcs_set_warm_start(ctx, x=None, y=None, omega=0.0):
+    xa = None if x is None else _f64(x)
+    ya = None if y is None else _f64(y)
+    st = lib().pdcs_set_warm_start(ctx, _ptr(xa), _ptr(ya), float(omega))
+    if st != OK:
+        raise PdcsError(st, pdcs_last_error(ctx))
+
+
+def pdcs_destroy(ctx):
+    if ctx:
+        lib().pdcs_destroy(ctx)
+
+
+def pdcs_proj_cones_device(v_ptr, d_ptr, m, types, dims, dual, out_ptr, stream=None):
+    """Device-pointer projection (pointers are integers, e.g. torch ``data_ptr()``)."""
+    cones = _cones(types, dims)
+    st = lib().pdcs_proj_cones_device(v_ptr, d_ptr, int(m), cones, len(cones), int(dual), out_ptr, stream)
+    if st != OK:
+        raise PdcsError(st, "pdcs_proj_cones_device failed")
+
+
+class Solver:
+    """Owning wrapper of one solver context."""
+
+    def __init__(self, prob, stream=None, **options):
+        self.m, self.n = int(prob["m"]), int(prob["n"])
+        self.options = pdcs_default_options(**options)
+        self.ctx = pdcs_create(prob, self.options, stream)
+
+    def solve(self, tol=1e-6, max_iter=1_000_000):
+        return pdcs_solve(self.ctx, tol, max_iter)
+
+    def run(self, attempts):
+        """Exactly ``attempts`` PDHG evaluations with termination off."""
+        return pdcs_solve(self.ctx, 0.0, attempts)
+
+    def solution(self, want_lambda=False):
+        return pdcs_get_solution(self.ctx, self.m, self.n, want_lambda)
+
+    def iterate(self):
+        return pdcs_get_iterate(self.ctx, self.m, self.n)
+
+    def scaling(self):
+        return pdcs_get_scaling(self.ctx, self.m, self.n)
+
+    def info(self):
+        return pdcs_get_info(self.ctx)
+
+    def warm_start(self, x=None, y=None, omega=0.0):
+        pdcs_set_warm_start(self.ctx, x, y, omega)
+
+    def close(self):
+        if self.ctx:
+            pdcs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,283 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Tolerances: projections 1e-12 relative to the block norm; iterates 1e-12
+relative (infinity norm) while both sides take the same discrete decisions
+(step acceptance, restarts); final solutions by the oracle's KKT evaluator.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_00311_gb300 import build as B
+from paper_2505_00311_gb300 import instances as I
+from paper_2505_00311_gb300 import pdcs as P
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    oracle.build()
+
+
+def rel_inf(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
+
+
+# ---------------------------------------------------------------------------
+# projections through pdcs_proj_cones_device
+# ---------------------------------------------------------------------------
+def _random_cones(rng, n_blocks):
+    types, dims = [], []
+    for _ in range(n_blocks):
+        t = int(rng.integers(0, 5))
+        d = {0: int(rng.integers(1, 5)), 1: int(rng.integers(1, 5)), 2: int(rng.integers(1, 70)),
+             3: int(rng.integers(2, 70)), 4: 3}[t]
+        types.append(t)
+        dims.append(d)
+    return np.array(types, np.int32), np.array(dims, np.int64)
+
+
+def _gpu_proj(v, d, types, dims, dual):
+    import torch
+    tv = torch.tensor(v, dtype=torch.float64, device="cuda")
+    td = None if d is None else torch.tensor(d, dtype=torch.float64, device="cuda")
+    to = torch.empty_like(tv)
+    P.pdcs_proj_cones_device(tv.data_ptr(), 0 if td is None else td.data_ptr(), v.size, types, dims, dual,
+                             to.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return to.cpu().numpy()
+
+
+@pytest.mark.parametrize("dual", [0, 1])
+@pytest.mark.parametrize("scaled", [False, True])
+def test_projection_parity(dual, scaled):
+    rng = np.random.default_rng(7 + dual + 2 * scaled)
+    types, dims = _random_cones(rng, 400)
+    m = int(dims.sum())
+    v = rng.standard_normal(m) * np.exp(rng.normal(0, 1.5, m))
+    d = np.exp(rng.normal(0, 1.0, m)) if scaled else None
+    if d is not None:  # RSOC blocks share the scale of their first two rows
+        o = 0
+        for t, k in zip(types, dims):
+            if t == 3:
+                d[o + 1] = d[o]
+            o += k
+    got = _gpu_proj(v, d, types, dims, dual)
+    ref = oracle.proj_cones(v, types, dims, d, dual=bool(dual))
+    o = 0
+    for t, k in zip(types, dims):
+        blk = slice(o, o + k)
+        scale = max(np.linalg.norm(v[blk]), 1e-300)
+        assert np.linalg.norm(got[blk] - ref[blk]) <= 1e-12 * scale, (t, k, got[blk], ref[blk])
+        o += k
+
+
+def test_exp_projection_stressed():
+    """Roots near the interval endpoints and rho beyond 709 (constructed Moreau pairs)."""
+    rows = []
+    for rho, sp, rd in [(120.0, 1e-40, 1.0), (300.0, 1e-120, 2.0), (-120.0, 1.0, 1e-40), (0.5, 1e-8, 1e-8),
+                        (3.0, 1.0, 1.0), (-3.0, 0.1, 10.0)]:
+        for d in [np.ones(3), np.array([0.3, 2.5, 1.7])]:
+            with np.errstate(over="ignore"):
+                vp = sp * np.array([d[0] * rho, d[1], d[2] * np.exp(rho)])
+                vd = rd * np.array([1 / d[0], (1 - rho) / d[1], -np.exp(-rho) / d[2]])
+            if np.all(np.isfinite(vp)) and np.all(np.isfinite(vd)):
+                rows.append((vp + vd, d, vp))
+    v = np.concatenate([r[0] for r in rows])
+    d = np.concatenate([r[1] for r in rows])
+    n = len(rows)
+    got = _gpu_proj(v, d, np.full(n, 4, np.int32), np.full(n, 3, np.int64), 0)
+    for k, (v0, _, vp) in enumerate(rows):
+        assert np.linalg.norm(got[3 * k:3 * k + 3] - vp) <= 1e-12 * np.linalg.norm(v0)
+
+
+# ---------------------------------------------------------------------------
+# solver parity
+# ---------------------------------------------------------------------------
+def _pair(prob, **opts):
+    g = P.Solver(prob, **opts)
+    o = oracle.Solver(prob, **{k: v for k, v in opts.items() if k in
+                               ("rescale", "ruiz_iters", "pock_chambolle", "step_mode", "check_period", "beta",
+                                "power_iters")})
+    return g, o
+
+
+def _compare_iterates(g, o, tol=RTOL):
+    gx, gy, gxh, gyh = g.iterate()
+    ox, oy, oxh, oyh = o.iterate()
+    return max(rel_inf(gx, ox), rel_inf(gy, oy), rel_inf(gxh, oxh), rel_inf(gyh, oyh))
+
+
+def test_scaling_parity():
+    p = I.small_socp(0)
+    for mode in [oracle.RESCALE_COORD, oracle.RESCALE_BLOCK, oracle.RESCALE_NONE]:
+        g, o = _pair(p, rescale=mode)
+        gdr, gdc = g.scaling()
+        odr, odc = o.scaling()
+        assert rel_inf(gdr, odr) <= 1e-13 and rel_inf(gdc, odc) <= 1e-13
+        g.close()
+
+
+# The adaptive step rule feeds the iterates back into eta through a ratio of
+# small quantities, so a rounding difference between the two sides grows by
+# about 10x every 10 evaluations (measured on these programs).  Per-iteration
+# parity is therefore checked on windows of 32 evaluations from a common state,
+# with checks every 16 evaluations so that restarts, averages and primal-weight
+# updates happen inside each window.
+WINDOW = [1, 2, 3, 5, 8, 10, 15, 16, 17, 20, 24, 31, 32]
+
+
+def _window(g, o, tol=RTOL):
+    done = 0
+    for target in WINDOW:
+        g.run(target - done)
+        o.run(target - done)
+        done = target
+        gs, os_ = g.info(), o.scalars()
+        assert gs["attempts"] == os_["attempts"]
+        assert gs["accepted"] == os_["accepted"] and gs["restarts"] == os_["restarts"], (target, gs, os_)
+        err = _compare_iterates(g, o)
+        assert err <= tol, (target, err)
+        assert abs(gs["eta"] - os_["eta"]) <= 1e-10 * os_["eta"]
+        assert abs(gs["omega"] - os_["omega"]) <= 1e-10 * os_["omega"]
+
+
+@pytest.mark.parametrize("prob_name", ["small_socp", "mixed_small"])
+def test_iteration_parity(prob_name):
+    p = I.small_socp(0) if prob_name == "small_socp" else I.scaled_mixed_cone(1, 0.01)
+    g, o = _pair(p, check_period=16)
+    _window(g, o)
+    g.close()
+
+
+@pytest.mark.parametrize("prob_name", ["small_socp", "mixed_small"])
+@pytest.mark.parametrize("start", [300, 2000])
+def test_iteration_parity_from_later_states(prob_name, start):
+    """Take the oracle's iterate after `start` evaluations as a common warm start."""
+    p = I.small_socp(0) if prob_name == "small_socp" else I.scaled_mixed_cone(1, 0.01)
+    ref = oracle.Solver(p)
+    ref.run(start)
+    x, y, _, _ = ref.iterate()
+    om = ref.scalars()["omega"]
+    g, o = _pair(p, check_period=16)
+    g.warm_start(x, y, om)
+    o.set_start(x, y, om)
+    _window(g, o)
+    g.close()
+
+
+@pytest.mark.parametrize("mode", [oracle.STEP_CONSTANT, oracle.STEP_PLAIN])
+def test_fixed_step_modes_parity(mode):
+    p = I.small_socp(0)
+    opts = dict(step_mode=mode)
+    if mode == oracle.STEP_PLAIN:
+        opts["rescale"] = oracle.RESCALE_NONE
+    g, o = _pair(p, **opts)
+    for k in [1, 7, 64, 130]:
+        g.run(k)
+        o.run(k)
+        assert _compare_iterates(g, o) <= 1e-11
+    g.close()
+
+
+def test_solve_small_socp_to_tolerance():
+    p = I.small_socp(0)
+    g = P.Solver(p)
+    st, info = g.solve(1e-6, 200_000)
+    assert st == P.OK
+    x, y = g.solution()
+    k = oracle.kkt(p, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1.01e-6
+    assert abs(k["pobj"] - p["obj_star"]) <= 1e-5 * (1 + abs(p["obj_star"]))
+    # the oracle needs about the same number of evaluations
+    o = oracle.Solver(p)
+    o.run(200_000, tol=1e-6)
+    assert abs(o.scalars()["attempts"] - info["attempts"]) <= 0.5 * info["attempts"] + 64
+    g.close()
+
+
+def test_solve_mixed_cones_to_tolerance():
+    p = I.scaled_mixed_cone(1, 0.01)
+    g = P.Solver(p)
+    st, info = g.solve(1e-6, 400_000)
+    assert st == P.OK, info
+    x, y, lam = g.solution(want_lambda=True)
+    k = oracle.kkt(p, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1.01e-6
+    assert abs(k["pobj"] - p["obj_star"]) <= 1e-5 * (1 + abs(p["obj_star"]))
+    from scipy.sparse import csr_matrix
+    K = csr_matrix((p["val"], p["col"], p["row_ptr"]), shape=(p["m"], p["n"]))
+    np.testing.assert_allclose(lam, p["c"] - K.T @ y, rtol=1e-9, atol=1e-9)
+    g.close()
+
+
+def test_warm_start_at_optimum_stops_at_first_check():
+    p = I.small_socp(0)
+    g = P.Solver(p)
+    g.warm_start(p["x_star"], p["y_star"])
+    st, info = g.solve(1e-6, 10_000)
+    assert st == P.OK and info["attempts"] <= 64
+    g.close()
+
+
+def test_edge_cases_rsoc_box_zero_rows_and_empty_rows():
+    """Rotated SOC blocks, finite boxes, free variables, zero rows and empty rows / columns."""
+    rng = np.random.default_rng(5)
+    m, n = 40, 30
+    rows = []
+    for i in range(m):
+        k = 0 if i % 7 == 3 else int(rng.integers(1, 6))       # some empty rows
+        cols = rng.choice(n - 2, size=k, replace=False)         # the last two columns stay empty
+        rows.append((np.sort(cols), rng.standard_normal(k)))
+    row_ptr = np.zeros(m + 1, np.int64)
+    row_ptr[1:] = np.cumsum([len(r[0]) for r in rows])
+    col = np.concatenate([r[0] for r in rows]).astype(np.int32)
+    val = np.concatenate([r[1] for r in rows])
+    types = np.array([P.CONE_ZERO, P.CONE_NONNEG, P.CONE_RSOC, P.CONE_SOC, P.CONE_EXP, P.CONE_RSOC], np.int32)
+    dims = np.array([5, 10, 6, 12, 3, 4], np.int64)
+    lb = np.where(rng.random(n) < 0.3, -np.inf, -rng.random(n))
+    ub = np.where(rng.random(n) < 0.3, np.inf, rng.random(n) + 0.5)
+    c = rng.standard_normal(n)
+    h = rng.standard_normal(m) * 0.1
+    prob = {"m": m, "n": n, "row_ptr": row_ptr, "col": col, "val": val, "c": c, "h": h, "lb": lb, "ub": ub,
+            "cone_types": types, "cone_dims": dims}
+    g, o = _pair(prob, check_period=16)
+    _window(g, o)
+    g.close()
+    g = P.Solver(prob)
+    st, info = g.solve(1e-6, 400_000)
+    assert st == P.OK, info
+    x, y = g.solution()
+    k = oracle.kkt(prob, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1.01e-6
+    assert np.all(x >= lb - 1e-12) and np.all(x <= ub + 1e-12)
+    g.close()
+
+
+def test_status_max_iter_and_repeat_calls():
+    p = I.small_socp(0)
+    g = P.Solver(p)
+    st, info = g.solve(1e-12, 100)
+    assert st == P.MAX_ITER and info["attempts"] == 100
+    st, info = g.solve(1e-12, 28)
+    assert st == P.MAX_ITER and info["attempts"] == 128
+    g.close()
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_graph_and_eager_paths_agree(graphs):
+    p = I.small_socp(0)
+    a = P.Solver(p, use_graphs=graphs)
+    b = P.Solver(p, use_graphs=1 - graphs)
+    a.run(256)
+    b.run(256)
+    xa, ya, _, _ = a.iterate()
+    xb, yb, _, _ = b.iterate()
+    np.testing.assert_array_equal(xa, xb)  # same kernels, deterministic reductions
+    np.testing.assert_array_equal(ya, yb)
+    a.close()
+    b.close()

@@ -221,6 +221,81 @@ def test_exp_roots_beyond_the_double_range():
             np.testing.assert_allclose(got, vp, rtol=0, atol=1e-12 * np.linalg.norm(v0))
 
 
+def _exp_case4_high_precision(v, d):
+    """Theorem 3 case 4 in high-precision arithmetic with the plain formulas of eqs. h_rho,
+    sp_rd and vpvd_defn: rho = anchor + dir e^L over (l_rho, u_rho) of eq. lrho_urho
+    (anchor a4 for r0 > 0, else a3), bisection on L from e^-1e6 up to the far end."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    r0, s0, t0 = [mp.mpf(float(x)) for x in v]
+    dr, ds, dt = [mp.mpf(float(x)) for x in d]
+    # offsets near an endpoint a can be as small as e^-|a|: carry enough digits to see them
+    span = max([abs(float(x)) for x in ([r0 * ds / (s0 * dr)] if s0 > 0 else []) +
+                ([1 - s0 * ds / (r0 * dr)] if r0 > 0 else [])] + [1.0])
+    mp.mp.dps = int(80 + 1.3 * span)
+    r0, s0, t0 = [mp.mpf(float(x)) for x in v]
+    dr, ds, dt = [mp.mpf(float(x)) for x in d]
+
+    def sp(rho):
+        return (s0 * ds / dr ** 2 - r0 * (1 - rho) / dr) / (ds ** 2 / dr ** 2 + rho * (rho - 1))
+
+    def rd(rho):
+        return (ds ** 2 / dr * (r0 - dr / ds * rho * s0)) / (ds ** 2 / dr ** 2 + rho * (rho - 1))
+
+    def h(rho):
+        return dt * mp.e ** rho * sp(rho) - mp.e ** (-rho) * rd(rho) / dt - t0
+
+    a3 = r0 * ds / (s0 * dr) if s0 > 0 else None
+    a4 = 1 - s0 * ds / (r0 * dr) if r0 > 0 else None
+    if r0 > 0:
+        anchor = a4
+        direction = mp.sign(a3 - a4) if s0 > 0 else 1
+    else:
+        anchor, direction = a3, -1
+    rho_of = lambda L: anchor + direction * mp.e ** L
+    if r0 > 0 and s0 > 0:
+        hiL = mp.log(abs(a3 - a4)) - mp.mpf(10) ** -100
+    else:
+        hiL = mp.mpf(0)
+        s_anchor = -1 if r0 > 0 else 1
+        while mp.sign(h(rho_of(hiL))) == s_anchor:
+            hiL = 2 * hiL + 1
+    loL = -mp.mpf(10) ** 6
+    s_lo = mp.sign(h(rho_of(loL)))
+    for _ in range(200 + 4 * mp.mp.dps):
+        mid = (loL + hiL) / 2
+        if mp.sign(h(rho_of(mid))) == s_lo:
+            loL = mid
+        else:
+            hiL = mid
+    rho = rho_of((loL + hiL) / 2)
+    return np.array([float(dr * rho * sp(rho)), float(ds * sp(rho)), float(dt * mp.e ** rho * sp(rho))])
+
+
+def test_exp_case4_matches_high_precision():
+    rng = np.random.default_rng(2024)
+    # an input where rho - 1 must come from the exact offset (a4 = 1, d_s / d_r tiny); the
+    # a4 ~ 1e11 regime is beyond any fixed precision and is pinned by constructed pairs above
+    for v, d in [([0.02731252431406897, 0.0, -0.006247328838628032],
+                  [14.790590072821251, 0.031791605882595476, 3.73337953357554])]:
+        v, d = np.array(v), np.array(d)
+        assert np.linalg.norm(oracle.proj_exp(v, d) - _exp_case4_high_precision(v, d)) <= 1e-12 * np.linalg.norm(v)
+    n = 0
+    while n < 60:
+        v = rng.standard_normal(3) * np.exp(rng.normal(0, 1.0))
+        d = np.exp(rng.normal(0, 1.5, 3))
+        if n % 4 == 1:
+            v[1] = 0.0   # a4 = 1 exactly
+        if n % 4 == 2:
+            v[0] = 0.0   # a3 = 0 exactly
+        got = oracle.proj_exp(v, d)
+        if np.array_equal(got, v) or not np.any(got) or (v[0] <= 0 and v[1] <= 0):
+            continue     # cases 1-3
+        ref = _exp_case4_high_precision(v, d)
+        assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(v), (v, d, got, ref)
+        n += 1
+
+
 def test_exp_certificate_extreme_magnitudes():
     """Moreau certificates with entries spread over many orders of magnitude."""
     rng = np.random.default_rng(99)
