@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark: PDHG iterations per second of the restarted primal-dual conic solver.
+
+Workload (default): the large mixed-cone LP/SOCP/exp program, n = 1,000,000
+variables, m = 500,000 rows, ~10M nonzeros (log-normal row degrees 2-200, N(0,1)
+values), 200k nonnegative rows, SOC blocks of dimension 4-64 filling 200k rows,
+20k exponential cones, 40k zero rows, known optimum; FP64.  A step is one check
+period: 64 PDHG evaluations (primal update, K xhat, dual update + cone
+projection, K' yhat) plus one restart / termination check, replayed as one CUDA
+graph.  The working set (K, K' and ~15 state vectors, ~0.5 GB) is larger than
+the 129 MB L2, so no flush is needed between steps.
+
+One JSON line is printed by rank 0.  Under torchrun each rank runs an
+independent replica (the method has no data-path exchange on one instance).
+``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EVALS_PER_STEP = 64
+METRIC = "PDHG iters/sec"
+WORKLOADS = {
+    "mixed_cone_1m": "mixed-cone LP/SOCP/exp, n=1,000,000, m=500,000, ~10M nnz, 200k nonneg rows, "
+                     "SOC(4-64) on 200k rows, 20k exp cones, 40k zero rows, known optimum, seed 1",
+    "small_socp": "random sparse SOCP, n=2,000, m=1,000, 20k nnz, 500 nonneg rows + 50 SOC(10), seed 0",
+}
+
+
+def make_workload(name):
+    from paper_2505_00311_gb300 import instances as I
+    if name == "mixed_cone_1m":
+        return I.mixed_cone(1)
+    if name == "small_socp":
+        return I.small_socp(0)
+    raise SystemExit("unknown workload " + name)
+
+
+def problem_bytes(p):
+    return (p["row_ptr"].size * 8 + p["col"].size * 4 + p["val"].size * 8 + p["c"].size * 8 + p["h"].size * 8
+            + len(p["cone_types"]) * 16)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline of the dominant kernel
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(p):
+    """Bytes one launch of each kernel class must move at least (FP64 values, int32 indices),
+    counting each gathered vector once (it stays in L2)."""
+    m, n, nnz = p["m"], p["n"], int(p["row_ptr"][-1])
+    types = np.asarray(p["cone_types"])
+    dims = np.asarray(p["cone_dims"])
+    cone_rows = int(dims[(types == 2) | (types == 3) | (types == 4)].sum())
+    return {
+        # val + col per nonzero, row_ptr, the gathered input once, the output
+        "spmv_K": nnz * 12 + (m + 1) * 4 + n * 8 + m * 8,
+        "spmv_KT": nnz * 12 + (n + 1) * 4 + m * 8 + n * 8,
+        # reads x, xhat, x0, K'y, K'yhat, K'y0, xsum, c, l, u; writes x, K'y, xsum, xhat
+        "primal_update": n * 14 * 8,
+        # reads y, yhat, y0, Kx, K xhat (both buffers), Kx0, ysum, h; writes y, Kx, ysum, yhat;
+        # plus the row scales of the SOC / exp rows
+        "dual_update": m * 13 * 8 + cone_rows * 8,
+    }
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2505_00311_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != source_hash():
+        return None
+    return rec.get("bytes_per_launch", {}).get(kernel)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def cpu_baseline(p, budget_s=15.0, steps=None):
+    import oracle
+    o = oracle.Solver(p)
+    t0 = time.perf_counter()
+    o.run(1)
+    one = time.perf_counter() - t0
+    n = steps if steps else max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    o.run(n)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": "%d PDHG evaluations of the FP64 oracle (single thread) after setup and one "
+                      "evaluation, same workload" % n, "seconds": dt}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pdcs", choices=["pdcs", "reference"])
+    ap.add_argument("--workload", default="mixed_cone_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-to-tol", default="1e-4,1e-6",
+                    help="comma list of tolerances for the time-to-solution runs ('' to skip)")
+    ap.add_argument("--ttt-limit", type=float, default=120.0, help="seconds allowed per time-to-tolerance run")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        p = make_workload(args.workload)
+        steps = max(1, args.steps)
+        cb = cpu_baseline(p, steps=steps + args.warmup)
+        line = {"metric": METRIC, "value": cb["value"], "unit": "iters/s", "n_gpus": args.gpus, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * EVALS_PER_STEP / cb["value"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOADS[args.workload], "step": "one PDHG evaluation on the CPU"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_2505_00311_gb300 import build as B
+    from paper_2505_00311_gb300 import pdcs as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    p = make_workload(args.workload)
+    stream = torch.cuda.Stream()
+    solver = P.Solver(p, stream=stream.cuda_stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up (also captures the CUDA graph)
+    for _ in range(args.warmup):
+        solver.run(EVALS_PER_STEP)
+    # per-kernel durations (CUDA events on the solver's stream), one check period
+    ktimes, kcounts = solver.kernel_times(EVALS_PER_STEP)
+    info0 = solver.info()
+
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        solver.run(EVALS_PER_STEP)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    info1 = solver.info()
+    launches = info1["kernel_launches"] - info0["kernel_launches"]
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    evals = args.steps * EVALS_PER_STEP
+    value = world * evals / (ms / 1000.0)
+    solver.close()
+
+    # end to end through the public API with host buffers: create (H2D + setup),
+    # the same number of evaluations, solution read back (D2H)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2 = P.Solver(p, stream=stream.cuda_stream)
+    s2.run(evals)
+    x, y = s2.solution()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s2.close()
+    e2e = {"value": evals / e2e_s, "unit": "iters/s",
+           "h2d_bytes_per_step": int(problem_bytes(p) / args.steps),
+           "d2h_bytes_per_step": int((x.size + y.size) * 8 / args.steps),
+           "includes": "pdcs_create from host arrays (copy + rescaling + K' build) + pdcs_solve + "
+                       "pdcs_get_solution"}
+
+    # time to tolerance (separate runs, wall clock of pdcs_solve)
+    ttt = []
+    if args.time_to_tol:
+        for tol in [float(t) for t in args.time_to_tol.split(",") if t]:
+            s3 = P.Solver(p, stream=stream.cuda_stream, time_limit=args.ttt_limit)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, inf = s3.solve(tol, 2_000_000)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            ttt.append({"tol": tol, "seconds": dt, "status": P.STATUS_NAMES.get(st, st),
+                        "evaluations": inf["attempts"], "restarts": inf["restarts"],
+                        "err": [inf["err_p"], inf["err_d"], inf["err_gap"]],
+                        "setup_seconds": inf["setup_seconds"]})
+            s3.close()
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel
+    alg = algorithmic_bytes(p)
+    per_step_ms = {k: ktimes[k] * kcounts[k] / 1.0 for k in alg}
+    dom = max(alg, key=lambda k: per_step_ms[k])
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    achieved = alg[dom] / (ktimes[dom] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if peak else None, "traffic": ncu_traffic(dom),
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak else "unavailable",
+            "algorithmic_bytes_per_launch": alg[dom], "ms_per_launch": ktimes[dom],
+            "kernels": {k: {"ms_per_launch": ktimes[k], "launches_per_step": kcounts[k],
+                            "GBps": (alg[k] / (ktimes[k] * 1e-3) / 1e9) if k in alg and ktimes[k] > 0 else None}
+                        for k in ktimes}}
+    cb = None
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(p)
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "step": "64 PDHG evaluations + 1 restart check",
+                       "precision": "fp64", "l2": "working set > L2 (no flush needed)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clk, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+            "time_to_tol": ttt}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

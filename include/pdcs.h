@@ -99,6 +99,7 @@ typedef struct {
     double solve_seconds;         /* time spent in pdcs_solve calls so far */
     int32_t status;               /* pdcs_status of the last pdcs_solve */
     int32_t fp64_phase;           /* 1 once FP32 mode has switched to FP64 polishing */
+    int64_t kernel_launches;      /* kernels this context has launched so far (graph nodes included) */
 } pdcs_info;
 
 typedef struct pdcs_ctx pdcs_ctx;
@@ -142,6 +143,16 @@ pdcs_status pdcs_get_info(pdcs_ctx* ctx, pdcs_info* info);
 /* Sets the starting point z^{0,0} = (x, y) (original scaling; NULL means 0) and,
  * when omega > 0, the initial primal weight; resets the counters. */
 pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y, double omega);
+
+/* Kernel timing for roofline measurements: runs `attempts` more PDHG evaluations
+ * (and the checks that fall due) launch by launch, with CUDA events recorded on
+ * the context's stream around every kernel, and writes the average duration in
+ * milliseconds per launch of each kernel class to ms[0..4]:
+ *   [0] primal update, [1] K xhat product, [2] dual update + cone projection,
+ *   [3] K' yhat product, [4] one whole restart / termination check;
+ * counts[0..4] (may be NULL) receive the number of launches timed per class.
+ * The iterate state advances exactly as in pdcs_solve with tol <= 0. */
+pdcs_status pdcs_kernel_times(pdcs_ctx* ctx, int64_t attempts, double* ms, int64_t* counts);
 
 /* Text of the last error of ctx (or of the last failed pdcs_create when ctx is NULL). */
 const char* pdcs_last_error(const pdcs_ctx* ctx);

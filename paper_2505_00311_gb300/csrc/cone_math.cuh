@@ -109,8 +109,14 @@ __device__ int soc_project_warp(double* buf, const double* __restrict__ d, int d
             int s = g > 0.0 ? 1 : -1;
             if (s == slo) lo = lam; else hi = lam;
             double nl = lam - g / dg;
+            // a Newton step below 1e-10 relative leaves an error of order its square
+            // (lam itself has just become an end of the bracket, so test this first)
+            if (nl >= lo && nl <= hi && fabs(nl - lam) <= 1e-10 * lam) {
+                lam = nl;
+                break;
+            }
             if (!(nl > lo && nl < hi)) nl = 0.5 * (lo + hi);
-            bool done = fabs(nl - lam) <= 2e-16 * fabs(nl) || !(nl > lo && nl < hi) || (hi - lo) <= 2e-16 * hi;
+            const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 4e-16 * hi;
             lam = nl;
             if (done) break;
         }
@@ -223,15 +229,26 @@ __host__ __device__ __forceinline__ void exp_F(const ExpCase4& e, double L, doub
     const double B = -e.ldt - rho + lrd;
     const double dA = e.dir * delta + dlst - dldt;
     const double dB = -e.dir * delta + dlrt - dldt;
+    // log(e^a + e^b) = max + log1p(q), q = e^(min - max); the weight e^(a - lse) of a
+    // comes from the same q, so each evaluation needs one exp and one log1p here
+    auto lse_w = [](double a, double b, double& wa) {
+        if (a == -INFINITY) { wa = 0.0; return b; }
+        if (b == -INFINITY) { wa = 1.0; return a; }
+        const bool amax = a >= b;
+        const double q = exp(amax ? b - a : a - b);
+        wa = amax ? 1.0 / (1.0 + q) : q / (1.0 + q);
+        return (amax ? a : b) + log1p(q);
+    };
     if (e.t0 >= 0.0) {
-        const double rhs = e.t0 > 0.0 ? lse2(B, e.lt0) : B;
+        double wB = 1.0;
+        const double rhs = e.t0 > 0.0 ? lse_w(B, e.lt0, wB) : B;
+        if (B == -INFINITY) wB = 0.0;
         F = A - rhs;
-        const double wB = (B == -INFINITY) ? 0.0 : exp(B - rhs);
         dF = dA - wB * dB;
     } else {
-        const double lhs = lse2(A, e.lt0);
+        double wA;
+        const double lhs = lse_w(A, e.lt0, wA);
         F = lhs - B;
-        const double wA = (A == -INFINITY) ? 0.0 : exp(A - lhs);
         dF = wA * dA - dB;
     }
     rho_out = rho;
@@ -271,8 +288,14 @@ __host__ __device__ __forceinline__ double exp_newton(const ExpCase4& e, double 
         const int s = F > 0.0 ? 1 : -1;
         if (s == slo) lo = L; else hi = L;
         double nl = L - F / dF;
-        if (!(nl > lo && nl < hi)) nl = 0.5 * (lo + hi);
-        const bool done = fabs(nl - L) <= 4e-16 * fmax(1.0, fabs(nl)) || !(nl > lo && nl < hi);
+        // a Newton step below 1e-10 relative leaves an error of order its square
+        // (L itself has just become an end of the bracket, so test this first)
+        if (nl >= lo && nl <= hi && fabs(nl - L) <= 1e-10 * fmax(1.0, fabs(L))) {
+            L = nl;
+            break;
+        }
+        if (!(nl > lo && nl < hi)) nl = (lo == -INFINITY) ? hi - 2.0 * fmax(1.0, fabs(hi - L)) : 0.5 * (lo + hi);
+        const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 4e-16 * fmax(1.0, fabs(hi));
         L = nl;
         if (done) break;
     }

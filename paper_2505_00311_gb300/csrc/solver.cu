@@ -90,6 +90,7 @@ struct pdcs_ctx {
     bool started = false;
     double setup_seconds = 0.0, solve_seconds = 0.0;
     double norm2 = 0.0;
+    long long launches = 0;
     int last_status = PDCS_OK;
 
     ~pdcs_ctx() {
@@ -141,21 +142,44 @@ int choose_lanes(long long nnz, long long rows) {
     return std::min(32, std::max(2, g));
 }
 
+// Optional CUDA-event recorder for kernel timing: event pairs per kernel class.
+struct Prof {
+    std::vector<cudaEvent_t> ev[5];
+    void mark(int cls, cudaStream_t s) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) == cudaSuccess) {
+            cudaEventRecord(e, s);
+            ev[cls].push_back(e);
+        }
+    }
+};
+
+constexpr int kLaunchesPerAttempt = 4;
+constexpr int kLaunchesPerCheck = 12;
+
 // one PDHG evaluation
-void enqueue_attempt(pdcs_ctx* ctx) {
+void enqueue_attempt(pdcs_ctx* ctx, Prof* P = nullptr) {
     cudaStream_t s = ctx->stream;
     Dev<double>& D = ctx->D;
+    if (P) P->mark(0, s);
     primal_update<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
+    if (P) { P->mark(0, s); P->mark(1, s); }
     launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, ctx->m, D.rp, D.ci, D.val, D.xh, D.kxh0, D.kxh1, D.ctrl, 1, 1);
+    if (P) { P->mark(1, s); P->mark(2, s); }
     dual_update<double><<<ctx->g_dual, kBlock, 0, s>>>(D);
+    if (P) { P->mark(2, s); P->mark(3, s); }
     launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, ctx->n, D.rpT, D.ciT, D.valT, D.yh, D.ktyh, nullptr,
                                 D.ctrl, 0, 2);
+    if (P) P->mark(3, s);
+    ctx->launches += kLaunchesPerAttempt;
 }
 
 // restart / termination check (or the initial evaluation of the anchor)
-void enqueue_check(pdcs_ctx* ctx) {
+void enqueue_check(pdcs_ctx* ctx, Prof* P = nullptr) {
     cudaStream_t s = ctx->stream;
     Dev<double>& D = ctx->D;
+    if (P) P->mark(4, s);
+    ctx->launches += kLaunchesPerCheck;
     flush_primal<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
     flush_dual<double><<<ctx->g_vec_m, kBlock, 0, s>>>(D);
     cand_primal<double><<<dim3(ctx->g_vec_n, 2), kBlock, 0, s>>>(D);
@@ -170,6 +194,7 @@ void enqueue_check(pdcs_ctx* ctx) {
     kkt_dual<double><<<ctx->g_kktd, kBlock, 0, s>>>(D);
     restart_primal<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
     restart_dual<double><<<ctx->g_vec_m, kBlock, 0, s>>>(D);
+    if (P) P->mark(4, s);
 }
 
 __global__ void clear_pending(Ctrl* C) { C->pending = 0; }
@@ -504,6 +529,7 @@ void fill_info(pdcs_ctx* ctx, pdcs_info* info) {
     info->solve_seconds = ctx->solve_seconds;
     info->status = ctx->last_status;
     info->fp64_phase = 1;
+    info->kernel_launches = ctx->launches;
 }
 
 }  // namespace
@@ -642,6 +668,7 @@ pdcs_status pdcs_solve(pdcs_ctx* ctx, double tol, int64_t max_iter, pdcs_info* i
         if (remaining >= to_b) {
             if (to_b == period && ctx->graph) {
                 CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+                ctx->launches += (long long)period * kLaunchesPerAttempt + kLaunchesPerCheck;
             } else {
                 for (long long a = 0; a < to_b; ++a) enqueue_attempt(ctx);
                 enqueue_check(ctx);
@@ -711,6 +738,7 @@ pdcs_status pdcs_get_iterate(pdcs_ctx* ctx, double* x, double* y, double* xhat, 
     flush_primal<double><<<ctx->g_vec_n, kBlock, 0, ctx->stream>>>(ctx->D);
     flush_dual<double><<<ctx->g_vec_m, kBlock, 0, ctx->stream>>>(ctx->D);
     clear_pending<<<1, 1, 0, ctx->stream>>>(ctx->ctrl);
+    ctx->launches += 3;
     CK(cudaGetLastError());
     pdcs_status st = unscale_out(ctx, ctx->D.x, ctx->D.y, x, y);
     if (st != PDCS_OK) return st;
@@ -772,6 +800,41 @@ pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y,
     CK(cudaStreamSynchronize(s));
     ctx->started = false;
     return PDCS_OK;
+}
+
+pdcs_status pdcs_kernel_times(pdcs_ctx* ctx, int64_t attempts, double* ms, int64_t* counts) {
+    if (!ctx || !ms || attempts < 1) return PDCS_ERR_INVALID;
+    pdcs_status st = read_ctrl(ctx);
+    if (st != PDCS_OK) return st;
+    if (!ctx->started) {
+        const int one = 1;
+        CK(cudaMemcpyAsync(&ctx->ctrl->check_mode, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        enqueue_check(ctx);
+        ctx->started = true;
+    }
+    const double zero = 0.0;
+    CK(cudaMemcpyAsync(&ctx->ctrl->tol, &zero, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    Prof P;
+    long long done = ctx->h_ctrl->attempts;
+    for (int64_t a = 0; a < attempts; ++a) {
+        enqueue_attempt(ctx, &P);
+        ++done;
+        if (done % ctx->opt.check_period == 0) enqueue_check(ctx, &P);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < 5; ++c) {
+        double tot = 0.0;
+        const size_t pairs = P.ev[c].size() / 2;
+        for (size_t i = 0; i < pairs; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, P.ev[c][2 * i], P.ev[c][2 * i + 1]) == cudaSuccess) tot += t;
+        }
+        ms[c] = pairs ? tot / (double)pairs : 0.0;
+        if (counts) counts[c] = (int64_t)pairs;
+        for (cudaEvent_t e : P.ev[c]) cudaEventDestroy(e);
+    }
+    return read_ctrl(ctx);
 }
 
 const char* pdcs_last_error(const pdcs_ctx* ctx) {

@@ -79,14 +79,34 @@ def _exp_pair(rng):
     return np.zeros(3), np.array([r, s_, t])
 
 
-def _finish(rng, m, n, row_ptr, cols, vals, cone_types, cone_dims, name):
-    """Draw (x*, lambda*, s*, y*) and set c, h so that (x*, y*) is optimal."""
-    K = sp.csr_matrix((vals, cols, row_ptr), shape=(m, n))
+def _primal_pair(rng, n, lb, ub):
+    """x* in [l, u] and lambda* in Lambda (eq. defn_Lambda1) with l'lam^+ - u'lam^- = lam'x*."""
     x = np.zeros(n)
     lam = np.zeros(n)
-    pos = rng.random(n) < 0.5
-    x[pos] = rng.uniform(0.1, 1.0, int(pos.sum()))
-    lam[~pos] = rng.uniform(0.1, 1.0, int((~pos).sum()))
+    if lb is None and ub is None:
+        pos = rng.random(n) < 0.5
+        x[pos] = rng.uniform(0.1, 1.0, int(pos.sum()))
+        lam[~pos] = rng.uniform(0.1, 1.0, int((~pos).sum()))
+        return x, lam
+    for j in range(n):
+        lf, uf = np.isfinite(lb[j]), np.isfinite(ub[j])
+        opts = ["in"] + (["lo"] if lf else []) + (["up"] if uf else [])
+        k = opts[rng.integers(0, len(opts))]
+        if k == "lo":
+            x[j], lam[j] = lb[j], rng.uniform(0.1, 1.0)
+        elif k == "up":
+            x[j], lam[j] = ub[j], -rng.uniform(0.1, 1.0)
+        else:
+            a = lb[j] if lf else (ub[j] - 2.0 if uf else -1.0)
+            b = ub[j] if uf else a + 2.0
+            x[j] = a + (b - a) * rng.uniform(0.2, 0.8)
+    return x, lam
+
+
+def _finish(rng, m, n, row_ptr, cols, vals, cone_types, cone_dims, name, lb=None, ub=None):
+    """Draw (x*, lambda*, s*, y*) and set c, h so that (x*, y*) is optimal."""
+    K = sp.csr_matrix((vals, cols, row_ptr), shape=(m, n))
+    x, lam = _primal_pair(rng, n, lb, ub)
     s = np.zeros(m)
     y = np.zeros(m)
     o = 0
@@ -103,6 +123,12 @@ def _finish(rng, m, n, row_ptr, cols, vals, cone_types, cone_dims, name):
                 s[o] = rng.uniform(0.1, 1.0)
             else:
                 s[o:o + d], y[o:o + d] = _soc_pair(rng, d)
+        elif t == RSOC:  # K_rsoc = Q K_soc, Q = [[1, 1], [1, -1]] / sqrt2 (+) I, orthogonal
+            ss, yy = _soc_pair(rng, d)
+            for v in (ss, yy):
+                a, b = v[0], v[1]
+                v[0], v[1] = (a + b) / np.sqrt(2.0), (a - b) / np.sqrt(2.0)
+            s[o:o + d], y[o:o + d] = ss, yy
         elif t == EXP:
             s[o:o + 3], y[o:o + 3] = _exp_pair(rng)
         else:
@@ -112,7 +138,7 @@ def _finish(rng, m, n, row_ptr, cols, vals, cone_types, cone_dims, name):
     h = K @ x - s
     return {
         "name": name, "m": m, "n": n, "row_ptr": row_ptr, "col": cols, "val": vals,
-        "c": c, "h": h, "lb": None, "ub": None,
+        "c": c, "h": h, "lb": lb, "ub": ub,
         "cone_types": np.asarray(cone_types, dtype=np.int32),
         "cone_dims": np.asarray(cone_dims, dtype=np.int64),
         "x_star": x, "y_star": y, "s_star": s, "lambda_star": lam, "obj_star": float(c @ x),
@@ -179,3 +205,21 @@ def scaled_mixed_cone(seed: int = 1, scale: float = 0.01):
     return mixed_cone(seed=seed, n=n, m=m, nnz=int(10_000_000 * scale),
                       n_nonneg=int(200_000 * scale), soc_rows=int(200_000 * scale),
                       n_exp=int(20_000 * scale), scalar_chunk=max(1, int(1000 * scale)))
+
+
+def edge_cases(seed: int = 5, m: int = 40, n: int = 30):
+    """Small program with every cone kind (zero, nonneg, RSOC, SOC, exp), empty rows,
+    two empty columns, finite boxes, one-sided bounds and free variables; known optimum."""
+    rng = np.random.default_rng(seed)
+    degs = [0 if i % 7 == 3 else int(rng.integers(1, 6)) for i in range(m)]
+    row_ptr = np.zeros(m + 1, np.int64)
+    row_ptr[1:] = np.cumsum(degs)
+    cols = np.concatenate([np.sort(rng.choice(n - 2, size=k, replace=False)) for k in degs]).astype(np.int32)
+    vals = rng.standard_normal(int(row_ptr[-1]))
+    types = [ZERO, NONNEG, RSOC, SOC, EXP, RSOC]
+    dims = [5, 10, 6, 12, 3, 4]
+    assert sum(dims) == m
+    kind = rng.integers(0, 4, n)  # 0 box, 1 lower only, 2 upper only, 3 free
+    lb = np.where((kind == 0) | (kind == 1), -rng.uniform(0.0, 1.0, n), -np.inf)
+    ub = np.where((kind == 0) | (kind == 2), rng.uniform(0.5, 1.5, n), np.inf)
+    return _finish(rng, m, n, row_ptr, cols, vals, types, dims, "edge_cases", lb=lb, ub=ub)

@@ -50,7 +50,8 @@ class pdcs_info(ctypes.Structure):
                 ("err_p", ctypes.c_double), ("err_d", ctypes.c_double), ("err_gap", ctypes.c_double),
                 ("pobj", ctypes.c_double), ("dobj", ctypes.c_double), ("eta", ctypes.c_double),
                 ("omega", ctypes.c_double), ("setup_seconds", ctypes.c_double),
-                ("solve_seconds", ctypes.c_double), ("status", ctypes.c_int32), ("fp64_phase", ctypes.c_int32)]
+                ("solve_seconds", ctypes.c_double), ("status", ctypes.c_int32), ("fp64_phase", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,6 +72,7 @@ SIGNATURES = {
     "pdcs_get_scaling": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     "pdcs_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pdcs_info)]),
     "pdcs_set_warm_start": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_double]),
+    "pdcs_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _dp, _i64p]),
     "pdcs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "pdcs_destroy": (None, [ctypes.c_void_p]),
     "pdcs_proj_cones_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -204,6 +206,19 @@ def pdcs_set_warm_start(ctx, x=None, y=None, omega=0.0):
         raise PdcsError(st, pdcs_last_error(ctx))
 
 
+KERNEL_CLASSES = ["primal_update", "spmv_K", "dual_update", "spmv_KT", "check"]
+
+
+def pdcs_kernel_times(ctx, attempts):
+    """Average ms per launch of each kernel class over `attempts` evaluations (CUDA events)."""
+    ms = np.zeros(5)
+    cnt = np.zeros(5, dtype=np.int64)
+    st = lib().pdcs_kernel_times(ctx, int(attempts), _ptr(ms), _ptr(cnt, _i64p))
+    if st != OK:
+        raise PdcsError(st, pdcs_last_error(ctx))
+    return dict(zip(KERNEL_CLASSES, ms.tolist())), dict(zip(KERNEL_CLASSES, cnt.tolist()))
+
+
 def pdcs_destroy(ctx):
     if ctx:
         lib().pdcs_destroy(ctx)
@@ -243,6 +258,9 @@ class Solver:
 
     def info(self):
         return pdcs_get_info(self.ctx)
+
+    def kernel_times(self, attempts):
+        return pdcs_kernel_times(self.ctx, attempts)
 
     def warm_start(self, x=None, y=None, omega=0.0):
         pdcs_set_warm_start(self.ctx, x, y, omega)
