@@ -170,6 +170,32 @@ void pdcs_destroy(pdcs_ctx* ctx);
 pdcs_status pdcs_proj_cones_device(const double* v, const double* d, int64_t m, const pdcs_cone* cones,
                                    int64_t n_cones, int32_t dual, double* out, void* cuda_stream);
 
+/* Largest cone list pdcs_proj_cones_device_noalloc accepts. */
+#define PDCS_NOALLOC_MAX_CONES 262144
+
+/* The same projection as pdcs_proj_cones_device, for callers that cannot allocate
+ * device memory: code that runs inside a framework whose allocator owns the whole
+ * device (a memory pool sized up front, where a foreign cudaMalloc would fail or
+ * fragment the pool), or latency-critical loops that must not pay for an
+ * allocation and its implicit synchronisation.  There is no counterpart in the
+ * paper; this is a library convenience.
+ *   - Scratch: the cone list and one 64-bit row offset per cone are kept in a
+ *     file-scope device array of PDCS_NOALLOC_MAX_CONES entries (6 MiB), which every
+ *     GPU that loads the library holds until the process exits.  The call performs
+ *     no cudaMalloc, cudaFree or other allocating routine.
+ *   - The first call on a device looks up that array's device address (once per
+ *     device, with the device current); make this first call before any stream
+ *     capture.
+ *   - The array is shared by all calls and keeps the last call's contents; every
+ *     entry a call reads is written by the same call first.  Calls that overlap on
+ *     the GPU (different streams, no ordering between them) race on it.
+ *   - Arguments and layout as pdcs_proj_cones_device: v, d (may be NULL), out are
+ *     DEVICE pointers, cones a HOST array that must stay unchanged until the queued
+ *     work has run.  Returns PDCS_ERR_INVALID for a malformed cone list or
+ *     n_cones > PDCS_NOALLOC_MAX_CONES, PDCS_ERR_CUDA if a CUDA call fails. */
+pdcs_status pdcs_proj_cones_device_noalloc(const double* v, const double* d, int64_t m, const pdcs_cone* cones,
+                                           int64_t n_cones, int32_t dual, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,7 +78,11 @@ SIGNATURES = {
     "pdcs_proj_cones_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                               ctypes.POINTER(pdcs_cone), ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_void_p, ctypes.c_void_p]),
+    "pdcs_proj_cones_device_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                      ctypes.POINTER(pdcs_cone), ctypes.c_int64, ctypes.c_int32,
+                                                      ctypes.c_void_p, ctypes.c_void_p]),
 }
+NOALLOC_MAX_CONES = 262144
 
 
 def lib():
@@ -230,6 +234,13 @@ def pdcs_proj_cones_device(v_ptr, d_ptr, m, types, dims, dual, out_ptr, stream=N
     st = lib().pdcs_proj_cones_device(v_ptr, d_ptr, int(m), cones, len(cones), int(dual), out_ptr, stream)
     if st != OK:
         raise PdcsError(st, "pdcs_proj_cones_device failed")
+
+
+def pdcs_proj_cones_device_noalloc(v_ptr, d_ptr, m, types, dims, dual, out_ptr, stream=None):
+    """As pdcs_proj_cones_device, without any device allocation (scratch in a fixed
+    device array of NOALLOC_MAX_CONES cones); returns the pdcs_status code."""
+    cones = _cones(types, dims)
+    return lib().pdcs_proj_cones_device_noalloc(v_ptr, d_ptr, int(m), cones, len(cones), int(dual), out_ptr, stream)
 
 
 class Solver:
