@@ -147,10 +147,13 @@ pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y,
 /* Kernel timing for roofline measurements: runs `attempts` more PDHG evaluations
  * (and the checks that fall due) launch by launch, with CUDA events recorded on
  * the context's stream around every kernel, and writes the average duration in
- * milliseconds per launch of each kernel class to ms[0..4]:
+ * milliseconds per launch of each kernel class to ms[0..11]:
  *   [0] primal update, [1] K xhat product, [2] dual update + cone projection,
- *   [3] K' yhat product, [4] one whole restart / termination check;
- * counts[0..4] (may be NULL) receive the number of launches timed per class.
+ *   [3] K' yhat product, [4] one whole restart / termination check, and inside a
+ *   check: [5] flush of the pending Halpern update, [6] primal candidates,
+ *   [7] dual candidates (cone projections), [8] the four candidate products,
+ *   [9] primal-side KKT, [10] dual-side KKT and the controller, [11] restart copy;
+ * counts[0..11] (may be NULL) receive the number of launches timed per class.
  * The iterate state advances exactly as in pdcs_solve with tol <= 0. */
 pdcs_status pdcs_kernel_times(pdcs_ctx* ctx, int64_t attempts, double* ms, int64_t* counts);
 

@@ -1,0 +1,211 @@
+// cone_f32.cuh -- FP32 cone projections for the FP32-iterate mode.
+//
+// Same case analysis as cone_math.cuh (Theorem 1 for SOC / RSOC, Theorem 3 and the
+// Remark of App. A.2 for exp and exp*), carried out in FP32 only: no FP64 polish.
+// Used by the dual update while the iterates are FP32; the restart / termination
+// checks always project in FP64 (cone_math.cuh).
+#pragma once
+#include "cone_math.cuh"
+
+namespace pdcs {
+
+// ---------------------------------------------------------------------------
+// SOC, entries in registers (dim - 1 <= 32 R), weights w_i = dhat_i^{-2}
+// ---------------------------------------------------------------------------
+template <int R>
+__device__ void soc_project_warp_f32(float* buf, const float* __restrict__ w, int dim, float* lam_cache) {
+    const int lane = threadIdx.x & 31;
+    const int nx = dim - 1;
+    const float t = buf[0];
+    float xr[R], wr[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = lane + 32 * k;
+        const bool in = i < nx;
+        xr[k] = in ? buf[1 + i] : 0.0f;
+        wr[k] = in ? w[i] : 1.0f;
+    }
+    float a = 0.0f, b = 0.0f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float x2 = xr[k] * xr[k];
+        a += x2 / wr[k];
+        b += wr[k] * x2;
+    }
+    a = warp_sum_f(a);
+    b = warp_sum_f(b);
+    const float nDx = sqrtf(a), nDinvx = sqrtf(b);
+    __syncwarp();
+    if (t <= 0.0f && nDx <= -t) {  // case 1
+#pragma unroll
+        for (int k = 0; k < R; ++k) if (lane + 32 * k < nx) buf[1 + lane + 32 * k] = 0.0f;
+        if (lane == 0) buf[0] = 0.0f;
+        __syncwarp();
+        return;
+    }
+    if (nDinvx <= t) return;  // case 2
+    float lam = 0.5f;         // case 3
+    if (t != 0.0f) {          // case 4: safeguarded Newton on G(l) = (1 - 2l)^2 S(l) - t^2
+        auto G = [&](float l, float& g, float& dg) {
+            float S = 0.0f, S1 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const float r = __frcp_rn(1.0f + 2.0f * l * wr[k]);
+                const float term = wr[k] * xr[k] * xr[k] * r * r;
+                S += term;
+                S1 -= 4.0f * wr[k] * term * r;
+            }
+            S = warp_sum_f(S);
+            S1 = warp_sum_f(S1);
+            const float u = 1.0f - 2.0f * l;
+            g = u * u * S - t * t;
+            dg = -4.0f * u * S + u * u * S1;
+        };
+        float lo, hi, g, dg;
+        int slo;
+        if (t > 0.0f) {
+            lo = 0.0f; hi = 0.5f; slo = 1;
+        } else {
+            lo = 0.5f; hi = 1.0f; slo = -1;
+            for (int it = 0; it < 130; ++it) {
+                G(hi, g, dg);
+                if (g > 0.0f || !(hi < 1e30f)) break;
+                lo = hi;
+                hi *= 2.0f;
+            }
+        }
+        float guess = (nDinvx - t) / (2.0f * (nDinvx + t));
+        if (lam_cache && *lam_cache > lo && *lam_cache < hi) guess = *lam_cache;
+        lam = (guess > lo && guess < hi) ? guess : 0.5f * (lo + hi);
+        for (int it = 0; it < 100; ++it) {
+            G(lam, g, dg);
+            if (!(g == g) || g == 0.0f) break;
+            if ((g > 0.0f ? 1 : -1) == slo) lo = lam; else hi = lam;
+            float nl = lam - g / dg;
+            if (nl >= lo && nl <= hi && fabsf(nl - lam) <= 2e-6f * lam) { lam = nl; break; }
+            if (!(nl > lo && nl < hi)) nl = 0.5f * (lo + hi);
+            const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 2e-7f * hi;
+            lam = nl;
+            if (done) break;
+        }
+        if (lam_cache && lane == 0) *lam_cache = lam;
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float y = xr[k] / (1.0f + 2.0f * lam * wr[k]);
+        s += wr[k] * y * y;
+        if (lane + 32 * k < nx) buf[1 + lane + 32 * k] = y;
+    }
+    s = warp_sum_f(s);
+    __syncwarp();
+    if (lane == 0) buf[0] = sqrtf(s);
+    __syncwarp();
+}
+
+// SOC / RSOC of any size from an FP32 buffer: registers up to dim 129; larger blocks
+// go through the FP64 scratch `tmp` (same rows) and the FP64 memory-loop projection
+// onto Dr^{-1} K (kInv, scales dr).
+__device__ __forceinline__ void soc_project_any_f32(float* buf, const float* __restrict__ w32, double* tmp,
+                                                    const double* __restrict__ dr, int dim, bool rot,
+                                                    float* lam_cache) {
+    const int lane = threadIdx.x & 31;
+    const float r2 = 0.70710678118654752440f;
+    const int nx = dim - 1;
+    if (nx > 128) {
+        for (int i = lane; i < dim; i += 32) tmp[i] = (double)buf[i];
+        __syncwarp();
+        if (rot) rsoc_project_warp<true>(tmp, dr, dim, nullptr);
+        else soc_project_warp<true>(tmp, dr, dim, nullptr);
+        for (int i = lane; i < dim; i += 32) buf[i] = (float)tmp[i];
+        __syncwarp();
+        return;
+    }
+    if (rot && lane == 0) {
+        const float p = buf[0], q = buf[1];
+        buf[0] = (p + q) * r2;
+        buf[1] = (p - q) * r2;
+    }
+    __syncwarp();
+    const int R = (nx + 31) / 32;
+    if (R <= 1) soc_project_warp_f32<1>(buf, w32, dim, lam_cache);
+    else if (R == 2) soc_project_warp_f32<2>(buf, w32, dim, lam_cache);
+    else if (R == 3) soc_project_warp_f32<3>(buf, w32, dim, lam_cache);
+    else soc_project_warp_f32<4>(buf, w32, dim, lam_cache);
+    if (rot && lane == 0) {
+        const float p = buf[0], q = buf[1];
+        buf[0] = (p + q) * r2;
+        buf[1] = (p - q) * r2;
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Exponential cone in FP32 (Theorem 3), log scales given
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool in_kexp_f(float r, float s, float t) {
+    if (s > 0.0f) return t > 0.0f && (logf(t) - logf(s)) >= r / s;
+    if (s == 0.0f) return t >= 0.0f && r <= 0.0f;
+    return false;
+}
+
+__device__ __forceinline__ bool in_kexp_dual_f(float r, float s, float t) {
+    if (r < 0.0f) return t > 0.0f && (1.0f + logf(t) - logf(-r)) >= s / r;
+    if (r == 0.0f) return s >= 0.0f && t >= 0.0f;
+    return false;
+}
+
+// Projection onto D K_exp in FP32; lg = log of the scales.  Falls back to the FP64
+// search when the FP32 root search does not give a finite result.
+__device__ inline void exp_project_f32(float r0, float s0, float t0, float dr, float ds, float dt, const float* lg,
+                                       float* out, float* L_cache) {
+    if (in_kexp_f(r0 / dr, s0 / ds, t0 / dt)) { out[0] = r0; out[1] = s0; out[2] = t0; return; }
+    if (in_kexp_dual_f(-dr * r0, -ds * s0, -dt * t0)) { out[0] = 0.0f; out[1] = 0.0f; out[2] = 0.0f; return; }
+    if (r0 <= 0.0f && s0 <= 0.0f) { out[0] = r0; out[1] = 0.0f; out[2] = t0 > 0.0f ? t0 : 0.0f; return; }
+    ExpCase4T<float> e;
+    e.r0 = r0; e.s0 = s0; e.t0 = t0; e.dr = dr; e.ds = ds;
+    e.tau = ds / dr;
+    e.ldr = lg[0]; e.lds = lg[1]; e.ldt = lg[2];
+    const float ninf = -INFINITY;
+    e.lr0 = r0 > 0.0f ? logf(r0) : ninf;
+    e.ls0 = s0 > 0.0f ? logf(s0) : ninf;
+    e.lt0 = t0 > 0.0f ? logf(t0) : (t0 < 0.0f ? logf(-t0) : ninf);
+    e.a3 = s0 > 0.0f ? (r0 * ds) / (s0 * dr) : 0.0f;
+    e.a4m1 = r0 > 0.0f ? -(s0 * ds) / (r0 * dr) : -1.0f;
+    e.a4 = r0 > 0.0f ? 1.0f + e.a4m1 : 0.0f;
+    e.w34 = e.a3 - e.a4;
+    int evals = 0;
+    float L = 0.0f;
+    bool ok = isfinite(e.a3) && isfinite(e.a4) && exp_case4_solve(e, L_cache ? *L_cache : NAN, L, evals) && !(L != L);
+    float F, dF, rho, lsp, lrd, Fs;
+    if (ok) {
+        exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
+        ok = rho == rho;
+    }
+    if (!ok) {
+        double o[3], Lc = NAN;
+        exp_project((double)r0, (double)s0, (double)t0, (double)dr, (double)ds, (double)dt, o, &Lc, nullptr);
+        out[0] = (float)o[0]; out[1] = (float)o[1]; out[2] = (float)o[2];
+        return;
+    }
+    if (L_cache) *L_cache = L;
+    const float sp = expf(lsp), rd = expf(lrd);
+    const float vp[3] = {dr * rho * sp, ds * sp, expf(e.ldt + rho + lsp)};
+    const float vd[3] = {rd / dr, (1.0f - rho) * rd / ds, -expf(-e.ldt - rho + lrd)};
+    const float v0[3] = {r0, s0, t0};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) out[k] = fabsf(vp[k]) <= fabsf(vd[k]) ? vp[k] : v0[k] - vd[k];
+    out[2] = t0 >= 0.0f ? t0 - vd[2] : vp[2];
+}
+
+// Projection onto D^{-1} K_exp^* (Remark of App. A.2) in FP32.
+__device__ __forceinline__ void exp_dual_project_f32(float r, float s, float t, float dr, float ds, float dt,
+                                                     const float* lg, float* out, float* L_cache) {
+    float p[3];
+    exp_project_f32(-r, -s, -t, dr, ds, dt, lg, p, L_cache);
+    out[0] = r + p[0];
+    out[1] = s + p[1];
+    out[2] = t + p[2];
+}
+
+}  // namespace pdcs

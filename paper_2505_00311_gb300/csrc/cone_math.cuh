@@ -25,6 +25,10 @@
 
 namespace pdcs {
 
+// Newton step (relative) below which the SOC root search stops: the error left is of
+// order its square.
+constexpr double RootTolSoc = 1e-10;
+
 // ---------------------------------------------------------------------------
 // Second-order cone
 // ---------------------------------------------------------------------------
@@ -111,7 +115,7 @@ __device__ int soc_project_warp(double* buf, const double* __restrict__ d, int d
             double nl = lam - g / dg;
             // a Newton step below 1e-10 relative leaves an error of order its square
             // (lam itself has just become an end of the bracket, so test this first)
-            if (nl >= lo && nl <= hi && fabs(nl - lam) <= 1e-10 * lam) {
+            if (nl >= lo && nl <= hi && fabs(nl - lam) <= RootTolSoc * lam) {
                 lam = nl;
                 break;
             }
@@ -161,6 +165,252 @@ __device__ int rsoc_project_warp(double* buf, const double* __restrict__ d, int 
 }
 
 // ---------------------------------------------------------------------------
+// Second-order cone, mixed precision (cones with dim - 1 <= 32 R): the entries
+// stay in registers, weights w_i come precomputed, the root of G is found in FP32
+// and polished by at most three FP64 Newton steps, in which 1 / (1 + 2 lambda w) is
+// an FP32 reciprocal refined by two Newton-Raphson steps r <- r (2 - a r) in FP64.
+// Whatever the FP32 pass cannot settle falls back to the full FP64 search.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rcp_refined(double a) {
+    double r = (double)__frcp_rn((float)a);
+    r = r * (2.0 - a * r);
+    return r * (2.0 - a * r);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// buf[0..dim): the block, projected in place onto E K_soc where the weight of x entry
+// i is w[i] = dhat_i^{-2} (w may be null: all ones).  lam_cache may be null.
+template <int R>
+__device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w, int dim, float* lam_cache) {
+    const int lane = threadIdx.x & 31;
+    const int nx = dim - 1;
+    const double t = buf[0];
+    double xr[R], wr[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = lane + 32 * k;
+        const bool in = i < nx;
+        xr[k] = in ? buf[1 + i] : 0.0;
+        wr[k] = in ? (w ? w[i] : 1.0) : 1.0;
+    }
+    double a = 0.0, b = 0.0;  // ||Dhat x||^2, ||Dhat^{-1} x||^2
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const double x2 = xr[k] * xr[k];
+        a += x2 / wr[k];
+        b += wr[k] * x2;
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const double nDx = sqrt(a), nDinvx = sqrt(b);
+    __syncwarp();
+    if (t <= 0.0 && nDx <= -t) {  // case 1
+#pragma unroll
+        for (int k = 0; k < R; ++k) if (lane + 32 * k < nx) buf[1 + lane + 32 * k] = 0.0;
+        if (lane == 0) buf[0] = 0.0;
+        __syncwarp();
+        return;
+    }
+    if (nDinvx <= t) return;  // case 2
+    double lam = 0.5;         // case 3 (t == 0)
+    if (t != 0.0) {           // case 4
+        // ---- FP32 root of G(l) = (1 - 2l)^2 S(l) - t^2
+        float xf[R], wf[R];
+        bool rng = fabs(t) < 1e30 && fabs(t) > 1e-30 && nDinvx < 1e30;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            xf[k] = (float)xr[k];
+            wf[k] = (float)wr[k];
+            rng = rng && wr[k] < 1e30 && wr[k] > 1e-30;
+        }
+        rng = __all_sync(0xffffffffu, rng);
+        const float tf = (float)t;
+        auto G32 = [&](float l, float& g, float& dg) {
+            float S = 0.0f, S1 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const float r = __frcp_rn(1.0f + 2.0f * l * wf[k]);
+                const float term = wf[k] * xf[k] * xf[k] * r * r;
+                S += term;
+                S1 -= 4.0f * wf[k] * term * r;
+            }
+            S = warp_sum_f(S);
+            S1 = warp_sum_f(S1);
+            const float u = 1.0f - 2.0f * l;
+            g = u * u * S - tf * tf;
+            dg = -4.0f * u * S + u * u * S1;
+        };
+        bool ok = rng;
+        float lf = 0.5f;
+        if (ok) {
+            float lo, hi, g, dg;
+            int slo;
+            if (tf > 0.0f) {
+                lo = 0.0f; hi = 0.5f; slo = 1;
+            } else {
+                lo = 0.5f; hi = 1.0f; slo = -1;
+                for (int it = 0; it < 130; ++it) {
+                    G32(hi, g, dg);
+                    if (g > 0.0f || !(hi < 1e30f)) break;
+                    lo = hi;
+                    hi *= 2.0f;
+                }
+            }
+            float guess = (float)((nDinvx - t) / (2.0 * (nDinvx + t)));
+            if (lam_cache && *lam_cache > lo && *lam_cache < hi) guess = *lam_cache;
+            lf = (guess > lo && guess < hi) ? guess : 0.5f * (lo + hi);
+            for (int it = 0; it < 100; ++it) {
+                G32(lf, g, dg);
+                if (!(g == g)) { ok = false; break; }
+                if (g == 0.0f) break;
+                if ((g > 0.0f ? 1 : -1) == slo) lo = lf; else hi = lf;
+                float nl = lf - g / dg;
+                if (nl >= lo && nl <= hi && fabsf(nl - lf) <= 2e-6f * lf) { lf = nl; break; }
+                if (!(nl > lo && nl < hi)) nl = 0.5f * (lo + hi);
+                const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 2e-7f * hi;
+                lf = nl;
+                if (done) break;
+            }
+        }
+        // ---- FP64 polish
+        bool conv = false;
+        if (ok) {
+            double x2w[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) x2w[k] = wr[k] * xr[k] * xr[k];
+            lam = (double)lf;
+            for (int it = 0; it < 3; ++it) {
+                double S = 0.0, S1 = 0.0;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const double r = rcp_refined(1.0 + 2.0 * lam * wr[k]);
+                    const double term = x2w[k] * r * r;
+                    S += term;
+                    S1 -= 4.0 * wr[k] * term * r;
+                }
+                S = warp_sum(S);
+                S1 = warp_sum(S1);
+                const double u = 1.0 - 2.0 * lam;
+                const double step = (u * u * S - t * t) / (-4.0 * u * S + u * u * S1);
+                if (!isfinite(step)) break;
+                lam -= step;
+                if (fabs(step) <= RootTolSoc * lam) { conv = true; break; }
+            }
+            conv = conv && (t > 0.0 ? (lam > 0.0 && lam < 0.5) : lam > 0.5);
+        }
+        if (!conv) {
+            // full FP64 safeguarded search on the registers
+            double lo, hi;
+            int slo;
+            auto G = [&](double l, double& g, double& dg) {
+                double S = 0.0, S1 = 0.0;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const double r = 1.0 / (1.0 + 2.0 * l * wr[k]);
+                    const double term = wr[k] * xr[k] * xr[k] * r * r;
+                    S += term;
+                    S1 -= 4.0 * wr[k] * term * r;
+                }
+                S = warp_sum(S);
+                S1 = warp_sum(S1);
+                const double u = 1.0 - 2.0 * l;
+                g = u * u * S - t * t;
+                dg = -4.0 * u * S + u * u * S1;
+            };
+            double g, dg;
+            if (t > 0.0) {
+                lo = 0.0; hi = 0.5; slo = 1;
+            } else {
+                lo = 0.5; hi = 1.0; slo = -1;
+                for (int it = 0; it < 1100; ++it) {
+                    G(hi, g, dg);
+                    if (g > 0.0) break;
+                    lo = hi;
+                    hi *= 2.0;
+                }
+            }
+            double guess = (nDinvx - t) / (2.0 * (nDinvx + t));
+            lam = (guess > lo && guess < hi) ? guess : 0.5 * (lo + hi);
+            for (int it = 0; it < 200; ++it) {
+                G(lam, g, dg);
+                if (g == 0.0) break;
+                if ((g > 0.0 ? 1 : -1) == slo) lo = lam; else hi = lam;
+                double nl = lam - g / dg;
+                if (nl >= lo && nl <= hi && fabs(nl - lam) <= RootTolSoc * lam) { lam = nl; break; }
+                if (!(nl > lo && nl < hi)) nl = 0.5 * (lo + hi);
+                const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 4e-16 * hi;
+                lam = nl;
+                if (done) break;
+            }
+        }
+        if (lam_cache && lane == 0) *lam_cache = (float)lam;
+    }
+    // y = (I + 2 lambda Dhat^{-2})^{-1} x ;  s = ||Dhat^{-1} y||
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const double y = xr[k] * rcp_refined(1.0 + 2.0 * lam * wr[k]);
+        s += wr[k] * y * y;
+        if (lane + 32 * k < nx) buf[1 + lane + 32 * k] = y;
+    }
+    s = warp_sum(s);
+    __syncwarp();
+    if (lane == 0) buf[0] = sqrt(s);
+    __syncwarp();
+}
+
+// Rotated SOC through Q (see rsoc_project_warp) on the mixed-precision SOC path.
+template <int R>
+__device__ void rsoc_project_warp_fast(double* buf, const double* __restrict__ w, int dim, float* lam_cache) {
+    const int lane = threadIdx.x & 31;
+    const double r2 = 0.70710678118654752440;
+    __syncwarp();
+    if (lane == 0) {
+        const double p = buf[0], q = buf[1];
+        buf[0] = (p + q) * r2;
+        buf[1] = (p - q) * r2;
+    }
+    __syncwarp();
+    soc_project_warp_fast<R>(buf, w, dim, lam_cache);
+    if (lane == 0) {
+        const double p = buf[0], q = buf[1];
+        buf[0] = (p + q) * r2;
+        buf[1] = (p - q) * r2;
+    }
+    __syncwarp();
+}
+
+// Picks the register count for the block (dim - 1 <= 128); larger blocks use the
+// FP64 memory-loop projection with weights formed from the scales d (kInv as there).
+template <bool kInv>
+__device__ __forceinline__ void soc_project_any(double* buf, const double* __restrict__ w,
+                                                const double* __restrict__ d, int dim, bool rot, float* lam_cache) {
+    const int nx = dim - 1;
+    if (nx > 128) {
+        if (rot) rsoc_project_warp<kInv>(buf, d, dim, nullptr);
+        else soc_project_warp<kInv>(buf, d, dim, nullptr);
+        return;
+    }
+    const int R = (nx + 31) / 32;
+    if (rot) {
+        if (R <= 1) rsoc_project_warp_fast<1>(buf, w, dim, lam_cache);
+        else if (R == 2) rsoc_project_warp_fast<2>(buf, w, dim, lam_cache);
+        else if (R == 3) rsoc_project_warp_fast<3>(buf, w, dim, lam_cache);
+        else rsoc_project_warp_fast<4>(buf, w, dim, lam_cache);
+    } else {
+        if (R <= 1) soc_project_warp_fast<1>(buf, w, dim, lam_cache);
+        else if (R == 2) soc_project_warp_fast<2>(buf, w, dim, lam_cache);
+        else if (R == 3) soc_project_warp_fast<3>(buf, w, dim, lam_cache);
+        else soc_project_warp_fast<4>(buf, w, dim, lam_cache);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Exponential cone
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ bool in_kexp(double r, double s, double t) {
@@ -175,135 +425,246 @@ __host__ __device__ __forceinline__ bool in_kexp_dual(double r, double s, double
     return false;
 }
 
-__host__ __device__ __forceinline__ double lse2(double a, double b) {  // log(e^a + e^b)
-    if (a == -INFINITY) return b;
-    if (b == -INFINITY) return a;
-    double mx = fmax(a, b), mn = fmin(a, b);
-    return mx + log1p(exp(mn - mx));
-}
+// Tolerances of the root search in each precision: the Newton step below which the
+// iteration stops (its square is the remaining error) and the bracket collapse.
+template <typename R> struct RootTol;
+template <> struct RootTol<double> {
+    static constexpr double newton = 1e-10, collapse = 4e-16;
+};
+template <> struct RootTol<float> {
+    static constexpr float newton = 2e-6f, collapse = 2e-7f;
+};
 
-struct ExpCase4 {
-    double r0, s0, t0, dr, ds, tau, a3, a4, a4m1, w34, ldt, dir, lt0, lr0, ls0, ldr, lds;
+template <typename R>
+struct ExpCase4T {
+    R r0, s0, t0, dr, ds, tau, a3, a4, a4m1, w34, ldt, dir, lt0, lr0, ls0, ldr, lds;
     int anchor;  // 3 or 4: endpoint rho is measured from
     int kind;    // 1: r0 > 0, s0 > 0;  2: r0 <= 0 < s0;  3: s0 <= 0 < r0
 };
+using ExpCase4 = ExpCase4T<double>;
 
 // At log-offset L (rho = anchor + dir e^L): rho, log s_p, log r_d (eq. sp_rd via
 // eq. tilde_defs, the vanishing factor as log r0 + L or log s0 + L), and
 // F(L) = lhs - rhs with the sign of h(rho) (eq. h_rho) decided in logs:
 //   t0 >= 0: lhs = A, rhs = log(e^B + t0);  t0 < 0: lhs = log(e^A - t0), rhs = B,
 //   A = log(d_t e^rho s_p), B = log(d_t^{-1} e^{-rho} r_d);  dF = dF/dL.
-__host__ __device__ __forceinline__ void exp_F(const ExpCase4& e, double L, double& F, double& dF, double& rho_out,
-                                               double& lsp_out, double& lrd_out) {
-    const double delta = exp(L);
-    double rho, rm1, lst, lrt, dlst, dlrt;  // rm1 = rho - 1 from the exact offset; logs of |s~|, |r~|
+template <typename R>
+__host__ __device__ __forceinline__ void exp_F(const ExpCase4T<R>& e, R L, R& F, R& dF, R& rho_out, R& lsp_out,
+                                               R& lrd_out, R& Fscale_out) {
+    const R one = R(1), zero = R(0);
+    const R delta = exp(L);
+    R rho, rm1, lst, lrt, dlst, dlrt;  // rm1 = rho - 1 from the exact offset; logs of |s~|, |r~|
     int sst, srt;
     if (e.anchor == 4) {
         rho = e.a4 + e.dir * delta;
         rm1 = e.a4m1 + e.dir * delta;
         lst = e.lr0 + L;
-        dlst = 1.0;
-        sst = e.dir > 0.0 ? 1 : -1;
-        const double rt = (e.kind == 1) ? e.s0 * (e.w34 - e.dir * delta) : e.tau * e.r0 - rho * e.s0;
+        dlst = one;
+        sst = e.dir > zero ? 1 : -1;
+        const R rt = (e.kind == 1) ? e.s0 * (e.w34 - e.dir * delta) : e.tau * e.r0 - rho * e.s0;
         lrt = log(fabs(rt));
         dlrt = (-e.s0 / rt) * e.dir * delta;
-        srt = (rt > 0.0) - (rt < 0.0);
+        srt = (rt > zero) - (rt < zero);
     } else {
         rho = e.a3 + e.dir * delta;
-        rm1 = (e.a3 - 1.0) + e.dir * delta;
+        rm1 = (e.a3 - one) + e.dir * delta;
         lrt = e.ls0 + L;
-        dlrt = 1.0;
-        srt = e.dir < 0.0 ? 1 : -1;
-        const double st = (e.kind == 1) ? e.r0 * (e.w34 + e.dir * delta) : e.s0 * e.tau - e.r0 + e.r0 * rho;
+        dlrt = one;
+        srt = e.dir < zero ? 1 : -1;
+        const R st = (e.kind == 1) ? e.r0 * (e.w34 + e.dir * delta) : e.s0 * e.tau - e.r0 + e.r0 * rho;
         lst = log(fabs(st));
         dlst = (e.r0 / st) * e.dir * delta;
-        sst = (st > 0.0) - (st < 0.0);
+        sst = (st > zero) - (st < zero);
     }
-    const double dt_ = rho * rm1 + e.tau * e.tau;  // d~ = rho (rho - 1) + tau^2
-    const int sdt = (dt_ > 0.0) - (dt_ < 0.0);
-    const double ldt_ = log(fabs(dt_));
-    const double dldt = ((2.0 * rho - 1.0) / dt_) * e.dir * delta;
-    const double lsp = (sst != 0 && sst == sdt) ? lst - e.ldr - ldt_ : -INFINITY;
-    const double lrd = (srt != 0 && srt == sdt) ? e.lds + lrt - ldt_ : -INFINITY;
-    const double A = e.ldt + rho + lsp;
-    const double B = -e.ldt - rho + lrd;
-    const double dA = e.dir * delta + dlst - dldt;
-    const double dB = -e.dir * delta + dlrt - dldt;
+    const R dt_ = rho * rm1 + e.tau * e.tau;  // d~ = rho (rho - 1) + tau^2
+    const int sdt = (dt_ > zero) - (dt_ < zero);
+    const R ldt_ = log(fabs(dt_));
+    const R dldt = ((R(2) * rho - one) / dt_) * e.dir * delta;
+    const R ninf = -R(INFINITY);
+    const R lsp = (sst != 0 && sst == sdt) ? lst - e.ldr - ldt_ : ninf;
+    const R lrd = (srt != 0 && srt == sdt) ? e.lds + lrt - ldt_ : ninf;
+    const R A = e.ldt + rho + lsp;
+    const R B = -e.ldt - rho + lrd;
+    const R dA = e.dir * delta + dlst - dldt;
+    const R dB = -e.dir * delta + dlrt - dldt;
     // log(e^a + e^b) = max + log1p(q), q = e^(min - max); the weight e^(a - lse) of a
     // comes from the same q, so each evaluation needs one exp and one log1p here
-    auto lse_w = [](double a, double b, double& wa) {
-        if (a == -INFINITY) { wa = 0.0; return b; }
-        if (b == -INFINITY) { wa = 1.0; return a; }
+    auto lse_w = [ninf, one](R a, R b, R& wa) {
+        if (a == ninf) { wa = R(0); return b; }
+        if (b == ninf) { wa = one; return a; }
         const bool amax = a >= b;
-        const double q = exp(amax ? b - a : a - b);
-        wa = amax ? 1.0 / (1.0 + q) : q / (1.0 + q);
+        const R q = exp(amax ? b - a : a - b);
+        wa = amax ? one / (one + q) : q / (one + q);
         return (amax ? a : b) + log1p(q);
     };
-    if (e.t0 >= 0.0) {
-        double wB = 1.0;
-        const double rhs = e.t0 > 0.0 ? lse_w(B, e.lt0, wB) : B;
-        if (B == -INFINITY) wB = 0.0;
+    if (e.t0 >= zero) {
+        R wB = one;
+        const R rhs = e.t0 > zero ? lse_w(B, e.lt0, wB) : B;
+        if (B == ninf) wB = zero;
         F = A - rhs;
         dF = dA - wB * dB;
+        Fscale_out = fabs(A) + fabs(rhs);
     } else {
-        double wA;
-        const double lhs = lse_w(A, e.lt0, wA);
+        R wA;
+        const R lhs = lse_w(A, e.lt0, wA);
         F = lhs - B;
         dF = wA * dA - dB;
+        Fscale_out = fabs(lhs) + fabs(B);
     }
     rho_out = rho;
     lsp_out = lsp;
     lrd_out = lrd;
 }
 
-__host__ __device__ __forceinline__ int exp_sign(const ExpCase4& e, double L, int& evals) {
-    double F, dF, rho, lsp, lrd;
-    exp_F(e, L, F, dF, rho, lsp, lrd);
+template <typename R>
+__host__ __device__ __forceinline__ int exp_sign(const ExpCase4T<R>& e, R L, int& evals) {
+    R F, dF, rho, lsp, lrd, Fs;
+    exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
     ++evals;
-    return (F > 0.0) - (F < 0.0);
+    return (F > R(0)) - (F < R(0));
 }
 
 // Lower end of the search: step down from hi by 1, 2, 4, ... until F shows the
-// sign it has next to the anchor.
-__host__ __device__ __forceinline__ double exp_lower(const ExpCase4& e, double hi, int slo, int& evals) {
-    double step = 1.0;
-    for (int it = 0; it < 1100; ++it) {
-        const double lo = hi - step;
-        if (lo == -INFINITY || exp_sign(e, lo, evals) == slo) return lo;
-        step *= 2.0;
+// sign it has next to the anchor.  First F at the anchor itself (offset 0, L = -inf)
+// is evaluated: it is the endpoint value h(a4) or h(a3) of App. A.2 in log form.
+// When it is zero to working precision or has the other sign (v0 on the boundary
+// of the polar cone or of the cone, up to rounding), the root is the endpoint:
+// at_end is set and -inf returned.
+template <typename R>
+__host__ __device__ __forceinline__ R exp_lower(const ExpCase4T<R>& e, R hi, int slo, int& evals, bool& at_end) {
+    const R ninf = -R(INFINITY);
+    at_end = false;
+    {
+        R F0, dF, rho, lsp, lrd, Fs;
+        exp_F(e, ninf, F0, dF, rho, lsp, lrd, Fs);
+        ++evals;
+        const int s0 = (F0 > R(0)) - (F0 < R(0));
+        const bool tiny = fabs(F0) < R(INFINITY) && fabs(F0) <= R(16) * RootTol<R>::collapse * Fs;
+        if (F0 == F0 && (s0 != slo || tiny)) {
+            at_end = true;
+            return ninf;
+        }
     }
-    return -INFINITY;
+    R step = R(1);
+    for (int it = 0; it < 1100; ++it) {
+        const R lo = hi - step;
+        if (lo == ninf) return lo;
+        const int s = exp_sign(e, lo, evals);
+        if (s == slo || s == 0) return lo;
+        step *= R(2);
+    }
+    return ninf;
 }
 
 // Safeguarded Newton for F(L) = 0 on (lo, hi); sign(F) at the lo end is slo.
-__host__ __device__ __forceinline__ double exp_newton(const ExpCase4& e, double lo, double hi, int slo, double L,
-                                                      int& evals) {
-    if (!(L > lo && L < hi)) L = (lo == -INFINITY) ? hi - 1.0 : 0.5 * (lo + hi);
+template <typename R>
+__host__ __device__ __forceinline__ R exp_newton(const ExpCase4T<R>& e, R lo, R hi, int slo, R L, int& evals) {
+    const R one = R(1), ninf = -R(INFINITY);
+    if (!(L > lo && L < hi)) L = (lo == ninf) ? hi - one : R(0.5) * (lo + hi);
     for (int it = 0; it < 400; ++it) {
-        double F, dF, rho, lsp, lrd;
-        exp_F(e, L, F, dF, rho, lsp, lrd);
+        R F, dF, rho, lsp, lrd, Fs;
+        exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
         ++evals;
         if (!(F == F)) break;  // NaN: both sides infinite, already at the limit
-        if (F == 0.0) break;
-        const int s = F > 0.0 ? 1 : -1;
+        if (F == R(0)) break;
+        const int s = F > R(0) ? 1 : -1;
         if (s == slo) lo = L; else hi = L;
-        double nl = L - F / dF;
-        // a Newton step below 1e-10 relative leaves an error of order its square
+        R nl = L - F / dF;
+        // a Newton step below RootTol::newton relative leaves an error of order its square
         // (L itself has just become an end of the bracket, so test this first)
-        if (nl >= lo && nl <= hi && fabs(nl - L) <= 1e-10 * fmax(1.0, fabs(L))) {
+        if (nl >= lo && nl <= hi && fabs(nl - L) <= RootTol<R>::newton * fmax(one, fabs(L))) {
             L = nl;
             break;
         }
-        if (!(nl > lo && nl < hi)) nl = (lo == -INFINITY) ? hi - 2.0 * fmax(1.0, fabs(hi - L)) : 0.5 * (lo + hi);
-        const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 4e-16 * fmax(1.0, fabs(hi));
+        if (!(nl > lo && nl < hi)) nl = (lo == ninf) ? hi - R(2) * fmax(one, fabs(hi - L)) : R(0.5) * (lo + hi);
+        const bool done = !(nl > lo && nl < hi) || (hi - lo) <= RootTol<R>::collapse * fmax(one, fabs(hi));
         L = nl;
         if (done) break;
     }
     return L;
 }
 
-// Projection of v0 onto D K_exp, D = diag(dr, ds, dt) (Theorem 3).
-// L_cache (may be null): last log-offset of this cone, used as the Newton start and updated.
+// Case 4 of Theorem 3 for the prepared e (logs and a3, a4 filled in): chooses the
+// interval branch of eq. lrho_urho and the anchor, and returns the log-offset L of
+// the root of h.  Returns false when the interval is empty by rounding.
+template <typename R>
+__host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R guess, R& L, int& evals) {
+    const R zero = R(0), one = R(1);
+    if (e.r0 > zero && e.s0 > zero) {
+        e.kind = 1;
+        const R W = fabs(e.w34);
+        if (!(W > zero)) return false;
+        const R Lh = log(R(0.5) * W);
+        e.anchor = 4;
+        e.dir = e.w34 > zero ? one : -one;
+        const int sm = exp_sign(e, Lh, evals);
+        if (sm == 0) {
+            L = Lh;
+            return true;
+        }
+        if (sm < 0) {  // h(mid) < 0 < h(a3): root in the half next to a3
+            e.anchor = 3;
+            e.dir = -e.dir;
+        }
+        const int slo = sm > 0 ? -1 : +1;
+        bool at_end;
+        const R lo = exp_lower(e, Lh, slo, evals, at_end);
+        L = at_end ? lo : exp_newton(e, lo, Lh, slo, guess, evals);
+    } else if (e.s0 > zero) {  // r0 <= 0: (-inf, a3)
+        e.kind = 2; e.anchor = 3; e.dir = -one;
+        R hi = zero;
+        for (int it = 0; it < 8 && exp_sign(e, hi, evals) > 0 && hi < R(60); ++it) hi = R(2) * hi + one;
+        bool at_end;
+        const R lo = exp_lower(e, hi, +1, evals, at_end);
+        L = at_end ? lo : exp_newton(e, lo, hi, +1, guess, evals);
+    } else {  // s0 <= 0 < r0: (a4, inf)
+        e.kind = 3; e.anchor = 4; e.dir = one;
+        R hi = zero;
+        for (int it = 0; it < 8 && exp_sign(e, hi, evals) < 0 && hi < R(60); ++it) hi = R(2) * hi + one;
+        bool at_end;
+        const R lo = exp_lower(e, hi, -1, evals, at_end);
+        L = at_end ? lo : exp_newton(e, lo, hi, -1, guess, evals);
+    }
+    return true;
+}
+
+// Fills the case-4 data of v0 = (r0, s0, t0), D = diag(dr, ds, dt), in precision R
+// from values given in double (logs of the scales passed in).
+template <typename R>
+__host__ __device__ __forceinline__ void exp_case4_setup(ExpCase4T<R>& e, double r0, double s0, double t0, double dr,
+                                                         double ds, R ldr, R lds, R ldt) {
+    e.r0 = R(r0); e.s0 = R(s0); e.t0 = R(t0); e.dr = R(dr); e.ds = R(ds);
+    e.tau = R(ds / dr);
+    e.ldt = ldt; e.ldr = ldr; e.lds = lds;
+    const R ninf = -R(INFINITY);
+    e.lr0 = r0 > 0.0 ? R(log(R(r0))) : ninf;
+    e.ls0 = s0 > 0.0 ? R(log(R(s0))) : ninf;
+    e.lt0 = t0 > 0.0 ? R(log(R(t0))) : (t0 < 0.0 ? R(log(R(-t0))) : ninf);
+    e.a3 = (s0 > 0.0) ? R((r0 * ds) / (s0 * dr)) : R(0);
+    e.a4 = (r0 > 0.0) ? R(1.0 - (s0 * ds) / (r0 * dr)) : R(0);
+    e.a4m1 = (r0 > 0.0) ? R(-(s0 * ds) / (r0 * dr)) : R(-1);
+    e.w34 = e.a3 - e.a4;
+}
+
+// Result of case 4 at the root L (eq. vpvd_defn with v0 = v_p + v_d, eq. diagonal_moreau):
+// per coordinate the smaller part from its formula, v_p = v0 - v_d when v_d is larger.
+__host__ __device__ __forceinline__ void exp_case4_output(const ExpCase4& e, double L, double r0, double s0, double t0,
+                                                          double dr, double ds, double* out) {
+    double F, dF, rho, lsp, lrd, Fs;
+    exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
+    const double sp = exp(lsp), rd = exp(lrd);
+    const double vp[3] = {dr * rho * sp, ds * sp, exp(e.ldt + rho + lsp)};
+    const double vd[3] = {rd / dr, (1.0 - rho) * rd / ds, -exp(-e.ldt - rho + lrd)};
+    const double v0[3] = {r0, s0, t0};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) out[k] = fabs(vp[k]) <= fabs(vd[k]) ? vp[k] : v0[k] - vd[k];
+    // t entry: h(rho) = 0 says e^A - e^B = t0, so v_d is the smaller part when t0 >= 0
+    out[2] = t0 >= 0.0 ? t0 - vd[2] : vp[2];
+}
+
+// Projection of v0 onto D K_exp, D = diag(dr, ds, dt) (Theorem 3), all in FP64 with
+// the safeguarded search.  L_cache (may be null): last log-offset of this cone, used
+// as the Newton start and updated.
 __host__ __device__ inline void exp_project(double r0, double s0, double t0, double dr, double ds, double dt,
                                             double* out, double* L_cache, int* evals_out) {
     int evals = 0;
@@ -321,69 +682,117 @@ __host__ __device__ inline void exp_project(double r0, double s0, double t0, dou
         return;
     }
     ExpCase4 e;
-    e.r0 = r0; e.s0 = s0; e.t0 = t0; e.dr = dr; e.ds = ds;
-    e.tau = ds / dr;
-    e.ldt = log(dt);
-    e.ldr = log(dr);
-    e.lds = log(ds);
-    e.lr0 = r0 > 0.0 ? log(r0) : -INFINITY;
-    e.ls0 = s0 > 0.0 ? log(s0) : -INFINITY;
-    e.lt0 = t0 > 0.0 ? log(t0) : (t0 < 0.0 ? log(-t0) : -INFINITY);
-    e.a3 = (s0 > 0.0) ? (r0 * ds) / (s0 * dr) : 0.0;
-    e.a4 = (r0 > 0.0) ? 1.0 - (s0 * ds) / (r0 * dr) : 0.0;
-    e.a4m1 = (r0 > 0.0) ? -(s0 * ds) / (r0 * dr) : -1.0;
-    e.w34 = e.a3 - e.a4;
+    exp_case4_setup(e, r0, s0, t0, dr, ds, log(dr), log(ds), log(dt));
     const double guess = L_cache ? *L_cache : NAN;
     double L;
-    if (r0 > 0.0 && s0 > 0.0) {
-        e.kind = 1;
-        const double W = fabs(e.w34);
-        if (!(W > 0.0)) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
-        const double Lh = log(0.5 * W);
-        e.anchor = 4;
-        e.dir = e.w34 > 0.0 ? 1.0 : -1.0;
-        const int sm = exp_sign(e, Lh, evals);
-        if (sm == 0) {
-            L = Lh;
-        } else if (sm > 0) {  // root in the half next to a4
-            L = exp_newton(e, exp_lower(e, Lh, -1, evals), Lh, -1, guess, evals);
-        } else {              // root in the half next to a3
-            e.anchor = 3;
-            e.dir = -e.dir;
-            L = exp_newton(e, exp_lower(e, Lh, +1, evals), Lh, +1, guess, evals);
-        }
-    } else if (s0 > 0.0) {  // r0 <= 0: (-inf, a3)
-        e.kind = 2; e.anchor = 3; e.dir = -1.0;
-        double hi = 0.0;
-        for (int it = 0; it < 8 && exp_sign(e, hi, evals) > 0 && hi < 60.0; ++it) hi = 2.0 * hi + 1.0;
-        L = exp_newton(e, exp_lower(e, hi, +1, evals), hi, +1, guess, evals);
-    } else {  // s0 <= 0 < r0: (a4, inf)
-        e.kind = 3; e.anchor = 4; e.dir = 1.0;
-        double hi = 0.0;
-        for (int it = 0; it < 8 && exp_sign(e, hi, evals) < 0 && hi < 60.0; ++it) hi = 2.0 * hi + 1.0;
-        L = exp_newton(e, exp_lower(e, hi, -1, evals), hi, -1, guess, evals);
-    }
+    if (!exp_case4_solve(e, guess, L, evals)) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
     if (L_cache) *L_cache = L;
-    double F, dF, rho, lsp, lrd;
-    exp_F(e, L, F, dF, rho, lsp, lrd);
     if (evals_out) *evals_out = evals;
-    // eq. vpvd_defn with v0 = v_p + v_d (eq. diagonal_moreau): per coordinate the
-    // smaller part from its formula, v_p = v0 - v_d when v_d is the larger one.
-    const double sp = exp(lsp), rd = exp(lrd);
-    const double vp[3] = {dr * rho * sp, ds * sp, exp(e.ldt + rho + lsp)};
-    const double vd[3] = {rd / dr, (1.0 - rho) * rd / ds, -exp(-e.ldt - rho + lrd)};
-    const double v0[3] = {r0, s0, t0};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) out[k] = fabs(vp[k]) <= fabs(vd[k]) ? vp[k] : v0[k] - vd[k];
-    // t entry: h(rho) = 0 says e^A - e^B = t0, so v_d is the smaller part when t0 >= 0
-    out[2] = t0 >= 0.0 ? t0 - vd[2] : vp[2];
+    exp_case4_output(e, L, r0, s0, t0, dr, ds, out);
 }
 
 // Projection onto D^{-1} K_exp^* (Remark of App. A.2): v + Proj_{D K_exp}(-v).
 __host__ __device__ __forceinline__ void exp_dual_project(double r, double s, double t, double dr, double ds, double dt,
-                                                 double* out, double* L_cache, int* evals) {
+                                                          double* out, double* L_cache, int* evals) {
     double p[3];
     exp_project(-r, -s, -t, dr, ds, dt, p, L_cache, evals);
+    out[0] = r + p[0];
+    out[1] = s + p[1];
+    out[2] = t + p[2];
+}
+
+// ---------------------------------------------------------------------------
+// Exponential cone, mixed precision: the same projection with the case tests
+// screened in FP32 (FP64 only when the FP32 margin is too small), the root of h
+// found in FP32 and polished by at most three FP64 Newton steps; anything the
+// FP32 pass cannot settle (values outside the FP32 range, no convergence) falls
+// back to exp_project.  FP64 transcendentals cost ~50x their FP32 forms on GB300.
+// ---------------------------------------------------------------------------
+// +1: surely in K_exp, -1: surely not, 0: undecided at FP32 precision
+__host__ __device__ __forceinline__ int kexp_screen32(float r, float s, float t) {
+    if (!(fabsf(r) < 1e30f && fabsf(s) < 1e30f && fabsf(t) < 1e30f)) return 0;
+    if (s > 1e-30f) {
+        if (t < 0.0f) return -1;
+        if (!(t > 1e-30f)) return 0;
+        const float lhs = logf(t) - logf(s), rhs = r / s;
+        const float tol = 1e-4f * (1.0f + fabsf(lhs) + fabsf(rhs));
+        return lhs - rhs > tol ? 1 : (lhs - rhs < -tol ? -1 : 0);
+    }
+    return s < -1e-30f ? -1 : 0;
+}
+
+// +1: surely in K_exp^*, -1: surely not, 0: undecided
+__host__ __device__ __forceinline__ int kexpdual_screen32(float r, float s, float t) {
+    if (!(fabsf(r) < 1e30f && fabsf(s) < 1e30f && fabsf(t) < 1e30f)) return 0;
+    if (r < -1e-30f) {
+        if (t < 0.0f) return -1;
+        if (!(t > 1e-30f)) return 0;
+        const float lhs = 1.0f + logf(t) - logf(-r), rhs = s / r;
+        const float tol = 1e-4f * (1.0f + fabsf(lhs) + fabsf(rhs));
+        return lhs - rhs > tol ? 1 : (lhs - rhs < -tol ? -1 : 0);
+    }
+    return r > 1e-30f ? -1 : 0;
+}
+
+// Projection onto D K_exp with precomputed logs of the scales (lg[0..2] = log dr, ds, dt).
+// L_cache (may be null): FP32 copy of the last log-offset of this cone.
+__host__ __device__ inline void exp_project_fast(double r0, double s0, double t0, double dr, double ds, double dt,
+                                                 const double* lg, double* out, float* L_cache) {
+    // cases 1-3, screened in FP32
+    int c1 = kexp_screen32((float)r0 / (float)dr, (float)s0 / (float)ds, (float)t0 / (float)dt);
+    if (c1 == 0) c1 = in_kexp(r0 / dr, s0 / ds, t0 / dt) ? 1 : -1;
+    if (c1 > 0) { out[0] = r0; out[1] = s0; out[2] = t0; return; }
+    int c2 = kexpdual_screen32(-(float)dr * (float)r0, -(float)ds * (float)s0, -(float)dt * (float)t0);
+    if (c2 == 0) c2 = in_kexp_dual(-dr * r0, -ds * s0, -dt * t0) ? 1 : -1;
+    if (c2 > 0) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
+    if (r0 <= 0.0 && s0 <= 0.0) { out[0] = r0; out[1] = 0.0; out[2] = t0 > 0.0 ? t0 : 0.0; return; }
+    // case 4: root in FP32
+    const bool in_range = fabs(r0) < 1e30 && fabs(s0) < 1e30 && fabs(t0) < 1e30 && (r0 == 0.0 || fabs(r0) > 1e-30) &&
+                          (s0 == 0.0 || fabs(s0) > 1e-30) && (t0 == 0.0 || fabs(t0) > 1e-30);
+    ExpCase4T<float> ef;
+    float Lf = 0.0f;
+    int evals = 0;
+    bool ok = in_range;
+    if (ok) {
+        exp_case4_setup(ef, r0, s0, t0, dr, ds, (float)lg[0], (float)lg[1], (float)lg[2]);
+        ok = fabsf(ef.a3) < 1e30f && fabsf(ef.a4) < 1e30f && exp_case4_solve(ef, L_cache ? *L_cache : NAN, Lf, evals) &&
+             isfinite(Lf);
+    }
+    if (ok) {
+        // FP64 polish from the FP32 root, same branch and anchor
+        ExpCase4 e;
+        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2]);
+        e.kind = ef.kind;
+        e.anchor = ef.anchor;
+        e.dir = (double)ef.dir;
+        double L = (double)Lf;
+        ok = false;
+        for (int it = 0; it < 3; ++it) {
+            double F, dF, rho, lsp, lrd, Fs;
+            exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
+            if (F == 0.0) { ok = true; break; }
+            const double step = F / dF;
+            if (!isfinite(step)) break;
+            L -= step;
+            if (fabs(step) <= RootTol<double>::newton * fmax(1.0, fabs(L))) { ok = true; break; }
+        }
+        if (ok) {
+            if (L_cache) *L_cache = (float)L;
+            exp_case4_output(e, L, r0, s0, t0, dr, ds, out);
+            return;
+        }
+    }
+    double Lc = L_cache ? (double)*L_cache : NAN;
+    exp_project(r0, s0, t0, dr, ds, dt, out, &Lc, nullptr);
+    if (L_cache) *L_cache = (float)Lc;
+}
+
+// Projection onto D^{-1} K_exp^* (Remark of App. A.2) with the mixed-precision search.
+__host__ __device__ __forceinline__ void exp_dual_project_fast(double r, double s, double t, double dr, double ds,
+                                                               double dt, const double* lg, double* out,
+                                                               float* L_cache) {
+    double p[3];
+    exp_project_fast(-r, -s, -t, dr, ds, dt, lg, p, L_cache);
     out[0] = r + p[0];
     out[1] = s + p[1];
     out[2] = t + p[2];

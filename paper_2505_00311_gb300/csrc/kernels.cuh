@@ -17,6 +17,7 @@
 // The cached products follow from linearity: K z^{k+1} = ha K zhat + hb K z^k + hc K z^0.
 #pragma once
 #include "common.cuh"
+#include "cone_f32.cuh"
 #include "cone_math.cuh"
 #include "state.h"
 
@@ -50,9 +51,12 @@ struct Dev {
     const int* soc_off;
     const int* soc_dim;
     const unsigned char* soc_rot;
-    double* soc_lam;
+    float* soc_lam;        // last SOC root per cone (FP32 start of the next search)
+    const double* soc_w;   // per SOC row: weight of the dual projection, (dr_row / dr_first)^2
+    const double* soc_wp;  // per SOC row: weight of the primal projection, (dr_first / dr_row)^2
     int exp_row0, n_exp;
-    double* exp_L;
+    float* exp_L;          // last log-offset per exp cone
+    const double* exp_lg;  // per exp cone: log dr of its three rows
     // blocks of the cone-structured kernels
     int nb_scal, nb_soc, nb_exp;
     int nb_primal;
@@ -69,6 +73,14 @@ struct Dev {
     // original-scale data for the unscaled KKT (FP64)
     const double* l_orig;
     const double* u_orig;
+    // scaled data in FP64 for the checks (equal to c, h, l, u when T is double)
+    const double* c64;
+    const double* h64;
+    const double* l64;
+    const double* u64;
+    // FP32 copies of the SOC weights and exp log-scales (FP32 iterates)
+    const float* soc_w32;
+    const float* exp_lg32;
 };
 
 // ---------------------------------------------------------------------------
@@ -264,8 +276,11 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
                 D.yh[o + i] = y + sigma * (D.h[o + i] - T(2) * p[o + i] + kx);
             }
             __syncwarp();
-            if (D.soc_rot[cidx]) rsoc_project_warp<true>(D.yh + o, D.dr + o, dim, D.soc_lam + cidx);
-            else soc_project_warp<true>(D.yh + o, D.dr + o, dim, D.soc_lam + cidx);
+            if constexpr (sizeof(T) == 8)
+                soc_project_any<true>(D.yh + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, D.soc_lam + cidx);
+            else
+                soc_project_any_f32(D.yh + o, D.soc_w32 + o + 1, D.scr + o, D.dr + o, dim, D.soc_rot[cidx] != 0,
+                                    D.soc_lam + cidx);
             for (int i = lane; i < dim; i += 32) {
                 const double dy = (double)D.yh[o + i] - (double)D.y[o + i];
                 acc[0] += dy * dy;
@@ -277,14 +292,18 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
         const int stride = D.nb_exp * blockDim.x;
         for (int e = (b - D.nb_scal - D.nb_soc) * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
             const int r = D.exp_row0 + 3 * e;
-            T y[3], kx[3];
-            double v[3], out[3];
+            T y[3], kx[3], v[3], out[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 dual_row_halpern(D, r + q, pend, ha, hb, hc, hw, pprev, y[q], kx[q]);
-                v[q] = (double)(y[q] + sigma * (D.h[r + q] - T(2) * p[r + q] + kx[q]));
+                v[q] = y[q] + sigma * (D.h[r + q] - T(2) * p[r + q] + kx[q]);
             }
-            exp_dual_project(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], out, D.exp_L + e, nullptr);
+            if constexpr (sizeof(T) == 8)
+                exp_dual_project_fast(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, out,
+                                      D.exp_L + e);
+            else
+                exp_dual_project_f32(v[0], v[1], v[2], (float)D.dr[r], (float)D.dr[r + 1], (float)D.dr[r + 2],
+                                     D.exp_lg32 + 3 * e, out, D.exp_L + e);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const T yh = (T)out[q];
@@ -353,7 +372,7 @@ __global__ void __launch_bounds__(kBlock) cand_primal(Dev<T> D) {
     const int stride = gridDim.x * blockDim.x;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
         const double s = q ? (double)D.xsum[j] * iw : (double)D.x[j];
-        out[j] = fmin(fmax(s, (double)D.l[j]), (double)D.u[j]);
+        out[j] = fmin(fmax(s, D.l64[j]), D.u64[j]);
     }
 }
 
@@ -382,15 +401,15 @@ __global__ void __launch_bounds__(kBlock) cand_dual(Dev<T> D) {
             const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
             for (int i = lane; i < dim; i += 32) out[o + i] = val(o + i);
             __syncwarp();
-            if (D.soc_rot[cidx]) rsoc_project_warp<true>(out + o, D.dr + o, dim, nullptr);
-            else soc_project_warp<true>(out + o, D.dr + o, dim, nullptr);
+            soc_project_any<true>(out + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, nullptr);
         }
     } else {
         const int stride = D.nb_exp * blockDim.x;
         for (int e = (b - D.nb_scal - D.nb_soc) * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
             const int r = D.exp_row0 + 3 * e;
             double o3[3];
-            exp_dual_project(val(r), val(r + 1), val(r + 2), D.dr[r], D.dr[r + 1], D.dr[r + 2], o3, nullptr, nullptr);
+            exp_dual_project_fast(val(r), val(r + 1), val(r + 2), D.dr[r], D.dr[r + 1], D.dr[r + 2],
+                                  D.exp_lg + 3 * e, o3, nullptr);
             out[r] = o3[0];
             out[r + 1] = o3[1];
             out[r + 2] = o3[2];
@@ -419,7 +438,7 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     auto common = [&](int i) {
-        sums[1] += (double)D.h[i] * yc[i];
+        sums[1] += D.h64[i] * yc[i];
         const double dy = yc[i] - (double)D.y0[i];
         sums[2] += dy * dy;
         mx[1] = fmax(mx[1], fabs(kx[i] / D.dr[i]));
@@ -427,7 +446,7 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
     if (b < D.nb_scal) {
         const int stride = D.nb_scal * blockDim.x;
         for (int i = b * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
-            const double v = kx[i] - (double)D.h[i];
+            const double v = kx[i] - D.h64[i];
             const double w = v / D.dr[i];
             double rs, ru, pu;
             if (i < D.m_zero) { rs = v; ru = w; pu = 0.0; }
@@ -443,23 +462,21 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
             const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
             const bool rot = D.soc_rot[cidx] != 0;
             // scaled residual: project v onto Dr K
-            for (int i = lane; i < dim; i += 32) s1[o + i] = kx[o + i] - (double)D.h[o + i];
+            for (int i = lane; i < dim; i += 32) s1[o + i] = kx[o + i] - D.h64[o + i];
             __syncwarp();
-            if (rot) rsoc_project_warp<false>(s1 + o, D.dr + o, dim, nullptr);
-            else soc_project_warp<false>(s1 + o, D.dr + o, dim, nullptr);
+            soc_project_any<false>(s1 + o, D.soc_wp + o + 1, D.dr + o, dim, rot, nullptr);
             for (int i = lane; i < dim; i += 32) {
-                const double v = kx[o + i] - (double)D.h[o + i];
+                const double v = kx[o + i] - D.h64[o + i];
                 const double r = v - s1[o + i];
                 sums[0] += r * r;
             }
             __syncwarp();
             // unscaled residual: project w = v / dr onto K (D = I)
-            for (int i = lane; i < dim; i += 32) s1[o + i] = (kx[o + i] - (double)D.h[o + i]) / D.dr[o + i];
+            for (int i = lane; i < dim; i += 32) s1[o + i] = (kx[o + i] - D.h64[o + i]) / D.dr[o + i];
             __syncwarp();
-            if (rot) rsoc_project_warp<false>(s1 + o, nullptr, dim, nullptr);
-            else soc_project_warp<false>(s1 + o, nullptr, dim, nullptr);
+            soc_project_any<false>(s1 + o, nullptr, nullptr, dim, rot, nullptr);
             for (int i = lane; i < dim; i += 32) {
-                const double w = (kx[o + i] - (double)D.h[o + i]) / D.dr[o + i];
+                const double w = (kx[o + i] - D.h64[o + i]) / D.dr[o + i];
                 mx[0] = fmax(mx[0], fabs(w - s1[o + i]));
                 mx[2] = fmax(mx[2], fabs(s1[o + i]));
                 common(o + i);
@@ -472,11 +489,12 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
             const int r = D.exp_row0 + 3 * e;
             double v[3], w[3], ps[3], pu[3];
             for (int k = 0; k < 3; ++k) {
-                v[k] = kx[r + k] - (double)D.h[r + k];
+                v[k] = kx[r + k] - D.h64[r + k];
                 w[k] = v[k] / D.dr[r + k];
             }
-            exp_project(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], ps, nullptr, nullptr);
-            exp_project(w[0], w[1], w[2], 1.0, 1.0, 1.0, pu, nullptr, nullptr);
+            const double lg0[3] = {0.0, 0.0, 0.0};
+            exp_project_fast(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, ps, nullptr);
+            exp_project_fast(w[0], w[1], w[2], 1.0, 1.0, 1.0, lg0, pu, nullptr);
             for (int k = 0; k < 3; ++k) {
                 const double rs = v[k] - ps[k];
                 sums[0] += rs * rs;
@@ -624,11 +642,11 @@ __global__ void __launch_bounds__(kBlock) kkt_dual(Dev<T> D) {
         double mx[2] = {0.0, 0.0};
         const int stride = gridDim.x * blockDim.x;
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
-            const double ls = (double)D.l[j], us = (double)D.u[j];
-            const double lam = (double)D.c[j] - kty[j];
+            const double ls = D.l64[j], us = D.u64[j];
+            const double lam = D.c64[j] - kty[j];
             const double mu = proj_lambda(lam, ls, us);
             sums[0] += (lam - mu) * (lam - mu);
-            sums[1] += (double)D.c[j] * xc[j];
+            sums[1] += D.c64[j] * xc[j];
             if (mu > 0.0) sums[2] += ls * mu;
             if (mu < 0.0) sums[2] += us * mu;
             const double dx = xc[j] - (double)D.x0[j];

@@ -106,4 +106,28 @@ __global__ void scale_by_inv(long long k, const double* __restrict__ u, const do
         v[i] = u[i] * inv;
 }
 
+// Per SOC row: weights of the dual projection onto Dr^{-1} K_soc, (dr_row / dr_first)^2,
+// and of the primal projection onto Dr K_soc, (dr_first / dr_row)^2 (Theorem 1: w = dhat^-2).
+__global__ void cone_constants(int n_soc, const int* __restrict__ off, const int* __restrict__ dim,
+                               const double* __restrict__ dr, double* w, double* wp) {
+    const int lane = threadIdx.x & 31;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= n_soc) return;
+    const int o = off[c], d = dim[c];
+    const double d0 = dr[o];
+    for (int i = lane; i < d; i += 32) {
+        if (i == 0) { w[o] = 1.0; wp[o] = 1.0; continue; }
+        const double q = dr[o + i] / d0, p = d0 / dr[o + i];
+        w[o + i] = q * q;
+        wp[o + i] = p * p;
+    }
+}
+
+// Per exp cone: log dr of its three rows (scales of the rescaled cone, Theorem 3).
+__global__ void exp_constants(int n_exp, int row0, const double* __restrict__ dr, double* lg) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_exp) return;
+    for (int k = 0; k < 3; ++k) lg[3 * e + k] = log(dr[row0 + 3 * e + k]);
+}
+
 }  // namespace pdcs

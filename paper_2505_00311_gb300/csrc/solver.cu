@@ -76,7 +76,8 @@ struct pdcs_ctx {
     unsigned char* soc_rot = nullptr;
     int *tie_off = nullptr, *tie_len = nullptr;
     int n_tie = 0;
-    double *soc_lam = nullptr, *exp_L = nullptr;
+    float *soc_lam = nullptr, *exp_L = nullptr;
+    double *soc_w = nullptr, *soc_wp = nullptr, *exp_lg = nullptr;
     double* part = nullptr;
     Ctrl* ctrl = nullptr;
     double* scal = nullptr;  // small scalar scratch
@@ -142,9 +143,12 @@ int choose_lanes(long long nnz, long long rows) {
     return std::min(32, std::max(2, g));
 }
 
+// Kernel classes of pdcs_kernel_times (see include/pdcs.h).
+constexpr int kKernelClasses = 12;
+
 // Optional CUDA-event recorder for kernel timing: event pairs per kernel class.
 struct Prof {
-    std::vector<cudaEvent_t> ev[5];
+    std::vector<cudaEvent_t> ev[kKernelClasses];
     void mark(int cls, cudaStream_t s) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) == cudaSuccess) {
@@ -178,23 +182,32 @@ void enqueue_attempt(pdcs_ctx* ctx, Prof* P = nullptr) {
 void enqueue_check(pdcs_ctx* ctx, Prof* P = nullptr) {
     cudaStream_t s = ctx->stream;
     Dev<double>& D = ctx->D;
-    if (P) P->mark(4, s);
+    auto mark = [&](int c) { if (P) P->mark(c, s); };
+    mark(4);
     ctx->launches += kLaunchesPerCheck;
+    mark(5);
     flush_primal<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
     flush_dual<double><<<ctx->g_vec_m, kBlock, 0, s>>>(D);
+    mark(5); mark(6);
     cand_primal<double><<<dim3(ctx->g_vec_n, 2), kBlock, 0, s>>>(D);
+    mark(6); mark(7);
     cand_dual<double><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(D);
+    mark(7); mark(8);
     for (int q = 0; q < 2; ++q) {
         launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, ctx->m, D.rp, D.ci, D.val, D.xc + (size_t)q * ctx->n,
                                     D.kxc + (size_t)q * ctx->m, nullptr, D.ctrl, 0, 1);
         launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, ctx->n, D.rpT, D.ciT, D.valT,
                                     D.yc + (size_t)q * ctx->m, D.ktyc + (size_t)q * ctx->n, nullptr, D.ctrl, 0, 1);
     }
+    mark(8); mark(9);
     kkt_primal<double><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(D);
+    mark(9); mark(10);
     kkt_dual<double><<<ctx->g_kktd, kBlock, 0, s>>>(D);
+    mark(10); mark(11);
     restart_primal<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
     restart_dual<double><<<ctx->g_vec_m, kBlock, 0, s>>>(D);
-    if (P) P->mark(4, s);
+    mark(11);
+    mark(4);
 }
 
 __global__ void clear_pending(Ctrl* C) { C->pending = 0; }
@@ -330,7 +343,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     A.reserve<double>(m); A.reserve<double>(n); A.reserve<double>(m); A.reserve<double>(n);  // dr dc rn cn
     A.reserve<int>(ctx->n_soc + 1); A.reserve<int>(ctx->n_soc + 1); A.reserve<unsigned char>(ctx->n_soc + 1);
     A.reserve<int>(ctx->n_tie + 1); A.reserve<int>(ctx->n_tie + 1);
-    A.reserve<double>(ctx->n_soc + 1); A.reserve<double>(ctx->n_exp + 1);
+    A.reserve<float>(ctx->n_soc + 1); A.reserve<float>(ctx->n_exp + 1);
+    A.reserve<double>(m); A.reserve<double>(m); A.reserve<double>(3LL * ctx->n_exp + 1);
     A.reserve<double>(pl.total);
     A.reserve<Ctrl>(1);
     A.reserve<double>(16);
@@ -357,7 +371,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     ctx->soc_off = A.take<int>(ctx->n_soc + 1); ctx->soc_dim = A.take<int>(ctx->n_soc + 1);
     ctx->soc_rot = A.take<unsigned char>(ctx->n_soc + 1);
     ctx->tie_off = A.take<int>(ctx->n_tie + 1); ctx->tie_len = A.take<int>(ctx->n_tie + 1);
-    ctx->soc_lam = A.take<double>(ctx->n_soc + 1); ctx->exp_L = A.take<double>(ctx->n_exp + 1);
+    ctx->soc_lam = A.take<float>(ctx->n_soc + 1); ctx->exp_L = A.take<float>(ctx->n_exp + 1);
+    ctx->soc_w = A.take<double>(m); ctx->soc_wp = A.take<double>(m); ctx->exp_lg = A.take<double>(3LL * ctx->n_exp + 1);
     ctx->part = A.take<double>(pl.total);
     ctx->ctrl = A.take<Ctrl>(1);
     ctx->scal = A.take<double>(16);
@@ -465,7 +480,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.c = ctx->cs; D.h = ctx->hs; D.l = ctx->ls; D.u = ctx->us; D.dr = ctx->dr; D.dc = ctx->dc;
     D.m_zero = ctx->m_zero; D.m_scalar = ctx->m_scalar;
     D.n_soc = ctx->n_soc; D.soc_off = ctx->soc_off; D.soc_dim = ctx->soc_dim; D.soc_rot = ctx->soc_rot;
-    D.soc_lam = ctx->soc_lam;
+    D.soc_lam = ctx->soc_lam; D.soc_w = ctx->soc_w; D.soc_wp = ctx->soc_wp; D.exp_lg = ctx->exp_lg;
     D.exp_row0 = ctx->exp_row0; D.n_exp = ctx->n_exp; D.exp_L = ctx->exp_L;
     D.nb_scal = nb_scal; D.nb_soc = nb_soc; D.nb_exp = nb_exp; D.nb_primal = ctx->g_vec_n;
     D.part = ctx->part; D.pl = pl; D.ctrl = ctx->ctrl;
@@ -482,9 +497,14 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     C.status = kRunning;
     *ctx->h_ctrl = C;
     CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
-    std::vector<double> nanv(std::max(ctx->n_soc, ctx->n_exp) + 1, NAN);
-    CK(cudaMemcpyAsync(ctx->exp_L, nanv.data(), sizeof(double) * (ctx->n_exp + 1), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->soc_lam, nanv.data(), sizeof(double) * (ctx->n_soc + 1), cudaMemcpyHostToDevice, s));
+    std::vector<float> nanv(std::max(ctx->n_soc, ctx->n_exp) + 1, NAN);
+    CK(cudaMemcpyAsync(ctx->exp_L, nanv.data(), sizeof(float) * (ctx->n_exp + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->soc_lam, nanv.data(), sizeof(float) * (ctx->n_soc + 1), cudaMemcpyHostToDevice, s));
+    if (ctx->n_soc)
+        cone_constants<<<(ctx->n_soc + kWarpsPerBlock - 1) / kWarpsPerBlock, kBlock, 0, s>>>(
+            ctx->n_soc, ctx->soc_off, ctx->soc_dim, ctx->dr, ctx->soc_w, ctx->soc_wp);
+    if (ctx->n_exp)
+        exp_constants<<<(ctx->n_exp + 255) / 256, 256, 0, s>>>(ctx->n_exp, ctx->exp_row0, ctx->dr, ctx->exp_lg);
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     return PDCS_OK;
@@ -823,7 +843,7 @@ pdcs_status pdcs_kernel_times(pdcs_ctx* ctx, int64_t attempts, double* ms, int64
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
-    for (int c = 0; c < 5; ++c) {
+    for (int c = 0; c < kKernelClasses; ++c) {
         double tot = 0.0;
         const size_t pairs = P.ev[c].size() / 2;
         for (size_t i = 0; i < pairs; ++i) {

@@ -210,13 +210,14 @@ def pdcs_set_warm_start(ctx, x=None, y=None, omega=0.0):
         raise PdcsError(st, pdcs_last_error(ctx))
 
 
-KERNEL_CLASSES = ["primal_update", "spmv_K", "dual_update", "spmv_KT", "check"]
+KERNEL_CLASSES = ["primal_update", "spmv_K", "dual_update", "spmv_KT", "check", "check_flush", "check_cand_primal",
+                  "check_cand_dual", "check_spmv", "check_kkt_primal", "check_kkt_dual", "check_restart"]
 
 
 def pdcs_kernel_times(ctx, attempts):
     """Average ms per launch of each kernel class over `attempts` evaluations (CUDA events)."""
-    ms = np.zeros(5)
-    cnt = np.zeros(5, dtype=np.int64)
+    ms = np.zeros(len(KERNEL_CLASSES))
+    cnt = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
     st = lib().pdcs_kernel_times(ctx, int(attempts), _ptr(ms), _ptr(cnt, _i64p))
     if st != OK:
         raise PdcsError(st, pdcs_last_error(ctx))

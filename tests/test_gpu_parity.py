@@ -93,6 +93,17 @@ def test_exp_projection_stressed():
     got = _gpu_proj(v, d, np.full(n, 4, np.int32), np.full(n, 3, np.int64), 0)
     for k, (v0, _, vp) in enumerate(rows):
         assert np.linalg.norm(got[3 * k:3 * k + 3] - vp) <= 1e-12 * np.linalg.norm(v0)
+    # dual iterates of inactive cones seen in solves: on the boundary of the polar cone up to
+    # rounding, where h vanishes at the end of the interval (Theorem 3, case 4)
+    deg = [([-4.299415668154342e-08, -7.8494703047673784e-09, 1.4137525101037436e-08],
+            [0.27129145063712506, 0.16152428936374849, 0.33836530019446764]),
+           ([-2.2567689319081326e-09, -3.3480056589393299e-09, 2.6134468709930082e-09],
+            [0.23750319892672211, 0.27946832641398711, 0.43229814581167908])]
+    v = np.concatenate([np.array(a) for a, _ in deg])
+    d = np.concatenate([np.array(b) for _, b in deg])
+    got = _gpu_proj(v, 1 / d, np.full(2, 4, np.int32), np.full(2, 3, np.int64), 1)
+    ref = oracle.proj_cones(v, [4, 4], [3, 3], 1 / d, dual=True)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(v)
 
 
 # ---------------------------------------------------------------------------
