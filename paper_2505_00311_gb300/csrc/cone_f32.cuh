@@ -13,7 +13,7 @@ namespace pdcs {
 // SOC, entries in registers (dim - 1 <= 32 R), weights w_i = dhat_i^{-2}
 // ---------------------------------------------------------------------------
 template <int R>
-__device__ void soc_project_warp_f32(float* buf, const float* __restrict__ w, int dim, float* lam_cache) {
+__device__ void soc_project_warp_f32(float* buf, const float* __restrict__ w, int dim, float* cache) {
     const int lane = threadIdx.x & 31;
     const int nx = dim - 1;
     const float t = buf[0];
@@ -44,56 +44,41 @@ __device__ void soc_project_warp_f32(float* buf, const float* __restrict__ w, in
         return;
     }
     if (nDinvx <= t) return;  // case 2
-    float lam = 0.5f;         // case 3
-    if (t != 0.0f) {          // case 4: safeguarded Newton on G(l) = (1 - 2l)^2 S(l) - t^2
-        auto G = [&](float l, float& g, float& dg) {
-            float S = 0.0f, S1 = 0.0f;
+    float mu = 1.0f;          // 2 lambda; case 3
+    if (t != 0.0f) {          // case 4: search variable as in cone_math.cuh
+        bool known, near = t > 0.0f && soc_cached_near(cache, known);
+        if (t > 0.0f && !known) {  // sign of phi at mu = 1/2
+            float S = 0.0f;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                const float r = __frcp_rn(1.0f + 2.0f * l * wr[k]);
+                const float r = __frcp_rn(1.0f + 0.5f * wr[k]);
+                S += wr[k] * xr[k] * xr[k] * r * r;
+            }
+            near = 0.5f * sqrtf(warp_sum_f(S)) < t;
+        }
+        const SocVar<float> V(t, near);
+        auto ev = [&](float u, float& ph, float& dph, float& sc) {
+            float S = 0.0f, S2 = 0.0f;
+            const float m = V.mu(u);
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const float r = __frcp_rn(1.0f + m * wr[k]);
                 const float term = wr[k] * xr[k] * xr[k] * r * r;
                 S += term;
-                S1 -= 4.0f * wr[k] * term * r;
+                S2 += wr[k] * term * r;
             }
             S = warp_sum_f(S);
-            S1 = warp_sum_f(S1);
-            const float u = 1.0f - 2.0f * l;
-            g = u * u * S - t * t;
-            dg = -4.0f * u * S + u * u * S1;
+            S2 = warp_sum_f(S2);
+            V.phi(u, sqrtf(S), S2, ph, dph, sc);
         };
-        float lo, hi, g, dg;
-        int slo;
-        if (t > 0.0f) {
-            lo = 0.0f; hi = 0.5f; slo = 1;
-        } else {
-            lo = 0.5f; hi = 1.0f; slo = -1;
-            for (int it = 0; it < 130; ++it) {
-                G(hi, g, dg);
-                if (g > 0.0f || !(hi < 1e30f)) break;
-                lo = hi;
-                hi *= 2.0f;
-            }
-        }
-        float guess = (nDinvx - t) / (2.0f * (nDinvx + t));
-        if (lam_cache && *lam_cache > lo && *lam_cache < hi) guess = *lam_cache;
-        lam = (guess > lo && guess < hi) ? guess : 0.5f * (lo + hi);
-        for (int it = 0; it < 100; ++it) {
-            G(lam, g, dg);
-            if (!(g == g) || g == 0.0f) break;
-            if ((g > 0.0f ? 1 : -1) == slo) lo = lam; else hi = lam;
-            float nl = lam - g / dg;
-            if (nl >= lo && nl <= hi && fabsf(nl - lam) <= 2e-6f * lam) { lam = nl; break; }
-            if (!(nl > lo && nl < hi)) nl = 0.5f * (lo + hi);
-            const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 2e-7f * hi;
-            lam = nl;
-            if (done) break;
-        }
-        if (lam_cache && lane == 0) *lam_cache = lam;
+        const float u = soc_root<float>(ev, V.tpos, V.guess(t, nDinvx, cache), 2e-6f, 2e-7f, 100);
+        if (cache && lane == 0) *cache = V.store(u);
+        mu = V.mu(u);
     }
     float s = 0.0f;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        const float y = xr[k] / (1.0f + 2.0f * lam * wr[k]);
+        const float y = xr[k] / (1.0f + mu * wr[k]);
         s += wr[k] * y * y;
         if (lane + 32 * k < nx) buf[1 + lane + 32 * k] = y;
     }
@@ -108,7 +93,7 @@ __device__ void soc_project_warp_f32(float* buf, const float* __restrict__ w, in
 // onto Dr^{-1} K (kInv, scales dr).
 __device__ __forceinline__ void soc_project_any_f32(float* buf, const float* __restrict__ w32, double* tmp,
                                                     const double* __restrict__ dr, int dim, bool rot,
-                                                    float* lam_cache) {
+                                                    float* cache) {
     const int lane = threadIdx.x & 31;
     const float r2 = 0.70710678118654752440f;
     const int nx = dim - 1;
@@ -128,10 +113,10 @@ __device__ __forceinline__ void soc_project_any_f32(float* buf, const float* __r
     }
     __syncwarp();
     const int R = (nx + 31) / 32;
-    if (R <= 1) soc_project_warp_f32<1>(buf, w32, dim, lam_cache);
-    else if (R == 2) soc_project_warp_f32<2>(buf, w32, dim, lam_cache);
-    else if (R == 3) soc_project_warp_f32<3>(buf, w32, dim, lam_cache);
-    else soc_project_warp_f32<4>(buf, w32, dim, lam_cache);
+    if (R <= 1) soc_project_warp_f32<1>(buf, w32, dim, cache);
+    else if (R == 2) soc_project_warp_f32<2>(buf, w32, dim, cache);
+    else if (R == 3) soc_project_warp_f32<3>(buf, w32, dim, cache);
+    else soc_project_warp_f32<4>(buf, w32, dim, cache);
     if (rot && lane == 0) {
         const float p = buf[0], q = buf[1];
         buf[0] = (p + q) * r2;

@@ -1,15 +1,12 @@
 // cone_math.cuh -- device projections onto diagonally rescaled cones.
 //
 // SOC: Theorem 1 (Sec. 3; proof in App. A.1).  Cases 1-3 in closed form; in
-//      case 4 the root lambda of eq. (bisection-soc) is found by Newton's method
-//      on the equivalent monotone function
-//          G(lambda) = (1 - 2 lambda)^2 S(lambda) - t^2,
-//          S(lambda) = sum_i w_i x_i^2 / (1 + 2 lambda w_i)^2,   w_i = dhat_i^{-2},
-//      (G = (1 - 2 lambda)^2 f(lambda) has the sign of f), safeguarded by the
-//      bracket (0, 1/2) for t > 0 and (1/2, hi) for t < 0.  One warp per cone;
-//      the last root is kept per cone and used as the next starting point.
-//      The first entry of the result is ||Dhat^{-1} y|| (the active constraint of
-//      eq. kkt_sys_fixed_2), which equals t / (1 - 2 lambda) at the root.
+//      case 4 the root of eq. (bisection-soc) is found by safeguarded Newton on
+//      the equivalent monotone function phi(g) of g = |1 - 2 lambda| (see below).
+//      One warp per cone; the last root is kept per cone and used as the next
+//      starting point.  The first entry of the result is ||Dhat^{-1} y|| (the
+//      active constraint of eq. kkt_sys_fixed_2), which equals t / (1 - 2 lambda)
+//      at the root.
 // EXP: Theorem 3 (App. A.2).  Cases 1-3 in closed form with log-form membership
 //      tests; in case 4 the root of h (eq. h_rho) on (l_rho, u_rho) is found by
 //      Newton's method on the logarithm L of the offset of rho from an endpoint
@@ -31,6 +28,24 @@ constexpr double RootTolSoc = 1e-10;
 
 // ---------------------------------------------------------------------------
 // Second-order cone
+//
+// Case 4 of Theorem 1 puts lambda in (0, 1/2) for t > 0 and in (1/2, inf) for
+// t < 0.  With mu = 2 lambda and w_i = dhat_i^{-2}, the root of eq. (bisection-soc)
+// multiplied by (1 - mu)^2 and square-rooted is the root of
+//     |1 - mu| sqrt(S(mu)) = |t|,   S(mu) = sum_i w_i x_i^2 / (1 + mu w_i)^2,
+// whose left side moves away from |t| monotonically as mu leaves 1.  The search runs
+// on a variable u chosen so that the root is a small u where it needs relative
+// precision:
+//   t > 0, root at mu >= 1/2:  u = 1 - mu in (0, 1)  (nearly inactive cones: u ~ t)
+//   t > 0, root at mu < 1/2:   u = mu in (0, 1)      (v almost in the cone: u ~ 0)
+//   t < 0:                     u = mu - 1 in (0, inf)
+// (for t > 0 the half is read off the cached root or the sign of phi at mu = 1/2, and
+// Newton's relative stopping test uses the smaller of u and 1 - u)
+// In each, phi(u) = (u - pm) sqrt(S) - c increases in u and is negative at u = 0
+// (pm = 0, c = |t| for the first and last; pm = 1, c = -t for the second), and it is
+// nearly affine in u near u = 0, so Newton with a relative test on u converges in a
+// few steps.  The projection is y = (I + mu Dhat^{-2})^{-1} x, s = ||Dhat^{-1} y||
+// (the active constraint of eq. kkt_sys_fixed_2).
 // ---------------------------------------------------------------------------
 // Weight of entry i (0-based over the x part) for the projection onto E K_soc,
 // E = diag(e_0, e_1, ...): dhat_i = e_{i+1} / e_0 and w_i = dhat_i^{-2}.
@@ -42,12 +57,102 @@ __device__ __forceinline__ double soc_weight(const double* __restrict__ d, doubl
     return q * q;
 }
 
-// Projects the SOC block stored at buf[0..dim) in place onto E K_soc (E as
-// above).  Called by all 32 lanes of a warp with identical arguments.
-// lam_cache (may be null): last root of this cone, updated.
-// Returns the number of Newton / bisection evaluations (for diagnostics).
+// The search variable of case 4 (see above): mu = a0 + a1 u, phi = (u - pm) sqrt(S) - c.
+// near (t > 0 only): the root has mu < 1/2, decided from the cached root or from the
+// sign of phi at mu = 1/2 (soc_near).  The cached value of a cone is u, negated for
+// the variable mu next to the cone.
+template <typename R>
+struct SocVar {
+    R a0, a1, pm, c;
+    bool near, tpos;
+    __device__ __forceinline__ SocVar(R t, bool near_) {
+        tpos = t > R(0);
+        near = tpos && near_;
+        const R at = fabs(t);
+        if (near) { a0 = R(0); a1 = R(1); pm = R(1); c = -at; }
+        else if (tpos) { a0 = R(1); a1 = R(-1); pm = R(0); c = at; }
+        else { a0 = R(1); a1 = R(1); pm = R(0); c = at; }
+    }
+    // Start: the cached u (converted between the two t > 0 variables), else the root
+    // when Dhat = I.
+    __device__ __forceinline__ R guess(R t, R nDinvx, const float* cache) const {
+        const R at = fabs(t);
+        R u = near ? (nDinvx - at) / (nDinvx + at)
+                   : (tpos ? R(2) * at / (nDinvx + at) : (nDinvx > at ? R(2) * at / (nDinvx - at) : R(-1)));
+        if (cache) {
+            const R cv = (R)*cache;
+            R cu = R(-1);
+            if (!tpos) cu = cv;
+            else if (near) cu = cv < R(0) ? -cv : R(1) - cv;
+            else cu = cv > R(0) ? cv : R(1) + cv;
+            if (cu > R(0) && (!tpos || cu < R(1))) u = cu;
+        }
+        return u;
+    }
+    // the same variable in another precision
+    template <typename Q>
+    __device__ __forceinline__ explicit SocVar(const SocVar<Q>& o)
+        : a0(R(o.a0)), a1(R(o.a1)), pm(R(o.pm)), c(R(o.c)), near(o.near), tpos(o.tpos) {}
+    __device__ __forceinline__ float store(R u) const { return near ? -(float)u : (float)u; }
+    __device__ __forceinline__ R mu(R u) const { return a0 + a1 * u; }
+    // phi and dphi/du from sq = sqrt(S) and S2 = sum w_i^2 x_i^2 / (1 + mu w_i)^3; sc is
+    // the size of the terms of phi (its rounding error is a few ulps of sc)
+    __device__ __forceinline__ void phi(R u, R sq, R S2, R& ph, R& dph, R& sc) const {
+        const R p = u - pm;
+        ph = p * sq - c;
+        dph = sq - p * a1 * S2 / sq;
+        sc = fabs(p) * sq + fabs(c);
+    }
+};
+
+// For t > 0: whether the cached root (see SocVar) has mu < 1/2; false with known = false
+// when the cache holds no usable value.
+__device__ __forceinline__ bool soc_cached_near(const float* cache, bool& known) {
+    known = false;
+    if (!cache) return false;
+    const float cv = *cache;
+    const float mu = cv < 0.0f ? -cv : 1.0f - cv;
+    known = cv == cv && cv != 0.0f && mu > 0.0f && mu < 1.0f;
+    return known && mu < 0.5f;
+}
+
+// Safeguarded Newton for phi(u) = 0 given an evaluator ev(u, phi, dphi, sc) (warp-
+// uniform results), with phi(0) < 0.  hi: 1 for t > 0; found by doubling for t < 0.
+// Stops on a relative Newton step below tol, on a bracket collapsed to collapse
+// relative, or on |phi| within 4 collapse of sc (zero to working precision: next to
+// the cone u is then fixed only to a few ulps, absolutely).
+template <typename R, typename Ev>
+__device__ __forceinline__ R soc_root(Ev ev, bool tpos, R guess, R tol, R collapse, int max_it) {
+    R lo = R(0), hi = R(1), ph, dph, sc;
+    if (!tpos) {
+        for (int it = 0; it < 1100; ++it) {
+            ev(hi, ph, dph, sc);
+            if (ph > R(0) || !(hi < (sizeof(R) == 4 ? R(1e30) : R(1e300)))) break;
+            lo = hi;
+            hi *= R(2);
+        }
+    }
+    R g = (guess > lo && guess < hi) ? guess : R(0.5) * (lo + hi);
+    for (int it = 0; it < max_it; ++it) {
+        ev(g, ph, dph, sc);
+        if (!(ph == ph) || fabs(ph) <= R(4) * collapse * sc) break;
+        if (ph < R(0)) lo = g; else hi = g;
+        R ng = g - ph / dph;
+        // relative to the smaller of u and 1 - u for t > 0 (both mu and 1 - mu matter)
+        if (ng >= lo && ng <= hi && fabs(ng - g) <= tol * (tpos ? fmin(g, R(1) - g) : g)) { g = ng; break; }
+        if (!(ng > lo && ng < hi)) ng = R(0.5) * (lo + hi);
+        const bool done = !(ng > lo && ng < hi) || (hi - lo) <= collapse * hi;
+        g = ng;
+        if (done) break;
+    }
+    return g;
+}
+
+// Projects the SOC block stored at buf[0..dim) in place onto E K_soc (E as above),
+// entries read from memory (any dim).  Called by all 32 lanes of a warp with
+// identical arguments.  cache (may be null): last u of this cone (see SocVar), updated.
 template <bool kInv>
-__device__ int soc_project_warp(double* buf, const double* __restrict__ d, int dim, double* lam_cache) {
+__device__ int soc_project_warp(double* buf, const double* __restrict__ d, int dim, float* cache) {
     const int lane = threadIdx.x & 31;
     const int nx = dim - 1;
     const double t = buf[0];
@@ -68,69 +173,44 @@ __device__ int soc_project_warp(double* buf, const double* __restrict__ d, int d
         return 0;
     }
     if (nDinvx <= t) return 0;    // case 2: in the cone
-    double lam;
+    double mu = 1.0;              // 2 lambda; case 3 (t == 0): lambda = 1/2
     int evals = 0;
-    if (t == 0.0) {               // case 3: lambda = 1/2
-        lam = 0.5;
-    } else {                      // case 4
-        double lo, hi;
-        int slo;
-        auto G = [&](double l, double& g, double& dg) {
-            double S = 0.0, S1 = 0.0;
+    if (t != 0.0) {               // case 4
+        bool known, near = t > 0.0 && soc_cached_near(cache, known);
+        if (t > 0.0 && !known) {  // sign of phi at mu = 1/2
+            double S = 0.0;
             for (int i = lane; i < nx; i += 32) {
-                double x = buf[1 + i], w = soc_weight<kInv>(d, d0, i);
-                double r = 1.0 / (1.0 + 2.0 * l * w);
-                double term = w * x * x * r * r;
+                const double x = buf[1 + i], w = soc_weight<kInv>(d, d0, i);
+                const double r = 1.0 / (1.0 + 0.5 * w);
+                S += w * x * x * r * r;
+            }
+            near = 0.5 * sqrt(warp_sum(S)) < t;
+        }
+        const SocVar<double> V(t, near);
+        auto ev = [&](double u, double& ph, double& dph, double& sc) {
+            double S = 0.0, S2 = 0.0;
+            const double m = V.mu(u);
+            for (int i = lane; i < nx; i += 32) {
+                const double x = buf[1 + i], w = soc_weight<kInv>(d, d0, i);
+                const double r = 1.0 / (1.0 + m * w);
+                const double term = w * x * x * r * r;
                 S += term;
-                S1 -= 4.0 * w * term * r;
+                S2 += w * term * r;
             }
             S = warp_sum(S);
-            S1 = warp_sum(S1);
-            double u = 1.0 - 2.0 * l;
-            g = u * u * S - t * t;
-            dg = -4.0 * u * S + u * u * S1;
-        };
-        double g, dg;
-        if (t > 0.0) {
-            lo = 0.0; hi = 0.5; slo = 1;
-        } else {
-            lo = 0.5; hi = 1.0; slo = -1;
-            for (int it = 0; it < 1100; ++it) {  // G(hi) -> ||Dhat x||^2 - t^2 > 0
-                G(hi, g, dg);
-                ++evals;
-                if (g > 0.0) break;
-                lo = hi;
-                hi *= 2.0;
-            }
-        }
-        double guess = (nDinvx - t) / (2.0 * (nDinvx + t));  // exact root when Dhat = I
-        if (lam_cache && *lam_cache > lo && *lam_cache < hi) guess = *lam_cache;
-        lam = (guess > lo && guess < hi) ? guess : 0.5 * (lo + hi);
-        for (int it = 0; it < 200; ++it) {
-            G(lam, g, dg);
+            S2 = warp_sum(S2);
+            V.phi(u, sqrt(S), S2, ph, dph, sc);
             ++evals;
-            if (g == 0.0) break;
-            int s = g > 0.0 ? 1 : -1;
-            if (s == slo) lo = lam; else hi = lam;
-            double nl = lam - g / dg;
-            // a Newton step below 1e-10 relative leaves an error of order its square
-            // (lam itself has just become an end of the bracket, so test this first)
-            if (nl >= lo && nl <= hi && fabs(nl - lam) <= RootTolSoc * lam) {
-                lam = nl;
-                break;
-            }
-            if (!(nl > lo && nl < hi)) nl = 0.5 * (lo + hi);
-            const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 4e-16 * hi;
-            lam = nl;
-            if (done) break;
-        }
-        if (lam_cache && lane == 0) *lam_cache = lam;
+        };
+        const double u = soc_root<double>(ev, V.tpos, V.guess(t, nDinvx, cache), RootTolSoc, 4e-16, 200);
+        if (cache && lane == 0) *cache = V.store(u);
+        mu = V.mu(u);
     }
     // y = (I + 2 lambda Dhat^{-2})^{-1} x ;  s = ||Dhat^{-1} y||
     double s = 0.0;
     for (int i = lane; i < nx; i += 32) {
         double x = buf[1 + i], w = soc_weight<kInv>(d, d0, i);
-        double y = x / (1.0 + 2.0 * lam * w);
+        double y = x / (1.0 + mu * w);
         s += w * y * y;
         buf[1 + i] = y;
     }
@@ -144,7 +224,7 @@ __device__ int soc_project_warp(double* buf, const double* __restrict__ d, int d
 // Rotated SOC as Q K_soc with Q = [[1, 1], [1, -1]] / sqrt2 (+) I: with equal
 // scales on the first two rows, Proj_{E K_rsoc}(v) = Q Proj_{E K_soc}(Q v).
 template <bool kInv>
-__device__ int rsoc_project_warp(double* buf, const double* __restrict__ d, int dim, double* lam_cache) {
+__device__ int rsoc_project_warp(double* buf, const double* __restrict__ d, int dim, float* cache) {
     const int lane = threadIdx.x & 31;
     const double r2 = 0.70710678118654752440;
     __syncwarp();
@@ -154,7 +234,7 @@ __device__ int rsoc_project_warp(double* buf, const double* __restrict__ d, int 
         buf[1] = (p - q) * r2;
     }
     __syncwarp();
-    int ev = soc_project_warp<kInv>(buf, d, dim, lam_cache);
+    int ev = soc_project_warp<kInv>(buf, d, dim, cache);
     if (lane == 0) {
         double p = buf[0], q = buf[1];
         buf[0] = (p + q) * r2;
@@ -166,8 +246,8 @@ __device__ int rsoc_project_warp(double* buf, const double* __restrict__ d, int 
 
 // ---------------------------------------------------------------------------
 // Second-order cone, mixed precision (cones with dim - 1 <= 32 R): the entries
-// stay in registers, weights w_i come precomputed, the root of G is found in FP32
-// and polished by at most three FP64 Newton steps, in which 1 / (1 + 2 lambda w) is
+// stay in registers, weights w_i come precomputed, the root of phi is found in
+// FP32 and polished by at most three FP64 Newton steps, in which 1 / (1 + mu w) is
 // an FP32 reciprocal refined by two Newton-Raphson steps r <- r (2 - a r) in FP64.
 // Whatever the FP32 pass cannot settle falls back to the full FP64 search.
 // ---------------------------------------------------------------------------
@@ -184,9 +264,9 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 }
 
 // buf[0..dim): the block, projected in place onto E K_soc where the weight of x entry
-// i is w[i] = dhat_i^{-2} (w may be null: all ones).  lam_cache may be null.
+// i is w[i] = dhat_i^{-2} (w may be null: all ones).  cache may be null.
 template <int R>
-__device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w, int dim, float* lam_cache) {
+__device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w, int dim, float* cache) {
     const int lane = threadIdx.x & 31;
     const int nx = dim - 1;
     const double t = buf[0];
@@ -217,9 +297,8 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
         return;
     }
     if (nDinvx <= t) return;  // case 2
-    double lam = 0.5;         // case 3 (t == 0)
+    double mu = 1.0;          // case 3 (t == 0)
     if (t != 0.0) {           // case 4
-        // ---- FP32 root of G(l) = (1 - 2l)^2 S(l) - t^2
         float xf[R], wf[R];
         bool rng = fabs(t) < 1e30 && fabs(t) > 1e-30 && nDinvx < 1e30;
 #pragma unroll
@@ -229,132 +308,107 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
             rng = rng && wr[k] < 1e30 && wr[k] > 1e-30;
         }
         rng = __all_sync(0xffffffffu, rng);
-        const float tf = (float)t;
-        auto G32 = [&](float l, float& g, float& dg) {
-            float S = 0.0f, S1 = 0.0f;
+        bool known, near = t > 0.0 && soc_cached_near(cache, known);
+        if (t > 0.0 && !known) {  // sign of phi at mu = 1/2
+            if (rng) {
+                float S = 0.0f;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const float r = __frcp_rn(1.0f + 0.5f * wf[k]);
+                    S += wf[k] * xf[k] * xf[k] * r * r;
+                }
+                near = 0.5f * sqrtf(warp_sum_f(S)) < (float)t;
+            } else {
+                double S = 0.0;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const double r = 1.0 / (1.0 + 0.5 * wr[k]);
+                    S += wr[k] * xr[k] * xr[k] * r * r;
+                }
+                near = 0.5 * sqrt(warp_sum(S)) < t;
+            }
+        }
+        const SocVar<double> V(t, near);
+        // ---- FP32 root of phi
+        const SocVar<float> Vf(V);
+        auto ev32 = [&](float u, float& ph, float& dph, float& sc) {
+            float S = 0.0f, S2 = 0.0f;
+            const float m = Vf.mu(u);
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                const float r = __frcp_rn(1.0f + 2.0f * l * wf[k]);
+                const float r = __frcp_rn(1.0f + m * wf[k]);
                 const float term = wf[k] * xf[k] * xf[k] * r * r;
                 S += term;
-                S1 -= 4.0f * wf[k] * term * r;
+                S2 += wf[k] * term * r;
             }
             S = warp_sum_f(S);
-            S1 = warp_sum_f(S1);
-            const float u = 1.0f - 2.0f * l;
-            g = u * u * S - tf * tf;
-            dg = -4.0f * u * S + u * u * S1;
+            S2 = warp_sum_f(S2);
+            Vf.phi(u, sqrtf(S), S2, ph, dph, sc);
         };
+        float uf = 0.0f;
         bool ok = rng;
-        float lf = 0.5f;
         if (ok) {
-            float lo, hi, g, dg;
-            int slo;
-            if (tf > 0.0f) {
-                lo = 0.0f; hi = 0.5f; slo = 1;
-            } else {
-                lo = 0.5f; hi = 1.0f; slo = -1;
-                for (int it = 0; it < 130; ++it) {
-                    G32(hi, g, dg);
-                    if (g > 0.0f || !(hi < 1e30f)) break;
-                    lo = hi;
-                    hi *= 2.0f;
-                }
-            }
-            float guess = (float)((nDinvx - t) / (2.0 * (nDinvx + t)));
-            if (lam_cache && *lam_cache > lo && *lam_cache < hi) guess = *lam_cache;
-            lf = (guess > lo && guess < hi) ? guess : 0.5f * (lo + hi);
-            for (int it = 0; it < 100; ++it) {
-                G32(lf, g, dg);
-                if (!(g == g)) { ok = false; break; }
-                if (g == 0.0f) break;
-                if ((g > 0.0f ? 1 : -1) == slo) lo = lf; else hi = lf;
-                float nl = lf - g / dg;
-                if (nl >= lo && nl <= hi && fabsf(nl - lf) <= 2e-6f * lf) { lf = nl; break; }
-                if (!(nl > lo && nl < hi)) nl = 0.5f * (lo + hi);
-                const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 2e-7f * hi;
-                lf = nl;
-                if (done) break;
-            }
+            uf = soc_root<float>(ev32, V.tpos, (float)V.guess(t, nDinvx, cache), 2e-6f, 2e-7f, 100);
+            ok = uf > 0.0f && isfinite(uf);
         }
         // ---- FP64 polish
         bool conv = false;
+        double u = (double)uf;
         if (ok) {
             double x2w[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) x2w[k] = wr[k] * xr[k] * xr[k];
-            lam = (double)lf;
             for (int it = 0; it < 3; ++it) {
-                double S = 0.0, S1 = 0.0;
+                double S = 0.0, S2 = 0.0;
+                const double m = V.mu(u);
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
-                    const double r = rcp_refined(1.0 + 2.0 * lam * wr[k]);
+                    const double r = rcp_refined(1.0 + m * wr[k]);
                     const double term = x2w[k] * r * r;
                     S += term;
-                    S1 -= 4.0 * wr[k] * term * r;
+                    S2 += wr[k] * term * r;
                 }
                 S = warp_sum(S);
-                S1 = warp_sum(S1);
-                const double u = 1.0 - 2.0 * lam;
-                const double step = (u * u * S - t * t) / (-4.0 * u * S + u * u * S1);
+                S2 = warp_sum(S2);
+                double ph, dph, sc;
+                V.phi(u, sqrt(S), S2, ph, dph, sc);
+                if (fabs(ph) <= 1.6e-15 * sc) {  // zero to working precision
+                    u = fmax(u, 0.0);
+                    conv = true;
+                    break;
+                }
+                const double step = ph / dph;
                 if (!isfinite(step)) break;
-                lam -= step;
-                if (fabs(step) <= RootTolSoc * lam) { conv = true; break; }
+                u -= step;
+                if (fabs(step) <= RootTolSoc * (V.tpos ? fmin(u, 1.0 - u) : u)) { conv = true; break; }
             }
-            conv = conv && (t > 0.0 ? (lam > 0.0 && lam < 0.5) : lam > 0.5);
+            conv = conv && u >= 0.0 && (!V.tpos || u < 1.0);
         }
-        if (!conv) {
-            // full FP64 safeguarded search on the registers
-            double lo, hi;
-            int slo;
-            auto G = [&](double l, double& g, double& dg) {
-                double S = 0.0, S1 = 0.0;
+        if (!conv) {  // full FP64 safeguarded search on the registers
+            auto ev = [&](double uu, double& ph, double& dph, double& sc) {
+                double S = 0.0, S2 = 0.0;
+                const double m = V.mu(uu);
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
-                    const double r = 1.0 / (1.0 + 2.0 * l * wr[k]);
+                    const double r = 1.0 / (1.0 + m * wr[k]);
                     const double term = wr[k] * xr[k] * xr[k] * r * r;
                     S += term;
-                    S1 -= 4.0 * wr[k] * term * r;
+                    S2 += wr[k] * term * r;
                 }
                 S = warp_sum(S);
-                S1 = warp_sum(S1);
-                const double u = 1.0 - 2.0 * l;
-                g = u * u * S - t * t;
-                dg = -4.0 * u * S + u * u * S1;
+                S2 = warp_sum(S2);
+                V.phi(uu, sqrt(S), S2, ph, dph, sc);
             };
-            double g, dg;
-            if (t > 0.0) {
-                lo = 0.0; hi = 0.5; slo = 1;
-            } else {
-                lo = 0.5; hi = 1.0; slo = -1;
-                for (int it = 0; it < 1100; ++it) {
-                    G(hi, g, dg);
-                    if (g > 0.0) break;
-                    lo = hi;
-                    hi *= 2.0;
-                }
-            }
-            double guess = (nDinvx - t) / (2.0 * (nDinvx + t));
-            lam = (guess > lo && guess < hi) ? guess : 0.5 * (lo + hi);
-            for (int it = 0; it < 200; ++it) {
-                G(lam, g, dg);
-                if (g == 0.0) break;
-                if ((g > 0.0 ? 1 : -1) == slo) lo = lam; else hi = lam;
-                double nl = lam - g / dg;
-                if (nl >= lo && nl <= hi && fabs(nl - lam) <= RootTolSoc * lam) { lam = nl; break; }
-                if (!(nl > lo && nl < hi)) nl = 0.5 * (lo + hi);
-                const bool done = !(nl > lo && nl < hi) || (hi - lo) <= 4e-16 * hi;
-                lam = nl;
-                if (done) break;
-            }
+            u = soc_root<double>(ev, V.tpos, V.guess(t, nDinvx, nullptr), RootTolSoc, 4e-16, 200);
         }
-        if (lam_cache && lane == 0) *lam_cache = (float)lam;
+        if (cache && lane == 0) *cache = V.store(u);
+        mu = V.mu(u);
     }
     // y = (I + 2 lambda Dhat^{-2})^{-1} x ;  s = ||Dhat^{-1} y||
     double s = 0.0;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        const double y = xr[k] * rcp_refined(1.0 + 2.0 * lam * wr[k]);
+        const double y = xr[k] * rcp_refined(1.0 + mu * wr[k]);
         s += wr[k] * y * y;
         if (lane + 32 * k < nx) buf[1 + lane + 32 * k] = y;
     }
@@ -366,7 +420,7 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
 
 // Rotated SOC through Q (see rsoc_project_warp) on the mixed-precision SOC path.
 template <int R>
-__device__ void rsoc_project_warp_fast(double* buf, const double* __restrict__ w, int dim, float* lam_cache) {
+__device__ void rsoc_project_warp_fast(double* buf, const double* __restrict__ w, int dim, float* cache) {
     const int lane = threadIdx.x & 31;
     const double r2 = 0.70710678118654752440;
     __syncwarp();
@@ -376,7 +430,7 @@ __device__ void rsoc_project_warp_fast(double* buf, const double* __restrict__ w
         buf[1] = (p - q) * r2;
     }
     __syncwarp();
-    soc_project_warp_fast<R>(buf, w, dim, lam_cache);
+    soc_project_warp_fast<R>(buf, w, dim, cache);
     if (lane == 0) {
         const double p = buf[0], q = buf[1];
         buf[0] = (p + q) * r2;
@@ -389,24 +443,24 @@ __device__ void rsoc_project_warp_fast(double* buf, const double* __restrict__ w
 // FP64 memory-loop projection with weights formed from the scales d (kInv as there).
 template <bool kInv>
 __device__ __forceinline__ void soc_project_any(double* buf, const double* __restrict__ w,
-                                                const double* __restrict__ d, int dim, bool rot, float* lam_cache) {
+                                                const double* __restrict__ d, int dim, bool rot, float* cache) {
     const int nx = dim - 1;
     if (nx > 128) {
-        if (rot) rsoc_project_warp<kInv>(buf, d, dim, nullptr);
-        else soc_project_warp<kInv>(buf, d, dim, nullptr);
+        if (rot) rsoc_project_warp<kInv>(buf, d, dim, cache);
+        else soc_project_warp<kInv>(buf, d, dim, cache);
         return;
     }
     const int R = (nx + 31) / 32;
     if (rot) {
-        if (R <= 1) rsoc_project_warp_fast<1>(buf, w, dim, lam_cache);
-        else if (R == 2) rsoc_project_warp_fast<2>(buf, w, dim, lam_cache);
-        else if (R == 3) rsoc_project_warp_fast<3>(buf, w, dim, lam_cache);
-        else rsoc_project_warp_fast<4>(buf, w, dim, lam_cache);
+        if (R <= 1) rsoc_project_warp_fast<1>(buf, w, dim, cache);
+        else if (R == 2) rsoc_project_warp_fast<2>(buf, w, dim, cache);
+        else if (R == 3) rsoc_project_warp_fast<3>(buf, w, dim, cache);
+        else rsoc_project_warp_fast<4>(buf, w, dim, cache);
     } else {
-        if (R <= 1) soc_project_warp_fast<1>(buf, w, dim, lam_cache);
-        else if (R == 2) soc_project_warp_fast<2>(buf, w, dim, lam_cache);
-        else if (R == 3) soc_project_warp_fast<3>(buf, w, dim, lam_cache);
-        else soc_project_warp_fast<4>(buf, w, dim, lam_cache);
+        if (R <= 1) soc_project_warp_fast<1>(buf, w, dim, cache);
+        else if (R == 2) soc_project_warp_fast<2>(buf, w, dim, cache);
+        else if (R == 3) soc_project_warp_fast<3>(buf, w, dim, cache);
+        else soc_project_warp_fast<4>(buf, w, dim, cache);
     }
 }
 
@@ -439,6 +493,8 @@ template <typename R>
 struct ExpCase4T {
     R r0, s0, t0, dr, ds, tau, a3, a4, a4m1, w34, ldt, dir, lt0, lr0, ls0, ldr, lds;
     int anchor;  // 3 or 4: endpoint rho is measured from
+    int slo;     // sign of F next to the anchor when the root is inside the interval
+    bool dm;     // F finite at the anchor: affine in delta = e^L next to it
     int kind;    // 1: r0 > 0, s0 > 0;  2: r0 <= 0 < s0;  3: s0 <= 0 < r0
 };
 using ExpCase4 = ExpCase4T<double>;
@@ -524,59 +580,113 @@ __host__ __device__ __forceinline__ int exp_sign(const ExpCase4T<R>& e, R L, int
     return (F > R(0)) - (F < R(0));
 }
 
-// Lower end of the search: step down from hi by 1, 2, 4, ... until F shows the
-// sign it has next to the anchor.  First F at the anchor itself (offset 0, L = -inf)
-// is evaluated: it is the endpoint value h(a4) or h(a3) of App. A.2 in log form.
-// When it is zero to working precision or has the other sign (v0 on the boundary
-// of the polar cone or of the cone, up to rounding), the root is the endpoint:
-// at_end is set and -inf returned.
+// Lower end of the search.  First F at the anchor itself (offset 0, L = -inf) is
+// evaluated: it is the endpoint value h(a4) or h(a3) of App. A.2 in log form.  When
+// it is zero to working precision or has the other sign (v0 on the boundary of the
+// polar cone or of the cone, up to rounding), the root is the endpoint: at_end is set
+// and -inf returned.  When it is finite, F is analytic in the offset delta = e^L next
+// to the anchor: F0 returns it and the search starts unbounded below, the anchor
+// itself being the lower end.  Otherwise (F -> +-inf linearly in L; F0 returned
+// infinite) step down from hi, doubling the distance (or going twice as far as the
+// Newton point in L when that is farther) until F shows the sign it has there.
 template <typename R>
-__host__ __device__ __forceinline__ R exp_lower(const ExpCase4T<R>& e, R hi, int slo, int& evals, bool& at_end) {
+__host__ __device__ __forceinline__ R exp_lower(const ExpCase4T<R>& e, R hi, int slo, int& evals, bool& at_end,
+                                                R& F0) {
     const R ninf = -R(INFINITY);
     at_end = false;
     {
-        R F0, dF, rho, lsp, lrd, Fs;
+        R dF, rho, lsp, lrd, Fs;
         exp_F(e, ninf, F0, dF, rho, lsp, lrd, Fs);
         ++evals;
         const int s0 = (F0 > R(0)) - (F0 < R(0));
-        const bool tiny = fabs(F0) < R(INFINITY) && fabs(F0) <= R(16) * RootTol<R>::collapse * Fs;
+        const bool finite = fabs(F0) < R(INFINITY);
+        const bool tiny = finite && fabs(F0) <= R(16) * RootTol<R>::collapse * Fs;
         if (F0 == F0 && (s0 != slo || tiny)) {
             at_end = true;
             return ninf;
         }
+        if (finite) return ninf;
+        F0 = R(INFINITY);
     }
     R step = R(1);
     for (int it = 0; it < 1100; ++it) {
         const R lo = hi - step;
         if (lo == ninf) return lo;
-        const int s = exp_sign(e, lo, evals);
+        R F, dF, rho, lsp, lrd, Fs;
+        exp_F(e, lo, F, dF, rho, lsp, lrd, Fs);
+        ++evals;
+        const int s = (F > R(0)) - (F < R(0));
         if (s == slo || s == 0) return lo;
-        step *= R(2);
+        // twice the distance, or past the Newton point by as much again when that is farther
+        const R nd = F / dF;
+        step = (nd > R(0) && nd < R(INFINITY)) ? fmax(R(2) * step, step + R(2) * nd) : R(2) * step;
     }
     return ninf;
 }
 
-// Safeguarded Newton for F(L) = 0 on (lo, hi); sign(F) at the lo end is slo.
+// Safeguarded Newton for F(L) = 0 on (lo, hi); sign(F) at the lo end is slo.  F0 is
+// F at the anchor (L = -inf) when finite.  Then F is affine in delta = e^L next to
+// the anchor, and the first step is Newton's in delta, L <- L + log1p(-F / dF), exact
+// for that model; without F0 (F linear in L there) it is Newton's in L.  Later steps
+// take whichever of the two models better predicts F at the previous point (far from
+// the anchor F can be affine in delta through rho, or linear in L through the logs).
+// A step that leaves the bracket is replaced by the other model's step; while no
+// lower end is known yet, by the farther of that and the secant in delta between the
+// anchor and L (or a doubling downward extension); otherwise by bisection, which
+// also replaces steps that fail to halve within a finite bracket.
 template <typename R>
-__host__ __device__ __forceinline__ R exp_newton(const ExpCase4T<R>& e, R lo, R hi, int slo, R L, int& evals) {
+__host__ __device__ __forceinline__ R exp_newton(const ExpCase4T<R>& e, R lo, R hi, int slo, R L, R F0, int& evals) {
     const R one = R(1), ninf = -R(INFINITY);
+    const bool dmodel = fabs(F0) < R(INFINITY);
     if (!(L > lo && L < hi)) L = (lo == ninf) ? hi - one : R(0.5) * (lo + hi);
+    R ext = one, Lp = R(NAN), Fp = R(NAN), dx = R(INFINITY), dxold = R(INFINITY);
     for (int it = 0; it < 400; ++it) {
         R F, dF, rho, lsp, lrd, Fs;
         exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
         ++evals;
         if (!(F == F)) break;  // NaN: both sides infinite, already at the limit
-        if (F == R(0)) break;
+        // F zero to working precision: no other L in reach is a better root
+        if (Fs < R(INFINITY) && fabs(F) <= R(4) * RootTol<R>::collapse * Fs) break;
         const int s = F > R(0) ? 1 : -1;
         if (s == slo) lo = L; else hi = L;
-        R nl = L - F / dF;
+        const R st = -F / dF;
+        // the model (affine in delta or in L) that better predicts the previous point
+        bool dstep = dmodel;
+        if (Lp == Lp) {
+            const R errL = fabs(F + dF * (Lp - L) - Fp), errD = fabs(F + dF * expm1(Lp - L) - Fp);
+            dstep = errD <= errL;
+        }
+        Lp = L;
+        Fp = F;
+        const R nD = st > -one ? L + log1p(st) : ninf, nL = L + st;
+        R nl = dstep ? nD : nL;
         // a Newton step below RootTol::newton relative leaves an error of order its square
         // (L itself has just become an end of the bracket, so test this first)
         if (nl >= lo && nl <= hi && fabs(nl - L) <= RootTol<R>::newton * fmax(one, fabs(L))) {
             L = nl;
             break;
         }
-        if (!(nl > lo && nl < hi)) nl = (lo == ninf) ? hi - R(2) * fmax(one, fabs(hi - L)) : R(0.5) * (lo + hi);
+        if (!(nl > lo && nl < hi)) {
+            const R alt = dstep ? nL : nD;  // the other model's step
+            if (lo != ninf) {
+                nl = (alt > lo && alt < hi) ? alt : R(0.5) * (lo + hi);
+            } else {
+                // the root is below L: the farther of the other step and, with F0, the
+                // secant in delta to the anchor (F0 / (F0 - F) in (0, 1)); else extend
+                R cand = (alt > lo && alt < hi) ? alt : R(INFINITY);
+                if (dmodel) cand = fmin(cand, L + log(F0 / (F0 - F)));
+                if (cand < hi) {
+                    nl = cand;
+                } else {
+                    nl = hi - ext;
+                    ext *= R(2);
+                }
+            }
+        }
+        // inside a finite bracket, bisect when the steps do not halve (as in rtsafe)
+        if (lo != ninf && fabs(nl - L) > R(0.5) * dxold) nl = R(0.5) * (lo + hi);
+        dxold = dx;
+        dx = fabs(nl - L);
         const bool done = !(nl > lo && nl < hi) || (hi - lo) <= RootTol<R>::collapse * fmax(one, fabs(hi));
         L = nl;
         if (done) break;
@@ -598,6 +708,8 @@ __host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R gues
         e.anchor = 4;
         e.dir = e.w34 > zero ? one : -one;
         const int sm = exp_sign(e, Lh, evals);
+        e.slo = -1;
+        e.dm = false;
         if (sm == 0) {
             L = Lh;
             return true;
@@ -607,23 +719,30 @@ __host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R gues
             e.dir = -e.dir;
         }
         const int slo = sm > 0 ? -1 : +1;
+        e.slo = slo;
         bool at_end;
-        const R lo = exp_lower(e, Lh, slo, evals, at_end);
-        L = at_end ? lo : exp_newton(e, lo, Lh, slo, guess, evals);
+        R F0;
+        const R lo = exp_lower(e, Lh, slo, evals, at_end, F0);
+        e.dm = fabs(F0) < R(INFINITY);
+        L = at_end ? lo : exp_newton(e, lo, Lh, slo, guess, F0, evals);
     } else if (e.s0 > zero) {  // r0 <= 0: (-inf, a3)
-        e.kind = 2; e.anchor = 3; e.dir = -one;
+        e.kind = 2; e.anchor = 3; e.dir = -one; e.slo = +1;
         R hi = zero;
         for (int it = 0; it < 8 && exp_sign(e, hi, evals) > 0 && hi < R(60); ++it) hi = R(2) * hi + one;
         bool at_end;
-        const R lo = exp_lower(e, hi, +1, evals, at_end);
-        L = at_end ? lo : exp_newton(e, lo, hi, +1, guess, evals);
+        R F0;
+        const R lo = exp_lower(e, hi, +1, evals, at_end, F0);
+        e.dm = fabs(F0) < R(INFINITY);
+        L = at_end ? lo : exp_newton(e, lo, hi, +1, guess, F0, evals);
     } else {  // s0 <= 0 < r0: (a4, inf)
-        e.kind = 3; e.anchor = 4; e.dir = one;
+        e.kind = 3; e.anchor = 4; e.dir = one; e.slo = -1;
         R hi = zero;
         for (int it = 0; it < 8 && exp_sign(e, hi, evals) < 0 && hi < R(60); ++it) hi = R(2) * hi + one;
         bool at_end;
-        const R lo = exp_lower(e, hi, -1, evals, at_end);
-        L = at_end ? lo : exp_newton(e, lo, hi, -1, guess, evals);
+        R F0;
+        const R lo = exp_lower(e, hi, -1, evals, at_end, F0);
+        e.dm = fabs(F0) < R(INFINITY);
+        L = at_end ? lo : exp_newton(e, lo, hi, -1, guess, F0, evals);
     }
     return true;
 }
@@ -755,8 +874,50 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
     bool ok = in_range;
     if (ok) {
         exp_case4_setup(ef, r0, s0, t0, dr, ds, (float)lg[0], (float)lg[1], (float)lg[2]);
-        ok = fabsf(ef.a3) < 1e30f && fabsf(ef.a4) < 1e30f && exp_case4_solve(ef, L_cache ? *L_cache : NAN, Lf, evals) &&
-             isfinite(Lf);
+        // rho (rho - 1) + tau^2 must stay finite in FP32 over the search
+        ok = fabsf(ef.a3) < 1e15f && fabsf(ef.a4) < 1e15f && fabsf(ef.tau) < 1e15f &&
+             exp_case4_solve(ef, L_cache ? *L_cache : NAN, Lf, evals) &&
+             !(Lf != Lf) && Lf < INFINITY;
+    }
+    if (ok && Lf == -INFINITY) {
+        // FP32 puts the root at the anchor.  In FP64, F at a tiny offset delta_z = e^-200
+        // is F at the anchor to all digits and dF = c delta_z, c = dF/ddelta there: the
+        // anchor stands when F has the sign beyond the root or is zero to precision;
+        // otherwise the root next to it is delta = -F / c, polished by Newton in delta.
+        ExpCase4 e;
+        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2]);
+        e.kind = ef.kind;
+        e.anchor = ef.anchor;
+        e.dir = (double)ef.dir;
+        const double Lz = -200.0;
+        double F, dF, rho, lsp, lrd, Fs;
+        exp_F(e, Lz, F, dF, rho, lsp, lrd, Fs);
+        const int sF = (F > 0.0) - (F < 0.0);
+        if (F == F && Fs < INFINITY && (sF != ef.slo || fabs(F) <= 16.0 * RootTol<double>::collapse * Fs)) {
+            if (L_cache) *L_cache = -INFINITY;
+            exp_case4_output(e, -INFINITY, r0, s0, t0, dr, ds, out);
+            return;
+        }
+        bool conv = false;
+        double L = Lz;
+        if (F == F && fabs(F) < INFINITY && fabs(dF) < 1e-60 && -F / dF > 0.0) {
+            L = Lz + log(-F / dF);
+            for (int it = 0; it < 4 && !conv; ++it) {
+                exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
+                if (Fs < INFINITY && fabs(F) <= 4.0 * RootTol<double>::collapse * Fs) { conv = true; break; }
+                const double st = -F / dF;
+                if (!(st > -1.0) || !isfinite(st)) break;
+                const double step = log1p(st);
+                L += step;
+                conv = fabs(step) <= RootTol<double>::newton * fmax(1.0, fabs(L));
+            }
+        }
+        if (conv) {
+            if (L_cache) *L_cache = (float)L;
+            exp_case4_output(e, L, r0, s0, t0, dr, ds, out);
+            return;
+        }
+        ok = false;
     }
     if (ok) {
         // FP64 polish from the FP32 root, same branch and anchor
@@ -770,10 +931,11 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
         for (int it = 0; it < 3; ++it) {
             double F, dF, rho, lsp, lrd, Fs;
             exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
-            if (F == 0.0) { ok = true; break; }
-            const double step = F / dF;
+            if (Fs < INFINITY && fabs(F) <= 4.0 * RootTol<double>::collapse * Fs) { ok = true; break; }
+            const double st = -F / dF;  // Newton in delta next to the anchor (see exp_newton), else in L
+            const double step = ef.dm ? (st > -1.0 ? log1p(st) : NAN) : st;
             if (!isfinite(step)) break;
-            L -= step;
+            L += step;
             if (fabs(step) <= RootTol<double>::newton * fmax(1.0, fabs(L))) { ok = true; break; }
         }
         if (ok) {

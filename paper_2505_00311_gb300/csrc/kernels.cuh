@@ -57,7 +57,8 @@ struct Dev {
     int exp_row0, n_exp;
     float* exp_L;          // last log-offset per exp cone
     const double* exp_lg;  // per exp cone: log dr of its three rows
-    // blocks of the cone-structured kernels
+    // blocks of the cone-structured kernels: exp cones in [0, nb_exp), SOC cones in the
+    // next nb_soc, scalar rows in the last nb_scal (the costliest work is dispatched first)
     int nb_scal, nb_soc, nb_exp;
     int nb_primal;
     // reductions and control
@@ -253,9 +254,9 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
     double acc[2] = {0.0, 0.0};
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (b < D.nb_scal) {
+    if (b >= D.nb_exp + D.nb_soc) {  // scalar rows (blocks dispatched last)
         const int stride = D.nb_scal * blockDim.x;
-        for (int i = b * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
+        for (int i = (b - D.nb_exp - D.nb_soc) * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
             T y, kx;
             dual_row_halpern(D, i, pend, ha, hb, hc, hw, pprev, y, kx);
             const T pi = p[i];
@@ -266,9 +267,9 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
             acc[0] += dy * dy;
             acc[1] += dy * ((double)pi - (double)kx);
         }
-    } else if (b < D.nb_scal + D.nb_soc) {
+    } else if (b >= D.nb_exp) {  // SOC / RSOC blocks
         const int stride = D.nb_soc * kWarpsPerBlock;
-        for (int cidx = (b - D.nb_scal) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
+        for (int cidx = (b - D.nb_exp) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
             const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
             for (int i = lane; i < dim; i += 32) {
                 T y, kx;
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
         }
     } else {
         const int stride = D.nb_exp * blockDim.x;
-        for (int e = (b - D.nb_scal - D.nb_soc) * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
+        for (int e = b * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
             const int r = D.exp_row0 + 3 * e;
             T y[3], kx[3], v[3], out[3];
 #pragma unroll
@@ -389,15 +390,15 @@ __global__ void __launch_bounds__(kBlock) cand_dual(Dev<T> D) {
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     auto val = [&](int i) { return q ? (double)src[i] * iw : (double)src[i]; };
-    if (b < D.nb_scal) {
+    if (b >= D.nb_exp + D.nb_soc) {  // scalar rows (blocks dispatched last)
         const int stride = D.nb_scal * blockDim.x;
-        for (int i = b * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
+        for (int i = (b - D.nb_exp - D.nb_soc) * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
             const double v = val(i);
             out[i] = (i < D.m_zero) ? v : fmax(v, 0.0);
         }
-    } else if (b < D.nb_scal + D.nb_soc) {
+    } else if (b >= D.nb_exp) {  // SOC / RSOC blocks
         const int stride = D.nb_soc * kWarpsPerBlock;
-        for (int cidx = (b - D.nb_scal) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
+        for (int cidx = (b - D.nb_exp) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
             const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
             for (int i = lane; i < dim; i += 32) out[o + i] = val(o + i);
             __syncwarp();
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(kBlock) cand_dual(Dev<T> D) {
         }
     } else {
         const int stride = D.nb_exp * blockDim.x;
-        for (int e = (b - D.nb_scal - D.nb_soc) * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
+        for (int e = b * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
             const int r = D.exp_row0 + 3 * e;
             double o3[3];
             exp_dual_project_fast(val(r), val(r + 1), val(r + 2), D.dr[r], D.dr[r + 1], D.dr[r + 2],
@@ -443,9 +444,9 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
         sums[2] += dy * dy;
         mx[1] = fmax(mx[1], fabs(kx[i] / D.dr[i]));
     };
-    if (b < D.nb_scal) {
+    if (b >= D.nb_exp + D.nb_soc) {  // scalar rows (blocks dispatched last)
         const int stride = D.nb_scal * blockDim.x;
-        for (int i = b * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
+        for (int i = (b - D.nb_exp - D.nb_soc) * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
             const double v = kx[i] - D.h64[i];
             const double w = v / D.dr[i];
             double rs, ru, pu;
@@ -456,9 +457,9 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
             mx[2] = fmax(mx[2], fabs(pu));
             common(i);
         }
-    } else if (b < D.nb_scal + D.nb_soc) {
+    } else if (b >= D.nb_exp) {  // SOC / RSOC blocks
         const int stride = D.nb_soc * kWarpsPerBlock;
-        for (int cidx = (b - D.nb_scal) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
+        for (int cidx = (b - D.nb_exp) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
             const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
             const bool rot = D.soc_rot[cidx] != 0;
             // scaled residual: project v onto Dr K
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
         }
     } else {
         const int stride = D.nb_exp * blockDim.x;
-        for (int e = (b - D.nb_scal - D.nb_soc) * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
+        for (int e = b * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
             const int r = D.exp_row0 + 3 * e;
             double v[3], w[3], ps[3], pu[3];
             for (int k = 0; k < 3; ++k) {

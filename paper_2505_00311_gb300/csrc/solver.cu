@@ -478,6 +478,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.rp = ctx->rp; D.ci = ctx->ci; D.val = ctx->val;
     D.rpT = ctx->rpT; D.ciT = ctx->ciT; D.valT = ctx->valT;
     D.c = ctx->cs; D.h = ctx->hs; D.l = ctx->ls; D.u = ctx->us; D.dr = ctx->dr; D.dc = ctx->dc;
+    D.c64 = ctx->cs; D.h64 = ctx->hs; D.l64 = ctx->ls; D.u64 = ctx->us;
     D.m_zero = ctx->m_zero; D.m_scalar = ctx->m_scalar;
     D.n_soc = ctx->n_soc; D.soc_off = ctx->soc_off; D.soc_dim = ctx->soc_dim; D.soc_rot = ctx->soc_rot;
     D.soc_lam = ctx->soc_lam; D.soc_w = ctx->soc_w; D.soc_wp = ctx->soc_wp; D.exp_lg = ctx->exp_lg;
