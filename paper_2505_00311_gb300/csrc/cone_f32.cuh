@@ -47,7 +47,7 @@ __device__ void soc_project_warp_f32(float* buf, const float* __restrict__ w, in
     float mu = 1.0f;          // 2 lambda; case 3
     if (t != 0.0f) {          // case 4: search variable as in cone_math.cuh
         bool known, near = t > 0.0f && soc_cached_near(cache, known);
-        if (t > 0.0f && !known) {  // sign of phi at mu = 1/2
+        if (t > 0.0f && !known) {  // sign of psi at mu = 1/2
             float S = 0.0f;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
@@ -69,7 +69,7 @@ __device__ void soc_project_warp_f32(float* buf, const float* __restrict__ w, in
             }
             S = warp_sum_f(S);
             S2 = warp_sum_f(S2);
-            V.phi(u, sqrtf(S), S2, ph, dph, sc);
+            V.psi(u, sqrtf(S), S2, ph, dph, sc);
         };
         const float u = soc_root<float>(ev, V.tpos, V.guess(t, nDinvx, cache), 2e-6f, 2e-7f, 100);
         if (cache && lane == 0) *cache = V.store(u);

@@ -2,7 +2,7 @@
 //
 // SOC: Theorem 1 (Sec. 3; proof in App. A.1).  Cases 1-3 in closed form; in
 //      case 4 the root of eq. (bisection-soc) is found by safeguarded Newton on
-//      the equivalent monotone function phi(g) of g = |1 - 2 lambda| (see below).
+//      an equivalent monotone, nearly affine function psi (see below).
 //      One warp per cone; the last root is kept per cone and used as the next
 //      starting point.  The first entry of the result is ||Dhat^{-1} y|| (the
 //      active constraint of eq. kkt_sys_fixed_2), which equals t / (1 - 2 lambda)
@@ -39,13 +39,17 @@ constexpr double RootTolSoc = 1e-10;
 //   t > 0, root at mu >= 1/2:  u = 1 - mu in (0, 1)  (nearly inactive cones: u ~ t)
 //   t > 0, root at mu < 1/2:   u = mu in (0, 1)      (v almost in the cone: u ~ 0)
 //   t < 0:                     u = mu - 1 in (0, inf)
-// (for t > 0 the half is read off the cached root or the sign of phi at mu = 1/2, and
+// (for t > 0 the half is read off the cached root or the sign of psi at mu = 1/2, and
 // Newton's relative stopping test uses the smaller of u and 1 - u)
-// In each, phi(u) = (u - pm) sqrt(S) - c increases in u and is negative at u = 0
-// (pm = 0, c = |t| for the first and last; pm = 1, c = -t for the second), and it is
-// nearly affine in u near u = 0, so Newton with a relative test on u converges in a
-// few steps.  The projection is y = (I + mu Dhat^{-2})^{-1} x, s = ||Dhat^{-1} y||
-// (the active constraint of eq. kkt_sys_fixed_2).
+// The equation is solved in the reciprocal form used for trust-region secular
+// equations (More and Sorensen, 1983): 1 / sqrt(S(mu)) is affine in mu when one term
+// of S dominates, so
+//     psi(u) = (u - pm) / |t| + eps / sqrt(S(mu)),
+// (pm = 0, eps = -1 for the first and last variable; pm = 1, eps = +1 for the second)
+// increases in u, is negative at u = 0, and is nearly affine: safeguarded Newton with
+// a relative test on u converges in a few steps even where the poles -1/w_i of S are
+// close.  The projection is y = (I + mu Dhat^{-2})^{-1} x, s = ||Dhat^{-1} y|| (the
+// active constraint of eq. kkt_sys_fixed_2).
 // ---------------------------------------------------------------------------
 // Weight of entry i (0-based over the x part) for the projection onto E K_soc,
 // E = diag(e_0, e_1, ...): dhat_i = e_{i+1} / e_0 and w_i = dhat_i^{-2}.
@@ -57,21 +61,22 @@ __device__ __forceinline__ double soc_weight(const double* __restrict__ d, doubl
     return q * q;
 }
 
-// The search variable of case 4 (see above): mu = a0 + a1 u, phi = (u - pm) sqrt(S) - c.
+// The search variable of case 4 (see above): mu = a0 + a1 u, psi = (u - pm) / |t| + eps / sqrt(S).
 // near (t > 0 only): the root has mu < 1/2, decided from the cached root or from the
-// sign of phi at mu = 1/2 (soc_near).  The cached value of a cone is u, negated for
+// sign of psi at mu = 1/2.  The cached value of a cone is u, negated for
 // the variable mu next to the cone.
 template <typename R>
 struct SocVar {
-    R a0, a1, pm, c;
+    R a0, a1, pm, iat, eps;
     bool near, tpos;
     __device__ __forceinline__ SocVar(R t, bool near_) {
         tpos = t > R(0);
         near = tpos && near_;
-        const R at = fabs(t);
-        if (near) { a0 = R(0); a1 = R(1); pm = R(1); c = -at; }
-        else if (tpos) { a0 = R(1); a1 = R(-1); pm = R(0); c = at; }
-        else { a0 = R(1); a1 = R(1); pm = R(0); c = at; }
+        iat = R(1) / fabs(t);
+        eps = near ? R(1) : R(-1);
+        if (near) { a0 = R(0); a1 = R(1); pm = R(1); }
+        else if (tpos) { a0 = R(1); a1 = R(-1); pm = R(0); }
+        else { a0 = R(1); a1 = R(1); pm = R(0); }
     }
     // Start: the cached u (converted between the two t > 0 variables), else the root
     // when Dhat = I.
@@ -92,16 +97,17 @@ struct SocVar {
     // the same variable in another precision
     template <typename Q>
     __device__ __forceinline__ explicit SocVar(const SocVar<Q>& o)
-        : a0(R(o.a0)), a1(R(o.a1)), pm(R(o.pm)), c(R(o.c)), near(o.near), tpos(o.tpos) {}
+        : a0(R(o.a0)), a1(R(o.a1)), pm(R(o.pm)), iat(R(o.iat)), eps(R(o.eps)), near(o.near), tpos(o.tpos) {}
     __device__ __forceinline__ float store(R u) const { return near ? -(float)u : (float)u; }
     __device__ __forceinline__ R mu(R u) const { return a0 + a1 * u; }
-    // phi and dphi/du from sq = sqrt(S) and S2 = sum w_i^2 x_i^2 / (1 + mu w_i)^3; sc is
-    // the size of the terms of phi (its rounding error is a few ulps of sc)
-    __device__ __forceinline__ void phi(R u, R sq, R S2, R& ph, R& dph, R& sc) const {
-        const R p = u - pm;
-        ph = p * sq - c;
-        dph = sq - p * a1 * S2 / sq;
-        sc = fabs(p) * sq + fabs(c);
+    // psi and dpsi/du from sq = sqrt(S) and S2 = sum w_i^2 x_i^2 / (1 + mu w_i)^3 (so
+    // dS/dmu = -2 S2); sc is the size of the terms of psi (its rounding error is a few
+    // ulps of sc)
+    __device__ __forceinline__ void psi(R u, R sq, R S2, R& ph, R& dph, R& sc) const {
+        const R p = u - pm, isq = R(1) / sq;
+        ph = p * iat + eps * isq;
+        dph = iat + eps * a1 * S2 * isq * isq * isq;
+        sc = fabs(p) * iat + isq;
     }
 };
 
@@ -116,10 +122,10 @@ __device__ __forceinline__ bool soc_cached_near(const float* cache, bool& known)
     return known && mu < 0.5f;
 }
 
-// Safeguarded Newton for phi(u) = 0 given an evaluator ev(u, phi, dphi, sc) (warp-
-// uniform results), with phi(0) < 0.  hi: 1 for t > 0; found by doubling for t < 0.
+// Safeguarded Newton for psi(u) = 0 given an evaluator ev(u, psi, dpsi, sc) (warp-
+// uniform results), with psi(0) < 0.  hi: 1 for t > 0; found by doubling for t < 0.
 // Stops on a relative Newton step below tol, on a bracket collapsed to collapse
-// relative, or on |phi| within 4 collapse of sc (zero to working precision: next to
+// relative, or on |psi| within 4 collapse of sc (zero to working precision: next to
 // the cone u is then fixed only to a few ulps, absolutely).
 template <typename R, typename Ev>
 __device__ __forceinline__ R soc_root(Ev ev, bool tpos, R guess, R tol, R collapse, int max_it) {
@@ -177,7 +183,7 @@ __device__ int soc_project_warp(double* buf, const double* __restrict__ d, int d
     int evals = 0;
     if (t != 0.0) {               // case 4
         bool known, near = t > 0.0 && soc_cached_near(cache, known);
-        if (t > 0.0 && !known) {  // sign of phi at mu = 1/2
+        if (t > 0.0 && !known) {  // sign of psi at mu = 1/2
             double S = 0.0;
             for (int i = lane; i < nx; i += 32) {
                 const double x = buf[1 + i], w = soc_weight<kInv>(d, d0, i);
@@ -199,7 +205,7 @@ __device__ int soc_project_warp(double* buf, const double* __restrict__ d, int d
             }
             S = warp_sum(S);
             S2 = warp_sum(S2);
-            V.phi(u, sqrt(S), S2, ph, dph, sc);
+            V.psi(u, sqrt(S), S2, ph, dph, sc);
             ++evals;
         };
         const double u = soc_root<double>(ev, V.tpos, V.guess(t, nDinvx, cache), RootTolSoc, 4e-16, 200);
@@ -246,7 +252,7 @@ __device__ int rsoc_project_warp(double* buf, const double* __restrict__ d, int 
 
 // ---------------------------------------------------------------------------
 // Second-order cone, mixed precision (cones with dim - 1 <= 32 R): the entries
-// stay in registers, weights w_i come precomputed, the root of phi is found in
+// stay in registers, weights w_i come precomputed, the root of psi is found in
 // FP32 and polished by at most three FP64 Newton steps, in which 1 / (1 + mu w) is
 // an FP32 reciprocal refined by two Newton-Raphson steps r <- r (2 - a r) in FP64.
 // Whatever the FP32 pass cannot settle falls back to the full FP64 search.
@@ -309,7 +315,7 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
         }
         rng = __all_sync(0xffffffffu, rng);
         bool known, near = t > 0.0 && soc_cached_near(cache, known);
-        if (t > 0.0 && !known) {  // sign of phi at mu = 1/2
+        if (t > 0.0 && !known) {  // sign of psi at mu = 1/2
             if (rng) {
                 float S = 0.0f;
 #pragma unroll
@@ -329,7 +335,7 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
             }
         }
         const SocVar<double> V(t, near);
-        // ---- FP32 root of phi
+        // ---- FP32 root of psi
         const SocVar<float> Vf(V);
         auto ev32 = [&](float u, float& ph, float& dph, float& sc) {
             float S = 0.0f, S2 = 0.0f;
@@ -343,7 +349,7 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
             }
             S = warp_sum_f(S);
             S2 = warp_sum_f(S2);
-            Vf.phi(u, sqrtf(S), S2, ph, dph, sc);
+            Vf.psi(u, sqrtf(S), S2, ph, dph, sc);
         };
         float uf = 0.0f;
         bool ok = rng;
@@ -371,7 +377,7 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
                 S = warp_sum(S);
                 S2 = warp_sum(S2);
                 double ph, dph, sc;
-                V.phi(u, sqrt(S), S2, ph, dph, sc);
+                V.psi(u, sqrt(S), S2, ph, dph, sc);
                 if (fabs(ph) <= 1.6e-15 * sc) {  // zero to working precision
                     u = fmax(u, 0.0);
                     conv = true;
@@ -397,7 +403,7 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
                 }
                 S = warp_sum(S);
                 S2 = warp_sum(S2);
-                V.phi(uu, sqrt(S), S2, ph, dph, sc);
+                V.psi(uu, sqrt(S), S2, ph, dph, sc);
             };
             u = soc_root<double>(ev, V.tpos, V.guess(t, nDinvx, nullptr), RootTolSoc, 4e-16, 200);
         }

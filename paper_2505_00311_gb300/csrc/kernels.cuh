@@ -60,6 +60,7 @@ struct Dev {
     // blocks of the cone-structured kernels: exp cones in [0, nb_exp), SOC cones in the
     // next nb_soc, scalar rows in the last nb_scal (the costliest work is dispatched first)
     int nb_scal, nb_soc, nb_exp;
+    int exp_pb;  // exp cones per exp block (threads beyond it idle): spreads them over all SMs
     int nb_primal;
     // reductions and control
     double* part;
@@ -290,8 +291,8 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
             __syncwarp();
         }
     } else {
-        const int stride = D.nb_exp * blockDim.x;
-        for (int e = b * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
+        const int stride = D.nb_exp * D.exp_pb;
+        for (int e = b * D.exp_pb + threadIdx.x; threadIdx.x < D.exp_pb && e < D.n_exp; e += stride) {
             const int r = D.exp_row0 + 3 * e;
             T y[3], kx[3], v[3], out[3];
 #pragma unroll
@@ -405,8 +406,8 @@ __global__ void __launch_bounds__(kBlock) cand_dual(Dev<T> D) {
             soc_project_any<true>(out + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, nullptr);
         }
     } else {
-        const int stride = D.nb_exp * blockDim.x;
-        for (int e = b * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
+        const int stride = D.nb_exp * D.exp_pb;
+        for (int e = b * D.exp_pb + threadIdx.x; threadIdx.x < D.exp_pb && e < D.n_exp; e += stride) {
             const int r = D.exp_row0 + 3 * e;
             double o3[3];
             exp_dual_project_fast(val(r), val(r + 1), val(r + 2), D.dr[r], D.dr[r + 1], D.dr[r + 2],
@@ -485,8 +486,8 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
             __syncwarp();
         }
     } else {
-        const int stride = D.nb_exp * blockDim.x;
-        for (int e = b * blockDim.x + threadIdx.x; e < D.n_exp; e += stride) {
+        const int stride = D.nb_exp * D.exp_pb;
+        for (int e = b * D.exp_pb + threadIdx.x; threadIdx.x < D.exp_pb && e < D.n_exp; e += stride) {
             const int r = D.exp_row0 + 3 * e;
             double v[3], w[3], ps[3], pu[3];
             for (int k = 0; k < 3; ++k) {

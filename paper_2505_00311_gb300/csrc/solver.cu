@@ -321,7 +321,10 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     const int nb_soc = ctx->n_soc > 0 ? (int)std::min<long long>((ctx->n_soc + kWarpsPerBlock - 1) / kWarpsPerBlock,
                                                                  (long long)ctx->sms * 8)
                                       : 0;
-    const int nb_exp = ctx->n_exp > 0 ? vec_grid(ctx->n_exp, ctx->sms) : 0;
+    // exp cones: one thread each, at most 256 per block but no fewer blocks than SMs
+    // while each keeps a full warp (their FP64 work is bound by each SM's FP64 units)
+    const int exp_pb = (int)std::min<long long>(256, std::max<long long>(32, (ctx->n_exp / std::max(1, ctx->sms)) / 32 * 32));
+    const int nb_exp = ctx->n_exp > 0 ? (int)std::min<long long>((ctx->n_exp + exp_pb - 1) / exp_pb, (long long)ctx->sms * 8) : 0;
     ctx->g_dual = std::max(1, nb_scal + nb_soc + nb_exp);
     PartLayout pl;
     pl.primal_blocks = ctx->g_vec_n;
@@ -483,7 +486,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.n_soc = ctx->n_soc; D.soc_off = ctx->soc_off; D.soc_dim = ctx->soc_dim; D.soc_rot = ctx->soc_rot;
     D.soc_lam = ctx->soc_lam; D.soc_w = ctx->soc_w; D.soc_wp = ctx->soc_wp; D.exp_lg = ctx->exp_lg;
     D.exp_row0 = ctx->exp_row0; D.n_exp = ctx->n_exp; D.exp_L = ctx->exp_L;
-    D.nb_scal = nb_scal; D.nb_soc = nb_soc; D.nb_exp = nb_exp; D.nb_primal = ctx->g_vec_n;
+    D.nb_scal = nb_scal; D.nb_soc = nb_soc; D.nb_exp = nb_exp; D.exp_pb = exp_pb; D.nb_primal = ctx->g_vec_n;
     D.part = ctx->part; D.pl = pl; D.ctrl = ctx->ctrl;
     D.l_orig = ctx->l0; D.u_orig = ctx->u0;
 
