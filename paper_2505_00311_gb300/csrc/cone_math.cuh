@@ -386,7 +386,12 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
                 const double step = ph / dph;
                 if (!isfinite(step)) break;
                 u -= step;
-                if (fabs(step) <= RootTolSoc * (V.tpos ? fmin(u, 1.0 - u) : u)) { conv = true; break; }
+                // psi is nearly affine: the error after a Newton step is of order its
+                // square, so a first step below 1e-7 relative (from the FP32 root) is final
+                if (fabs(step) <= (it == 0 ? 1e-7 : RootTolSoc) * (V.tpos ? fmin(u, 1.0 - u) : u)) {
+                    conv = true;
+                    break;
+                }
             }
             conv = conv && u >= 0.0 && (!V.tpos || u < 1.0);
         }
@@ -505,14 +510,20 @@ struct ExpCase4T {
 };
 using ExpCase4 = ExpCase4T<double>;
 
+// Everything known at one log-offset L (see exp_eval).
+template <typename R>
+struct ExpAt {
+    R F, dF, rho, lsp, lrd, Fs;  // F, dF/dL, rho, log s_p, log r_d, size of the terms of F
+    R A, B, dA, dB, drho;        // A, B of F and their derivatives, drho/dL
+};
+
 // At log-offset L (rho = anchor + dir e^L): rho, log s_p, log r_d (eq. sp_rd via
 // eq. tilde_defs, the vanishing factor as log r0 + L or log s0 + L), and
 // F(L) = lhs - rhs with the sign of h(rho) (eq. h_rho) decided in logs:
 //   t0 >= 0: lhs = A, rhs = log(e^B + t0);  t0 < 0: lhs = log(e^A - t0), rhs = B,
 //   A = log(d_t e^rho s_p), B = log(d_t^{-1} e^{-rho} r_d);  dF = dF/dL.
 template <typename R>
-__host__ __device__ __forceinline__ void exp_F(const ExpCase4T<R>& e, R L, R& F, R& dF, R& rho_out, R& lsp_out,
-                                               R& lrd_out, R& Fscale_out) {
+__host__ __device__ __forceinline__ void exp_eval(const ExpCase4T<R>& e, R L, ExpAt<R>& o) {
     const R one = R(1), zero = R(0);
     const R delta = exp(L);
     R rho, rm1, lst, lrt, dlst, dlrt;  // rm1 = rho - 1 from the exact offset; logs of |s~|, |r~|
@@ -563,19 +574,37 @@ __host__ __device__ __forceinline__ void exp_F(const ExpCase4T<R>& e, R L, R& F,
         R wB = one;
         const R rhs = e.t0 > zero ? lse_w(B, e.lt0, wB) : B;
         if (B == ninf) wB = zero;
-        F = A - rhs;
-        dF = dA - wB * dB;
-        Fscale_out = fabs(A) + fabs(rhs);
+        o.F = A - rhs;
+        o.dF = dA - wB * dB;
+        o.Fs = fabs(A) + fabs(rhs);
     } else {
         R wA;
         const R lhs = lse_w(A, e.lt0, wA);
-        F = lhs - B;
-        dF = wA * dA - dB;
-        Fscale_out = fabs(lhs) + fabs(B);
+        o.F = lhs - B;
+        o.dF = wA * dA - dB;
+        o.Fs = fabs(lhs) + fabs(B);
     }
-    rho_out = rho;
-    lsp_out = lsp;
-    lrd_out = lrd;
+    o.rho = rho;
+    o.lsp = lsp;
+    o.lrd = lrd;
+    o.A = A;
+    o.B = B;
+    o.dA = dA;
+    o.dB = dB;
+    o.drho = e.dir * delta;
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ void exp_F(const ExpCase4T<R>& e, R L, R& F, R& dF, R& rho_out, R& lsp_out,
+                                               R& lrd_out, R& Fscale_out) {
+    ExpAt<R> o;
+    exp_eval(e, L, o);
+    F = o.F;
+    dF = o.dF;
+    rho_out = o.rho;
+    lsp_out = o.lsp;
+    lrd_out = o.lrd;
+    Fscale_out = o.Fs;
 }
 
 template <typename R>
@@ -787,6 +816,24 @@ __host__ __device__ __forceinline__ void exp_case4_output(const ExpCase4& e, dou
     out[2] = t0 >= 0.0 ? t0 - vd[2] : vp[2];
 }
 
+// The result of case 4 at the root L* = L + s from the values at L (s small): v_p and
+// v_d of eq. vpvd_defn to first order in s (the error is of order s^2), then the same
+// per-coordinate choice as exp_case4_output.
+__host__ __device__ __forceinline__ void exp_case4_output_lin(const ExpAt<double>& a, double s, double r0, double s0,
+                                                              double t0, double dr, double ds, double* out) {
+    const double sp = exp(a.lsp), rd = exp(a.lrd), eA = exp(a.A), eB = exp(a.B);
+    const double dlsp = a.dA - a.drho, dlrd = a.dB + a.drho;  // A = ldt + rho + lsp, B = -ldt - rho + lrd
+    const double dsp = sp > 0.0 ? sp * dlsp : 0.0, drd = rd > 0.0 ? rd * dlrd : 0.0;
+    const double vp[3] = {dr * (a.rho * sp + s * (a.drho * sp + a.rho * dsp)), ds * (sp + s * dsp),
+                          eA > 0.0 ? eA * (1.0 + s * a.dA) : 0.0};
+    const double vd[3] = {(rd + s * drd) / dr, ((1.0 - a.rho) * rd + s * ((1.0 - a.rho) * drd - a.drho * rd)) / ds,
+                          eB > 0.0 ? -eB * (1.0 + s * a.dB) : 0.0};
+    const double v0[3] = {r0, s0, t0};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) out[k] = fabs(vp[k]) <= fabs(vd[k]) ? vp[k] : v0[k] - vd[k];
+    out[2] = t0 >= 0.0 ? t0 - vd[2] : vp[2];
+}
+
 // Projection of v0 onto D K_exp, D = diag(dr, ds, dt) (Theorem 3), all in FP64 with
 // the safeguarded search.  L_cache (may be null): last log-offset of this cone, used
 // as the Newton start and updated.
@@ -932,22 +979,24 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
         e.kind = ef.kind;
         e.anchor = ef.anchor;
         e.dir = (double)ef.dir;
+        // Newton steps s until one is small enough that the result at L + s follows from
+        // the values at L to first order (error of order s^2)
         double L = (double)Lf;
-        ok = false;
         for (int it = 0; it < 3; ++it) {
-            double F, dF, rho, lsp, lrd, Fs;
-            exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
-            if (Fs < INFINITY && fabs(F) <= 4.0 * RootTol<double>::collapse * Fs) { ok = true; break; }
-            const double st = -F / dF;  // Newton in delta next to the anchor (see exp_newton), else in L
-            const double step = ef.dm ? (st > -1.0 ? log1p(st) : NAN) : st;
-            if (!isfinite(step)) break;
-            L += step;
-            if (fabs(step) <= RootTol<double>::newton * fmax(1.0, fabs(L))) { ok = true; break; }
-        }
-        if (ok) {
-            if (L_cache) *L_cache = (float)L;
-            exp_case4_output(e, L, r0, s0, t0, dr, ds, out);
-            return;
+            ExpAt<double> a;
+            exp_eval(e, L, a);
+            double st = 0.0;
+            if (!(a.Fs < INFINITY && fabs(a.F) <= 4.0 * RootTol<double>::collapse * a.Fs)) {
+                st = -a.F / a.dF;  // Newton in delta next to the anchor (see exp_newton), else in L
+                st = ef.dm ? (st > -1.0 ? log1p(st) : NAN) : st;
+                if (!isfinite(st)) break;
+            }
+            if (fabs(st) <= 1e-8) {  // (1e-7 left errors near 1e-12 on stressed inputs)
+                if (L_cache) *L_cache = (float)(L + st);
+                exp_case4_output_lin(a, st, r0, s0, t0, dr, ds, out);
+                return;
+            }
+            L += st;
         }
     }
     double Lc = L_cache ? (double)*L_cache : NAN;
