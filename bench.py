@@ -222,7 +222,7 @@ def main():
     B.build()
     p = make_workload(args.workload)
     stream = torch.cuda.Stream()
-    solver = P.Solver(p, stream=stream.cuda_stream)
+    solver = P.Solver(p, stream=stream.cuda_stream, spmv_autotune=1)
 
     def barrier():
         if dist is not None:
@@ -263,7 +263,7 @@ def main():
     # the same number of evaluations, solution read back (D2H)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s2 = P.Solver(p, stream=stream.cuda_stream)
+    s2 = P.Solver(p, stream=stream.cuda_stream, spmv_autotune=1)
     s2.run(evals)
     x, y = s2.solution()
     torch.cuda.synchronize()
@@ -279,7 +279,7 @@ def main():
     ttt = []
     if args.time_to_tol:
         for tol in [float(t) for t in args.time_to_tol.split(",") if t]:
-            s3 = P.Solver(p, stream=stream.cuda_stream, time_limit=args.ttt_limit)
+            s3 = P.Solver(p, stream=stream.cuda_stream, time_limit=args.ttt_limit, spmv_autotune=1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st, inf = s3.solve(tol, 2_000_000)

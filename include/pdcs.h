@@ -84,8 +84,13 @@ typedef struct {
     int32_t precision;      /* PDCS_PRECISION_*: FP32 iterates with FP64 checks and FP64 polish */
     double fp32_switch_tol; /* FP32 mode: switch to FP64 once the relative KKT error is below this */
     int32_t use_graphs;     /* 1: replay each check period as one CUDA graph, default 1 */
-    int32_t spmv_lanes;     /* lanes per CSR row in SpMV (1..32, power of 2); 0: autotune */
+    int32_t spmv_lanes;     /* lanes per CSR row in SpMV (1..32, power of 2) for every row; 0: rows
+                               binned by length, lanes per row matched to each bin */
     double time_limit;      /* seconds for pdcs_solve; 0: none */
+    int32_t spmv_autotune;  /* 1: at create, time the candidate SpMV plans of K and K' (bin shift,
+                               unroll) over 20 launches each and keep the fastest; the choice is
+                               cached per process by matrix signature (rows, nnz, length histogram).
+                               0 (default): the fixed plan (shift 2, unroll 2) */
 } pdcs_options;
 
 typedef struct {

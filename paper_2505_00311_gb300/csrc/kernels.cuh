@@ -86,33 +86,81 @@ struct Dev {
 };
 
 // ---------------------------------------------------------------------------
-// SpMV: y = A x, CSR, G lanes per row, a warp covers 32 / G rows at a time.
+// SpMV: y = A x, CSR.  The rows are grouped in bins by length (host side, once per
+// matrix); bin k runs lanes[k] lanes per row (a power of two, so that each lane
+// takes a few entries), a warp covering 32 / lanes rows at a time, and the bins of
+// the longest rows come first in the grid.  Each lane issues U independent
+// (column, value) loads before the gathers of x, for memory-level parallelism; its
+// entries are summed in order, then the row's lanes by a shuffle tree, so a row's
+// result depends only on its lane count.
 // sel: 0 -> write y0;  1 -> write y0 / y1 by the parity of ctrl->attempts.
 // skip: 0 never; 1 when not running; 2 when not running or the step was rejected.
 // ---------------------------------------------------------------------------
-template <typename T, typename TO, int G>
-__global__ void __launch_bounds__(kBlock) spmv_csr(int rows, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                   const T* __restrict__ val, const T* __restrict__ x, TO* y0, TO* y1,
-                                                   const Ctrl* ctrl, int sel, int skip) {
+constexpr int kSpmvMaxBins = 6;  // lane counts 32, 16, 8, 4, 2, 1
+struct SpmvBins {
+    int nbins;
+    int blk[kSpmvMaxBins + 1];  // first block of each bin; blk[nbins] = grid size
+    int row[kSpmvMaxBins + 1];  // first entry of each bin in the row list
+    int lanes[kSpmvMaxBins];
+};
+
+template <typename T, typename TO, int G, int U>
+__device__ __forceinline__ void spmv_bin_rows(const int* __restrict__ list, int count, int wb, int nwb,
+                                              const int* __restrict__ rp, const int* __restrict__ ci,
+                                              const T* __restrict__ val, const T* __restrict__ x, TO* y) {
+    constexpr int RPW = 32 / G;
+    const int lane = threadIdx.x & 31, g = lane / G, gl = lane % G;
+    for (long long i0 = (long long)wb * RPW; i0 < count; i0 += (long long)nwb * RPW) {
+        const long long i = i0 + g;
+        T acc = T(0);
+        int r = -1;
+        if (i < count) {
+            r = __ldg(list + i);
+            const int e = __ldg(rp + r + 1);
+            for (int p = __ldg(rp + r) + gl; p < e; p += G * U) {
+                int c[U];
+                T v[U], xv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int q = p + u * G;
+                    c[u] = q < e ? __ldg(ci + q) : -1;
+                    v[u] = q < e ? __ldg(val + q) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : T(0);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (c[u] >= 0) acc += v[u] * xv[u];
+            }
+        }
+        acc = group_sum<G>(acc);
+        if (r >= 0 && gl == 0) y[r] = (TO)acc;
+    }
+}
+
+template <typename T, typename TO, int U>
+__global__ void __launch_bounds__(kBlock) spmv_binned(SpmvBins B, const int* __restrict__ list,
+                                                      const int* __restrict__ rp, const int* __restrict__ ci,
+                                                      const T* __restrict__ val, const T* __restrict__ x, TO* y0,
+                                                      TO* y1, const Ctrl* ctrl, int sel, int skip) {
     if (skip) {
         if (ctrl->status != kRunning) return;
         if (skip == 2 && !ctrl->pending) return;
     }
     TO* y = (sel == 1 && (ctrl->attempts & 1)) ? y1 : y0;
-    const int lane = threadIdx.x & 31;
-    const int g = lane / G, gl = lane % G;
-    constexpr int RPW = 32 / G;
-    const long long wglob = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long r0 = wglob * RPW; r0 < rows; r0 += nw * RPW) {
-        const long long r = r0 + g;
-        T acc = T(0);
-        if (r < rows) {
-            const int e = __ldg(rp + r + 1);
-            for (int p = __ldg(rp + r) + gl; p < e; p += G) acc += __ldg(val + p) * __ldg(x + __ldg(ci + p));
-        }
-        acc = group_sum<G>(acc);
-        if (r < rows && gl == 0) y[r] = (TO)acc;
+    int k = 0;
+    while (k + 1 < B.nbins && (int)blockIdx.x >= B.blk[k + 1]) ++k;
+    const int wb = ((int)blockIdx.x - B.blk[k]) * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int nwb = (B.blk[k + 1] - B.blk[k]) * kWarpsPerBlock;
+    const int* l = list + B.row[k];
+    const int cnt = B.row[k + 1] - B.row[k];
+    switch (B.lanes[k]) {
+        case 1: spmv_bin_rows<T, TO, 1, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        case 2: spmv_bin_rows<T, TO, 2, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        case 4: spmv_bin_rows<T, TO, 4, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        case 8: spmv_bin_rows<T, TO, 8, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        case 16: spmv_bin_rows<T, TO, 16, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        default: spmv_bin_rows<T, TO, 32, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
     }
 }
 

@@ -8,6 +8,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -50,6 +52,14 @@ struct Arena {
     }
 };
 
+// SpMV plan of one matrix: rows binned by length (see spmv_binned) and the unroll.
+struct SpmvPlan {
+    SpmvBins B{};
+    int* list = nullptr;  // device row list, bin by bin
+    int shift = 2;        // lanes = 2^(ceil(log2(length)) - shift), clamped to 1..32
+    int unroll = 2;
+};
+
 }  // namespace
 
 struct pdcs_ctx {
@@ -84,8 +94,8 @@ struct pdcs_ctx {
     Ctrl* h_ctrl = nullptr;  // pinned host mirror
 
     Dev<double> D;
-    int G = 8, GT = 4;
-    int g_vec_n = 0, g_vec_m = 0, g_dual = 0, g_spmv_k = 0, g_spmv_kt = 0, g_kktd = 0;
+    SpmvPlan pk, pkt;  // K (m rows) and K' (n rows)
+    int g_vec_n = 0, g_vec_m = 0, g_dual = 0, g_kktd = 0;
 
     cudaGraphExec_t graph = nullptr;
     bool started = false;
@@ -114,16 +124,75 @@ struct pdcs_ctx {
 namespace {
 
 template <typename T, typename TO>
-void launch_spmv(int G, int grid, cudaStream_t s, int rows, const int* rp, const int* ci, const T* val, const T* x,
-                 TO* y0, TO* y1, const Ctrl* ctrl, int sel, int skip) {
-    switch (G) {
-        case 1: spmv_csr<T, TO, 1><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
-        case 2: spmv_csr<T, TO, 2><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
-        case 4: spmv_csr<T, TO, 4><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
-        case 8: spmv_csr<T, TO, 8><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
-        case 16: spmv_csr<T, TO, 16><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
-        default: spmv_csr<T, TO, 32><<<grid, kBlock, 0, s>>>(rows, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
+void launch_spmv(const SpmvPlan& P, cudaStream_t s, const int* rp, const int* ci, const T* val, const T* x, TO* y0,
+                 TO* y1, const Ctrl* ctrl, int sel, int skip) {
+    const int grid = P.B.blk[P.B.nbins];
+    if (grid <= 0) return;
+    switch (P.unroll) {
+        case 1: spmv_binned<T, TO, 1><<<grid, kBlock, 0, s>>>(P.B, P.list, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
+        case 4: spmv_binned<T, TO, 4><<<grid, kBlock, 0, s>>>(P.B, P.list, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
+        default: spmv_binned<T, TO, 2><<<grid, kBlock, 0, s>>>(P.B, P.list, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
     }
+}
+
+// Bins of a CSR matrix: lanes per row 2^(ceil(log2(len)) - shift) clamped to 1..32 (or
+// `fixed` for every row), bins ordered by decreasing lanes, rows increasing within a
+// bin; a bin gets enough blocks for one pass over its rows (at most 32 per SM).
+void plan_bins(const std::vector<int>& rp, int rows, int shift, int fixed, int sms, std::vector<int>& list,
+               SpmvBins& B) {
+    std::vector<unsigned char> bin_of(rows);
+    long long cnt[kSpmvMaxBins] = {0};
+    for (int r = 0; r < rows; ++r) {
+        int lanes = fixed;
+        if (lanes <= 0) {
+            const int len = rp[r + 1] - rp[r];
+            int lg = 0;
+            while ((1 << lg) < len) ++lg;  // ceil(log2(len))
+            lanes = 1 << std::min(5, std::max(0, lg - shift));
+        }
+        int k = 0;  // bin 0: 32 lanes ... bin 5: 1 lane
+        while ((32 >> k) > lanes) ++k;
+        bin_of[r] = (unsigned char)k;
+        ++cnt[k];
+    }
+    list.resize(rows);
+    long long pos[kSpmvMaxBins] = {0};
+    B.nbins = 0;
+    int blk = 0, row = 0;
+    for (int k = 0; k < kSpmvMaxBins; ++k) {
+        if (!cnt[k]) continue;
+        const int lanes = 32 >> k;
+        const long long rows_per_block = (long long)kWarpsPerBlock * (32 / lanes);
+        const long long nb = std::min((cnt[k] + rows_per_block - 1) / rows_per_block, (long long)sms * 32);
+        B.blk[B.nbins] = blk;
+        B.row[B.nbins] = row;
+        B.lanes[B.nbins] = lanes;
+        pos[k] = row;
+        blk += (int)nb;
+        row += (int)cnt[k];
+        ++B.nbins;
+    }
+    B.blk[B.nbins] = blk;
+    B.row[B.nbins] = row;
+    for (int r = 0; r < rows; ++r) list[pos[bin_of[r]]++] = r;
+}
+
+// Process-wide cache of tuned SpMV plans (shift, unroll), keyed by matrix signature.
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+std::string spmv_signature(const std::vector<int>& rp, int rows) {
+    long long hist[40] = {0};
+    for (int r = 0; r < rows; ++r) {
+        const int len = rp[r + 1] - rp[r];
+        int lg = 0;
+        while ((1 << lg) < len && lg < 39) ++lg;
+        ++hist[lg];
+    }
+    std::string sig = std::to_string(rows) + ":" + std::to_string(rp[rows]);
+    for (int k = 0; k < 40; ++k)
+        if (hist[k]) sig += ":" + std::to_string(k) + "=" + std::to_string(hist[k]);
+    return sig;
 }
 
 int spmv_grid(int rows, int G, int sms) {
@@ -137,11 +206,6 @@ int vec_grid(long long k, int sms) {
     return (int)std::max(1LL, std::min(g, (long long)sms * 8));
 }
 
-int choose_lanes(long long nnz, long long rows) {
-    double avg = rows > 0 ? (double)nnz / (double)rows : 1.0;
-    int g = pow2_floor(std::max(1, (int)std::ceil(avg / 3.0)));
-    return std::min(32, std::max(2, g));
-}
 
 // Kernel classes of pdcs_kernel_times (see include/pdcs.h).
 constexpr int kKernelClasses = 12;
@@ -158,6 +222,61 @@ struct Prof {
     }
 };
 
+// Times the candidate plans of one matrix (bin shift 1..4, unroll 1, 2, 4; 3 warm-up and
+// 20 timed launches each on the given vectors) and keeps the fastest in P, with its
+// row list uploaded.  The choice is cached per process by the matrix signature.
+cudaError_t tune_spmv(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, int rows, const int* drp,
+                      const int* dci, const double* dval, const double* x, double* y) {
+    cudaStream_t s = ctx->stream;
+    if (rows <= 0) return cudaSuccess;
+    const std::string sig = spmv_signature(rp, rows);
+    int shift = P.shift, unroll = P.unroll;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(sig);
+        if (it != g_tune_cache.end()) { shift = it->second.first; unroll = it->second.second; cached = true; }
+    }
+    std::vector<int> list;
+    cudaError_t e = cudaSuccess;
+    if (!cached) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+        if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+        float best = 1e30f;
+        for (int sh = 1; sh <= 4 && e == cudaSuccess; ++sh) {
+            SpmvPlan c = P;
+            plan_bins(rp, rows, sh, 0, ctx->sms, list, c.B);
+            e = cudaMemcpyAsync(P.list, list.data(), sizeof(int) * rows, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            for (int un = 1; un <= 4 && e == cudaSuccess; un *= 2) {
+                c.shift = sh;
+                c.unroll = un;
+                for (int r = 0; r < 3; ++r) launch_spmv<double, double>(c, s, drp, dci, dval, x, y, nullptr, nullptr, 0, 0);
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 20; ++r) launch_spmv<double, double>(c, s, drp, dci, dval, x, y, nullptr, nullptr, 0, 0);
+                cudaEventRecord(e1, s);
+                e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && ms < best) { best = ms; shift = sh; unroll = un; }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[sig] = std::make_pair(shift, unroll);
+    }
+    P.shift = shift;
+    P.unroll = unroll;
+    plan_bins(rp, rows, shift, 0, ctx->sms, list, P.B);
+    e = cudaMemcpyAsync(P.list, list.data(), sizeof(int) * rows, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
 constexpr int kLaunchesPerAttempt = 4;
 constexpr int kLaunchesPerCheck = 12;
 
@@ -168,11 +287,11 @@ void enqueue_attempt(pdcs_ctx* ctx, Prof* P = nullptr) {
     if (P) P->mark(0, s);
     primal_update<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
     if (P) { P->mark(0, s); P->mark(1, s); }
-    launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, ctx->m, D.rp, D.ci, D.val, D.xh, D.kxh0, D.kxh1, D.ctrl, 1, 1);
+    launch_spmv<double, double>(ctx->pk, s, D.rp, D.ci, D.val, D.xh, D.kxh0, D.kxh1, D.ctrl, 1, 1);
     if (P) { P->mark(1, s); P->mark(2, s); }
     dual_update<double><<<ctx->g_dual, kBlock, 0, s>>>(D);
     if (P) { P->mark(2, s); P->mark(3, s); }
-    launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, ctx->n, D.rpT, D.ciT, D.valT, D.yh, D.ktyh, nullptr,
+    launch_spmv<double, double>(ctx->pkt, s, D.rpT, D.ciT, D.valT, D.yh, D.ktyh, nullptr,
                                 D.ctrl, 0, 2);
     if (P) P->mark(3, s);
     ctx->launches += kLaunchesPerAttempt;
@@ -194,9 +313,9 @@ void enqueue_check(pdcs_ctx* ctx, Prof* P = nullptr) {
     cand_dual<double><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(D);
     mark(7); mark(8);
     for (int q = 0; q < 2; ++q) {
-        launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, ctx->m, D.rp, D.ci, D.val, D.xc + (size_t)q * ctx->n,
+        launch_spmv<double, double>(ctx->pk, s, D.rp, D.ci, D.val, D.xc + (size_t)q * ctx->n,
                                     D.kxc + (size_t)q * ctx->m, nullptr, D.ctrl, 0, 1);
-        launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, ctx->n, D.rpT, D.ciT, D.valT,
+        launch_spmv<double, double>(ctx->pkt, s, D.rpT, D.ciT, D.valT,
                                     D.yc + (size_t)q * ctx->m, D.ktyc + (size_t)q * ctx->n, nullptr, D.ctrl, 0, 1);
     }
     mark(8); mark(9);
@@ -310,12 +429,11 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     for (int j = 0; j < n; ++j) cmax = std::max(cmax, std::fabs(c[j]));
 
     // ---- device memory plan
-    ctx->G = ctx->opt.spmv_lanes > 0 ? ctx->opt.spmv_lanes : choose_lanes(nnz, m);
-    ctx->GT = ctx->opt.spmv_lanes > 0 ? ctx->opt.spmv_lanes : choose_lanes(nnz, n);
+    std::vector<int> list_k, list_kt;  // SpMV row lists (default plans; tuned below on request)
+    plan_bins(rp_i, m, ctx->pk.shift, ctx->opt.spmv_lanes, ctx->sms, list_k, ctx->pk.B);
+    plan_bins(rpT, n, ctx->pkt.shift, ctx->opt.spmv_lanes, ctx->sms, list_kt, ctx->pkt.B);
     ctx->g_vec_n = vec_grid(n, ctx->sms);
     ctx->g_vec_m = vec_grid(m, ctx->sms);
-    ctx->g_spmv_k = spmv_grid(m, ctx->G, ctx->sms);
-    ctx->g_spmv_kt = spmv_grid(n, ctx->GT, ctx->sms);
     ctx->g_kktd = vec_grid(n, ctx->sms);
     const int nb_scal = ctx->m_scalar > 0 ? vec_grid(ctx->m_scalar, ctx->sms) : 0;
     const int nb_soc = ctx->n_soc > 0 ? (int)std::min<long long>((ctx->n_soc + kWarpsPerBlock - 1) / kWarpsPerBlock,
@@ -339,6 +457,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
 
     Arena& A = ctx->arena;
     A.reserve<int>(m + 1); A.reserve<int>(nnz); A.reserve<int>(n + 1); A.reserve<int>(nnz);
+    A.reserve<int>(m + 1); A.reserve<int>(n + 1);                    // SpMV row lists
     for (int k = 0; k < 4; ++k) A.reserve<double>(nnz);              // val0, val0T, val, valT
     for (int k = 0; k < 4; ++k) A.reserve<double>(n);                // c0 l0 u0 + cs
     A.reserve<double>(m); A.reserve<double>(m);                      // h0, hs
@@ -365,6 +484,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     }
     ctx->rp = A.take<int>(m + 1); ctx->ci = A.take<int>(nnz);
     ctx->rpT = A.take<int>(n + 1); ctx->ciT = A.take<int>(nnz);
+    ctx->pk.list = A.take<int>(m + 1); ctx->pkt.list = A.take<int>(n + 1);
     ctx->val0 = A.take<double>(nnz); ctx->val0T = A.take<double>(nnz);
     ctx->val = A.take<double>(nnz); ctx->valT = A.take<double>(nnz);
     ctx->c0 = A.take<double>(n); ctx->l0 = A.take<double>(n); ctx->u0 = A.take<double>(n); ctx->cs = A.take<double>(n);
@@ -393,6 +513,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     CK(cudaMemcpyAsync(ctx->ci, ci_i.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->rpT, rpT.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->ciT, ciT.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+    if (m) CK(cudaMemcpyAsync(ctx->pk.list, list_k.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    if (n) CK(cudaMemcpyAsync(ctx->pkt.list, list_kt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->val0, v_i.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->val0T, vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->c0, c, sizeof(double) * n, cudaMemcpyHostToDevice, s));
@@ -410,6 +532,12 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     }
     // the host copies above are pageable: wait before the vectors go out of scope
     CK(cudaStreamSynchronize(s));
+
+    // ---- SpMV plans timed on the unscaled matrices (same structure), on request
+    if (ctx->opt.spmv_autotune && ctx->opt.spmv_lanes == 0) {
+        CK(tune_spmv(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val0, ctx->D.x, ctx->D.kx));
+        CK(tune_spmv(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->val0T, ctx->D.y, ctx->D.kty));
+    }
 
     // ---- diagonal rescaling: Ruiz (infinity norm) then Pock-Chambolle (alpha = 1)
     std::vector<double> ones_m(m, 1.0), ones_n(n, 1.0);
@@ -456,8 +584,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         CK(cudaStreamSynchronize(s));
         double est = 0.0;
         for (int it = 0; it < ctx->opt.power_iters; ++it) {
-            launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, m, ctx->rp, ctx->ci, ctx->val, v, w, nullptr, nullptr, 0, 0);
-            launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, n, ctx->rpT, ctx->ciT, ctx->valT, w, u, nullptr, nullptr, 0, 0);
+            launch_spmv<double, double>(ctx->pk, s, ctx->rp, ctx->ci, ctx->val, v, w, nullptr, nullptr, 0, 0);
+            launch_spmv<double, double>(ctx->pkt, s, ctx->rpT, ctx->ciT, ctx->valT, w, u, nullptr, nullptr, 0, 0);
             reduce_small<<<1, kBlock, 0, s>>>(n, u, nullptr, 0, ctx->scal + 3);
             double ss;
             CK(cudaMemcpyAsync(&ss, ctx->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -577,6 +705,7 @@ void pdcs_default_options(pdcs_options* o) {
     o->use_graphs = 1;
     o->spmv_lanes = 0;
     o->time_limit = 0.0;
+    o->spmv_autotune = 0;
 }
 
 pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, const double* lb, const double* ub,
@@ -625,6 +754,7 @@ pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, con
     if (o.precision != PDCS_PRECISION_FP64) return bad("only FP64 precision is available in this build");
     if (o.spmv_lanes != 0 && (o.spmv_lanes > 32 || (o.spmv_lanes & (o.spmv_lanes - 1)) != 0))
         return bad("spmv_lanes must be 0 or a power of two <= 32");
+    if (o.spmv_autotune != 0 && o.spmv_autotune != 1) return bad("spmv_autotune must be 0 or 1");
 
     pdcs_ctx* ctx = new (std::nothrow) pdcs_ctx();
     if (!ctx) return bad("host allocation failed");
@@ -804,8 +934,8 @@ pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y,
     CK(cudaMemcpyAsync(D.y, ys.data(), sizeof(double) * ctx->m, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(D.y0, ys.data(), sizeof(double) * ctx->m, cudaMemcpyHostToDevice, s));
     // cached products of the start: K x, K'y
-    launch_spmv<double, double>(ctx->G, ctx->g_spmv_k, s, ctx->m, D.rp, D.ci, D.val, D.x, D.kx, nullptr, nullptr, 0, 0);
-    launch_spmv<double, double>(ctx->GT, ctx->g_spmv_kt, s, ctx->n, D.rpT, D.ciT, D.valT, D.y, D.kty, nullptr, nullptr, 0, 0);
+    launch_spmv<double, double>(ctx->pk, s, D.rp, D.ci, D.val, D.x, D.kx, nullptr, nullptr, 0, 0);
+    launch_spmv<double, double>(ctx->pkt, s, D.rpT, D.ciT, D.valT, D.y, D.kty, nullptr, nullptr, 0, 0);
     CK(cudaMemcpyAsync(D.kx0, D.kx, sizeof(double) * ctx->m, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(D.kty0, D.kty, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(D.xsum, 0, sizeof(double) * ctx->n, s));

@@ -42,7 +42,8 @@ class pdcs_options(ctypes.Structure):
                 ("step_mode", ctypes.c_int32), ("check_period", ctypes.c_int32), ("beta", ctypes.c_double),
                 ("power_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("fp32_switch_tol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
-                ("spmv_lanes", ctypes.c_int32), ("time_limit", ctypes.c_double)]
+                ("spmv_lanes", ctypes.c_int32), ("time_limit", ctypes.c_double),
+                ("spmv_autotune", ctypes.c_int32)]
 
 
 class pdcs_info(ctypes.Structure):

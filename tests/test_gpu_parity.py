@@ -277,3 +277,17 @@ def test_graph_and_eager_paths_agree(graphs):
     np.testing.assert_array_equal(ya, yb)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prob_name", ["small_socp", "mixed_small"])
+def test_spmv_plans_agree_with_oracle(prob_name):
+    """Every SpMV plan (rows binned by length, one fixed lane count, the tuned plan)
+    computes the same products up to the order of summation: 16 evaluations stay at
+    the oracle to the iteration-parity tolerance."""
+    p = I.small_socp(0) if prob_name == "small_socp" else I.scaled_mixed_cone(1, 0.01)
+    for opts in [dict(spmv_lanes=1), dict(spmv_lanes=32), dict(spmv_autotune=1)]:
+        g, o = _pair(p, check_period=16, **opts)
+        g.run(16)
+        o.run(16)
+        assert _compare_iterates(g, o) <= RTOL, opts
+        g.close()
