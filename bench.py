@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--impl", default="pdcs", choices=["pdcs", "reference"])
     ap.add_argument("--workload", default="mixed_cone_1m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run (profiling runs)")
     ap.add_argument("--time-to-tol", default="1e-4,1e-6",
                     help="comma list of tolerances for the time-to-solution runs ('' to skip)")
     ap.add_argument("--ttt-limit", type=float, default=120.0, help="seconds allowed per time-to-tolerance run")
@@ -261,19 +262,21 @@ def main():
 
     # end to end through the public API with host buffers: create (H2D + setup),
     # the same number of evaluations, solution read back (D2H)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s2 = P.Solver(p, stream=stream.cuda_stream, spmv_autotune=1)
-    s2.run(evals)
-    x, y = s2.solution()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    s2.close()
-    e2e = {"value": evals / e2e_s, "unit": "iters/s",
-           "h2d_bytes_per_step": int(problem_bytes(p) / args.steps),
-           "d2h_bytes_per_step": int((x.size + y.size) * 8 / args.steps),
-           "includes": "pdcs_create from host arrays (copy + rescaling + K' build) + pdcs_solve + "
-                       "pdcs_get_solution"}
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = P.Solver(p, stream=stream.cuda_stream, spmv_autotune=1)
+        s2.run(evals)
+        x, y = s2.solution()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        s2.close()
+        e2e = {"value": evals / e2e_s, "unit": "iters/s",
+               "h2d_bytes_per_step": int(problem_bytes(p) / args.steps),
+               "d2h_bytes_per_step": int((x.size + y.size) * 8 / args.steps),
+               "includes": "pdcs_create from host arrays (copy + rescaling + K' build) + pdcs_solve + "
+                           "pdcs_get_solution"}
 
     # time to tolerance (separate runs, wall clock of pdcs_solve)
     ttt = []
