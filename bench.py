@@ -184,6 +184,7 @@ def main():
     ap.add_argument("--workload", default="mixed_cone_1m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run (profiling runs)")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-iterate mode measurements")
     ap.add_argument("--time-to-tol", default="1e-4,1e-6",
                     help="comma list of tolerances for the time-to-solution runs ('' to skip)")
     ap.add_argument("--ttt-limit", type=float, default=120.0, help="seconds allowed per time-to-tolerance run")
@@ -294,6 +295,41 @@ def main():
                         "setup_seconds": inf["setup_seconds"]})
             s3.close()
 
+    # the FP32-iterate mode on the same workload: steady-state rate and time to tolerance
+    # (FP32 iterates, FP64 checks, FP64 iterations once the FP32 phase hands over)
+    fp32 = None
+    if not args.no_fp32:
+        s4 = P.Solver(p, stream=stream.cuda_stream, precision=P.PRECISION_FP32, spmv_autotune=1)
+        for _ in range(args.warmup):
+            s4.run(EVALS_PER_STEP)
+        kt32, _ = s4.kernel_times(EVALS_PER_STEP)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            s4.run(EVALS_PER_STEP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1)
+        phase = s4.info()["fp64_phase"]
+        s4.close()
+        ttt32 = []
+        for tol in [float(t) for t in args.time_to_tol.split(",") if t]:
+            s5 = P.Solver(p, stream=stream.cuda_stream, precision=P.PRECISION_FP32, time_limit=args.ttt_limit,
+                          spmv_autotune=1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, inf = s5.solve(tol, 2_000_000)
+            torch.cuda.synchronize()
+            ttt32.append({"tol": tol, "seconds": time.perf_counter() - t0, "status": P.STATUS_NAMES.get(st, st),
+                          "evaluations": inf["attempts"], "fp64_phase_reached": bool(inf["fp64_phase"]),
+                          "err": [inf["err_p"], inf["err_d"], inf["err_gap"]]})
+            s5.close()
+        fp32 = {"value": world * evals / (ms32 / 1000.0), "unit": "iters/s", "ms_per_step": ms32 / args.steps,
+                "dtype": "f32 iterates, f64 checks", "still_fp32_phase": phase == 0,
+                "kernels_ms_per_launch": kt32, "time_to_tol": ttt32}
+
     if rank != 0:
         return
     # roofline of the dominant kernel
@@ -320,7 +356,7 @@ def main():
                        "precision": "fp64", "l2": "working set > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clk, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-            "time_to_tol": ttt}
+            "time_to_tol": ttt, "fp32_iterates": fp32}
     print(json.dumps(line))
 
 

@@ -81,8 +81,15 @@ typedef struct {
     int32_t check_period;   /* restart / termination check every this many PDHG evaluations, default 64 */
     double beta;            /* reflection parameter of ReflectedHalpern, default 1 */
     int32_t power_iters;    /* power iterations for ||K||_2 (constant / plain modes), default 50 */
-    int32_t precision;      /* PDCS_PRECISION_*: FP32 iterates with FP64 checks and FP64 polish */
-    double fp32_switch_tol; /* FP32 mode: switch to FP64 once the relative KKT error is below this */
+    int32_t precision;      /* PDCS_PRECISION_FP64 (default), or PDCS_PRECISION_FP32: SpMV, primal
+                               / dual updates and cone projections on FP32 copies of K~, K~', the
+                               scaled data and the iterates, while the checks (candidates, their
+                               products, KKT residuals, restart and primal-weight decisions) stay
+                               FP64; the FP32 phase hands over to FP64 iterations started from the
+                               check's candidate (see fp32_switch_tol) */
+    double fp32_switch_tol; /* FP32 mode: hand over once the relative KKT error of a check is at
+                               most this (or the requested tol), or when its best value has not
+                               improved by 10 % over 50 checks; default 1e-4 */
     int32_t use_graphs;     /* 1: replay each check period as one CUDA graph, default 1 */
     int32_t spmv_lanes;     /* lanes per CSR row in SpMV (1..32, power of 2) for every row; 0: rows
                                binned by length, lanes per row matched to each bin */
@@ -90,7 +97,7 @@ typedef struct {
     int32_t spmv_autotune;  /* 1: at create, time the candidate SpMV plans of K and K' (bin shift,
                                unroll) over 20 launches each and keep the fastest; the choice is
                                cached per process by matrix signature (rows, nnz, length histogram).
-                               0 (default): the fixed plan (shift 2, unroll 2) */
+                               0 (default): the fixed plan (shift 3, unroll 4) */
 } pdcs_options;
 
 typedef struct {
@@ -105,6 +112,7 @@ typedef struct {
     int32_t status;               /* pdcs_status of the last pdcs_solve */
     int32_t fp64_phase;           /* 1 once FP32 mode has switched to FP64 polishing */
     int64_t kernel_launches;      /* kernels this context has launched so far (graph nodes included) */
+    int32_t spmv_plan[4];         /* SpMV plans in use: bin shift and unroll of K, then of K' */
 } pdcs_info;
 
 typedef struct pdcs_ctx pdcs_ctx;

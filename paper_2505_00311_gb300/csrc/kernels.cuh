@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kBlock) primal_update(Dev<T> D) {
     __shared__ double sm[1][kWarpsPerBlock];
     const bool pend = C->pending != 0;
     const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw, tau = (T)C->tau;
-    double acc[1] = {0.0};
+    T acc_t = T(0);  // per-thread partial in the iterate precision, then FP64 across threads
     const int stride = gridDim.x * blockDim.x;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
         T x = D.x[j], kty = D.kty[j];
@@ -216,9 +216,10 @@ __global__ void __launch_bounds__(kBlock) primal_update(Dev<T> D) {
         }
         T xh = fmin(fmax(x - tau * (D.c[j] - kty), D.l[j]), D.u[j]);
         D.xh[j] = xh;
-        double dx = (double)xh - (double)x;
-        acc[0] += dx * dx;
+        const T dx = xh - x;
+        acc_t += dx * dx;
     }
+    double acc[1] = {(double)acc_t};
     block_sum<1>(acc, sm);
     if (threadIdx.x == 0) D.part[D.pl.off_px + blockIdx.x] = acc[0];
 }
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
     const T* pprev = (att & 1) ? D.kxh0 : D.kxh1;
     const bool pend = C->pending != 0;
     const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw, sigma = (T)C->sigma;
-    double acc[2] = {0.0, 0.0};
+    T acc_t[2] = {T(0), T(0)};  // per-thread partials in the iterate precision, then FP64
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (b >= D.nb_exp + D.nb_soc) {  // scalar rows (blocks dispatched last)
@@ -312,9 +313,9 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
             const T v = y + sigma * (D.h[i] - T(2) * pi + kx);
             const T yh = (i < D.m_zero) ? v : fmax(v, T(0));
             D.yh[i] = yh;
-            const double dy = (double)yh - (double)y;
-            acc[0] += dy * dy;
-            acc[1] += dy * ((double)pi - (double)kx);
+            const T dy = yh - y;
+            acc_t[0] += dy * dy;
+            acc_t[1] += dy * (pi - kx);
         }
     } else if (b >= D.nb_exp) {  // SOC / RSOC blocks
         const int stride = D.nb_soc * kWarpsPerBlock;
@@ -332,9 +333,9 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
                 soc_project_any_f32(D.yh + o, D.soc_w32 + o + 1, D.scr + o, D.dr + o, dim, D.soc_rot[cidx] != 0,
                                     D.soc_lam + cidx);
             for (int i = lane; i < dim; i += 32) {
-                const double dy = (double)D.yh[o + i] - (double)D.y[o + i];
-                acc[0] += dy * dy;
-                acc[1] += dy * ((double)p[o + i] - (double)D.kx[o + i]);
+                const T dy = D.yh[o + i] - D.y[o + i];
+                acc_t[0] += dy * dy;
+                acc_t[1] += dy * (p[o + i] - D.kx[o + i]);
             }
             __syncwarp();
         }
@@ -358,12 +359,13 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
             for (int q = 0; q < 3; ++q) {
                 const T yh = (T)out[q];
                 D.yh[r + q] = yh;
-                const double dy = (double)yh - (double)y[q];
-                acc[0] += dy * dy;
-                acc[1] += dy * ((double)p[r + q] - (double)kx[q]);
+                const T dy = yh - y[q];
+                acc_t[0] += dy * dy;
+                acc_t[1] += dy * (p[r + q] - kx[q]);
             }
         }
     }
+    double acc[2] = {(double)acc_t[0], (double)acc_t[1]};
     block_sum<2>(acc, sm);
     if (threadIdx.x == 0) {
         D.part[D.pl.off_dy + b] = acc[0];

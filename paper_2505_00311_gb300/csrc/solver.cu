@@ -56,8 +56,8 @@ struct Arena {
 struct SpmvPlan {
     SpmvBins B{};
     int* list = nullptr;  // device row list, bin by bin
-    int shift = 2;        // lanes = 2^(ceil(log2(length)) - shift), clamped to 1..32
-    int unroll = 2;
+    int shift = 3;        // lanes = 2^(ceil(log2(length)) - shift), clamped to 1..32
+    int unroll = 4;
 };
 
 }  // namespace
@@ -95,9 +95,16 @@ struct pdcs_ctx {
 
     Dev<double> D;
     SpmvPlan pk, pkt;  // K (m rows) and K' (n rows)
+    // FP32-iterate mode: FP32 copies of K~, K~', c~, h~, l~, u~ and the iterate state;
+    // checks, restarts and the final phase stay FP64 (D)
+    Dev<float> DF;
+    float *val_f = nullptr, *valT_f = nullptr;
+    bool fp32_active = false;          // the FP32 phase is running
+    double fp32_best = INFINITY;       // best relative KKT error seen in the FP32 phase
+    int fp32_stall = 0;                // checks since it last improved by 10 %
     int g_vec_n = 0, g_vec_m = 0, g_dual = 0, g_kktd = 0;
 
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr, graph32 = nullptr;
     bool started = false;
     double setup_seconds = 0.0, solve_seconds = 0.0;
     double norm2 = 0.0;
@@ -106,6 +113,7 @@ struct pdcs_ctx {
 
     ~pdcs_ctx() {
         if (graph) cudaGraphExecDestroy(graph);
+        if (graph32) cudaGraphExecDestroy(graph32);
         if (arena.base) cudaFree(arena.base);
         if (h_ctrl) cudaFreeHost(h_ctrl);
         if (own_stream && stream) cudaStreamDestroy(stream);
@@ -223,13 +231,15 @@ struct Prof {
 };
 
 // Times the candidate plans of one matrix (bin shift 1..4, unroll 1, 2, 4; 3 warm-up and
-// 20 timed launches each on the given vectors) and keeps the fastest in P, with its
-// row list uploaded.  The choice is cached per process by the matrix signature.
+// 20 timed launches each on the given vectors, in the value type T the iterations use)
+// and keeps the fastest in P, with its row list uploaded.  The choice is cached per
+// process by the matrix signature and T.
+template <typename T>
 cudaError_t tune_spmv(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, int rows, const int* drp,
-                      const int* dci, const double* dval, const double* x, double* y) {
+                      const int* dci, const T* dval, const T* x, T* y) {
     cudaStream_t s = ctx->stream;
     if (rows <= 0) return cudaSuccess;
-    const std::string sig = spmv_signature(rp, rows);
+    const std::string sig = spmv_signature(rp, rows) + (sizeof(T) == 4 ? ":f32" : ":f64");
     int shift = P.shift, unroll = P.unroll;
     bool cached = false;
     {
@@ -252,9 +262,9 @@ cudaError_t tune_spmv(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, in
             for (int un = 1; un <= 4 && e == cudaSuccess; un *= 2) {
                 c.shift = sh;
                 c.unroll = un;
-                for (int r = 0; r < 3; ++r) launch_spmv<double, double>(c, s, drp, dci, dval, x, y, nullptr, nullptr, 0, 0);
+                for (int r = 0; r < 3; ++r) launch_spmv<T, T>(c, s, drp, dci, dval, x, y, nullptr, nullptr, 0, 0);
                 cudaEventRecord(e0, s);
-                for (int r = 0; r < 20; ++r) launch_spmv<double, double>(c, s, drp, dci, dval, x, y, nullptr, nullptr, 0, 0);
+                for (int r = 0; r < 20; ++r) launch_spmv<T, T>(c, s, drp, dci, dval, x, y, nullptr, nullptr, 0, 0);
                 cudaEventRecord(e1, s);
                 e = cudaEventSynchronize(e1);
                 if (e == cudaSuccess) e = cudaGetLastError();
@@ -280,37 +290,39 @@ cudaError_t tune_spmv(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, in
 constexpr int kLaunchesPerAttempt = 4;
 constexpr int kLaunchesPerCheck = 12;
 
-// one PDHG evaluation
-void enqueue_attempt(pdcs_ctx* ctx, Prof* P = nullptr) {
+// one PDHG evaluation on the state DT (FP64, or FP32 in the FP32 phase) with the matrix
+// copies of its precision
+template <typename T>
+void enqueue_attempt_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     cudaStream_t s = ctx->stream;
-    Dev<double>& D = ctx->D;
     if (P) P->mark(0, s);
-    primal_update<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
+    primal_update<T><<<ctx->g_vec_n, kBlock, 0, s>>>(DT);
     if (P) { P->mark(0, s); P->mark(1, s); }
-    launch_spmv<double, double>(ctx->pk, s, D.rp, D.ci, D.val, D.xh, D.kxh0, D.kxh1, D.ctrl, 1, 1);
+    launch_spmv<T, T>(ctx->pk, s, DT.rp, DT.ci, DT.val, DT.xh, DT.kxh0, DT.kxh1, DT.ctrl, 1, 1);
     if (P) { P->mark(1, s); P->mark(2, s); }
-    dual_update<double><<<ctx->g_dual, kBlock, 0, s>>>(D);
+    dual_update<T><<<ctx->g_dual, kBlock, 0, s>>>(DT);
     if (P) { P->mark(2, s); P->mark(3, s); }
-    launch_spmv<double, double>(ctx->pkt, s, D.rpT, D.ciT, D.valT, D.yh, D.ktyh, nullptr,
-                                D.ctrl, 0, 2);
+    launch_spmv<T, T>(ctx->pkt, s, DT.rpT, DT.ciT, DT.valT, DT.yh, DT.ktyh, nullptr, DT.ctrl, 0, 2);
     if (P) P->mark(3, s);
     ctx->launches += kLaunchesPerAttempt;
 }
 
-// restart / termination check (or the initial evaluation of the anchor)
-void enqueue_check(pdcs_ctx* ctx, Prof* P = nullptr) {
+// restart / termination check (or the initial evaluation of the anchor): candidates
+// from the state DT, their products and KKT always in FP64
+template <typename T>
+void enqueue_check_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     cudaStream_t s = ctx->stream;
     Dev<double>& D = ctx->D;
     auto mark = [&](int c) { if (P) P->mark(c, s); };
     mark(4);
     ctx->launches += kLaunchesPerCheck;
     mark(5);
-    flush_primal<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
-    flush_dual<double><<<ctx->g_vec_m, kBlock, 0, s>>>(D);
+    flush_primal<T><<<ctx->g_vec_n, kBlock, 0, s>>>(DT);
+    flush_dual<T><<<ctx->g_vec_m, kBlock, 0, s>>>(DT);
     mark(5); mark(6);
-    cand_primal<double><<<dim3(ctx->g_vec_n, 2), kBlock, 0, s>>>(D);
+    cand_primal<T><<<dim3(ctx->g_vec_n, 2), kBlock, 0, s>>>(DT);
     mark(6); mark(7);
-    cand_dual<double><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(D);
+    cand_dual<T><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(DT);
     mark(7); mark(8);
     for (int q = 0; q < 2; ++q) {
         launch_spmv<double, double>(ctx->pk, s, D.rp, D.ci, D.val, D.xc + (size_t)q * ctx->n,
@@ -319,17 +331,31 @@ void enqueue_check(pdcs_ctx* ctx, Prof* P = nullptr) {
                                     D.yc + (size_t)q * ctx->m, D.ktyc + (size_t)q * ctx->n, nullptr, D.ctrl, 0, 1);
     }
     mark(8); mark(9);
-    kkt_primal<double><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(D);
+    kkt_primal<T><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(DT);
     mark(9); mark(10);
-    kkt_dual<double><<<ctx->g_kktd, kBlock, 0, s>>>(D);
+    kkt_dual<T><<<ctx->g_kktd, kBlock, 0, s>>>(DT);
     mark(10); mark(11);
-    restart_primal<double><<<ctx->g_vec_n, kBlock, 0, s>>>(D);
-    restart_dual<double><<<ctx->g_vec_m, kBlock, 0, s>>>(D);
+    restart_primal<T><<<ctx->g_vec_n, kBlock, 0, s>>>(DT);
+    restart_dual<T><<<ctx->g_vec_m, kBlock, 0, s>>>(DT);
     mark(11);
     mark(4);
 }
 
+void enqueue_attempt(pdcs_ctx* ctx, Prof* P = nullptr) {
+    if (ctx->fp32_active) enqueue_attempt_t<float>(ctx, ctx->DF, P);
+    else enqueue_attempt_t<double>(ctx, ctx->D, P);
+}
+
+void enqueue_check(pdcs_ctx* ctx, Prof* P = nullptr) {
+    if (ctx->fp32_active) enqueue_check_t<float>(ctx, ctx->DF, P);
+    else enqueue_check_t<double>(ctx, ctx->D, P);
+}
+
 __global__ void clear_pending(Ctrl* C) { C->pending = 0; }
+
+__global__ void widen(int k, const float* __restrict__ in, double* out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) out[i] = (double)in[i];
+}
 
 pdcs_status read_ctrl(pdcs_ctx* ctx) {
     CK(cudaMemcpyAsync(ctx->h_ctrl, ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
@@ -474,6 +500,15 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     for (int k = 0; k < 8; ++k) A.reserve<double>(m);  // y yh y0 kx kxh0 kxh1 kx0 ysum
     A.reserve<double>(2LL * n); A.reserve<double>(2LL * m); A.reserve<double>(2LL * m); A.reserve<double>(2LL * n);
     A.reserve<double>(2LL * m);  // scr
+    const bool f32 = ctx->opt.precision == PDCS_PRECISION_FP32;
+    if (f32) {
+        A.reserve<float>(nnz); A.reserve<float>(nnz);                    // val_f, valT_f
+        for (int k = 0; k < 3; ++k) A.reserve<float>(n);                 // c l u
+        A.reserve<float>(m);                                             // h
+        for (int k = 0; k < 7; ++k) A.reserve<float>(n);                 // x xh x0 kty ktyh kty0 xsum
+        for (int k = 0; k < 8; ++k) A.reserve<float>(m);                 // y yh y0 kx kxh0 kxh1 kx0 ysum
+        A.reserve<float>(m); A.reserve<float>(3LL * ctx->n_exp + 1);      // soc_w32, exp_lg32
+    }
     {
         cudaError_t e = cudaMalloc(&A.base, A.plan);
         if (e != cudaSuccess) {
@@ -506,6 +541,17 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.kxh0 = A.take<double>(m); D.kxh1 = A.take<double>(m); D.kx0 = A.take<double>(m); D.ysum = A.take<double>(m);
     D.xc = A.take<double>(2LL * n); D.yc = A.take<double>(2LL * m); D.kxc = A.take<double>(2LL * m);
     D.ktyc = A.take<double>(2LL * n); D.scr = A.take<double>(2LL * m);
+    Dev<float>& DF = ctx->DF;
+    float *c_f = nullptr, *l_f = nullptr, *u_f = nullptr, *h_f = nullptr, *soc_w32 = nullptr, *exp_lg32 = nullptr;
+    if (f32) {
+        ctx->val_f = A.take<float>(nnz); ctx->valT_f = A.take<float>(nnz);
+        c_f = A.take<float>(n); l_f = A.take<float>(n); u_f = A.take<float>(n); h_f = A.take<float>(m);
+        DF.x = A.take<float>(n); DF.xh = A.take<float>(n); DF.x0 = A.take<float>(n); DF.kty = A.take<float>(n);
+        DF.ktyh = A.take<float>(n); DF.kty0 = A.take<float>(n); DF.xsum = A.take<float>(n);
+        DF.y = A.take<float>(m); DF.yh = A.take<float>(m); DF.y0 = A.take<float>(m); DF.kx = A.take<float>(m);
+        DF.kxh0 = A.take<float>(m); DF.kxh1 = A.take<float>(m); DF.kx0 = A.take<float>(m); DF.ysum = A.take<float>(m);
+        soc_w32 = A.take<float>(m); exp_lg32 = A.take<float>(3LL * ctx->n_exp + 1);
+    }
 
     cudaStream_t s = ctx->stream;
     CK(cudaMemsetAsync(A.base, 0, A.used, s));
@@ -533,10 +579,12 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     // the host copies above are pageable: wait before the vectors go out of scope
     CK(cudaStreamSynchronize(s));
 
-    // ---- SpMV plans timed on the unscaled matrices (same structure), on request
-    if (ctx->opt.spmv_autotune && ctx->opt.spmv_lanes == 0) {
-        CK(tune_spmv(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val0, ctx->D.x, ctx->D.kx));
-        CK(tune_spmv(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->val0T, ctx->D.y, ctx->D.kty));
+    // ---- SpMV plans timed on the unscaled matrices (same structure), on request; in the
+    // FP32-iterate mode they are timed below on the FP32 copies instead
+    const bool tune = ctx->opt.spmv_autotune && ctx->opt.spmv_lanes == 0;
+    if (tune && !f32) {
+        CK(tune_spmv<double>(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val0, ctx->D.x, ctx->D.kx));
+        CK(tune_spmv<double>(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->val0T, ctx->D.y, ctx->D.kty));
     }
 
     // ---- diagonal rescaling: Ruiz (infinity norm) then Pock-Chambolle (alpha = 1)
@@ -637,26 +685,104 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
             ctx->n_soc, ctx->soc_off, ctx->soc_dim, ctx->dr, ctx->soc_w, ctx->soc_wp);
     if (ctx->n_exp)
         exp_constants<<<(ctx->n_exp + 255) / 256, 256, 0, s>>>(ctx->n_exp, ctx->exp_row0, ctx->dr, ctx->exp_lg);
+    if (f32) {
+        const int g = vec_grid(std::max<long long>(nnz, std::max(m, n)), ctx->sms);
+        if (nnz) {
+            cast_vec<float><<<g, kBlock, 0, s>>>(nnz, ctx->val, ctx->val_f);
+            cast_vec<float><<<g, kBlock, 0, s>>>(nnz, ctx->valT, ctx->valT_f);
+        }
+        cast_vec<float><<<g, kBlock, 0, s>>>(n, ctx->cs, c_f);
+        cast_vec<float><<<g, kBlock, 0, s>>>(n, ctx->ls, l_f);
+        cast_vec<float><<<g, kBlock, 0, s>>>(n, ctx->us, u_f);
+        cast_vec<float><<<g, kBlock, 0, s>>>(m, ctx->hs, h_f);
+        cast_vec<float><<<g, kBlock, 0, s>>>(m, ctx->soc_w, soc_w32);
+        cast_vec<float><<<g, kBlock, 0, s>>>(3LL * ctx->n_exp, ctx->exp_lg, exp_lg32);
+        // the FP32 view: FP32 matrix, data and state; everything else shared with D
+        float *x = DF.x, *xh = DF.xh, *x0 = DF.x0, *kty = DF.kty, *ktyh = DF.ktyh, *kty0 = DF.kty0, *xsum = DF.xsum;
+        float *y = DF.y, *yh = DF.yh, *y0 = DF.y0, *kx = DF.kx, *kxh0 = DF.kxh0, *kxh1 = DF.kxh1, *kx0 = DF.kx0,
+              *ysum = DF.ysum;
+        static_assert(sizeof(Dev<float>) == sizeof(Dev<double>), "Dev layouts differ only in pointee types");
+        std::memcpy(static_cast<void*>(&DF), static_cast<const void*>(&D), sizeof(Dev<float>));
+        DF.val = ctx->val_f; DF.valT = ctx->valT_f;
+        DF.c = c_f; DF.h = h_f; DF.l = l_f; DF.u = u_f;
+        DF.x = x; DF.xh = xh; DF.x0 = x0; DF.kty = kty; DF.ktyh = ktyh; DF.kty0 = kty0; DF.xsum = xsum;
+        DF.y = y; DF.yh = yh; DF.y0 = y0; DF.kx = kx; DF.kxh0 = kxh0; DF.kxh1 = kxh1; DF.kx0 = kx0; DF.ysum = ysum;
+        DF.soc_w32 = soc_w32; DF.exp_lg32 = exp_lg32;
+        ctx->fp32_active = true;
+        if (tune) {
+            CK(tune_spmv<float>(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val_f, DF.x, DF.kx));
+            CK(tune_spmv<float>(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->valT_f, DF.y, DF.kty));
+        }
+    }
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     return PDCS_OK;
 }
 
+// One check period (attempts + check) of the running phase as a CUDA graph.
 pdcs_status capture_graph(pdcs_ctx* ctx) {
-    if (ctx->graph) return PDCS_OK;
+    cudaGraphExec_t& G = ctx->fp32_active ? ctx->graph32 : ctx->graph;
+    if (G) return PDCS_OK;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     for (int a = 0; a < ctx->opt.check_period; ++a) enqueue_attempt(ctx);
     enqueue_check(ctx);
     CK(cudaStreamEndCapture(ctx->stream, &g));
-    cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaError_t e = cudaGraphInstantiate(&G, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        ctx->graph = nullptr;
+        G = nullptr;
         ctx->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
         return PDCS_ERR_CUDA;
     }
     return PDCS_OK;
+}
+
+// FP32 phase -> FP64 phase: the FP64 state restarts from the check's returned candidate
+// (FP64 values and products), keeping the step size, primal weight and counters; the
+// next check re-evaluates it as the new anchor (as at the start).
+pdcs_status switch_to_fp64(pdcs_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    Dev<double>& D = ctx->D;
+    const int q = ctx->h_ctrl->sol_cand;
+    const size_t n = ctx->n, m = ctx->m;
+    CK(cudaMemcpyAsync(D.x, D.xc + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(D.x0, D.xc + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(D.kty, D.ktyc + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(D.kty0, D.ktyc + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(D.y, D.yc + q * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(D.y0, D.yc + q * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(D.kx, D.kxc + q * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(D.kx0, D.kxc + q * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(D.xsum, 0, sizeof(double) * n, s));
+    CK(cudaMemsetAsync(D.ysum, 0, sizeof(double) * m, s));
+    Ctrl C = *ctx->h_ctrl;
+    C.pending = 0; C.wsum = 0.0; C.k = 0; C.check_mode = 1; C.phi_prev = INFINITY;
+    *ctx->h_ctrl = C;
+    CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    ctx->fp32_active = false;
+    enqueue_check(ctx);  // anchor evaluation in FP64 (may already meet the tolerance)
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return PDCS_OK;
+}
+
+// Whether the FP32 phase should hand over: the relative KKT error of the last check is
+// at most fp32_switch_tol or the requested tolerance, or its best value has not improved
+// by 10 % over 50 checks (the FP32 rounding floor; restarts make the error itself
+// non-monotone, so the window is long).
+bool fp32_done(pdcs_ctx* ctx, double tol) {
+    const Ctrl& C = *ctx->h_ctrl;
+    const double err = std::max(C.err[0], std::max(C.err[1], C.err[2]));
+    if (!(err == err)) return false;
+    if (err <= ctx->opt.fp32_switch_tol || err <= tol) return true;
+    if (err < 0.9 * ctx->fp32_best) {
+        ctx->fp32_best = err;
+        ctx->fp32_stall = 0;
+    } else if (++ctx->fp32_stall >= 50) {
+        return true;
+    }
+    return false;
 }
 
 pdcs_status status_of(const Ctrl& C) {
@@ -680,8 +806,12 @@ void fill_info(pdcs_ctx* ctx, pdcs_info* info) {
     info->setup_seconds = ctx->setup_seconds;
     info->solve_seconds = ctx->solve_seconds;
     info->status = ctx->last_status;
-    info->fp64_phase = 1;
+    info->fp64_phase = ctx->fp32_active ? 0 : 1;
     info->kernel_launches = ctx->launches;
+    info->spmv_plan[0] = ctx->pk.shift;
+    info->spmv_plan[1] = ctx->pk.unroll;
+    info->spmv_plan[2] = ctx->pkt.shift;
+    info->spmv_plan[3] = ctx->pkt.unroll;
 }
 
 }  // namespace
@@ -751,7 +881,8 @@ pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, con
     if (o.check_period < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || o.rescale < 0 || o.rescale > 2 ||
         o.step_mode < 0 || o.step_mode > 2 || !(o.beta >= 0.0) || o.beta > 1.0)
         return bad("invalid options");
-    if (o.precision != PDCS_PRECISION_FP64) return bad("only FP64 precision is available in this build");
+    if (o.precision != PDCS_PRECISION_FP64 && o.precision != PDCS_PRECISION_FP32) return bad("unknown precision");
+    if (!(o.fp32_switch_tol >= 0.0)) return bad("fp32_switch_tol must be >= 0");
     if (o.spmv_lanes != 0 && (o.spmv_lanes > 32 || (o.spmv_lanes & (o.spmv_lanes - 1)) != 0))
         return bad("spmv_lanes must be 0 or a power of two <= 32");
     if (o.spmv_autotune != 0 && o.spmv_autotune != 1) return bad("spmv_autotune must be 0 or 1");
@@ -809,10 +940,6 @@ pdcs_status pdcs_solve(pdcs_ctx* ctx, double tol, int64_t max_iter, pdcs_info* i
         CK(cudaGetLastError());
         ctx->started = true;
     }
-    if (ctx->opt.use_graphs) {
-        st = capture_graph(ctx);
-        if (st != PDCS_OK) return st;
-    }
     const int period = ctx->opt.check_period;
     long long done = ctx->h_ctrl->attempts;
     long long remaining = max_iter;
@@ -820,8 +947,10 @@ pdcs_status pdcs_solve(pdcs_ctx* ctx, double tol, int64_t max_iter, pdcs_info* i
     while (remaining > 0) {
         const long long to_b = period - (done % period);
         if (remaining >= to_b) {
-            if (to_b == period && ctx->graph) {
-                CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+            if (to_b == period && ctx->opt.use_graphs) {
+                st = capture_graph(ctx);
+                if (st != PDCS_OK) return st;
+                CK(cudaGraphLaunch(ctx->fp32_active ? ctx->graph32 : ctx->graph, ctx->stream));
                 ctx->launches += (long long)period * kLaunchesPerAttempt + kLaunchesPerCheck;
             } else {
                 for (long long a = 0; a < to_b; ++a) enqueue_attempt(ctx);
@@ -837,7 +966,15 @@ pdcs_status pdcs_solve(pdcs_ctx* ctx, double tol, int64_t max_iter, pdcs_info* i
         CK(cudaGetLastError());
         st = read_ctrl(ctx);
         if (st != PDCS_OK) return st;
+        const bool at_check = done % period == 0;
         if (ctx->h_ctrl->status != kRunning) break;
+        if (ctx->fp32_active && at_check && fp32_done(ctx, tol)) {
+            st = switch_to_fp64(ctx);
+            if (st != PDCS_OK) return st;
+            st = read_ctrl(ctx);
+            if (st != PDCS_OK) return st;
+            if (ctx->h_ctrl->status != kRunning) break;
+        }
         if (ctx->opt.time_limit > 0.0 && now_s() - t0 > ctx->opt.time_limit) { result = PDCS_TIME_LIMIT; break; }
     }
     st = read_ctrl(ctx);
@@ -889,11 +1026,31 @@ pdcs_status pdcs_get_solution(pdcs_ctx* ctx, double* x, double* y, double* lambd
 pdcs_status pdcs_get_iterate(pdcs_ctx* ctx, double* x, double* y, double* xhat, double* yhat) {
     if (!ctx) return PDCS_ERR_INVALID;
     // materialise a pending Halpern update (same arithmetic as the next evaluation would apply)
-    flush_primal<double><<<ctx->g_vec_n, kBlock, 0, ctx->stream>>>(ctx->D);
-    flush_dual<double><<<ctx->g_vec_m, kBlock, 0, ctx->stream>>>(ctx->D);
+    if (ctx->fp32_active) {
+        flush_primal<float><<<ctx->g_vec_n, kBlock, 0, ctx->stream>>>(ctx->DF);
+        flush_dual<float><<<ctx->g_vec_m, kBlock, 0, ctx->stream>>>(ctx->DF);
+    } else {
+        flush_primal<double><<<ctx->g_vec_n, kBlock, 0, ctx->stream>>>(ctx->D);
+        flush_dual<double><<<ctx->g_vec_m, kBlock, 0, ctx->stream>>>(ctx->D);
+    }
     clear_pending<<<1, 1, 0, ctx->stream>>>(ctx->ctrl);
     ctx->launches += 3;
     CK(cudaGetLastError());
+    if (ctx->fp32_active) {  // FP32 state widened into the FP64 check scratch, then unscaled
+        double* tx = ctx->D.xc + ctx->n;  // second candidate slots, rewritten by every check
+        double* ty = ctx->D.yc + ctx->m;
+        const int g = vec_grid(std::max(ctx->m, ctx->n), ctx->sms);
+        pdcs_status st = PDCS_OK;
+        const float* src[2][2] = {{ctx->DF.x, ctx->DF.y}, {ctx->DF.xh, ctx->DF.yh}};
+        double* dst[2][2] = {{x, y}, {xhat, yhat}};
+        for (int k = 0; k < 2 && st == PDCS_OK; ++k) {
+            widen<<<g, kBlock, 0, ctx->stream>>>(ctx->n, src[k][0], tx);
+            widen<<<g, kBlock, 0, ctx->stream>>>(ctx->m, src[k][1], ty);
+            CK(cudaGetLastError());
+            st = unscale_out(ctx, tx, ty, dst[k][0], dst[k][1]);
+        }
+        return st;
+    }
     pdcs_status st = unscale_out(ctx, ctx->D.x, ctx->D.y, x, y);
     if (st != PDCS_OK) return st;
     return unscale_out(ctx, ctx->D.xh, ctx->D.yh, xhat, yhat);
@@ -940,6 +1097,24 @@ pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y,
     CK(cudaMemcpyAsync(D.kty0, D.kty, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(D.xsum, 0, sizeof(double) * ctx->n, s));
     CK(cudaMemsetAsync(D.ysum, 0, sizeof(double) * ctx->m, s));
+    ctx->fp32_active = ctx->opt.precision == PDCS_PRECISION_FP32;
+    if (ctx->fp32_active) {  // the FP32 phase starts again, from the same point
+        Dev<float>& F = ctx->DF;
+        const int g = vec_grid(std::max(ctx->m, ctx->n), ctx->sms);
+        cast_vec<float><<<g, kBlock, 0, s>>>(ctx->n, D.x, F.x);
+        cast_vec<float><<<g, kBlock, 0, s>>>(ctx->n, D.x, F.x0);
+        cast_vec<float><<<g, kBlock, 0, s>>>(ctx->m, D.y, F.y);
+        cast_vec<float><<<g, kBlock, 0, s>>>(ctx->m, D.y, F.y0);
+        cast_vec<float><<<g, kBlock, 0, s>>>(ctx->m, D.kx, F.kx);
+        cast_vec<float><<<g, kBlock, 0, s>>>(ctx->m, D.kx, F.kx0);
+        cast_vec<float><<<g, kBlock, 0, s>>>(ctx->n, D.kty, F.kty);
+        cast_vec<float><<<g, kBlock, 0, s>>>(ctx->n, D.kty, F.kty0);
+        CK(cudaMemsetAsync(F.xsum, 0, sizeof(float) * ctx->n, s));
+        CK(cudaMemsetAsync(F.ysum, 0, sizeof(float) * ctx->m, s));
+        CK(cudaGetLastError());
+        ctx->fp32_best = INFINITY;
+        ctx->fp32_stall = 0;
+    }
     CK(cudaStreamSynchronize(s));
     pdcs_status st = read_ctrl(ctx);
     if (st != PDCS_OK) return st;

@@ -52,10 +52,11 @@ class pdcs_info(ctypes.Structure):
                 ("pobj", ctypes.c_double), ("dobj", ctypes.c_double), ("eta", ctypes.c_double),
                 ("omega", ctypes.c_double), ("setup_seconds", ctypes.c_double),
                 ("solve_seconds", ctypes.c_double), ("status", ctypes.c_int32), ("fp64_phase", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("spmv_plan", ctypes.c_int32 * 4)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: (list(getattr(self, k)) if isinstance(getattr(self, k), ctypes.Array) else getattr(self, k))
+                for k, _ in self._fields_}
 
 
 _lock = threading.Lock()
