@@ -187,7 +187,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-iterate mode measurements")
     ap.add_argument("--time-to-tol", default="1e-4,1e-6",
                     help="comma list of tolerances for the time-to-solution runs ('' to skip)")
-    ap.add_argument("--ttt-limit", type=float, default=120.0, help="seconds allowed per time-to-tolerance run")
+    ap.add_argument("--ttt-limit", type=float, default=45.0, help="seconds allowed per time-to-tolerance run")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")

@@ -94,6 +94,9 @@ typedef struct {
     int32_t spmv_lanes;     /* lanes per CSR row in SpMV (1..32, power of 2) for every row; 0: rows
                                binned by length, lanes per row matched to each bin */
     double time_limit;      /* seconds for pdcs_solve; 0: none */
+    const float* exp_mlp;   /* NULL (default), or PDCS_EXP_MLP_PARAMS weights of the learned starting
+                               point of the exponential-cone root search (host array, copied at
+                               create); used wherever a cone has no cached root (see below) */
     int32_t spmv_autotune;  /* 1: at create, time the candidate SpMV plans of K and K' (bin shift,
                                unroll) over 20 launches each and keep the fastest; the choice is
                                cached per process by matrix signature (rows, nnz, length histogram).
@@ -211,6 +214,49 @@ pdcs_status pdcs_proj_cones_device(const double* v, const double* d, int64_t m, 
  *     n_cones > PDCS_NOALLOC_MAX_CONES, PDCS_ERR_CUDA if a CUDA call fails. */
 pdcs_status pdcs_proj_cones_device_noalloc(const double* v, const double* d, int64_t m, const pdcs_cone* cones,
                                            int64_t n_cones, int32_t dual, double* out, void* cuda_stream);
+
+/* ------------------------------------------------------------------------------------
+ * Learned starting point of the exponential-cone root search (case 4 of Theorem 3).
+ * A 9 -> 32 -> 32 -> 1 ReLU network (FP32) maps the direction of v0, the log ratios
+ * log(ds/dr), log(dt/dr) of the scales and the branch of the search (one-hot: both
+ * r0, s0 > 0 searched from a4 or from a3, r0 <= 0, s0 <= 0) to the log-offset L of the
+ * root from the branch's endpoint.  It replaces only the cold starting point of the
+ * safeguarded Newton search; the bracket and the stopping tests are unchanged, so the
+ * projection is the plain search's to its tolerance.  There is no counterpart in the
+ * paper.  Parameter layout (PDCS_EXP_MLP_PARAMS floats): W1[32][9], b1[32], W2[32][32],
+ * b2[32], w3[32], b3.  All arrays below are HOST arrays; each call allocates and frees
+ * its own device memory and synchronises.
+ * ------------------------------------------------------------------------------------ */
+#define PDCS_EXP_MLP_IN 9
+#define PDCS_EXP_MLP_HIDDEN 32
+#define PDCS_EXP_MLP_PARAMS (32 * 9 + 32 + 32 * 32 + 32 + 32 + 1)
+
+/* Training pairs from the plain projector: for each of n inputs v0 = v[3i..3i+2] with
+ * scales d[3i..3i+2] (> 0) whose projection onto D K_exp falls in case 4 with a root
+ * inside its interval and |L| <= 50, the FP64 search (no starting point) gives L; features[9k..9k+8]
+ * and target[k] receive the k-th such pair, k < *kept.  Returns PDCS_ERR_INVALID for
+ * n < 0 or NULL arrays, PDCS_ERR_CUDA on a CUDA failure. */
+pdcs_status pdcs_exp_mlp_dataset(int64_t n, const double* v, const double* d, float* features, float* target,
+                                 int64_t* kept);
+
+/* Mean squared error of the network on n pairs and its gradient (same layout as the
+ * weights), by the library's forward / backward kernels.  loss and grad are outputs. */
+pdcs_status pdcs_exp_mlp_loss_grad(int64_t n, const float* features, const float* target, const float* weights,
+                                   float* grad, float* loss);
+
+/* Trains the network in place on the GPU: `steps` Adam steps (beta1 0.9, beta2 0.999,
+ * eps 1e-8, learning rate lr) on minibatches of `batch` pairs drawn with replacement by
+ * the SplitMix64 generator from `seed`; weights is read as the initial point and
+ * overwritten; loss_trace (may be NULL) receives the minibatch loss of every step. */
+pdcs_status pdcs_exp_mlp_train(int64_t n, const float* features, const float* target, int32_t steps, int32_t batch,
+                               float lr, uint64_t seed, float* weights, float* loss_trace);
+
+/* Projects n vectors onto D K_exp (inputs as in pdcs_exp_mlp_dataset) with the mixed-
+ * precision search from a cold start, using the network when weights is not NULL;
+ * out[3i..3i+2] is the projection, evals[2i] and evals[2i+1] the FP32 and FP64
+ * evaluations of h it took (0 outside case 4). */
+pdcs_status pdcs_exp_proj_stats(int64_t n, const double* v, const double* d, const float* weights, double* out,
+                                int32_t* evals);
 
 #ifdef __cplusplus
 }

@@ -143,7 +143,7 @@ __device__ __forceinline__ bool in_kexp_dual_f(float r, float s, float t) {
 // Projection onto D K_exp in FP32; lg = log of the scales.  Falls back to the FP64
 // search when the FP32 root search does not give a finite result.
 __device__ inline void exp_project_f32(float r0, float s0, float t0, float dr, float ds, float dt, const float* lg,
-                                       float* out, float* L_cache) {
+                                       float* out, float* L_cache, const float* mlp = nullptr) {
     if (in_kexp_f(r0 / dr, s0 / ds, t0 / dt)) { out[0] = r0; out[1] = s0; out[2] = t0; return; }
     if (in_kexp_dual_f(-dr * r0, -ds * s0, -dt * t0)) { out[0] = 0.0f; out[1] = 0.0f; out[2] = 0.0f; return; }
     if (r0 <= 0.0f && s0 <= 0.0f) { out[0] = r0; out[1] = 0.0f; out[2] = t0 > 0.0f ? t0 : 0.0f; return; }
@@ -161,7 +161,7 @@ __device__ inline void exp_project_f32(float r0, float s0, float t0, float dr, f
     e.w34 = e.a3 - e.a4;
     int evals = 0;
     float L = 0.0f;
-    bool ok = isfinite(e.a3) && isfinite(e.a4) && exp_case4_solve(e, L_cache ? *L_cache : NAN, L, evals) && !(L != L);
+    bool ok = isfinite(e.a3) && isfinite(e.a4) && exp_case4_solve(e, L_cache ? *L_cache : NAN, L, evals, mlp) && !(L != L);
     float F, dF, rho, lsp, lrd, Fs;
     if (ok) {
         exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
@@ -185,9 +185,10 @@ __device__ inline void exp_project_f32(float r0, float s0, float t0, float dr, f
 
 // Projection onto D^{-1} K_exp^* (Remark of App. A.2) in FP32.
 __device__ __forceinline__ void exp_dual_project_f32(float r, float s, float t, float dr, float ds, float dt,
-                                                     const float* lg, float* out, float* L_cache) {
+                                                     const float* lg, float* out, float* L_cache,
+                                                     const float* mlp = nullptr) {
     float p[3];
-    exp_project_f32(-r, -s, -t, dr, ds, dt, lg, p, L_cache);
+    exp_project_f32(-r, -s, -t, dr, ds, dt, lg, p, L_cache, mlp);
     out[0] = r + p[0];
     out[1] = s + p[1];
     out[2] = t + p[2];

@@ -729,11 +729,74 @@ __host__ __device__ __forceinline__ R exp_newton(const ExpCase4T<R>& e, R lo, R 
     return L;
 }
 
+// ---------------------------------------------------------------------------
+// Learned starting point of the case-4 search: a 9 -> 32 -> 32 -> 1 ReLU network of the
+// direction of v0, the log ratios of the scales and the branch (kind, anchor) predicts
+// the log-offset L of the root.  It only replaces the cold starting point: the bracket,
+// the safeguarded Newton iteration and its stopping tests are unchanged, so the result
+// is the plain search's.  Parameters (kExpMlpParams floats): W1[32][9], b1[32],
+// W2[32][32], b2[32], w3[32], b3.
+// ---------------------------------------------------------------------------
+constexpr int kExpMlpIn = 9, kExpMlpHidden = 32;
+constexpr int kExpMlpParams = kExpMlpHidden * kExpMlpIn + kExpMlpHidden + kExpMlpHidden * kExpMlpHidden +
+                              kExpMlpHidden + kExpMlpHidden + 1;
+
+template <typename R>
+__host__ __device__ __forceinline__ void exp_mlp_features(const ExpCase4T<R>& e, float* f) {
+    const float r = (float)e.r0, s = (float)e.s0, t = (float)e.t0;
+    const float nv = sqrtf(r * r + s * s + t * t);
+    const float inv = nv > 0.0f ? 1.0f / nv : 0.0f;
+    f[0] = r * inv;
+    f[1] = s * inv;
+    f[2] = t * inv;
+    f[3] = (float)(e.lds - e.ldr);
+    f[4] = (float)(e.ldt - e.ldr);
+    f[5] = (e.kind == 1 && e.anchor == 4) ? 1.0f : 0.0f;
+    f[6] = (e.kind == 1 && e.anchor == 3) ? 1.0f : 0.0f;
+    f[7] = e.kind == 2 ? 1.0f : 0.0f;
+    f[8] = e.kind == 3 ? 1.0f : 0.0f;
+}
+
+__host__ __device__ __forceinline__ float exp_mlp_eval(const float* __restrict__ W, const float* f) {
+    const float* W1 = W;
+    const float* b1 = W1 + kExpMlpHidden * kExpMlpIn;
+    const float* W2 = b1 + kExpMlpHidden;
+    const float* b2 = W2 + kExpMlpHidden * kExpMlpHidden;
+    const float* w3 = b2 + kExpMlpHidden;
+    const float b3 = w3[kExpMlpHidden];
+    float h1[kExpMlpHidden];
+#pragma unroll 4
+    for (int i = 0; i < kExpMlpHidden; ++i) {
+        float a = b1[i];
+#pragma unroll
+        for (int j = 0; j < kExpMlpIn; ++j) a = fmaf(W1[i * kExpMlpIn + j], f[j], a);
+        h1[i] = fmaxf(a, 0.0f);
+    }
+    float y = b3;
+#pragma unroll 2
+    for (int i = 0; i < kExpMlpHidden; ++i) {
+        float a = b2[i];
+#pragma unroll
+        for (int j = 0; j < kExpMlpHidden; ++j) a = fmaf(W2[i * kExpMlpHidden + j], h1[j], a);
+        y = fmaf(w3[i], fmaxf(a, 0.0f), y);
+    }
+    return y;
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ R exp_mlp_guess(const ExpCase4T<R>& e, const float* mlp, R guess) {
+    if (!mlp || guess == guess) return guess;  // no network, or a cached root to start from
+    float f[kExpMlpIn];
+    exp_mlp_features(e, f);
+    return (R)exp_mlp_eval(mlp, f);
+}
+
 // Case 4 of Theorem 3 for the prepared e (logs and a3, a4 filled in): chooses the
 // interval branch of eq. lrho_urho and the anchor, and returns the log-offset L of
 // the root of h.  Returns false when the interval is empty by rounding.
 template <typename R>
-__host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R guess, R& L, int& evals) {
+__host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R guess, R& L, int& evals,
+                                                         const float* mlp = nullptr) {
     const R zero = R(0), one = R(1);
     if (e.r0 > zero && e.s0 > zero) {
         e.kind = 1;
@@ -759,7 +822,7 @@ __host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R gues
         R F0;
         const R lo = exp_lower(e, Lh, slo, evals, at_end, F0);
         e.dm = fabs(F0) < R(INFINITY);
-        L = at_end ? lo : exp_newton(e, lo, Lh, slo, guess, F0, evals);
+        L = at_end ? lo : exp_newton(e, lo, Lh, slo, exp_mlp_guess(e, mlp, guess), F0, evals);
     } else if (e.s0 > zero) {  // r0 <= 0: (-inf, a3)
         e.kind = 2; e.anchor = 3; e.dir = -one; e.slo = +1;
         R hi = zero;
@@ -768,7 +831,7 @@ __host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R gues
         R F0;
         const R lo = exp_lower(e, hi, +1, evals, at_end, F0);
         e.dm = fabs(F0) < R(INFINITY);
-        L = at_end ? lo : exp_newton(e, lo, hi, +1, guess, F0, evals);
+        L = at_end ? lo : exp_newton(e, lo, hi, +1, exp_mlp_guess(e, mlp, guess), F0, evals);
     } else {  // s0 <= 0 < r0: (a4, inf)
         e.kind = 3; e.anchor = 4; e.dir = one; e.slo = -1;
         R hi = zero;
@@ -777,7 +840,7 @@ __host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R gues
         R F0;
         const R lo = exp_lower(e, hi, -1, evals, at_end, F0);
         e.dm = fabs(F0) < R(INFINITY);
-        L = at_end ? lo : exp_newton(e, lo, hi, -1, guess, F0, evals);
+        L = at_end ? lo : exp_newton(e, lo, hi, -1, exp_mlp_guess(e, mlp, guess), F0, evals);
     }
     return true;
 }
@@ -907,9 +970,12 @@ __host__ __device__ __forceinline__ int kexpdual_screen32(float r, float s, floa
 }
 
 // Projection onto D K_exp with precomputed logs of the scales (lg[0..2] = log dr, ds, dt).
-// L_cache (may be null): FP32 copy of the last log-offset of this cone.
+// L_cache (may be null): FP32 copy of the last log-offset of this cone.  mlp (may be
+// null): device weights of the learned starting point, used when there is no cached
+// root.  ev (may be null): ev[0] += FP32 and ev[1] += FP64 evaluations of h.
 __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0, double dr, double ds, double dt,
-                                                 const double* lg, double* out, float* L_cache) {
+                                                 const double* lg, double* out, float* L_cache,
+                                                 const float* mlp = nullptr, int* ev = nullptr) {
     // cases 1-3, screened in FP32
     int c1 = kexp_screen32((float)r0 / (float)dr, (float)s0 / (float)ds, (float)t0 / (float)dt);
     if (c1 == 0) c1 = in_kexp(r0 / dr, s0 / ds, t0 / dt) ? 1 : -1;
@@ -929,9 +995,10 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
         exp_case4_setup(ef, r0, s0, t0, dr, ds, (float)lg[0], (float)lg[1], (float)lg[2]);
         // rho (rho - 1) + tau^2 must stay finite in FP32 over the search
         ok = fabsf(ef.a3) < 1e15f && fabsf(ef.a4) < 1e15f && fabsf(ef.tau) < 1e15f &&
-             exp_case4_solve(ef, L_cache ? *L_cache : NAN, Lf, evals) &&
+             exp_case4_solve(ef, L_cache ? *L_cache : NAN, Lf, evals, mlp) &&
              !(Lf != Lf) && Lf < INFINITY;
     }
+    if (ev) ev[0] += evals;
     if (ok && Lf == -INFINITY) {
         // FP32 puts the root at the anchor.  In FP64, F at a tiny offset delta_z = e^-200
         // is F at the anchor to all digits and dF = c delta_z, c = dF/ddelta there: the
@@ -945,10 +1012,12 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
         const double Lz = -200.0;
         double F, dF, rho, lsp, lrd, Fs;
         exp_F(e, Lz, F, dF, rho, lsp, lrd, Fs);
+        if (ev) ev[1] += 1;
         const int sF = (F > 0.0) - (F < 0.0);
         if (F == F && Fs < INFINITY && (sF != ef.slo || fabs(F) <= 16.0 * RootTol<double>::collapse * Fs)) {
             if (L_cache) *L_cache = -INFINITY;
             exp_case4_output(e, -INFINITY, r0, s0, t0, dr, ds, out);
+            if (ev) ev[1] += 1;
             return;
         }
         bool conv = false;
@@ -957,6 +1026,7 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
             L = Lz + log(-F / dF);
             for (int it = 0; it < 4 && !conv; ++it) {
                 exp_F(e, L, F, dF, rho, lsp, lrd, Fs);
+                if (ev) ev[1] += 1;
                 if (Fs < INFINITY && fabs(F) <= 4.0 * RootTol<double>::collapse * Fs) { conv = true; break; }
                 const double st = -F / dF;
                 if (!(st > -1.0) || !isfinite(st)) break;
@@ -968,6 +1038,7 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
         if (conv) {
             if (L_cache) *L_cache = (float)L;
             exp_case4_output(e, L, r0, s0, t0, dr, ds, out);
+            if (ev) ev[1] += 1;
             return;
         }
         ok = false;
@@ -985,6 +1056,7 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
         for (int it = 0; it < 3; ++it) {
             ExpAt<double> a;
             exp_eval(e, L, a);
+            if (ev) ev[1] += 1;
             double st = 0.0;
             if (!(a.Fs < INFINITY && fabs(a.F) <= 4.0 * RootTol<double>::collapse * a.Fs)) {
                 st = -a.F / a.dF;  // Newton in delta next to the anchor (see exp_newton), else in L
@@ -1000,16 +1072,18 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
         }
     }
     double Lc = L_cache ? (double)*L_cache : NAN;
-    exp_project(r0, s0, t0, dr, ds, dt, out, &Lc, nullptr);
+    int e64 = 0;
+    exp_project(r0, s0, t0, dr, ds, dt, out, &Lc, &e64);
+    if (ev) ev[1] += e64 + 1;
     if (L_cache) *L_cache = (float)Lc;
 }
 
 // Projection onto D^{-1} K_exp^* (Remark of App. A.2) with the mixed-precision search.
 __host__ __device__ __forceinline__ void exp_dual_project_fast(double r, double s, double t, double dr, double ds,
                                                                double dt, const double* lg, double* out,
-                                                               float* L_cache) {
+                                                               float* L_cache, const float* mlp = nullptr) {
     double p[3];
-    exp_project_fast(-r, -s, -t, dr, ds, dt, lg, p, L_cache);
+    exp_project_fast(-r, -s, -t, dr, ds, dt, lg, p, L_cache, mlp);
     out[0] = r + p[0];
     out[1] = s + p[1];
     out[2] = t + p[2];

@@ -83,6 +83,8 @@ struct Dev {
     // FP32 copies of the SOC weights and exp log-scales (FP32 iterates)
     const float* soc_w32;
     const float* exp_lg32;
+    // learned starting point of the exp root search (kExpMlpParams floats), or null
+    const float* exp_mlp;
 };
 
 // ---------------------------------------------------------------------------
@@ -351,10 +353,10 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
             }
             if constexpr (sizeof(T) == 8)
                 exp_dual_project_fast(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, out,
-                                      D.exp_L + e);
+                                      D.exp_L + e, D.exp_mlp);
             else
                 exp_dual_project_f32(v[0], v[1], v[2], (float)D.dr[r], (float)D.dr[r + 1], (float)D.dr[r + 2],
-                                     D.exp_lg32 + 3 * e, out, D.exp_L + e);
+                                     D.exp_lg32 + 3 * e, out, D.exp_L + e, D.exp_mlp);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const T yh = (T)out[q];
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(kBlock) cand_dual(Dev<T> D) {
             const int r = D.exp_row0 + 3 * e;
             double o3[3];
             exp_dual_project_fast(val(r), val(r + 1), val(r + 2), D.dr[r], D.dr[r + 1], D.dr[r + 2],
-                                  D.exp_lg + 3 * e, o3, nullptr);
+                                  D.exp_lg + 3 * e, o3, nullptr, D.exp_mlp);
             out[r] = o3[0];
             out[r + 1] = o3[1];
             out[r + 2] = o3[2];
@@ -545,8 +547,9 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
                 w[k] = v[k] / D.dr[r + k];
             }
             const double lg0[3] = {0.0, 0.0, 0.0};
-            exp_project_fast(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, ps, nullptr);
-            exp_project_fast(w[0], w[1], w[2], 1.0, 1.0, 1.0, lg0, pu, nullptr);
+            exp_project_fast(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, ps, nullptr,
+                             D.exp_mlp);
+            exp_project_fast(w[0], w[1], w[2], 1.0, 1.0, 1.0, lg0, pu, nullptr, D.exp_mlp);
             for (int k = 0; k < 3; ++k) {
                 const double rs = v[k] - ps[k];
                 sums[0] += rs * rs;

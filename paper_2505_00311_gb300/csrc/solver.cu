@@ -509,6 +509,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         for (int k = 0; k < 8; ++k) A.reserve<float>(m);                 // y yh y0 kx kxh0 kxh1 kx0 ysum
         A.reserve<float>(m); A.reserve<float>(3LL * ctx->n_exp + 1);      // soc_w32, exp_lg32
     }
+    if (ctx->opt.exp_mlp) A.reserve<float>(kExpMlpParams);
     {
         cudaError_t e = cudaMalloc(&A.base, A.plan);
         if (e != cudaSuccess) {
@@ -552,6 +553,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         DF.kxh0 = A.take<float>(m); DF.kxh1 = A.take<float>(m); DF.kx0 = A.take<float>(m); DF.ysum = A.take<float>(m);
         soc_w32 = A.take<float>(m); exp_lg32 = A.take<float>(3LL * ctx->n_exp + 1);
     }
+    float* exp_mlp = ctx->opt.exp_mlp ? A.take<float>(kExpMlpParams) : nullptr;
 
     cudaStream_t s = ctx->stream;
     CK(cudaMemsetAsync(A.base, 0, A.used, s));
@@ -567,6 +569,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     CK(cudaMemcpyAsync(ctx->l0, l_h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->u0, u_h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->h0, h_i.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    if (exp_mlp)
+        CK(cudaMemcpyAsync(exp_mlp, ctx->opt.exp_mlp, sizeof(float) * kExpMlpParams, cudaMemcpyHostToDevice, s));
     if (ctx->n_soc) {
         CK(cudaMemcpyAsync(ctx->soc_off, soc_off_i.data(), sizeof(int) * ctx->n_soc, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->soc_dim, soc_d.data(), sizeof(int) * ctx->n_soc, cudaMemcpyHostToDevice, s));
@@ -665,6 +669,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.nb_scal = nb_scal; D.nb_soc = nb_soc; D.nb_exp = nb_exp; D.exp_pb = exp_pb; D.nb_primal = ctx->g_vec_n;
     D.part = ctx->part; D.pl = pl; D.ctrl = ctx->ctrl;
     D.l_orig = ctx->l0; D.u_orig = ctx->u0;
+    D.exp_mlp = exp_mlp;
 
     // ---- controller scalars
     Ctrl C;
@@ -836,6 +841,7 @@ void pdcs_default_options(pdcs_options* o) {
     o->spmv_lanes = 0;
     o->time_limit = 0.0;
     o->spmv_autotune = 0;
+    o->exp_mlp = nullptr;
 }
 
 pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, const double* lb, const double* ub,

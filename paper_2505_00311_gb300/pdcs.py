@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid", 2: "cuda", 3: "oom", 4: "numeric", 5: "de
 _dp = ctypes.POINTER(ctypes.c_double)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _i32p = ctypes.POINTER(ctypes.c_int32)
+_fp = ctypes.POINTER(ctypes.c_float)
 
 
 class pdcs_csr(ctypes.Structure):
@@ -43,7 +44,7 @@ class pdcs_options(ctypes.Structure):
                 ("power_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("fp32_switch_tol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("spmv_lanes", ctypes.c_int32), ("time_limit", ctypes.c_double),
-                ("spmv_autotune", ctypes.c_int32)]
+                ("exp_mlp", ctypes.c_void_p), ("spmv_autotune", ctypes.c_int32)]
 
 
 class pdcs_info(ctypes.Structure):
@@ -83,7 +84,14 @@ SIGNATURES = {
     "pdcs_proj_cones_device_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                       ctypes.POINTER(pdcs_cone), ctypes.c_int64, ctypes.c_int32,
                                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "pdcs_exp_mlp_dataset": (ctypes.c_int, [ctypes.c_int64, _dp, _dp, _fp, _fp, _i64p]),
+    "pdcs_exp_mlp_loss_grad": (ctypes.c_int, [ctypes.c_int64, _fp, _fp, _fp, _fp, _fp]),
+    "pdcs_exp_mlp_train": (ctypes.c_int, [ctypes.c_int64, _fp, _fp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                          ctypes.c_uint64, _fp, _fp]),
+    "pdcs_exp_proj_stats": (ctypes.c_int, [ctypes.c_int64, _dp, _dp, _fp, _dp, _i32p]),
 }
+EXP_MLP_IN, EXP_MLP_HIDDEN = 9, 32
+EXP_MLP_PARAMS = EXP_MLP_HIDDEN * EXP_MLP_IN + EXP_MLP_HIDDEN + EXP_MLP_HIDDEN * EXP_MLP_HIDDEN + 2 * EXP_MLP_HIDDEN + 1
 NOALLOC_MAX_CONES = 262144
 
 
@@ -251,7 +259,13 @@ class Solver:
 
     def __init__(self, prob, stream=None, **options):
         self.m, self.n = int(prob["m"]), int(prob["n"])
+        mlp = options.pop("exp_mlp", None)
         self.options = pdcs_default_options(**options)
+        if mlp is not None:  # weights of the learned exp starting point, copied by pdcs_create
+            mlp = np.ascontiguousarray(mlp, dtype=np.float32)
+            if mlp.size != EXP_MLP_PARAMS:
+                raise ValueError("exp_mlp needs %d weights" % EXP_MLP_PARAMS)
+            self.options.exp_mlp = mlp.ctypes.data
         self.ctx = pdcs_create(prob, self.options, stream)
 
     def solve(self, tol=1e-6, max_iter=1_000_000):
@@ -289,3 +303,66 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# learned starting point of the exponential-cone root search
+# ---------------------------------------------------------------------------
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _check(st):
+    if st != OK:
+        raise PdcsError(st, pdcs_last_error())
+
+
+def exp_mlp_dataset(v, d):
+    """Case-4 training pairs from the plain projector: (features k x 9, target L, k)."""
+    v, d = _f64(v).reshape(-1, 3), _f64(d).reshape(-1, 3)
+    n = v.shape[0]
+    feats = np.empty((n, EXP_MLP_IN), dtype=np.float32)
+    target = np.empty(n, dtype=np.float32)
+    kept = ctypes.c_int64(0)
+    _check(lib().pdcs_exp_mlp_dataset(n, _ptr(v), _ptr(d), _ptr(feats, _fp), _ptr(target, _fp), ctypes.byref(kept)))
+    k = kept.value
+    return feats[:k].copy(), target[:k].copy()
+
+
+def exp_mlp_loss_grad(feats, target, weights):
+    feats, target, weights = _f32(feats), _f32(target), _f32(weights)
+    grad = np.empty(EXP_MLP_PARAMS, dtype=np.float32)
+    loss = np.empty(1, dtype=np.float32)
+    _check(lib().pdcs_exp_mlp_loss_grad(target.size, _ptr(feats, _fp), _ptr(target, _fp), _ptr(weights, _fp),
+                                        _ptr(grad, _fp), _ptr(loss, _fp)))
+    return float(loss[0]), grad
+
+
+def exp_mlp_train(feats, target, weights, steps=2000, batch=4096, lr=1e-3, seed=0):
+    """Adam training on the GPU; returns (trained weights, per-step minibatch loss)."""
+    feats, target = _f32(feats), _f32(target)
+    w = _f32(weights).copy()
+    trace = np.empty(max(steps, 1), dtype=np.float32)
+    _check(lib().pdcs_exp_mlp_train(target.size, _ptr(feats, _fp), _ptr(target, _fp), int(steps), int(batch),
+                                    float(lr), int(seed), _ptr(w, _fp), _ptr(trace, _fp)))
+    return w, trace[:steps]
+
+
+def exp_proj_stats(v, d, weights=None):
+    """Cold-start projections onto D K_exp: (out n x 3, evals n x 2: FP32, FP64 evaluations)."""
+    v, d = _f64(v).reshape(-1, 3), _f64(d).reshape(-1, 3)
+    n = v.shape[0]
+    out = np.empty((n, 3))
+    ev = np.empty((n, 2), dtype=np.int32)
+    w = None if weights is None else _f32(weights)
+    _check(lib().pdcs_exp_proj_stats(n, _ptr(v), _ptr(d), _ptr(w, _fp), _ptr(out), _ptr(ev, _i32p)))
+    return out, ev
+
+
+def exp_mlp_init(seed=0):
+    """He-initialised weights (W1, b1, W2, b2, w3, b3), seeded."""
+    rng = np.random.default_rng(seed)
+    H, I = EXP_MLP_HIDDEN, EXP_MLP_IN
+    parts = [rng.normal(0, np.sqrt(2.0 / I), H * I), np.zeros(H), rng.normal(0, np.sqrt(2.0 / H), H * H),
+             np.zeros(H), rng.normal(0, np.sqrt(1.0 / H), H), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
