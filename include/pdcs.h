@@ -101,6 +101,9 @@ typedef struct {
                                unroll) over 20 launches each and keep the fastest; the choice is
                                cached per process by matrix signature (rows, nnz, length histogram).
                                0 (default): the fixed plan (shift 3, unroll 4) */
+    int32_t batch_blocks;   /* 0 (default): grids sized per kernel; > 0: every vector / cone kernel
+                               of this program runs on exactly this many blocks (needed to join a
+                               batch, whose programs share one grid; see pdcs_batch_create) */
 } pdcs_options;
 
 typedef struct {
@@ -214,6 +217,31 @@ pdcs_status pdcs_proj_cones_device(const double* v, const double* d, int64_t m, 
  *     n_cones > PDCS_NOALLOC_MAX_CONES, PDCS_ERR_CUDA if a CUDA call fails. */
 pdcs_status pdcs_proj_cones_device_noalloc(const double* v, const double* d, int64_t m, const pdcs_cone* cones,
                                            int64_t n_cones, int32_t dual, double* out, void* cuda_stream);
+
+/* ------------------------------------------------------------------------------------
+ * Batches: many independent programs solved together, each with its own step size,
+ * primal weight, restart state and termination (Algorithm 1 per program), iterated in
+ * lockstep by launches whose third grid dimension is the program; one CUDA graph per
+ * check period covers the whole batch.  Programs that have converged skip their work.
+ * There is no counterpart in the paper (its experiments solve one program at a time).
+ * ------------------------------------------------------------------------------------ */
+typedef struct pdcs_batch pdcs_batch;
+
+/* Forms a batch of `count` (1..65535) contexts made by pdcs_create with the same
+ * options.batch_blocks > 0, FP64, the same check_period, no SpMV autotuning, and not yet
+ * solved.  The contexts stay owned by the caller (destroy them after the batch) and give
+ * each program's solution and info as usual.  Returns PDCS_ERR_INVALID (text in
+ * pdcs_batch_last_error(NULL)) or PDCS_ERR_CUDA / PDCS_ERR_OOM. */
+pdcs_status pdcs_batch_create(pdcs_ctx* const* ctxs, int64_t count, pdcs_batch** out);
+
+/* Runs up to max_iter PDHG evaluations of every program (all in lockstep) or until all
+ * have met tol.  *n_converged (may be NULL) receives how many have.  Returns PDCS_OK when
+ * all converged, PDCS_MAX_ITER otherwise, PDCS_ERR_NUMERIC if a program's iterates hold a
+ * NaN / Inf, PDCS_ERR_CUDA on a CUDA failure.  May be called again to continue. */
+pdcs_status pdcs_batch_solve(pdcs_batch* b, double tol, int64_t max_iter, int64_t* n_converged);
+
+const char* pdcs_batch_last_error(const pdcs_batch* b);
+void pdcs_batch_destroy(pdcs_batch* b);
 
 /* ------------------------------------------------------------------------------------
  * Learned starting point of the exponential-cone root search (case 4 of Theorem 3).

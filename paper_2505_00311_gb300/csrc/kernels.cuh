@@ -24,6 +24,15 @@
 namespace pdcs {
 
 // Device view of one problem and its iterate state (passed by value).
+// Rows of a CSR matrix binned by length for the SpMV (see spmv_binned).
+constexpr int kSpmvMaxBins = 6;  // lane counts 32, 16, 8, 4, 2, 1
+struct SpmvBins {
+    int nbins;
+    int blk[kSpmvMaxBins + 1];  // first block of each bin; blk[nbins] = grid size
+    int row[kSpmvMaxBins + 1];  // first entry of each bin in the row list
+    int lanes[kSpmvMaxBins];
+};
+
 template <typename T>
 struct Dev {
     int m, n;
@@ -85,6 +94,10 @@ struct Dev {
     const float* exp_lg32;
     // learned starting point of the exp root search (kExpMlpParams floats), or null
     const float* exp_mlp;
+    // SpMV plans of K and K' (used by the batched launches)
+    SpmvBins binsK, binsKT;
+    const int* listK;
+    const int* listKT;
 };
 
 // ---------------------------------------------------------------------------
@@ -98,13 +111,6 @@ struct Dev {
 // sel: 0 -> write y0;  1 -> write y0 / y1 by the parity of ctrl->attempts.
 // skip: 0 never; 1 when not running; 2 when not running or the step was rejected.
 // ---------------------------------------------------------------------------
-constexpr int kSpmvMaxBins = 6;  // lane counts 32, 16, 8, 4, 2, 1
-struct SpmvBins {
-    int nbins;
-    int blk[kSpmvMaxBins + 1];  // first block of each bin; blk[nbins] = grid size
-    int row[kSpmvMaxBins + 1];  // first entry of each bin in the row list
-    int lanes[kSpmvMaxBins];
-};
 
 template <typename T, typename TO, int G, int U>
 __device__ __forceinline__ void spmv_bin_rows(const int* __restrict__ list, int count, int wb, int nwb,
@@ -199,7 +205,8 @@ __device__ __forceinline__ double block_max_parts(const double* part, int cnt, d
 // primal update
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kBlock) primal_update(Dev<T> D) {
+__device__ __forceinline__ void primal_update_body(const Dev<T>& D, int qidx) {
+    (void)qidx;
     Ctrl* C = D.ctrl;
     if (C->status != kRunning) return;
     __shared__ double sm[1][kWarpsPerBlock];
@@ -294,7 +301,8 @@ __device__ void step_controller(const Dev<T>& D, double (*sm)[kWarpsPerBlock]) {
 // dual update + projection + step controller
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
+__device__ __forceinline__ void dual_update_body(const Dev<T>& D, int qidx) {
+    (void)qidx;
     Ctrl* C = D.ctrl;
     if (C->status != kRunning) return;
     __shared__ double sm[2][kWarpsPerBlock];
@@ -307,8 +315,9 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (b >= D.nb_exp + D.nb_soc) {  // scalar rows (blocks dispatched last)
+        const int sb = b - D.nb_exp - D.nb_soc;  // idle beyond this program's split (batches)
         const int stride = D.nb_scal * blockDim.x;
-        for (int i = (b - D.nb_exp - D.nb_soc) * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
+        for (int i = sb * blockDim.x + threadIdx.x; sb < D.nb_scal && i < D.m_scalar; i += stride) {
             T y, kx;
             dual_row_halpern(D, i, pend, ha, hb, hc, hw, pprev, y, kx);
             const T pi = p[i];
@@ -380,7 +389,8 @@ __global__ void __launch_bounds__(kBlock) dual_update(Dev<T> D) {
 // flush: apply a pending Halpern update without a PDHG step (before a check)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kBlock) flush_primal(Dev<T> D) {
+__device__ __forceinline__ void flush_primal_body(const Dev<T>& D, int qidx) {
+    (void)qidx;
     Ctrl* C = D.ctrl;
     if (C->status != kRunning || !C->pending) return;
     const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw;
@@ -394,7 +404,8 @@ __global__ void __launch_bounds__(kBlock) flush_primal(Dev<T> D) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) flush_dual(Dev<T> D) {
+__device__ __forceinline__ void flush_dual_body(const Dev<T>& D, int qidx) {
+    (void)qidx;
     Ctrl* C = D.ctrl;
     if (C->status != kRunning || !C->pending) return;
     // the pending evaluation is attempts - 1; its K xhat sits in buffer (attempts - 1) & 1
@@ -416,10 +427,10 @@ __device__ __forceinline__ int n_candidates(const Ctrl* C) {
 
 // xc[q] = Proj_[l,u](source_q): q = 0 current z, q = 1 the average zsum / wsum
 template <typename T>
-__global__ void __launch_bounds__(kBlock) cand_primal(Dev<T> D) {
+__device__ __forceinline__ void cand_primal_body(const Dev<T>& D, int qidx) {
     const Ctrl* C = D.ctrl;
     if (C->status != kRunning) return;
-    const int q = blockIdx.y;
+    const int q = qidx;
     if (q >= n_candidates(C)) return;
     const double iw = q ? 1.0 / C->wsum : 0.0;
     double* out = D.xc + (size_t)q * D.n;
@@ -432,10 +443,10 @@ __global__ void __launch_bounds__(kBlock) cand_primal(Dev<T> D) {
 
 // yc[q] = Proj_{Dr^{-1} C*}(source_q), same block split as dual_update
 template <typename T>
-__global__ void __launch_bounds__(kBlock) cand_dual(Dev<T> D) {
+__device__ __forceinline__ void cand_dual_body(const Dev<T>& D, int qidx) {
     const Ctrl* C = D.ctrl;
     if (C->status != kRunning) return;
-    const int q = blockIdx.y;
+    const int q = qidx;
     if (q >= n_candidates(C)) return;
     const double iw = q ? 1.0 / C->wsum : 0.0;
     double* out = D.yc + (size_t)q * D.m;
@@ -444,8 +455,9 @@ __global__ void __launch_bounds__(kBlock) cand_dual(Dev<T> D) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     auto val = [&](int i) { return q ? (double)src[i] * iw : (double)src[i]; };
     if (b >= D.nb_exp + D.nb_soc) {  // scalar rows (blocks dispatched last)
+        const int sb = b - D.nb_exp - D.nb_soc;  // idle beyond this program's split (batches)
         const int stride = D.nb_scal * blockDim.x;
-        for (int i = (b - D.nb_exp - D.nb_soc) * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
+        for (int i = sb * blockDim.x + threadIdx.x; sb < D.nb_scal && i < D.m_scalar; i += stride) {
             const double v = val(i);
             out[i] = (i < D.m_zero) ? v : fmax(v, 0.0);
         }
@@ -478,10 +490,10 @@ __global__ void __launch_bounds__(kBlock) cand_dual(Dev<T> D) {
 //   kpRmax : ||w - Proj_C(w)||_inf, w = K x - h = v / dr      (err_p numerator)
 //   kpKxmax: ||K x||_inf, kpPmax: ||Proj_C(K x - h)||_inf     (err_p denominator)
 template <typename T>
-__global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
+__device__ __forceinline__ void kkt_primal_body(const Dev<T>& D, int qidx) {
     const Ctrl* C = D.ctrl;
     if (C->status != kRunning) return;
-    const int q = blockIdx.y;
+    const int q = qidx;
     if (q >= n_candidates(C)) return;
     __shared__ double sm[3][kWarpsPerBlock];
     const double* kx = D.kxc + (size_t)q * D.m;
@@ -498,8 +510,9 @@ __global__ void __launch_bounds__(kBlock) kkt_primal(Dev<T> D) {
         mx[1] = fmax(mx[1], fabs(kx[i] / D.dr[i]));
     };
     if (b >= D.nb_exp + D.nb_soc) {  // scalar rows (blocks dispatched last)
+        const int sb = b - D.nb_exp - D.nb_soc;  // idle beyond this program's split (batches)
         const int stride = D.nb_scal * blockDim.x;
-        for (int i = (b - D.nb_exp - D.nb_soc) * blockDim.x + threadIdx.x; i < D.m_scalar; i += stride) {
+        for (int i = sb * blockDim.x + threadIdx.x; sb < D.nb_scal && i < D.m_scalar; i += stride) {
             const double v = kx[i] - D.h64[i];
             const double w = v / D.dr[i];
             double rs, ru, pu;
@@ -685,7 +698,8 @@ __device__ void check_controller(const Dev<T>& D, double (*sm)[kWarpsPerBlock]) 
 //   kdDx2  : ||xc - x0||^2
 //   kdDmax : ||lambda - Proj_Lambda(lambda)||_inf (original scale), kdKtymax : ||K'y||_inf
 template <typename T>
-__global__ void __launch_bounds__(kBlock) kkt_dual(Dev<T> D) {
+__device__ __forceinline__ void kkt_dual_body(const Dev<T>& D, int qidx) {
+    (void)qidx;
     Ctrl* C = D.ctrl;
     if (C->status != kRunning) return;
     const int nc = n_candidates(C);
@@ -728,7 +742,8 @@ __global__ void __launch_bounds__(kBlock) kkt_dual(Dev<T> D) {
 
 // restart: z^{t+1,0} <- candidate `best` (and its cached products), averages reset
 template <typename T>
-__global__ void __launch_bounds__(kBlock) restart_primal(Dev<T> D) {
+__device__ __forceinline__ void restart_primal_body(const Dev<T>& D, int qidx) {
+    (void)qidx;
     const Ctrl* C = D.ctrl;
     if (!C->restart_now) return;
     const int q = C->best;
@@ -743,7 +758,8 @@ __global__ void __launch_bounds__(kBlock) restart_primal(Dev<T> D) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) restart_dual(Dev<T> D) {
+__device__ __forceinline__ void restart_dual_body(const Dev<T>& D, int qidx) {
+    (void)qidx;
     const Ctrl* C = D.ctrl;
     if (!C->restart_now) return;
     const int q = C->best;
@@ -756,5 +772,72 @@ __global__ void __launch_bounds__(kBlock) restart_dual(Dev<T> D) {
         D.ysum[i] = T(0);
     }
 }
+
+
+// ---------------------------------------------------------------------------
+// Batched SpMV (FP64 programs): program blockIdx.z.  mode 0: K xhat into the buffer of
+// the evaluation's parity; 1: K' yhat (skipped after a rejected step); 2: K xc[q];
+// 3: K' yc[q] (q = blockIdx.y).  Blocks beyond a program's plan are idle.
+// ---------------------------------------------------------------------------
+template <int U>
+__global__ void __launch_bounds__(kBlock) spmv_batch(const Dev<double>* __restrict__ Ds, int mode) {
+    const Dev<double>& D = Ds[blockIdx.z];
+    const Ctrl* C = D.ctrl;
+    if (C->status != kRunning) return;
+    if (mode == 1 && !C->pending) return;
+    const bool kt = mode == 1 || mode == 3;
+    const SpmvBins& B = kt ? D.binsKT : D.binsK;
+    if ((int)blockIdx.x >= B.blk[B.nbins]) return;
+    int k = 0;
+    while (k + 1 < B.nbins && (int)blockIdx.x >= B.blk[k + 1]) ++k;
+    const int wb = ((int)blockIdx.x - B.blk[k]) * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int nwb = (B.blk[k + 1] - B.blk[k]) * kWarpsPerBlock;
+    const int* l = (kt ? D.listKT : D.listK) + B.row[k];
+    const int cnt = B.row[k + 1] - B.row[k];
+    const int q = blockIdx.y;
+    const double* x;
+    double* y;
+    if (mode == 0) { x = D.xh; y = (C->attempts & 1) ? D.kxh1 : D.kxh0; }
+    else if (mode == 1) { x = D.yh; y = D.ktyh; }
+    else if (mode == 2) { x = D.xc + (size_t)q * D.n; y = D.kxc + (size_t)q * D.m; }
+    else { x = D.yc + (size_t)q * D.m; y = D.ktyc + (size_t)q * D.n; }
+    const int* rp = kt ? D.rpT : D.rp;
+    const int* ci = kt ? D.ciT : D.ci;
+    const double* val = kt ? D.valT : D.val;
+    switch (B.lanes[k]) {
+        case 1: spmv_bin_rows<double, double, 1, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        case 2: spmv_bin_rows<double, double, 2, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        case 4: spmv_bin_rows<double, double, 4, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        case 8: spmv_bin_rows<double, double, 8, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        case 16: spmv_bin_rows<double, double, 16, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        default: spmv_bin_rows<double, double, 32, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch wrappers: one program (the view by value), or a batch of programs in one
+// launch (views in device memory; the program is blockIdx.z, the candidate blockIdx.y).
+// A batch shares one grid: every program is set up with the same block counts.
+// ---------------------------------------------------------------------------
+#define PDCS_KERNEL_PAIR(name)                                                               \
+    template <typename T>                                                                    \
+    __global__ void __launch_bounds__(kBlock) name(Dev<T> D) {                               \
+        name##_body(D, blockIdx.y);                                                          \
+    }                                                                                        \
+    template <typename T>                                                                    \
+    __global__ void __launch_bounds__(kBlock) name##_batch(const Dev<T>* __restrict__ Ds) {  \
+        name##_body(Ds[blockIdx.z], blockIdx.y);                                             \
+    }
+PDCS_KERNEL_PAIR(primal_update)
+PDCS_KERNEL_PAIR(dual_update)
+PDCS_KERNEL_PAIR(flush_primal)
+PDCS_KERNEL_PAIR(flush_dual)
+PDCS_KERNEL_PAIR(cand_primal)
+PDCS_KERNEL_PAIR(cand_dual)
+PDCS_KERNEL_PAIR(kkt_primal)
+PDCS_KERNEL_PAIR(kkt_dual)
+PDCS_KERNEL_PAIR(restart_primal)
+PDCS_KERNEL_PAIR(restart_dual)
+#undef PDCS_KERNEL_PAIR
 
 }  // namespace pdcs

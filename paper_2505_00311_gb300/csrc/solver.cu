@@ -25,6 +25,7 @@ using namespace pdcs;
 namespace {
 
 std::string g_create_error;  // text of the last failed pdcs_create
+std::string g_batch_error;   // text of the last failed pdcs_batch_create
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -461,15 +462,29 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     ctx->g_vec_n = vec_grid(n, ctx->sms);
     ctx->g_vec_m = vec_grid(m, ctx->sms);
     ctx->g_kktd = vec_grid(n, ctx->sms);
-    const int nb_scal = ctx->m_scalar > 0 ? vec_grid(ctx->m_scalar, ctx->sms) : 0;
-    const int nb_soc = ctx->n_soc > 0 ? (int)std::min<long long>((ctx->n_soc + kWarpsPerBlock - 1) / kWarpsPerBlock,
-                                                                 (long long)ctx->sms * 8)
-                                      : 0;
+    int nb_scal = ctx->m_scalar > 0 ? vec_grid(ctx->m_scalar, ctx->sms) : 0;
+    int nb_soc = ctx->n_soc > 0 ? (int)std::min<long long>((ctx->n_soc + kWarpsPerBlock - 1) / kWarpsPerBlock,
+                                                           (long long)ctx->sms * 8)
+                                : 0;
     // exp cones: one thread each, at most 256 per block but no fewer blocks than SMs
     // while each keeps a full warp (their FP64 work is bound by each SM's FP64 units)
     const int exp_pb = (int)std::min<long long>(256, std::max<long long>(32, (ctx->n_exp / std::max(1, ctx->sms)) / 32 * 32));
-    const int nb_exp = ctx->n_exp > 0 ? (int)std::min<long long>((ctx->n_exp + exp_pb - 1) / exp_pb, (long long)ctx->sms * 8) : 0;
+    int nb_exp = ctx->n_exp > 0 ? (int)std::min<long long>((ctx->n_exp + exp_pb - 1) / exp_pb, (long long)ctx->sms * 8) : 0;
     ctx->g_dual = std::max(1, nb_scal + nb_soc + nb_exp);
+    if (ctx->opt.batch_blocks > 0) {
+        // one grid for every launch, shared by the programs of a batch: the cone roles keep
+        // their share of it (at least one block each), blocks beyond the split stay idle
+        const int G = ctx->opt.batch_blocks;
+        ctx->g_vec_n = ctx->g_vec_m = ctx->g_kktd = ctx->g_dual = G;
+        const int kinds = (nb_scal > 0) + (nb_soc > 0) + (nb_exp > 0);
+        const int tot = nb_scal + nb_soc + nb_exp;
+        if (tot > G) {
+            auto share = [&](int nb) { return nb > 0 ? std::max(1, (int)((long long)nb * (G - kinds) / tot)) : 0; };
+            nb_exp = share(nb_exp);
+            nb_soc = share(nb_soc);
+            nb_scal = share(nb_scal);
+        }
+    }
     PartLayout pl;
     pl.primal_blocks = ctx->g_vec_n;
     pl.dual_blocks = ctx->g_dual;
@@ -670,6 +685,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.part = ctx->part; D.pl = pl; D.ctrl = ctx->ctrl;
     D.l_orig = ctx->l0; D.u_orig = ctx->u0;
     D.exp_mlp = exp_mlp;
+    D.binsK = ctx->pk.B; D.binsKT = ctx->pkt.B; D.listK = ctx->pk.list; D.listKT = ctx->pkt.list;
 
     // ---- controller scalars
     Ctrl C;
@@ -717,6 +733,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         if (tune) {
             CK(tune_spmv<float>(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val_f, DF.x, DF.kx));
             CK(tune_spmv<float>(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->valT_f, DF.y, DF.kty));
+            D.binsK = DF.binsK = ctx->pk.B;
+            D.binsKT = DF.binsKT = ctx->pkt.B;
         }
     }
     CK(cudaStreamSynchronize(s));
@@ -819,6 +837,86 @@ void fill_info(pdcs_ctx* ctx, pdcs_info* info) {
     info->spmv_plan[3] = ctx->pkt.unroll;
 }
 
+__global__ void batch_prepare(Dev<double>* views, int count, double tol, int start) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    Ctrl* C = views[i].ctrl;
+    C->tol = tol;
+    if (start) C->check_mode = 1;
+}
+
+__global__ void batch_status(const Dev<double>* views, int count, int* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = views[i].ctrl->status;
+}
+
+}  // namespace
+
+// A batch: programs created with the same batch_blocks, iterated in lockstep by launches
+// whose third grid dimension is the program (one CUDA graph per check period).
+struct pdcs_batch {
+    std::vector<pdcs_ctx*> ctxs;
+    cudaStream_t stream = nullptr;
+    Dev<double>* views = nullptr;  // device copies of the programs' views
+    int* d_status = nullptr;
+    int* h_status = nullptr;       // pinned
+    int G = 0, g_spmv = 0, period = 64;
+    cudaGraphExec_t graph = nullptr;
+    bool started = false;
+    std::string err;
+    ~pdcs_batch() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (views) cudaFree(views);
+        if (d_status) cudaFree(d_status);
+        if (h_status) cudaFreeHost(h_status);
+    }
+};
+
+namespace {
+
+void batch_attempt(pdcs_batch* b) {
+    const int B = (int)b->ctxs.size();
+    cudaStream_t s = b->stream;
+    primal_update_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
+    spmv_batch<4><<<dim3(b->g_spmv, 1, B), kBlock, 0, s>>>(b->views, 0);
+    dual_update_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
+    spmv_batch<4><<<dim3(b->g_spmv, 1, B), kBlock, 0, s>>>(b->views, 1);
+    for (pdcs_ctx* c : b->ctxs) c->launches += kLaunchesPerAttempt;
+}
+
+void batch_check(pdcs_batch* b) {
+    const int B = (int)b->ctxs.size();
+    cudaStream_t s = b->stream;
+    flush_primal_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
+    flush_dual_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
+    cand_primal_batch<double><<<dim3(b->G, 2, B), kBlock, 0, s>>>(b->views);
+    cand_dual_batch<double><<<dim3(b->G, 2, B), kBlock, 0, s>>>(b->views);
+    spmv_batch<4><<<dim3(b->g_spmv, 2, B), kBlock, 0, s>>>(b->views, 2);
+    spmv_batch<4><<<dim3(b->g_spmv, 2, B), kBlock, 0, s>>>(b->views, 3);
+    kkt_primal_batch<double><<<dim3(b->G, 2, B), kBlock, 0, s>>>(b->views);
+    kkt_dual_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
+    restart_primal_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
+    restart_dual_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
+    for (pdcs_ctx* c : b->ctxs) c->launches += kLaunchesPerCheck;
+}
+
+#define CKB(call)                                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            b->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            return e_ == cudaErrorMemoryAllocation ? PDCS_ERR_OOM : PDCS_ERR_CUDA;       \
+        }                                                                                \
+    } while (0)
+
+pdcs_status batch_read(pdcs_batch* b) {
+    const int B = (int)b->ctxs.size();
+    batch_status<<<(B + 255) / 256, 256, 0, b->stream>>>(b->views, B, b->d_status);
+    CKB(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * B, cudaMemcpyDeviceToHost, b->stream));
+    CKB(cudaStreamSynchronize(b->stream));
+    return PDCS_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -842,6 +940,7 @@ void pdcs_default_options(pdcs_options* o) {
     o->time_limit = 0.0;
     o->spmv_autotune = 0;
     o->exp_mlp = nullptr;
+    o->batch_blocks = 0;
 }
 
 pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, const double* lb, const double* ub,
@@ -892,6 +991,7 @@ pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, con
     if (o.spmv_lanes != 0 && (o.spmv_lanes > 32 || (o.spmv_lanes & (o.spmv_lanes - 1)) != 0))
         return bad("spmv_lanes must be 0 or a power of two <= 32");
     if (o.spmv_autotune != 0 && o.spmv_autotune != 1) return bad("spmv_autotune must be 0 or 1");
+    if (o.batch_blocks < 0 || o.batch_blocks > 1 << 20) return bad("batch_blocks must be in [0, 2^20]");
 
     pdcs_ctx* ctx = new (std::nothrow) pdcs_ctx();
     if (!ctx) return bad("host allocation failed");
@@ -1180,6 +1280,133 @@ void pdcs_destroy(pdcs_ctx* ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     delete ctx;
+}
+
+
+pdcs_status pdcs_batch_create(pdcs_ctx* const* ctxs, int64_t count, pdcs_batch** out) {
+    if (!out) return PDCS_ERR_INVALID;
+    *out = nullptr;
+    auto bad = [&](const char* m) { g_batch_error = m; return PDCS_ERR_INVALID; };
+    if (!ctxs || count < 1 || count > 65535) return bad("count must be in [1, 65535]");
+    const pdcs_ctx* c0 = ctxs[0];
+    if (!c0) return bad("NULL context");
+    for (int64_t i = 0; i < count; ++i) {
+        const pdcs_ctx* c = ctxs[i];
+        if (!c) return bad("NULL context");
+        if (c->opt.batch_blocks <= 0 || c->opt.batch_blocks != c0->opt.batch_blocks)
+            return bad("every program needs the same options.batch_blocks > 0");
+        if (c->opt.precision != PDCS_PRECISION_FP64) return bad("batches run FP64 programs");
+        if (c->opt.check_period != c0->opt.check_period) return bad("programs differ in check_period");
+        if (c->pk.unroll != 4 || c->pkt.unroll != 4) return bad("batches use the SpMV unroll 4 (no autotuning)");
+        if (c->started) return bad("a program has already been solved alone");
+        for (int64_t j = 0; j < i; ++j)
+            if (ctxs[j] == c) return bad("a program appears twice");
+    }
+    pdcs_batch* b = new (std::nothrow) pdcs_batch();
+    if (!b) return bad("host allocation failed");
+    b->ctxs.assign(ctxs, ctxs + count);
+    b->stream = c0->stream;
+    b->G = c0->opt.batch_blocks;
+    b->period = c0->opt.check_period;
+    for (pdcs_ctx* c : b->ctxs)
+        b->g_spmv = std::max({b->g_spmv, c->pk.B.blk[c->pk.B.nbins], c->pkt.B.blk[c->pkt.B.nbins], 1});
+    std::vector<Dev<double>> hv(count);
+    for (int64_t i = 0; i < count; ++i) hv[i] = ctxs[i]->D;
+    cudaError_t e = cudaMalloc(&b->views, sizeof(Dev<double>) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int) * count);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int) * count);
+    if (e == cudaSuccess) e = cudaMemcpy(b->views, hv.data(), sizeof(Dev<double>) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        g_batch_error = std::string("CUDA: ") + cudaGetErrorString(e);
+        delete b;
+        return e == cudaErrorMemoryAllocation ? PDCS_ERR_OOM : PDCS_ERR_CUDA;
+    }
+    *out = b;
+    return PDCS_OK;
+}
+
+pdcs_status pdcs_batch_solve(pdcs_batch* b, double tol, int64_t max_iter, int64_t* n_converged) {
+    if (!b) return PDCS_ERR_INVALID;
+    if (max_iter < 0) { b->err = "max_iter < 0"; return PDCS_ERR_INVALID; }
+    const int B = (int)b->ctxs.size();
+    const double t0 = now_s();
+    batch_prepare<<<(B + 255) / 256, 256, 0, b->stream>>>(b->views, B, tol, b->started ? 0 : 1);
+    if (!b->started) {
+        batch_check(b);  // each program's anchor evaluation
+        b->started = true;
+        for (pdcs_ctx* c : b->ctxs) c->started = true;
+    }
+    CKB(cudaGetLastError());
+    pdcs_status st = batch_read(b);
+    if (st != PDCS_OK) return st;
+    long long done = 0;  // all programs advance in lockstep
+    {
+        Ctrl C;
+        CKB(cudaMemcpy(&C, b->ctxs[0]->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+        done = C.attempts;
+    }
+    long long remaining = max_iter;
+    auto running = [&]() {
+        for (int i = 0; i < B; ++i)
+            if (b->h_status[i] == kRunning) return true;
+        return false;
+    };
+    while (remaining > 0 && running()) {
+        const long long to_b = b->period - (done % b->period);
+        if (remaining >= to_b) {
+            if (to_b == b->period) {
+                if (!b->graph) {
+                    cudaGraph_t g;
+                    CKB(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                    for (int a = 0; a < b->period; ++a) batch_attempt(b);
+                    batch_check(b);
+                    CKB(cudaStreamEndCapture(b->stream, &g));
+                    cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+                    cudaGraphDestroy(g);
+                    if (e != cudaSuccess) { b->graph = nullptr; CKB(e); }
+                    // capture only recorded the launches: undo their counts
+                    for (pdcs_ctx* c : b->ctxs) c->launches -= (long long)b->period * kLaunchesPerAttempt + kLaunchesPerCheck;
+                }
+                CKB(cudaGraphLaunch(b->graph, b->stream));
+                for (pdcs_ctx* c : b->ctxs) c->launches += (long long)b->period * kLaunchesPerAttempt + kLaunchesPerCheck;
+            } else {
+                for (long long a = 0; a < to_b; ++a) batch_attempt(b);
+                batch_check(b);
+            }
+            done += to_b;
+            remaining -= to_b;
+        } else {
+            for (long long a = 0; a < remaining; ++a) batch_attempt(b);
+            done += remaining;
+            remaining = 0;
+        }
+        CKB(cudaGetLastError());
+        st = batch_read(b);
+        if (st != PDCS_OK) return st;
+    }
+    int conv = 0, numeric = 0;
+    for (int i = 0; i < B; ++i) {
+        conv += b->h_status[i] == kConverged;
+        numeric += b->h_status[i] == kNumericError;
+    }
+    const double dt = now_s() - t0;
+    for (pdcs_ctx* c : b->ctxs) {
+        c->solve_seconds += dt;
+        pdcs_status s2 = read_ctrl(c);
+        if (s2 != PDCS_OK) return s2;
+        c->last_status = status_of(*c->h_ctrl);
+    }
+    if (n_converged) *n_converged = conv;
+    if (numeric) { b->err = "NaN or Inf in the iterates of a program"; return PDCS_ERR_NUMERIC; }
+    return conv == B ? PDCS_OK : PDCS_MAX_ITER;
+}
+
+const char* pdcs_batch_last_error(const pdcs_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+void pdcs_batch_destroy(pdcs_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    delete b;
 }
 
 }  // extern "C"

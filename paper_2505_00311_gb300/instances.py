@@ -223,3 +223,60 @@ def edge_cases(seed: int = 5, m: int = 40, n: int = 30):
     lb = np.where((kind == 0) | (kind == 1), -rng.uniform(0.0, 1.0, n), -np.inf)
     ub = np.where((kind == 0) | (kind == 2), rng.uniform(0.5, 1.5, n), np.inf)
     return _finish(rng, m, n, row_ptr, cols, vals, types, dims, "edge_cases", lb=lb, ub=ub)
+
+
+def lasso_socp(seed: int = 0, n: int = 200, m: int | None = None, lam: float | None = None):
+    """Lasso min ||A x - b||^2 + lam ||x||_1 as the SOCP of the paper's App. C (variables
+    w, r, y (m), x1, x2 (n each), x = x1 - x2): w = 1 and y = A(x1 - x2) - b as zero rows,
+    (w, r, y) in the rotated SOC ||y||^2 <= 2 w r, objective 2 r + lam 1'(x1 + x2), x1, x2 >= 0,
+    w, r, y free.  Data (batched-workload recipe): m = n / 2, A dense N(0, 1), a ground truth
+    with 5 % nonzero N(0, 1) entries, b = A x~ + 0.01 N(0, 1), lam ~ U[0.01, 1].  No known
+    optimum: solutions are judged by the KKT evaluator."""
+    rng = np.random.default_rng(seed)
+    m = max(1, n // 2) if m is None else m
+    A = rng.standard_normal((m, n))
+    xt = np.zeros(n)
+    nz = rng.random(n) < 0.05
+    xt[nz] = rng.standard_normal(int(nz.sum()))
+    b = A @ xt + 0.01 * rng.standard_normal(m)
+    lam = float(rng.uniform(0.01, 1.0)) if lam is None else float(lam)
+    nv = 2 + m + 2 * n
+    iw, ir, iy, ix1, ix2 = 0, 1, 2, 2 + m, 2 + m + n
+    rows, cols, vals = [], [], []
+    # zero rows: w = 1, then y - A x1 + A x2 = -b
+    rows.append([0]); cols.append([iw]); vals.append([1.0])
+    for i in range(m):
+        r = 1 + i
+        rows.append(np.full(1 + 2 * n, r))
+        cols.append(np.concatenate([[iy + i], ix1 + np.arange(n), ix2 + np.arange(n)]))
+        vals.append(np.concatenate([[1.0], -A[i], A[i]]))
+    # rotated SOC rows (w, r, y)
+    o = 1 + m
+    rows.append(o + np.arange(m + 2)); cols.append(np.concatenate([[iw, ir], iy + np.arange(m)]))
+    vals.append(np.ones(m + 2))
+    R = np.concatenate([np.asarray(x) for x in rows])
+    C = np.concatenate([np.asarray(x) for x in cols])
+    V = np.concatenate([np.asarray(x, dtype=float) for x in vals])
+    M = sp.csr_matrix((V, (R, C)), shape=(2 * m + 3, nv))
+    M.sort_indices()
+    c = np.zeros(nv)
+    c[ir] = 2.0
+    c[ix1:] = lam
+    h = np.zeros(2 * m + 3)
+    h[0] = 1.0
+    h[1:1 + m] = -b
+    lb = np.full(nv, -np.inf)
+    lb[ix1:] = 0.0
+    ub = np.full(nv, np.inf)
+    return {"name": "lasso_socp", "m": 2 * m + 3, "n": nv, "row_ptr": M.indptr.astype(np.int64),
+            "col": M.indices.astype(np.int32), "val": M.data, "c": c, "h": h, "lb": lb, "ub": ub,
+            "cone_types": np.asarray([ZERO, RSOC], dtype=np.int32),
+            "cone_dims": np.asarray([1 + m, m + 2], dtype=np.int64),
+            "lasso": {"A": A, "b": b, "lam": lam}}
+
+
+def lasso_batch(seed: int, count: int, n_lo: int = 50, n_hi: int = 1000):
+    """`count` Lasso SOCPs of uneven sizes, n ~ U{n_lo..n_hi}, each from its own seed."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(n_lo, n_hi + 1, count)
+    return [lasso_socp(int(seed) * 100_003 + k, int(nk)) for k, nk in enumerate(sizes)]

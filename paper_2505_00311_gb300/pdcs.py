@@ -44,7 +44,7 @@ class pdcs_options(ctypes.Structure):
                 ("power_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("fp32_switch_tol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("spmv_lanes", ctypes.c_int32), ("time_limit", ctypes.c_double),
-                ("exp_mlp", ctypes.c_void_p), ("spmv_autotune", ctypes.c_int32)]
+                ("exp_mlp", ctypes.c_void_p), ("spmv_autotune", ctypes.c_int32), ("batch_blocks", ctypes.c_int32)]
 
 
 class pdcs_info(ctypes.Structure):
@@ -89,6 +89,11 @@ SIGNATURES = {
     "pdcs_exp_mlp_train": (ctypes.c_int, [ctypes.c_int64, _fp, _fp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                           ctypes.c_uint64, _fp, _fp]),
     "pdcs_exp_proj_stats": (ctypes.c_int, [ctypes.c_int64, _dp, _dp, _fp, _dp, _i32p]),
+    "pdcs_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "pdcs_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, _i64p]),
+    "pdcs_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "pdcs_batch_destroy": (None, [ctypes.c_void_p]),
 }
 EXP_MLP_IN, EXP_MLP_HIDDEN = 9, 32
 EXP_MLP_PARAMS = EXP_MLP_HIDDEN * EXP_MLP_IN + EXP_MLP_HIDDEN + EXP_MLP_HIDDEN * EXP_MLP_HIDDEN + 2 * EXP_MLP_HIDDEN + 1
@@ -366,3 +371,39 @@ def exp_mlp_init(seed=0):
     parts = [rng.normal(0, np.sqrt(2.0 / I), H * I), np.zeros(H), rng.normal(0, np.sqrt(2.0 / H), H * H),
              np.zeros(H), rng.normal(0, np.sqrt(1.0 / H), H), np.zeros(1)]
     return np.concatenate(parts).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# batches of programs
+# ---------------------------------------------------------------------------
+class Batch:
+    """Solves the programs of several Solver objects together (they must have been made
+    with the same batch_blocks > 0 and not solved yet).  The solvers keep their
+    solutions and info; close them after the batch."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.ctx for s in self.solvers])
+        out = ctypes.c_void_p()
+        st = lib().pdcs_batch_create(arr, len(self.solvers), ctypes.byref(out))
+        if st != OK:
+            raise PdcsError(st, lib().pdcs_batch_last_error(None).decode())
+        self.b = out.value
+
+    def solve(self, tol=1e-6, max_iter=1_000_000):
+        n = ctypes.c_int64(0)
+        st = lib().pdcs_batch_solve(self.b, float(tol), int(max_iter), ctypes.byref(n))
+        if st not in (OK, MAX_ITER):
+            raise PdcsError(st, lib().pdcs_batch_last_error(self.b).decode())
+        return st, n.value
+
+    def close(self):
+        if self.b:
+            lib().pdcs_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
