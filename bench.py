@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run (profiling runs)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-iterate mode measurements")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-programs measurement")
+    ap.add_argument("--batch-count", type=int, default=256, help="Lasso programs in the batched measurement")
     ap.add_argument("--time-to-tol", default="1e-4,1e-6",
                     help="comma list of tolerances for the time-to-solution runs ('' to skip)")
     ap.add_argument("--ttt-limit", type=float, default=45.0, help="seconds allowed per time-to-tolerance run")
@@ -330,6 +332,41 @@ def main():
                 "dtype": "f32 iterates, f64 checks", "still_fp32_phase": phase == 0,
                 "kernels_ms_per_launch": kt32, "time_to_tol": ttt32}
 
+    # batched programs: uneven-size Lasso SOCPs solved to 1e-6 in one batch against the
+    # plain method solving them one after the other (same instances, same tolerance)
+    batch = None
+    if not args.no_batch:
+        from paper_2505_00311_gb300 import instances as I
+        probs = I.lasso_batch(7, args.batch_count, 50, 400)
+        G = 8
+        solvers = [P.Solver(q, stream=stream.cuda_stream, batch_blocks=G) for q in probs]
+        bt = P.Batch(solvers)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, nconv = bt.solve(1e-6, 100_000)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        evals_b = max(sv.info()["attempts"] for sv in solvers)
+        bt.close()
+        for sv in solvers:
+            sv.close()
+        t_seq, nseq, evals_s = 0.0, 0, 0
+        for q in probs:
+            sv = P.Solver(q, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st1, inf1 = sv.solve(1e-6, 100_000)
+            torch.cuda.synchronize()
+            t_seq += time.perf_counter() - t0
+            nseq += st1 == P.OK
+            evals_s += inf1["attempts"]
+            sv.close()
+        batch = {"workload": "%d Lasso SOCPs (App. C form), n ~ U{50..400} features, m = n/2, dense N(0,1) "
+                             "design, tol 1e-6, FP64" % len(probs),
+                 "batched_seconds": t_batch, "batched_converged": nconv, "batched_lockstep_evaluations": evals_b,
+                 "sequential_seconds": t_seq, "sequential_converged": nseq,
+                 "sequential_total_evaluations": evals_s, "speedup": t_seq / t_batch if t_batch > 0 else None}
+
     if rank != 0:
         return
     # roofline of the dominant kernel
@@ -356,7 +393,7 @@ def main():
                        "precision": "fp64", "l2": "working set > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clk, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-            "time_to_tol": ttt, "fp32_iterates": fp32}
+            "time_to_tol": ttt, "fp32_iterates": fp32, "batched_programs": batch}
     print(json.dumps(line))
 
 

@@ -855,7 +855,8 @@ __global__ void batch_status(const Dev<double>* views, int count, int* out) {
 // A batch: programs created with the same batch_blocks, iterated in lockstep by launches
 // whose third grid dimension is the program (one CUDA graph per check period).
 struct pdcs_batch {
-    std::vector<pdcs_ctx*> ctxs;
+    std::vector<pdcs_ctx*> ctxs;    // all programs
+    std::vector<int> active;        // programs in the launches (those still running, compacted)
     cudaStream_t stream = nullptr;
     Dev<double>* views = nullptr;  // device copies of the programs' views
     int* d_status = nullptr;
@@ -875,17 +876,17 @@ struct pdcs_batch {
 namespace {
 
 void batch_attempt(pdcs_batch* b) {
-    const int B = (int)b->ctxs.size();
+    const int B = (int)b->active.size();
     cudaStream_t s = b->stream;
     primal_update_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
     spmv_batch<4><<<dim3(b->g_spmv, 1, B), kBlock, 0, s>>>(b->views, 0);
     dual_update_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
     spmv_batch<4><<<dim3(b->g_spmv, 1, B), kBlock, 0, s>>>(b->views, 1);
-    for (pdcs_ctx* c : b->ctxs) c->launches += kLaunchesPerAttempt;
+    for (int i : b->active) b->ctxs[i]->launches += kLaunchesPerAttempt;
 }
 
 void batch_check(pdcs_batch* b) {
-    const int B = (int)b->ctxs.size();
+    const int B = (int)b->active.size();
     cudaStream_t s = b->stream;
     flush_primal_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
     flush_dual_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
@@ -897,7 +898,7 @@ void batch_check(pdcs_batch* b) {
     kkt_dual_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
     restart_primal_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
     restart_dual_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
-    for (pdcs_ctx* c : b->ctxs) c->launches += kLaunchesPerCheck;
+    for (int i : b->active) b->ctxs[i]->launches += kLaunchesPerCheck;
 }
 
 #define CKB(call)                                                                        \
@@ -909,11 +910,38 @@ void batch_check(pdcs_batch* b) {
         }                                                                                \
     } while (0)
 
+// Status of every program in the launches (h_status, in the order of `active`).
 pdcs_status batch_read(pdcs_batch* b) {
-    const int B = (int)b->ctxs.size();
+    const int B = (int)b->active.size();
     batch_status<<<(B + 255) / 256, 256, 0, b->stream>>>(b->views, B, b->d_status);
     CKB(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * B, cudaMemcpyDeviceToHost, b->stream));
     CKB(cudaStreamSynchronize(b->stream));
+    return PDCS_OK;
+}
+
+// Keeps only the running programs in the launches (their views moved to the front),
+// once at most half of the launched ones still run; the graph is captured again.
+// Each program's arithmetic does not depend on the others, so results are unchanged.
+pdcs_status batch_compact(pdcs_batch* b) {
+    std::vector<int> keep;
+    for (size_t k = 0; k < b->active.size(); ++k)
+        if (b->h_status[k] == kRunning) keep.push_back(b->active[k]);
+    if (keep.empty() || keep.size() * 2 > b->active.size()) return PDCS_OK;
+    std::vector<Dev<double>> hv(keep.size());
+    b->g_spmv = 1;
+    for (size_t k = 0; k < keep.size(); ++k) {
+        const pdcs_ctx* c = b->ctxs[keep[k]];
+        hv[k] = c->D;
+        b->g_spmv = std::max({b->g_spmv, c->pk.B.blk[c->pk.B.nbins], c->pkt.B.blk[c->pkt.B.nbins]});
+    }
+    CKB(cudaMemcpyAsync(b->views, hv.data(), sizeof(Dev<double>) * keep.size(), cudaMemcpyHostToDevice, b->stream));
+    CKB(cudaStreamSynchronize(b->stream));
+    b->active = keep;
+    for (size_t k = 0; k < keep.size(); ++k) b->h_status[k] = kRunning;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
     return PDCS_OK;
 }
 
@@ -1305,6 +1333,7 @@ pdcs_status pdcs_batch_create(pdcs_ctx* const* ctxs, int64_t count, pdcs_batch**
     pdcs_batch* b = new (std::nothrow) pdcs_batch();
     if (!b) return bad("host allocation failed");
     b->ctxs.assign(ctxs, ctxs + count);
+    for (int64_t i = 0; i < count; ++i) b->active.push_back((int)i);
     b->stream = c0->stream;
     b->G = c0->opt.batch_blocks;
     b->period = c0->opt.check_period;
@@ -1328,9 +1357,9 @@ pdcs_status pdcs_batch_create(pdcs_ctx* const* ctxs, int64_t count, pdcs_batch**
 pdcs_status pdcs_batch_solve(pdcs_batch* b, double tol, int64_t max_iter, int64_t* n_converged) {
     if (!b) return PDCS_ERR_INVALID;
     if (max_iter < 0) { b->err = "max_iter < 0"; return PDCS_ERR_INVALID; }
-    const int B = (int)b->ctxs.size();
     const double t0 = now_s();
-    batch_prepare<<<(B + 255) / 256, 256, 0, b->stream>>>(b->views, B, tol, b->started ? 0 : 1);
+    batch_prepare<<<((int)b->active.size() + 255) / 256, 256, 0, b->stream>>>(b->views, (int)b->active.size(), tol,
+                                                                             b->started ? 0 : 1);
     if (!b->started) {
         batch_check(b);  // each program's anchor evaluation
         b->started = true;
@@ -1347,7 +1376,7 @@ pdcs_status pdcs_batch_solve(pdcs_batch* b, double tol, int64_t max_iter, int64_
     }
     long long remaining = max_iter;
     auto running = [&]() {
-        for (int i = 0; i < B; ++i)
+        for (size_t i = 0; i < b->active.size(); ++i)
             if (b->h_status[i] == kRunning) return true;
         return false;
     };
@@ -1365,10 +1394,12 @@ pdcs_status pdcs_batch_solve(pdcs_batch* b, double tol, int64_t max_iter, int64_
                     cudaGraphDestroy(g);
                     if (e != cudaSuccess) { b->graph = nullptr; CKB(e); }
                     // capture only recorded the launches: undo their counts
-                    for (pdcs_ctx* c : b->ctxs) c->launches -= (long long)b->period * kLaunchesPerAttempt + kLaunchesPerCheck;
+                    for (int i : b->active)
+                        b->ctxs[i]->launches -= (long long)b->period * kLaunchesPerAttempt + kLaunchesPerCheck;
                 }
                 CKB(cudaGraphLaunch(b->graph, b->stream));
-                for (pdcs_ctx* c : b->ctxs) c->launches += (long long)b->period * kLaunchesPerAttempt + kLaunchesPerCheck;
+                for (int i : b->active)
+                    b->ctxs[i]->launches += (long long)b->period * kLaunchesPerAttempt + kLaunchesPerCheck;
             } else {
                 for (long long a = 0; a < to_b; ++a) batch_attempt(b);
                 batch_check(b);
@@ -1383,19 +1414,22 @@ pdcs_status pdcs_batch_solve(pdcs_batch* b, double tol, int64_t max_iter, int64_
         CKB(cudaGetLastError());
         st = batch_read(b);
         if (st != PDCS_OK) return st;
+        if (done % b->period == 0) {
+            st = batch_compact(b);
+            if (st != PDCS_OK) return st;
+        }
     }
     int conv = 0, numeric = 0;
-    for (int i = 0; i < B; ++i) {
-        conv += b->h_status[i] == kConverged;
-        numeric += b->h_status[i] == kNumericError;
-    }
     const double dt = now_s() - t0;
     for (pdcs_ctx* c : b->ctxs) {
         c->solve_seconds += dt;
         pdcs_status s2 = read_ctrl(c);
         if (s2 != PDCS_OK) return s2;
         c->last_status = status_of(*c->h_ctrl);
+        conv += c->h_ctrl->status == kConverged;
+        numeric += c->h_ctrl->status == kNumericError;
     }
+    const int B = (int)b->ctxs.size();
     if (n_converged) *n_converged = conv;
     if (numeric) { b->err = "NaN or Inf in the iterates of a program"; return PDCS_ERR_NUMERIC; }
     return conv == B ? PDCS_OK : PDCS_MAX_ITER;
