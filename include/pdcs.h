@@ -286,6 +286,35 @@ pdcs_status pdcs_exp_mlp_train(int64_t n, const float* features, const float* ta
 pdcs_status pdcs_exp_proj_stats(int64_t n, const double* v, const double* d, const float* weights, double* out,
                                 int32_t* evals);
 
+/* ------------------------------------------------------------------------------------
+ * A small fully connected network for warm starts of parametric program families (a
+ * summary of an instance's data -> initial dual iterate and log primal weight, given to
+ * pdcs_set_warm_start).  n_layers weight layers, sizes[0..n_layers] the widths (input
+ * first); ReLU after every layer but the last; loss: mean squared error over all outputs.
+ * Parameters: for each layer l, W_l (sizes[l+1] x sizes[l], row-major) then b_l.  FP32
+ * kernels with sums in a fixed order.  Host arrays; each call allocates its own device
+ * memory and synchronises.  There is no counterpart in the paper.
+ * ------------------------------------------------------------------------------------ */
+#define PDCS_MLP_MAX_LAYERS 8
+#define PDCS_MLP_MAX_WIDTH 4096
+
+/* Number of parameters of the network, or -1 for invalid sizes. */
+int64_t pdcs_mlp_params(int32_t n_layers, const int32_t* sizes);
+
+/* Outputs Y (n x sizes[n_layers]) of the network with parameters W for the rows X. */
+pdcs_status pdcs_mlp_forward(int32_t n_layers, const int32_t* sizes, int64_t n, const float* X, const float* W,
+                             float* Y);
+
+/* Loss on the n rows (targets T, n x sizes[n_layers]) and its gradient (layout of W). */
+pdcs_status pdcs_mlp_loss_grad(int32_t n_layers, const int32_t* sizes, int64_t n, const float* X, const float* T,
+                               const float* W, float* grad, float* loss);
+
+/* `steps` Adam steps (0.9, 0.999, 1e-8, learning rate lr) on minibatches of `batch` rows
+ * drawn with replacement by SplitMix64 from `seed`; W is the initial point and is
+ * overwritten; loss_trace (may be NULL) receives each minibatch loss. */
+pdcs_status pdcs_mlp_train(int32_t n_layers, const int32_t* sizes, int64_t n, const float* X, const float* T,
+                           int32_t steps, int32_t batch, float lr, uint64_t seed, float* W, float* loss_trace);
+
 #ifdef __cplusplus
 }
 #endif

@@ -280,3 +280,75 @@ def lasso_batch(seed: int, count: int, n_lo: int = 50, n_hi: int = 1000):
     rng = np.random.default_rng(seed)
     sizes = rng.integers(n_lo, n_hi + 1, count)
     return [lasso_socp(int(seed) * 100_003 + k, int(nk)) for k, nk in enumerate(sizes)]
+
+
+def portfolio_family(seed: int = 0, n_assets: int = 20_000, k: int = 100):
+    """A parametric family of long-only factor-model portfolio SOCPs: F ~ N(0, 1/k) (n_assets x
+    k, as N(0, 1/100) for k = 100), box [0, 0.05], budget 1'x = 1, factor exposures f = F'x and
+    the risk bound ||f|| <= gamma as one SOC of dim k + 1; gamma is half the mean factor risk
+    ||F'x_g|| of greedy box + budget portfolios x_g (the 1 / 0.05 best assets of five return
+    draws).  Instances differ only in the expected returns mu ~ N(0.05, 0.02) per asset."""
+    rng = np.random.default_rng(seed)
+    F = rng.normal(0.0, 1.0 / np.sqrt(k), (n_assets, k))
+    cap = 0.05
+    top = int(round(1.0 / cap))
+    risks = []
+    for _ in range(5):
+        mu = rng.normal(0.05, 0.02, n_assets)
+        xg = np.zeros(n_assets)
+        xg[np.argsort(-mu)[:top]] = cap
+        risks.append(np.linalg.norm(F.T @ xg))
+    return {"F": F, "gamma": 0.5 * float(np.mean(risks)), "cap": cap, "seed": seed}
+
+
+def portfolio_mu(family, seed: int):
+    """Expected returns of one instance of the family: N(0.05, 0.02) per asset."""
+    return np.random.default_rng(10_000_019 + seed).normal(0.05, 0.02, family["F"].shape[0])
+
+
+def portfolio_socp(family, mu):
+    """min -mu'x s.t. 1'x = 1, f - F'x = 0 (zero rows), (gamma, f) in SOC(k + 1), 0 <= x <= cap,
+    f free.  Variables (x, f); rows: budget, k exposure rows, then the SOC block whose first
+    row is empty with h = -gamma."""
+    F, gamma, cap = family["F"], family["gamma"], family["cap"]
+    na, k = F.shape
+    nv = na + k
+    rows = [np.zeros(na, dtype=np.int64)]
+    cols = [np.arange(na)]
+    vals = [np.ones(na)]
+    for j in range(k):
+        rows.append(np.full(na + 1, 1 + j))
+        cols.append(np.concatenate([np.arange(na), [na + j]]))
+        vals.append(np.concatenate([-F[:, j], [1.0]]))
+    o = 1 + k
+    rows.append(o + 1 + np.arange(k))
+    cols.append(na + np.arange(k))
+    vals.append(np.ones(k))
+    R = np.concatenate(rows)
+    C = np.concatenate(cols)
+    V = np.concatenate(vals)
+    m = 2 * k + 2
+    M = sp.csr_matrix((V, (R, C)), shape=(m, nv))
+    M.sort_indices()
+    c = np.concatenate([-np.asarray(mu, dtype=float), np.zeros(k)])
+    h = np.zeros(m)
+    h[0] = 1.0
+    h[o] = -gamma
+    lb = np.concatenate([np.zeros(na), np.full(k, -np.inf)])
+    ub = np.concatenate([np.full(na, cap), np.full(k, np.inf)])
+    return {"name": "portfolio_socp", "m": m, "n": nv, "row_ptr": M.indptr.astype(np.int64),
+            "col": M.indices.astype(np.int32), "val": M.data, "c": c, "h": h, "lb": lb, "ub": ub,
+            "cone_types": np.asarray([ZERO, SOC], dtype=np.int32),
+            "cone_dims": np.asarray([1 + k, k + 1], dtype=np.int64)}
+
+
+def portfolio_features(family, mu):
+    """Summary of the returns fed to the warm-start network (k + 7 values): the factor
+    exposures F'mu / n of the returns, and the mean, standard deviation, median, 90 % and
+    99 % quantiles, maximum and top-(1/cap) mean of mu."""
+    F, cap = family["F"], family["cap"]
+    mu = np.asarray(mu, dtype=float)
+    top = np.sort(mu)[::-1][:int(round(1.0 / cap))]
+    q = np.quantile(mu, [0.5, 0.9, 0.99])
+    stats = [mu.mean(), mu.std(), q[0], q[1], q[2], mu.max(), top.mean()]
+    return np.concatenate([F.T @ mu / np.sqrt(F.shape[0]), stats]).astype(np.float32)

@@ -94,6 +94,11 @@ SIGNATURES = {
     "pdcs_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, _i64p]),
     "pdcs_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "pdcs_batch_destroy": (None, [ctypes.c_void_p]),
+    "pdcs_mlp_params": (ctypes.c_int64, [ctypes.c_int32, _i32p]),
+    "pdcs_mlp_forward": (ctypes.c_int, [ctypes.c_int32, _i32p, ctypes.c_int64, _fp, _fp, _fp]),
+    "pdcs_mlp_loss_grad": (ctypes.c_int, [ctypes.c_int32, _i32p, ctypes.c_int64, _fp, _fp, _fp, _fp, _fp]),
+    "pdcs_mlp_train": (ctypes.c_int, [ctypes.c_int32, _i32p, ctypes.c_int64, _fp, _fp, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _fp, _fp]),
 }
 EXP_MLP_IN, EXP_MLP_HIDDEN = 9, 32
 EXP_MLP_PARAMS = EXP_MLP_HIDDEN * EXP_MLP_IN + EXP_MLP_HIDDEN + EXP_MLP_HIDDEN * EXP_MLP_HIDDEN + 2 * EXP_MLP_HIDDEN + 1
@@ -407,3 +412,49 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# warm-start network (fully connected, ReLU hidden layers, linear output, MSE)
+# ---------------------------------------------------------------------------
+def _sizes(sizes):
+    return np.ascontiguousarray(sizes, dtype=np.int32)
+
+
+def mlp_params(sizes):
+    sz = _sizes(sizes)
+    return int(lib().pdcs_mlp_params(sz.size - 1, _ptr(sz, _i32p)))
+
+
+def mlp_init(sizes, seed=0):
+    """He-initialised parameters (per layer W then b), seeded."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for din, dout in zip(sizes[:-1], sizes[1:]):
+        parts += [rng.normal(0.0, np.sqrt(2.0 / din), dout * din), np.zeros(dout)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_forward(sizes, X, W):
+    sz, X, W = _sizes(sizes), _f32(X), _f32(W)
+    Y = np.empty((X.shape[0], sz[-1]), dtype=np.float32)
+    _check(lib().pdcs_mlp_forward(sz.size - 1, _ptr(sz, _i32p), X.shape[0], _ptr(X, _fp), _ptr(W, _fp), _ptr(Y, _fp)))
+    return Y
+
+
+def mlp_loss_grad(sizes, X, T, W):
+    sz, X, T, W = _sizes(sizes), _f32(X), _f32(T), _f32(W)
+    g = np.empty(W.size, dtype=np.float32)
+    loss = np.empty(1, dtype=np.float32)
+    _check(lib().pdcs_mlp_loss_grad(sz.size - 1, _ptr(sz, _i32p), X.shape[0], _ptr(X, _fp), _ptr(T, _fp),
+                                    _ptr(W, _fp), _ptr(g, _fp), _ptr(loss, _fp)))
+    return float(loss[0]), g
+
+
+def mlp_train(sizes, X, T, W, steps=2000, batch=256, lr=1e-3, seed=0):
+    sz, X, T = _sizes(sizes), _f32(X), _f32(T)
+    w = _f32(W).copy()
+    trace = np.empty(max(steps, 1), dtype=np.float32)
+    _check(lib().pdcs_mlp_train(sz.size - 1, _ptr(sz, _i32p), X.shape[0], _ptr(X, _fp), _ptr(T, _fp), int(steps),
+                                int(batch), float(lr), int(seed), _ptr(w, _fp), _ptr(trace, _fp)))
+    return w, trace[:steps]
