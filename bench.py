@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run (profiling runs)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-iterate mode measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-programs measurement")
+    ap.add_argument("--no-proj", action="store_true", help="skip the standalone projection measurements")
     ap.add_argument("--batch-count", type=int, default=256, help="Lasso programs in the batched measurement")
     ap.add_argument("--time-to-tol", default="1e-4,1e-6",
                     help="comma list of tolerances for the time-to-solution runs ('' to skip)")
@@ -367,6 +368,55 @@ def main():
                  "sequential_seconds": t_seq, "sequential_converged": nseq,
                  "sequential_total_evaluations": evals_s, "speedup": t_seq / t_batch if t_batch > 0 else None}
 
+    # standalone cone projections (the projection step on its own): SOC blocks of several
+    # sizes over 2e8 entries and 2e6 exp cones, unscaled (D = I) and with scales
+    # exp(N(0, 0.5^2)); bytes: read v (and d) and write the result once; the time is the
+    # whole call (it uploads the cone list and lays out the blocks)
+    proj = None
+    if not args.no_proj:
+        proj = []
+        g = torch.Generator(device="cuda").manual_seed(3)
+        total = 200_000_000
+        peak = measured_peaks().get("hbm_gbs")
+
+        def timed(fn, reps=5):
+            fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        v = torch.randn(total, device="cuda", dtype=torch.float64, generator=g)
+        dsc = torch.exp(0.5 * torch.randn(total, device="cuda", dtype=torch.float64, generator=g))
+        out = torch.empty_like(v)
+        for nblk in [1_000, 100_000, 1_000_000]:
+            dim = total // nblk
+            types = np.full(nblk, P.CONE_SOC, np.int32)
+            dims = np.full(nblk, dim, np.int64)
+            for scaled in (False, True):
+                dp = dsc.data_ptr() if scaled else 0
+                ms = timed(lambda: P.pdcs_proj_cones_device(v.data_ptr(), dp, nblk * dim, types, dims, 0,
+                                                              out.data_ptr(), stream.cuda_stream))
+                byt = nblk * dim * (24 if scaled else 16)
+                proj.append({"cones": "SOC", "count": nblk, "dim": dim, "scaled": scaled, "ms": ms,
+                             "GBps": byt / (ms * 1e-3) / 1e9, "frac_of_hbm": byt / (ms * 1e-3) / 1e9 / peak
+                             if peak else None})
+        ne = 2_000_000
+        types = np.full(ne, P.CONE_EXP, np.int32)
+        dims = np.full(ne, 3, np.int64)
+        for scaled in (False, True):
+            dp = dsc.data_ptr() if scaled else 0
+            ms = timed(lambda: P.pdcs_proj_cones_device(v.data_ptr(), dp, 3 * ne, types, dims, 0, out.data_ptr(),
+                                                          stream.cuda_stream))
+            byt = 3 * ne * (24 if scaled else 16)
+            proj.append({"cones": "EXP", "count": ne, "dim": 3, "scaled": scaled, "ms": ms,
+                         "cones_per_s": ne / (ms * 1e-3), "GBps": byt / (ms * 1e-3) / 1e9})
+        del v, dsc, out
+
     if rank != 0:
         return
     # roofline of the dominant kernel
@@ -393,7 +443,7 @@ def main():
                        "precision": "fp64", "l2": "working set > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clk, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-            "time_to_tol": ttt, "fp32_iterates": fp32, "batched_programs": batch}
+            "time_to_tol": ttt, "fp32_iterates": fp32, "batched_programs": batch, "projections": proj}
     print(json.dumps(line))
 
 

@@ -269,10 +269,23 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
+// Weights of the SOC entries for the mixed-precision path: precomputed (w[i], or all ones
+// when w is null), or formed from the block's scales d as soc_weight<kInv> does.
+struct SocWeightsArray {
+    const double* w;
+    __device__ __forceinline__ double operator()(int i) const { return w ? w[i] : 1.0; }
+};
+template <bool kInv>
+struct SocWeightsScales {
+    const double* d;
+    double d0;
+    __device__ __forceinline__ double operator()(int i) const { return soc_weight<kInv>(d, d0, i); }
+};
+
 // buf[0..dim): the block, projected in place onto E K_soc where the weight of x entry
-// i is w[i] = dhat_i^{-2} (w may be null: all ones).  cache may be null.
-template <int R>
-__device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w, int dim, float* cache) {
+// i is wf(i) = dhat_i^{-2}.  cache may be null.
+template <int R, typename WF>
+__device__ void soc_project_warp_fast(double* buf, WF wf, int dim, float* cache) {
     const int lane = threadIdx.x & 31;
     const int nx = dim - 1;
     const double t = buf[0];
@@ -282,7 +295,7 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
         const int i = lane + 32 * k;
         const bool in = i < nx;
         xr[k] = in ? buf[1 + i] : 0.0;
-        wr[k] = in ? (w ? w[i] : 1.0) : 1.0;
+        wr[k] = in ? wf(i) : 1.0;
     }
     double a = 0.0, b = 0.0;  // ||Dhat x||^2, ||Dhat^{-1} x||^2
 #pragma unroll
@@ -430,8 +443,8 @@ __device__ void soc_project_warp_fast(double* buf, const double* __restrict__ w,
 }
 
 // Rotated SOC through Q (see rsoc_project_warp) on the mixed-precision SOC path.
-template <int R>
-__device__ void rsoc_project_warp_fast(double* buf, const double* __restrict__ w, int dim, float* cache) {
+template <int R, typename WF>
+__device__ void rsoc_project_warp_fast(double* buf, WF wf, int dim, float* cache) {
     const int lane = threadIdx.x & 31;
     const double r2 = 0.70710678118654752440;
     __syncwarp();
@@ -441,7 +454,7 @@ __device__ void rsoc_project_warp_fast(double* buf, const double* __restrict__ w
         buf[1] = (p - q) * r2;
     }
     __syncwarp();
-    soc_project_warp_fast<R>(buf, w, dim, cache);
+    soc_project_warp_fast<R>(buf, wf, dim, cache);
     if (lane == 0) {
         const double p = buf[0], q = buf[1];
         buf[0] = (p + q) * r2;
@@ -450,11 +463,11 @@ __device__ void rsoc_project_warp_fast(double* buf, const double* __restrict__ w
     __syncwarp();
 }
 
-// Picks the register count for the block (dim - 1 <= 128); larger blocks use the
-// FP64 memory-loop projection with weights formed from the scales d (kInv as there).
-template <bool kInv>
-__device__ __forceinline__ void soc_project_any(double* buf, const double* __restrict__ w,
-                                                const double* __restrict__ d, int dim, bool rot, float* cache) {
+// Picks the register count for the block (dim - 1 <= 128, weights from wf); larger blocks
+// use the FP64 memory-loop projection with weights formed from the scales d (kInv as there).
+template <bool kInv, typename WF>
+__device__ __forceinline__ void soc_project_wf(double* buf, WF wf, const double* __restrict__ d, int dim, bool rot,
+                                               float* cache) {
     const int nx = dim - 1;
     if (nx > 128) {
         if (rot) rsoc_project_warp<kInv>(buf, d, dim, cache);
@@ -463,16 +476,29 @@ __device__ __forceinline__ void soc_project_any(double* buf, const double* __res
     }
     const int R = (nx + 31) / 32;
     if (rot) {
-        if (R <= 1) rsoc_project_warp_fast<1>(buf, w, dim, cache);
-        else if (R == 2) rsoc_project_warp_fast<2>(buf, w, dim, cache);
-        else if (R == 3) rsoc_project_warp_fast<3>(buf, w, dim, cache);
-        else rsoc_project_warp_fast<4>(buf, w, dim, cache);
+        if (R <= 1) rsoc_project_warp_fast<1>(buf, wf, dim, cache);
+        else if (R == 2) rsoc_project_warp_fast<2>(buf, wf, dim, cache);
+        else if (R == 3) rsoc_project_warp_fast<3>(buf, wf, dim, cache);
+        else rsoc_project_warp_fast<4>(buf, wf, dim, cache);
     } else {
-        if (R <= 1) soc_project_warp_fast<1>(buf, w, dim, cache);
-        else if (R == 2) soc_project_warp_fast<2>(buf, w, dim, cache);
-        else if (R == 3) soc_project_warp_fast<3>(buf, w, dim, cache);
-        else soc_project_warp_fast<4>(buf, w, dim, cache);
+        if (R <= 1) soc_project_warp_fast<1>(buf, wf, dim, cache);
+        else if (R == 2) soc_project_warp_fast<2>(buf, wf, dim, cache);
+        else if (R == 3) soc_project_warp_fast<3>(buf, wf, dim, cache);
+        else soc_project_warp_fast<4>(buf, wf, dim, cache);
     }
+}
+
+// Precomputed weights w (w[i] for x entry i, or all ones when null).
+template <bool kInv>
+__device__ __forceinline__ void soc_project_any(double* buf, const double* __restrict__ w,
+                                                const double* __restrict__ d, int dim, bool rot, float* cache) {
+    soc_project_wf<kInv>(buf, SocWeightsArray{w}, d, dim, rot, cache);
+}
+
+// Weights formed from the block's scales d (may be null: D = I) on the fly.
+template <bool kInv>
+__device__ __forceinline__ void soc_project_scaled(double* buf, const double* __restrict__ d, int dim, bool rot) {
+    soc_project_wf<kInv>(buf, SocWeightsScales<kInv>{d, d ? d[0] : 1.0}, d, dim, rot, nullptr);
 }
 
 // ---------------------------------------------------------------------------

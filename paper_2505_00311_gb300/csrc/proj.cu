@@ -42,13 +42,9 @@ __global__ void proj_soc(int nc, const int* __restrict__ off, const int* __restr
             for (int i = lane; i < dm; i += 32) out[o + i] = v[o + i];
         __syncwarp();
         const double* dd = d ? d + o : nullptr;
-        if (rot[k]) {
-            if (dual) rsoc_project_warp<true>(out + o, dd, dm, nullptr);
-            else rsoc_project_warp<false>(out + o, dd, dm, nullptr);
-        } else {
-            if (dual) soc_project_warp<true>(out + o, dd, dm, nullptr);
-            else soc_project_warp<false>(out + o, dd, dm, nullptr);
-        }
+        // the solver's mixed-precision search (FP32 root, FP64 polish), weights from the scales
+        if (dual) soc_project_scaled<true>(out + o, dd, dm, rot[k] != 0);
+        else soc_project_scaled<false>(out + o, dd, dm, rot[k] != 0);
     }
 }
 
@@ -58,9 +54,11 @@ __global__ void proj_exp(int ne, const int* __restrict__ off, const double* v, c
         const int o = off[k];
         const double r = v[o], s = v[o + 1], t = v[o + 2];
         const double dr = d ? d[o] : 1.0, ds = d ? d[o + 1] : 1.0, dt = d ? d[o + 2] : 1.0;
+        const double lg[3] = {d ? log(dr) : 0.0, d ? log(ds) : 0.0, d ? log(dt) : 0.0};
         double p[3];
-        if (dual) exp_dual_project(r, s, t, dr, ds, dt, p, nullptr, nullptr);
-        else exp_project(r, s, t, dr, ds, dt, p, nullptr, nullptr);
+        // the solver's mixed-precision search (FP32 screening and root, FP64 result)
+        if (dual) exp_dual_project_fast(r, s, t, dr, ds, dt, lg, p, nullptr);
+        else exp_project_fast(r, s, t, dr, ds, dt, lg, p, nullptr);
         out[o] = p[0];
         out[o + 1] = p[1];
         out[o + 2] = p[2];

@@ -146,12 +146,14 @@ def pdcs_default_options(**kw):
 
 
 def _cones(types, dims):
+    """The cone list as a pdcs_cone array (built in one numpy pass)."""
     types = np.asarray(types)
     dims = np.asarray(dims)
-    arr = (pdcs_cone * len(types))()
-    for i, (t, d) in enumerate(zip(types.tolist(), dims.tolist())):
-        arr[i].type = int(t)
-        arr[i].dim = int(d)
+    rec = np.zeros(len(types), dtype=[("type", "<i4"), ("pad", "<i4"), ("dim", "<i8")])
+    assert rec.itemsize == ctypes.sizeof(pdcs_cone)
+    rec["type"] = types
+    rec["dim"] = dims
+    arr = (pdcs_cone * len(types)).from_buffer_copy(rec.tobytes())
     return arr
 
 
