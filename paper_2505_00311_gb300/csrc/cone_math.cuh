@@ -463,15 +463,160 @@ __device__ void rsoc_project_warp_fast(double* buf, WF wf, int dim, float* cache
     __syncwarp();
 }
 
+// Large blocks (memory loop), mixed precision: one FP64 pass forms the norms of the
+// case tests and an FP32 copy of x and of the weights in scr (2 (dim - 1) floats); the
+// root of psi is searched in FP32 over that copy, polished by at most three FP64 Newton
+// steps over the block (the first accepted below 1e-7 relative, as in registers), and
+// the projection is formed in FP64.  Anything the FP32 pass cannot settle falls back to
+// the FP64 search (soc_project_warp).  wf(i): weight of x entry i.
+template <bool kInv, typename WF>
+__device__ void soc_project_warp_mp(double* buf, WF wf, const double* __restrict__ d, int dim, float* cache,
+                                    float* __restrict__ scr) {
+    const int lane = threadIdx.x & 31;
+    const int nx = dim - 1;
+    float* x32 = scr;
+    float* w32 = scr + nx;
+    const double t = buf[0];
+    double a = 0.0, b = 0.0;
+    bool rng = fabs(t) < 1e30 && fabs(t) > 1e-30;
+    for (int i = lane; i < nx; i += 32) {
+        const double x = buf[1 + i], w = wf(i);
+        const double x2 = x * x;
+        a += x2 / w;
+        b += w * x2;
+        x32[i] = (float)x;
+        w32[i] = (float)w;
+        rng = rng && w < 1e30 && w > 1e-30 && fabs(x) < 1e30;
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    rng = __all_sync(0xffffffffu, rng) && sqrt(b) < 1e30;
+    const double nDx = sqrt(a), nDinvx = sqrt(b);
+    __syncwarp();
+    if (t <= 0.0 && nDx <= -t) {  // case 1
+        for (int i = lane; i < dim; i += 32) buf[i] = 0.0;
+        __syncwarp();
+        return;
+    }
+    if (nDinvx <= t) return;  // case 2
+    double mu = 1.0;          // case 3 (t == 0)
+    if (t != 0.0) {           // case 4
+        bool known, near = t > 0.0 && soc_cached_near(cache, known);
+        if (t > 0.0 && !known) {  // sign of psi at mu = 1/2 (in FP32 when in range)
+            float S = 0.0f;
+            for (int i = lane; i < nx; i += 32) {
+                const float r = __frcp_rn(1.0f + 0.5f * w32[i]);
+                S += w32[i] * x32[i] * x32[i] * r * r;
+            }
+            near = 0.5f * sqrtf(warp_sum_f(S)) < (float)t;
+        }
+        const SocVar<double> V(t, near);
+        const SocVar<float> Vf(V);
+        bool conv = false;
+        double u = 0.0;
+        if (rng) {
+            auto ev32 = [&](float uu, float& ph, float& dph, float& sc) {
+                float S = 0.0f, S2 = 0.0f;
+                const float m = Vf.mu(uu);
+                for (int i = lane; i < nx; i += 32) {
+                    const float w = w32[i], x = x32[i];
+                    const float r = __frcp_rn(1.0f + m * w);
+                    const float term = w * x * x * r * r;
+                    S += term;
+                    S2 += w * term * r;
+                }
+                S = warp_sum_f(S);
+                S2 = warp_sum_f(S2);
+                Vf.psi(uu, sqrtf(S), S2, ph, dph, sc);
+            };
+            const float uf = soc_root<float>(ev32, V.tpos, (float)V.guess(t, nDinvx, cache), 2e-6f, 2e-7f, 100);
+            u = (double)uf;
+            if (uf > 0.0f && isfinite(uf)) {
+                for (int it = 0; it < 3; ++it) {
+                    double S = 0.0, S2 = 0.0;
+                    const double m = V.mu(u);
+                    for (int i = lane; i < nx; i += 32) {
+                        const double x = buf[1 + i], w = wf(i);
+                        const double r = rcp_refined(1.0 + m * w);
+                        const double term = w * x * x * r * r;
+                        S += term;
+                        S2 += w * term * r;
+                    }
+                    S = warp_sum(S);
+                    S2 = warp_sum(S2);
+                    double ph, dph, sc;
+                    V.psi(u, sqrt(S), S2, ph, dph, sc);
+                    if (fabs(ph) <= 1.6e-15 * sc) {
+                        u = fmax(u, 0.0);
+                        conv = true;
+                        break;
+                    }
+                    const double step = ph / dph;
+                    if (!isfinite(step)) break;
+                    u -= step;
+                    if (fabs(step) <= (it == 0 ? 1e-7 : RootTolSoc) * (V.tpos ? fmin(u, 1.0 - u) : u)) {
+                        conv = true;
+                        break;
+                    }
+                }
+                conv = conv && u >= 0.0 && (!V.tpos || u < 1.0);
+            }
+        }
+        if (!conv) {
+            soc_project_warp<kInv>(buf, d, dim, cache);
+            return;
+        }
+        if (cache && lane == 0) *cache = V.store(u);
+        mu = V.mu(u);
+    }
+    double s = 0.0;
+    for (int i = lane; i < nx; i += 32) {
+        const double w = wf(i);
+        const double y = buf[1 + i] * rcp_refined(1.0 + mu * w);
+        s += w * y * y;
+        buf[1 + i] = y;
+    }
+    s = warp_sum(s);
+    __syncwarp();
+    if (lane == 0) buf[0] = sqrt(s);
+    __syncwarp();
+}
+
+template <bool kInv, typename WF>
+__device__ void rsoc_project_warp_mp(double* buf, WF wf, const double* __restrict__ d, int dim, float* cache,
+                                     float* __restrict__ scr) {
+    const int lane = threadIdx.x & 31;
+    const double r2 = 0.70710678118654752440;
+    __syncwarp();
+    if (lane == 0) {
+        const double p = buf[0], q = buf[1];
+        buf[0] = (p + q) * r2;
+        buf[1] = (p - q) * r2;
+    }
+    __syncwarp();
+    soc_project_warp_mp<kInv>(buf, wf, d, dim, cache, scr);
+    if (lane == 0) {
+        const double p = buf[0], q = buf[1];
+        buf[0] = (p + q) * r2;
+        buf[1] = (p - q) * r2;
+    }
+    __syncwarp();
+}
+
 // Picks the register count for the block (dim - 1 <= 128, weights from wf); larger blocks
 // use the FP64 memory-loop projection with weights formed from the scales d (kInv as there).
 template <bool kInv, typename WF>
 __device__ __forceinline__ void soc_project_wf(double* buf, WF wf, const double* __restrict__ d, int dim, bool rot,
-                                               float* cache) {
+                                               float* cache, float* scr) {
     const int nx = dim - 1;
     if (nx > 128) {
-        if (rot) rsoc_project_warp<kInv>(buf, d, dim, cache);
-        else soc_project_warp<kInv>(buf, d, dim, cache);
+        if (scr) {
+            if (rot) rsoc_project_warp_mp<kInv>(buf, wf, d, dim, cache, scr);
+            else soc_project_warp_mp<kInv>(buf, wf, d, dim, cache, scr);
+        } else {
+            if (rot) rsoc_project_warp<kInv>(buf, d, dim, cache);
+            else soc_project_warp<kInv>(buf, d, dim, cache);
+        }
         return;
     }
     const int R = (nx + 31) / 32;
@@ -488,17 +633,20 @@ __device__ __forceinline__ void soc_project_wf(double* buf, WF wf, const double*
     }
 }
 
-// Precomputed weights w (w[i] for x entry i, or all ones when null).
+// Precomputed weights w (w[i] for x entry i, or all ones when null).  scr (may be null):
+// 2 (dim - 1) floats of scratch for blocks beyond the registers (mixed precision there).
 template <bool kInv>
 __device__ __forceinline__ void soc_project_any(double* buf, const double* __restrict__ w,
-                                                const double* __restrict__ d, int dim, bool rot, float* cache) {
-    soc_project_wf<kInv>(buf, SocWeightsArray{w}, d, dim, rot, cache);
+                                                const double* __restrict__ d, int dim, bool rot, float* cache,
+                                                float* scr = nullptr) {
+    soc_project_wf<kInv>(buf, SocWeightsArray{w}, d, dim, rot, cache, scr);
 }
 
 // Weights formed from the block's scales d (may be null: D = I) on the fly.
 template <bool kInv>
-__device__ __forceinline__ void soc_project_scaled(double* buf, const double* __restrict__ d, int dim, bool rot) {
-    soc_project_wf<kInv>(buf, SocWeightsScales<kInv>{d, d ? d[0] : 1.0}, d, dim, rot, nullptr);
+__device__ __forceinline__ void soc_project_scaled(double* buf, const double* __restrict__ d, int dim, bool rot,
+                                                   float* scr = nullptr) {
+    soc_project_wf<kInv>(buf, SocWeightsScales<kInv>{d, d ? d[0] : 1.0}, d, dim, rot, nullptr, scr);
 }
 
 // ---------------------------------------------------------------------------

@@ -339,7 +339,8 @@ __device__ __forceinline__ void dual_update_body(const Dev<T>& D, int qidx) {
             }
             __syncwarp();
             if constexpr (sizeof(T) == 8)
-                soc_project_any<true>(D.yh + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, D.soc_lam + cidx);
+                soc_project_any<true>(D.yh + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, D.soc_lam + cidx,
+                                      reinterpret_cast<float*>(D.scr + o));  // scratch unused during the update
             else
                 soc_project_any_f32(D.yh + o, D.soc_w32 + o + 1, D.scr + o, D.dr + o, dim, D.soc_rot[cidx] != 0,
                                     D.soc_lam + cidx);
@@ -467,7 +468,8 @@ __device__ __forceinline__ void cand_dual_body(const Dev<T>& D, int qidx) {
             const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
             for (int i = lane; i < dim; i += 32) out[o + i] = val(o + i);
             __syncwarp();
-            soc_project_any<true>(out + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, nullptr);
+            soc_project_any<true>(out + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, nullptr,
+                                  reinterpret_cast<float*>(D.scr + (size_t)q * D.m + o));
         }
     } else {
         const int stride = D.nb_exp * D.exp_pb;

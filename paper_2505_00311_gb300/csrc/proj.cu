@@ -32,7 +32,7 @@ __global__ void proj_scalar(int nb, const int* __restrict__ off, const int* __re
 
 __global__ void proj_soc(int nc, const int* __restrict__ off, const int* __restrict__ dim,
                          const unsigned char* __restrict__ rot, const double* v, const double* d, int dual,
-                         double* out) {
+                         double* out, float* scr) {
     const int lane = threadIdx.x & 31;
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -42,9 +42,11 @@ __global__ void proj_soc(int nc, const int* __restrict__ off, const int* __restr
             for (int i = lane; i < dm; i += 32) out[o + i] = v[o + i];
         __syncwarp();
         const double* dd = d ? d + o : nullptr;
-        // the solver's mixed-precision search (FP32 root, FP64 polish), weights from the scales
-        if (dual) soc_project_scaled<true>(out + o, dd, dm, rot[k] != 0);
-        else soc_project_scaled<false>(out + o, dd, dm, rot[k] != 0);
+        // the solver's mixed-precision search (FP32 root, FP64 polish), weights from the
+        // scales; blocks beyond the registers keep an FP32 copy in scr (2 floats per row)
+        float* sc = scr ? scr + 2LL * o : nullptr;
+        if (dual) soc_project_scaled<true>(out + o, dd, dm, rot[k] != 0, sc);
+        else soc_project_scaled<false>(out + o, dd, dm, rot[k] != 0, sc);
     }
 }
 
@@ -111,11 +113,16 @@ extern "C" pdcs_status pdcs_proj_cones_device(const double* v, const double* d, 
         proj_scalar<<<g, kBlock, 0, s>>>((int)ns, (int*)(buf + o_soff), (int*)(buf + o_sdim),
                                          (unsigned char*)(buf + o_styp), v, dual, out);
     }
+    float* scr = nullptr;  // FP32 copies of the blocks beyond the registers
+    bool big = false;
+    for (int dm : soc_dim) big = big || dm - 1 > 128;
+    if (e == cudaSuccess && big && cudaMallocAsync(&scr, sizeof(float) * 2 * (size_t)m, s) != cudaSuccess) scr = nullptr;
     if (e == cudaSuccess && nc) {
         const int g = (int)std::min<long long>((nc + 7) / 8, (long long)sms * 16);
         proj_soc<<<g, kBlock, 0, s>>>((int)nc, (int*)(buf + o_coff), (int*)(buf + o_cdim),
-                                      (unsigned char*)(buf + o_crot), v, d, dual, out);
+                                      (unsigned char*)(buf + o_crot), v, d, dual, out, scr);
     }
+    if (scr) cudaFreeAsync(scr, s);
     if (e == cudaSuccess && ne) {
         const int g = (int)std::min<long long>((ne + kBlock - 1) / kBlock, (long long)sms * 16);
         proj_exp<<<g, kBlock, 0, s>>>((int)ne, (int*)(buf + o_eoff), v, d, dual, out);
