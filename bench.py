@@ -399,22 +399,22 @@ def main():
             dims = np.full(nblk, dim, np.int64)
             for scaled in (False, True):
                 dp = dsc.data_ptr() if scaled else 0
-                ms = timed(lambda: P.pdcs_proj_cones_device(v.data_ptr(), dp, nblk * dim, types, dims, 0,
+                pms = timed(lambda: P.pdcs_proj_cones_device(v.data_ptr(), dp, nblk * dim, types, dims, 0,
                                                               out.data_ptr(), stream.cuda_stream))
                 byt = nblk * dim * (24 if scaled else 16)
-                proj.append({"cones": "SOC", "count": nblk, "dim": dim, "scaled": scaled, "ms": ms,
-                             "GBps": byt / (ms * 1e-3) / 1e9, "frac_of_hbm": byt / (ms * 1e-3) / 1e9 / peak
+                proj.append({"cones": "SOC", "count": nblk, "dim": dim, "scaled": scaled, "ms": pms,
+                             "GBps": byt / (pms * 1e-3) / 1e9, "frac_of_hbm": byt / (pms * 1e-3) / 1e9 / peak
                              if peak else None})
         ne = 2_000_000
         types = np.full(ne, P.CONE_EXP, np.int32)
         dims = np.full(ne, 3, np.int64)
         for scaled in (False, True):
             dp = dsc.data_ptr() if scaled else 0
-            ms = timed(lambda: P.pdcs_proj_cones_device(v.data_ptr(), dp, 3 * ne, types, dims, 0, out.data_ptr(),
+            pms = timed(lambda: P.pdcs_proj_cones_device(v.data_ptr(), dp, 3 * ne, types, dims, 0, out.data_ptr(),
                                                           stream.cuda_stream))
             byt = 3 * ne * (24 if scaled else 16)
-            proj.append({"cones": "EXP", "count": ne, "dim": 3, "scaled": scaled, "ms": ms,
-                         "cones_per_s": ne / (ms * 1e-3), "GBps": byt / (ms * 1e-3) / 1e9})
+            proj.append({"cones": "EXP", "count": ne, "dim": 3, "scaled": scaled, "ms": pms,
+                         "cones_per_s": ne / (pms * 1e-3), "GBps": byt / (pms * 1e-3) / 1e9})
         del v, dsc, out
 
     if rank != 0:
