@@ -36,7 +36,8 @@ struct SpmvBins {
 template <typename T>
 struct Dev {
     int m, n;
-    // scaled matrix K~ (rows in internal order) and its transpose
+    // scaled matrix K~ and its transpose, each stored bin by bin for the SpMV (row
+    // pointer over the binned rows; binned row i is row listK[i] / listKT[i])
     const int* rp;
     const int* ci;
     const T* val;
@@ -94,24 +95,27 @@ struct Dev {
     const float* exp_lg32;
     // learned starting point of the exp root search (kExpMlpParams floats), or null
     const float* exp_mlp;
-    // SpMV plans of K and K' (used by the batched launches)
+    // SpMV plans of K and K': bins and the row each binned row stands for
     SpmvBins binsK, binsKT;
     const int* listK;
     const int* listKT;
 };
 
 // ---------------------------------------------------------------------------
-// SpMV: y = A x, CSR.  The rows are grouped in bins by length (host side, once per
+// SpMV: y = A x.  The rows are grouped in bins by length (host side, once per
 // matrix); bin k runs lanes[k] lanes per row (a power of two, so that each lane
 // takes a few entries), a warp covering 32 / lanes rows at a time, and the bins of
-// the longest rows come first in the grid.  Each lane issues U independent
-// (column, value) loads before the gathers of x, for memory-level parallelism; its
-// entries are summed in order, then the row's lanes by a shuffle tree, so a row's
-// result depends only on its lane count.
+// the longest rows come first in the grid.  The matrix is stored bin by bin: binned
+// row i has its entries at rp[i] .. rp[i+1] and is row list[i] of A, so the row
+// bounds come from one contiguous array and the list only names the output.  Each
+// lane issues U independent (column, value) loads before the gathers of x, for
+// memory-level parallelism; its entries are summed in order, then the row's lanes by
+// a shuffle tree, so a row's result depends only on its lane count.
 // sel: 0 -> write y0;  1 -> write y0 / y1 by the parity of ctrl->attempts.
 // skip: 0 never; 1 when not running; 2 when not running or the step was rejected.
 // ---------------------------------------------------------------------------
 
+// rows [0, count) of one bin: list, rp offset to the bin's first row
 template <typename T, typename TO, int G, int U>
 __device__ __forceinline__ void spmv_bin_rows(const int* __restrict__ list, int count, int wb, int nwb,
                                               const int* __restrict__ rp, const int* __restrict__ ci,
@@ -124,8 +128,8 @@ __device__ __forceinline__ void spmv_bin_rows(const int* __restrict__ list, int 
         int r = -1;
         if (i < count) {
             r = __ldg(list + i);
-            const int e = __ldg(rp + r + 1);
-            for (int p = __ldg(rp + r) + gl; p < e; p += G * U) {
+            const int e = __ldg(rp + i + 1);
+            for (int p = __ldg(rp + i) + gl; p < e; p += G * U) {
                 int c[U];
                 T v[U], xv[U];
 #pragma unroll
@@ -161,14 +165,35 @@ __global__ void __launch_bounds__(kBlock) spmv_binned(SpmvBins B, const int* __r
     const int wb = ((int)blockIdx.x - B.blk[k]) * kWarpsPerBlock + (threadIdx.x >> 5);
     const int nwb = (B.blk[k + 1] - B.blk[k]) * kWarpsPerBlock;
     const int* l = list + B.row[k];
+    const int* rb = rp + B.row[k];
     const int cnt = B.row[k + 1] - B.row[k];
     switch (B.lanes[k]) {
-        case 1: spmv_bin_rows<T, TO, 1, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
-        case 2: spmv_bin_rows<T, TO, 2, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
-        case 4: spmv_bin_rows<T, TO, 4, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
-        case 8: spmv_bin_rows<T, TO, 8, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
-        case 16: spmv_bin_rows<T, TO, 16, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
-        default: spmv_bin_rows<T, TO, 32, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+        case 1: spmv_bin_rows<T, TO, 1, U>(l, cnt, wb, nwb, rb, ci, val, x, y); break;
+        case 2: spmv_bin_rows<T, TO, 2, U>(l, cnt, wb, nwb, rb, ci, val, x, y); break;
+        case 4: spmv_bin_rows<T, TO, 4, U>(l, cnt, wb, nwb, rb, ci, val, x, y); break;
+        case 8: spmv_bin_rows<T, TO, 8, U>(l, cnt, wb, nwb, rb, ci, val, x, y); break;
+        case 16: spmv_bin_rows<T, TO, 16, U>(l, cnt, wb, nwb, rb, ci, val, x, y); break;
+        default: spmv_bin_rows<T, TO, 32, U>(l, cnt, wb, nwb, rb, ci, val, x, y); break;
+    }
+}
+
+// Stores a CSR matrix (rows in order, row pointer rp) bin by bin: binned row i is row
+// list[i]; rpb (the binned row pointer) is given.  One warp per binned row; the
+// entries keep their order within the row.  Values are converted to TD.
+template <typename TS, typename TD>
+__global__ void __launch_bounds__(kBlock) bin_rows_copy(int rows, const int* __restrict__ list,
+                                                        const int* __restrict__ rp, const int* __restrict__ ci,
+                                                        const TS* __restrict__ val, const int* __restrict__ rpb,
+                                                        int* __restrict__ cib, TD* __restrict__ valb) {
+    const int lane = threadIdx.x & 31;
+    for (long long i = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); i < rows;
+         i += (long long)gridDim.x * kWarpsPerBlock) {
+        const int r = list[i];
+        const int src = rp[r], len = rp[r + 1] - src, dst = rpb[i];
+        for (int p = lane; p < len; p += 32) {
+            if (cib) cib[dst + p] = ci[src + p];
+            valb[dst + p] = (TD)val[src + p];
+        }
     }
 }
 
@@ -796,6 +821,7 @@ __global__ void __launch_bounds__(kBlock) spmv_batch(const Dev<double>* __restri
     const int nwb = (B.blk[k + 1] - B.blk[k]) * kWarpsPerBlock;
     const int* l = (kt ? D.listKT : D.listK) + B.row[k];
     const int cnt = B.row[k + 1] - B.row[k];
+    const int* rp = (kt ? D.rpT : D.rp) + B.row[k];
     const int q = blockIdx.y;
     const double* x;
     double* y;
@@ -803,7 +829,6 @@ __global__ void __launch_bounds__(kBlock) spmv_batch(const Dev<double>* __restri
     else if (mode == 1) { x = D.yh; y = D.ktyh; }
     else if (mode == 2) { x = D.xc + (size_t)q * D.n; y = D.kxc + (size_t)q * D.m; }
     else { x = D.yc + (size_t)q * D.m; y = D.ktyc + (size_t)q * D.n; }
-    const int* rp = kt ? D.rpT : D.rp;
     const int* ci = kt ? D.ciT : D.ci;
     const double* val = kt ? D.valT : D.val;
     switch (B.lanes[k]) {

@@ -53,10 +53,13 @@ struct Arena {
     }
 };
 
-// SpMV plan of one matrix: rows binned by length (see spmv_binned) and the unroll.
+// SpMV plan of one matrix: rows binned by length (see spmv_binned), the matrix
+// stored bin by bin, and the unroll.
 struct SpmvPlan {
     SpmvBins B{};
-    int* list = nullptr;  // device row list, bin by bin
+    int* list = nullptr;  // device row list, bin by bin: binned row i is row list[i]
+    int* rp = nullptr;    // device row pointer over the binned rows
+    int* ci = nullptr;    // device columns, bin by bin
     int shift = 3;        // lanes = 2^(ceil(log2(length)) - shift), clamped to 1..32
     int unroll = 4;
 };
@@ -80,6 +83,7 @@ struct pdcs_ctx {
     // device buffers (FP64 path)
     int *rp = nullptr, *ci = nullptr, *rpT = nullptr, *ciT = nullptr;
     double *val0 = nullptr, *val0T = nullptr, *val = nullptr, *valT = nullptr;
+    double *valb = nullptr, *valbT = nullptr;  // K~, K~' bin by bin (in the memory of val0, val0T)
     double *c0 = nullptr, *h0 = nullptr, *l0 = nullptr, *u0 = nullptr;
     double *cs = nullptr, *hs = nullptr, *ls = nullptr, *us = nullptr;
     double *dr = nullptr, *dc = nullptr, *rn = nullptr, *cn = nullptr;
@@ -99,7 +103,7 @@ struct pdcs_ctx {
     // FP32-iterate mode: FP32 copies of K~, K~', c~, h~, l~, u~ and the iterate state;
     // checks, restarts and the final phase stay FP64 (D)
     Dev<float> DF;
-    float *val_f = nullptr, *valT_f = nullptr;
+    float *val_f = nullptr, *valT_f = nullptr;  // bin by bin
     bool fp32_active = false;          // the FP32 phase is running
     double fp32_best = INFINITY;       // best relative KKT error seen in the FP32 phase
     int fp32_stall = 0;                // checks since it last improved by 10 %
@@ -231,13 +235,44 @@ struct Prof {
     }
 };
 
+// Binned row pointer of a row list (host).
+void binned_rowptr(const std::vector<int>& rp, const std::vector<int>& list, std::vector<int>& rpb) {
+    rpb.resize(list.size() + 1);
+    rpb[0] = 0;
+    for (size_t i = 0; i < list.size(); ++i) rpb[i + 1] = rpb[i] + (rp[list[i] + 1] - rp[list[i]]);
+}
+
+// Stores a matrix (rows in order: host rp, device drp, dci, dval) bin by bin for the
+// row list `list` of plan P: uploads the list and the binned row pointer into P.list,
+// P.rp and gathers the values (as TD) into valb and, when cols, the columns into P.ci.
+template <typename TD>
+cudaError_t store_binned(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, const std::vector<int>& list,
+                         const int* drp, const int* dci, const double* dval, TD* valb, bool cols) {
+    const int rows = (int)list.size();
+    if (rows <= 0) return cudaSuccess;
+    std::vector<int> rpb;
+    binned_rowptr(rp, list, rpb);
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync(P.list, list.data(), sizeof(int) * rows, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.rp, rpb.data(), sizeof(int) * (rows + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const long long g = std::min(((long long)rows + kWarpsPerBlock - 1) / kWarpsPerBlock, (long long)ctx->sms * 32);
+        bin_rows_copy<double, TD><<<(int)g, kBlock, 0, s>>>(rows, P.list, drp, dci, dval, P.rp, cols ? P.ci : nullptr,
+                                                             valb);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors are pageable
+    return e;
+}
+
 // Times the candidate plans of one matrix (bin shift 1..4, unroll 1, 2, 4; 3 warm-up and
-// 20 timed launches each on the given vectors, in the value type T the iterations use)
-// and keeps the fastest in P, with its row list uploaded.  The choice is cached per
-// process by the matrix signature and T.
+// 20 timed launches each on the given vectors, in the value type T the iterations use,
+// each on the matrix stored for its bins) and keeps the fastest in P, with the matrix
+// stored bin by bin for it (columns in P.ci, values as T in valb).  The choice is cached
+// per process by the matrix signature and T.
 template <typename T>
 cudaError_t tune_spmv(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, int rows, const int* drp,
-                      const int* dci, const T* dval, const T* x, T* y) {
+                      const int* dci, const double* dval, T* valb, const T* x, T* y) {
     cudaStream_t s = ctx->stream;
     if (rows <= 0) return cudaSuccess;
     const std::string sig = spmv_signature(rp, rows) + (sizeof(T) == 4 ? ":f32" : ":f64");
@@ -258,14 +293,13 @@ cudaError_t tune_spmv(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, in
         for (int sh = 1; sh <= 4 && e == cudaSuccess; ++sh) {
             SpmvPlan c = P;
             plan_bins(rp, rows, sh, 0, ctx->sms, list, c.B);
-            e = cudaMemcpyAsync(P.list, list.data(), sizeof(int) * rows, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            e = store_binned<T>(ctx, P, rp, list, drp, dci, dval, valb, true);
             for (int un = 1; un <= 4 && e == cudaSuccess; un *= 2) {
                 c.shift = sh;
                 c.unroll = un;
-                for (int r = 0; r < 3; ++r) launch_spmv<T, T>(c, s, drp, dci, dval, x, y, nullptr, nullptr, 0, 0);
+                for (int r = 0; r < 3; ++r) launch_spmv<T, T>(c, s, P.rp, P.ci, valb, x, y, nullptr, nullptr, 0, 0);
                 cudaEventRecord(e0, s);
-                for (int r = 0; r < 20; ++r) launch_spmv<T, T>(c, s, drp, dci, dval, x, y, nullptr, nullptr, 0, 0);
+                for (int r = 0; r < 20; ++r) launch_spmv<T, T>(c, s, P.rp, P.ci, valb, x, y, nullptr, nullptr, 0, 0);
                 cudaEventRecord(e1, s);
                 e = cudaEventSynchronize(e1);
                 if (e == cudaSuccess) e = cudaGetLastError();
@@ -283,9 +317,7 @@ cudaError_t tune_spmv(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, in
     P.shift = shift;
     P.unroll = unroll;
     plan_bins(rp, rows, shift, 0, ctx->sms, list, P.B);
-    e = cudaMemcpyAsync(P.list, list.data(), sizeof(int) * rows, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return e;
+    return store_binned<T>(ctx, P, rp, list, drp, dci, dval, valb, true);
 }
 
 constexpr int kLaunchesPerAttempt = 4;
@@ -499,6 +531,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     Arena& A = ctx->arena;
     A.reserve<int>(m + 1); A.reserve<int>(nnz); A.reserve<int>(n + 1); A.reserve<int>(nnz);
     A.reserve<int>(m + 1); A.reserve<int>(n + 1);                    // SpMV row lists
+    A.reserve<int>(m + 1); A.reserve<int>(nnz); A.reserve<int>(n + 1); A.reserve<int>(nnz);  // binned rp, ci
     for (int k = 0; k < 4; ++k) A.reserve<double>(nnz);              // val0, val0T, val, valT
     for (int k = 0; k < 4; ++k) A.reserve<double>(n);                // c0 l0 u0 + cs
     A.reserve<double>(m); A.reserve<double>(m);                      // h0, hs
@@ -536,6 +569,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     ctx->rp = A.take<int>(m + 1); ctx->ci = A.take<int>(nnz);
     ctx->rpT = A.take<int>(n + 1); ctx->ciT = A.take<int>(nnz);
     ctx->pk.list = A.take<int>(m + 1); ctx->pkt.list = A.take<int>(n + 1);
+    ctx->pk.rp = A.take<int>(m + 1); ctx->pk.ci = A.take<int>(nnz);
+    ctx->pkt.rp = A.take<int>(n + 1); ctx->pkt.ci = A.take<int>(nnz);
     ctx->val0 = A.take<double>(nnz); ctx->val0T = A.take<double>(nnz);
     ctx->val = A.take<double>(nnz); ctx->valT = A.take<double>(nnz);
     ctx->c0 = A.take<double>(n); ctx->l0 = A.take<double>(n); ctx->u0 = A.take<double>(n); ctx->cs = A.take<double>(n);
@@ -576,8 +611,6 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     CK(cudaMemcpyAsync(ctx->ci, ci_i.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->rpT, rpT.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->ciT, ciT.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
-    if (m) CK(cudaMemcpyAsync(ctx->pk.list, list_k.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
-    if (n) CK(cudaMemcpyAsync(ctx->pkt.list, list_kt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->val0, v_i.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->val0T, vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->c0, c, sizeof(double) * n, cudaMemcpyHostToDevice, s));
@@ -597,14 +630,6 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     }
     // the host copies above are pageable: wait before the vectors go out of scope
     CK(cudaStreamSynchronize(s));
-
-    // ---- SpMV plans timed on the unscaled matrices (same structure), on request; in the
-    // FP32-iterate mode they are timed below on the FP32 copies instead
-    const bool tune = ctx->opt.spmv_autotune && ctx->opt.spmv_lanes == 0;
-    if (tune && !f32) {
-        CK(tune_spmv<double>(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val0, ctx->D.x, ctx->D.kx));
-        CK(tune_spmv<double>(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->val0T, ctx->D.y, ctx->D.kty));
-    }
 
     // ---- diagonal rescaling: Ruiz (infinity norm) then Pock-Chambolle (alpha = 1)
     std::vector<double> ones_m(m, 1.0), ones_n(n, 1.0);
@@ -639,6 +664,33 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     CK(cudaStreamSynchronize(s));
     const double nc = std::sqrt(sc[0]), nh = std::sqrt(sc[1]), amax = sc[2];
 
+    // ---- K~ and K~' stored bin by bin for the SpMV plans (timed on request, in the value
+    // type the iterations use); the unscaled values are dead, their memory holds the
+    // binned FP64 values
+    ctx->valb = ctx->val0;
+    ctx->valbT = ctx->val0T;
+    const bool tune = ctx->opt.spmv_autotune && ctx->opt.spmv_lanes == 0;
+    if (tune && f32) {
+        CK(tune_spmv<float>(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val, ctx->val_f, ctx->DF.x, ctx->DF.kx));
+        CK(tune_spmv<float>(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->valT, ctx->valT_f, ctx->DF.y,
+                            ctx->DF.kty));
+    } else if (tune) {
+        CK(tune_spmv<double>(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val, ctx->valb, D.x, D.kx));
+        CK(tune_spmv<double>(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->valT, ctx->valbT, D.y, D.kty));
+    }
+    if (tune) {  // the lists of the tuned plans (host) for the other value type
+        plan_bins(rp_i, m, ctx->pk.shift, 0, ctx->sms, list_k, ctx->pk.B);
+        plan_bins(rpT, n, ctx->pkt.shift, 0, ctx->sms, list_kt, ctx->pkt.B);
+    }
+    if (!tune || f32) {
+        CK(store_binned<double>(ctx, ctx->pk, rp_i, list_k, ctx->rp, ctx->ci, ctx->val, ctx->valb, !tune));
+        CK(store_binned<double>(ctx, ctx->pkt, rpT, list_kt, ctx->rpT, ctx->ciT, ctx->valT, ctx->valbT, !tune));
+    }
+    if (f32 && !tune) {
+        CK(store_binned<float>(ctx, ctx->pk, rp_i, list_k, ctx->rp, ctx->ci, ctx->val, ctx->val_f, false));
+        CK(store_binned<float>(ctx, ctx->pkt, rpT, list_kt, ctx->rpT, ctx->ciT, ctx->valT, ctx->valT_f, false));
+    }
+
     // ---- ||K~||_2 by power iteration (constant / plain step modes)
     double eta = amax > 0.0 ? 1.0 / amax : 1.0;
     double omega = (nc > 1e-10 && nh > 1e-10) ? nc / nh : 1.0;
@@ -651,8 +703,9 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         CK(cudaStreamSynchronize(s));
         double est = 0.0;
         for (int it = 0; it < ctx->opt.power_iters; ++it) {
-            launch_spmv<double, double>(ctx->pk, s, ctx->rp, ctx->ci, ctx->val, v, w, nullptr, nullptr, 0, 0);
-            launch_spmv<double, double>(ctx->pkt, s, ctx->rpT, ctx->ciT, ctx->valT, w, u, nullptr, nullptr, 0, 0);
+            launch_spmv<double, double>(ctx->pk, s, ctx->pk.rp, ctx->pk.ci, ctx->valb, v, w, nullptr, nullptr, 0, 0);
+            launch_spmv<double, double>(ctx->pkt, s, ctx->pkt.rp, ctx->pkt.ci, ctx->valbT, w, u, nullptr, nullptr, 0,
+                                        0);
             reduce_small<<<1, kBlock, 0, s>>>(n, u, nullptr, 0, ctx->scal + 3);
             double ss;
             CK(cudaMemcpyAsync(&ss, ctx->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -673,8 +726,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
 
     // ---- device view
     D.m = m; D.n = n;
-    D.rp = ctx->rp; D.ci = ctx->ci; D.val = ctx->val;
-    D.rpT = ctx->rpT; D.ciT = ctx->ciT; D.valT = ctx->valT;
+    D.rp = ctx->pk.rp; D.ci = ctx->pk.ci; D.val = ctx->valb;
+    D.rpT = ctx->pkt.rp; D.ciT = ctx->pkt.ci; D.valT = ctx->valbT;
     D.c = ctx->cs; D.h = ctx->hs; D.l = ctx->ls; D.u = ctx->us; D.dr = ctx->dr; D.dc = ctx->dc;
     D.c64 = ctx->cs; D.h64 = ctx->hs; D.l64 = ctx->ls; D.u64 = ctx->us;
     D.m_zero = ctx->m_zero; D.m_scalar = ctx->m_scalar;
@@ -708,10 +761,6 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         exp_constants<<<(ctx->n_exp + 255) / 256, 256, 0, s>>>(ctx->n_exp, ctx->exp_row0, ctx->dr, ctx->exp_lg);
     if (f32) {
         const int g = vec_grid(std::max<long long>(nnz, std::max(m, n)), ctx->sms);
-        if (nnz) {
-            cast_vec<float><<<g, kBlock, 0, s>>>(nnz, ctx->val, ctx->val_f);
-            cast_vec<float><<<g, kBlock, 0, s>>>(nnz, ctx->valT, ctx->valT_f);
-        }
         cast_vec<float><<<g, kBlock, 0, s>>>(n, ctx->cs, c_f);
         cast_vec<float><<<g, kBlock, 0, s>>>(n, ctx->ls, l_f);
         cast_vec<float><<<g, kBlock, 0, s>>>(n, ctx->us, u_f);
@@ -730,12 +779,6 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         DF.y = y; DF.yh = yh; DF.y0 = y0; DF.kx = kx; DF.kxh0 = kxh0; DF.kxh1 = kxh1; DF.kx0 = kx0; DF.ysum = ysum;
         DF.soc_w32 = soc_w32; DF.exp_lg32 = exp_lg32;
         ctx->fp32_active = true;
-        if (tune) {
-            CK(tune_spmv<float>(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val_f, DF.x, DF.kx));
-            CK(tune_spmv<float>(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->valT_f, DF.y, DF.kty));
-            D.binsK = DF.binsK = ctx->pk.B;
-            D.binsKT = DF.binsKT = ctx->pkt.B;
-        }
     }
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
