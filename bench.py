@@ -117,9 +117,10 @@ def algorithmic_bytes(p):
     dims = np.asarray(p["cone_dims"])
     cone_rows = int(dims[(types == 2) | (types == 3) | (types == 4)].sum())
     return {
-        # val + col per nonzero, row_ptr, the gathered input once, the output
-        "spmv_K": nnz * 12 + (m + 1) * 4 + n * 8 + m * 8,
-        "spmv_KT": nnz * 12 + (n + 1) * 4 + m * 8 + n * 8,
+        # val + col per nonzero, the binned row pointer and output row index, the gathered
+        # input once, the output
+        "spmv_K": nnz * 12 + (m + 1) * 4 + m * 4 + n * 8 + m * 8,
+        "spmv_KT": nnz * 12 + (n + 1) * 4 + n * 4 + m * 8 + n * 8,
         # reads x, xhat, x0, K'y, K'yhat, K'y0, xsum, c, l, u; writes x, K'y, xsum, xhat
         "primal_update": n * 14 * 8,
         # reads y, yhat, y0, Kx, K xhat (both buffers), Kx0, ysum, h; writes y, Kx, ysum, yhat;
