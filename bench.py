@@ -36,6 +36,9 @@ WORKLOADS = {
     "mixed_cone_1m": "mixed-cone LP/SOCP/exp, n=1,000,000, m=500,000, ~10M nnz, 200k nonneg rows, "
                      "SOC(4-64) on 200k rows, 20k exp cones, 40k zero rows, known optimum, seed 1",
     "small_socp": "random sparse SOCP, n=2,000, m=1,000, 20k nnz, 500 nonneg rows + 50 SOC(10), seed 0",
+    "logistic_exp_200k": "l1 logistic regression as an exp-cone program: 200,000 samples x 2,000 features at "
+                         "0.5 % density (N(0,1), labels +-1), 400k exp cones + 200k nonneg rows, n=604,000, "
+                         "m=1,400,000, ~5.2M nnz, lam = 0.1 ||X'b||_inf / 2, seed 2",
 }
 
 
@@ -45,12 +48,15 @@ def make_workload(name):
         return I.mixed_cone(1)
     if name == "small_socp":
         return I.small_socp(0)
+    if name == "logistic_exp_200k":
+        return I.logistic_exp(2)
     raise SystemExit("unknown workload " + name)
 
 
 def problem_bytes(p):
+    bounds = sum(p[k].size * 8 for k in ("lb", "ub") if p.get(k) is not None)
     return (p["row_ptr"].size * 8 + p["col"].size * 4 + p["val"].size * 8 + p["c"].size * 8 + p["h"].size * 8
-            + len(p["cone_types"]) * 16)
+            + bounds + len(p["cone_types"]) * 16)
 
 
 # ---------------------------------------------------------------------------
@@ -188,6 +194,8 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-iterate mode measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-programs measurement")
     ap.add_argument("--no-proj", action="store_true", help="skip the standalone projection measurements")
+    ap.add_argument("--no-exp", action="store_true",
+                    help="skip the exp-cone logistic program (plain vs learned exp root start)")
     ap.add_argument("--batch-count", type=int, default=256, help="Lasso programs in the batched measurement")
     ap.add_argument("--time-to-tol", default="1e-4,1e-6",
                     help="comma list of tolerances for the time-to-solution runs ('' to skip)")
@@ -418,6 +426,57 @@ def main():
                          "cones_per_s": ne / (pms * 1e-3), "GBps": byt / (pms * 1e-3) / 1e9})
         del v, dsc, out
 
+    # the exp-cone-heavy program (l1 logistic regression, 400k exp cones), plain exp root
+    # search against the learned starting point: the first evaluation (no cached roots), the
+    # steady-state rate and the time to 1e-6
+    exp_heavy = None
+    if not args.no_exp:
+        from paper_2505_00311_gb300 import instances as I
+        q = I.logistic_exp(2)
+        rng = np.random.default_rng(11)
+        v = rng.normal(size=(1_000_000, 3))
+        d = np.exp(rng.normal(0.0, 0.5, (1_000_000, 3)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        feats, target = P.exp_mlp_dataset(v, d)
+        w_mlp, _ = P.exp_mlp_train(feats, target, P.exp_mlp_init(0), steps=4000, batch=4096, lr=2e-3, seed=5)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        exp_heavy = {"workload": WORKLOADS["logistic_exp_200k"],
+                     "network": {"pairs": int(target.size), "steps": 4000, "batch": 4096, "seconds": train_s,
+                                 "data": "case-4 roots of the plain search for 1M N(0,1) 3-vectors with scales "
+                                         "exp(N(0, 0.5^2))"}}
+        for name, w in (("plain", None), ("learned", w_mlp)):
+            s6 = P.Solver(q, stream=stream.cuda_stream, spmv_autotune=1, exp_mlp=w)
+            first, _ = s6.kernel_times(1)
+            for _ in range(args.warmup):
+                s6.run(EVALS_PER_STEP)
+            kt6, _ = s6.kernel_times(EVALS_PER_STEP)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                s6.run(EVALS_PER_STEP)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms6 = e0.elapsed_time(e1)
+            s6.close()
+            s7 = P.Solver(q, stream=stream.cuda_stream, time_limit=args.ttt_limit, spmv_autotune=1, exp_mlp=w)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, inf = s7.solve(1e-6, 2_000_000)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            s7.close()
+            exp_heavy[name] = {
+                "first_evaluation_dual_update_ms": first["dual_update"],
+                "value": world * evals / (ms6 / 1000.0), "unit": "iters/s", "ms_per_step": ms6 / args.steps,
+                "dual_update_ms": kt6["dual_update"], "kernels_ms_per_launch": kt6,
+                "time_to_1e-6": {"seconds": dt, "status": P.STATUS_NAMES.get(st, st), "evaluations": inf["attempts"],
+                                 "restarts": inf["restarts"], "err": [inf["err_p"], inf["err_d"], inf["err_gap"]],
+                                 "setup_seconds": inf["setup_seconds"]}}
+
     if rank != 0:
         return
     # roofline of the dominant kernel
@@ -444,7 +503,8 @@ def main():
                        "precision": "fp64", "l2": "working set > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clk, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-            "time_to_tol": ttt, "fp32_iterates": fp32, "batched_programs": batch, "projections": proj}
+            "time_to_tol": ttt, "fp32_iterates": fp32, "batched_programs": batch, "projections": proj,
+            "exp_heavy": exp_heavy}
     print(json.dumps(line))
 
 

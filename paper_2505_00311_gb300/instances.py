@@ -275,6 +275,61 @@ def lasso_socp(seed: int = 0, n: int = 200, m: int | None = None, lam: float | N
             "lasso": {"A": A, "b": b, "lam": lam}}
 
 
+def logistic_exp(seed: int = 2, n_samples: int = 200_000, n_features: int = 2000, density: float = 0.005,
+                 lam_frac: float = 0.1):
+    """l1-regularised logistic regression, min sum_i log(1 + exp(-b_i x_i'w)) + lam ||w||_1,
+    as an exponential-cone program with two exp cones and one nonnegative row per sample
+    (EXP = closure{(r, s, t): s > 0, t >= s exp(r / s)}).  Variables w+, w- >= 0 (w = w+ - w-,
+    the l1 term through the bounds) and t, u, v free, one of each per sample:
+        (-t_i, 1, u_i) in EXP                   i.e. u_i >= exp(-t_i),
+        (-b_i x_i'w - t_i, 1, v_i) in EXP       i.e. v_i >= exp(-b_i x_i'w - t_i),
+        1 - u_i - v_i >= 0,
+    which together say t_i >= log(1 + exp(-b_i x_i'w)); objective 1't + lam 1'(w+ + w-).
+    Rows: sample i's two cones at rows 6i .. 6i+5 (their s rows empty, h = -1), then the N
+    nonnegative rows.  Variables: w+ (p), w- (p), t, u, v (N each).
+    Data: each entry of X (N x p) present with probability `density`, N(0, 1) values; labels
+    b_i = +-1 with probability 1/2; lam = lam_frac * ||X'b||_inf / 2 (w = 0 is optimal exactly
+    when lam >= ||X'b||_inf / 2).  No known optimum: solutions are judged by the KKT evaluator
+    and, on small instances, by a direct minimisation of the logistic objective."""
+    rng = np.random.default_rng(seed)
+    N, p = int(n_samples), int(n_features)
+    deg = np.minimum(rng.binomial(p, density, N), p).astype(np.int64)
+    xptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(deg, out=xptr[1:])
+    xcol = _unique_cols(rng, xptr, p)
+    xval = rng.standard_normal(int(xptr[-1]))
+    b = np.where(rng.random(N) < 0.5, 1.0, -1.0)
+    X = sp.csr_matrix((xval, xcol, xptr), shape=(N, p))
+    lam = lam_frac * 0.5 * float(np.abs(X.T @ b).max()) if N else 0.0
+    n = 2 * p + 3 * N
+    m = 7 * N
+    it, iu, iv = 2 * p, 2 * p + N, 2 * p + 2 * N
+    i = np.arange(N, dtype=np.int64)
+    srow = np.repeat(i, deg)                       # sample of each entry of X
+    bx = b[srow] * xval                            # b_i x_ij
+    rows = [6 * i, 6 * i + 2, 6 * srow + 3, 6 * srow + 3, 6 * i + 3, 6 * i + 5, 6 * N + i, 6 * N + i]
+    cols = [it + i, iu + i, xcol.astype(np.int64), p + xcol.astype(np.int64), it + i, iv + i, iu + i, iv + i]
+    vals = [-np.ones(N), np.ones(N), -bx, bx, -np.ones(N), np.ones(N), -np.ones(N), -np.ones(N)]
+    K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(m, n))
+    K.sort_indices()
+    c = np.zeros(n)
+    c[:2 * p] = lam
+    c[it:it + N] = 1.0
+    h = np.zeros(m)
+    h[6 * i + 1] = -1.0
+    h[6 * i + 4] = -1.0
+    h[6 * N:] = -1.0
+    lb = np.full(n, -np.inf)
+    lb[:2 * p] = 0.0
+    ub = np.full(n, np.inf)
+    types = np.concatenate([np.full(2 * N, EXP, dtype=np.int32), np.asarray([NONNEG] if N else [], dtype=np.int32)])
+    dims = np.concatenate([np.full(2 * N, 3, dtype=np.int64), np.asarray([N] if N else [], dtype=np.int64)])
+    return {"name": "logistic_exp", "m": m, "n": n, "row_ptr": K.indptr.astype(np.int64),
+            "col": K.indices.astype(np.int32), "val": K.data, "c": c, "h": h, "lb": lb, "ub": ub,
+            "cone_types": types, "cone_dims": dims,
+            "logistic": {"X": X, "labels": b, "lam": lam}}
+
+
 def lasso_batch(seed: int, count: int, n_lo: int = 50, n_hi: int = 1000):
     """`count` Lasso SOCPs of uneven sizes, n ~ U{n_lo..n_hi}, each from its own seed."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,100 @@
+"""GPU parity on the exponential-cone logistic-regression program (two exp cones and one
+nonnegative row per sample, the exp-cone-heavy workload): iterates against the oracle,
+the solution against a direct minimisation of the logistic objective, and the learned
+starting point of the exp root search leaving the solution unchanged."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_00311_gb300 import build as B
+from paper_2505_00311_gb300 import instances as I
+from paper_2505_00311_gb300 import pdcs as P
+from test_logistic_program import logistic_minimum
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    oracle.build()
+
+
+@pytest.fixture(scope="module")
+def prob():
+    return I.logistic_exp(5, n_samples=3000, n_features=100, density=0.05)
+
+
+def rel_inf(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
+
+
+def _window(g, o, targets):
+    done = 0
+    for target in targets:
+        g.run(target - done)
+        o.run(target - done)
+        done = target
+        gs, os_ = g.info(), o.scalars()
+        assert gs["attempts"] == os_["attempts"]
+        assert gs["accepted"] == os_["accepted"] and gs["restarts"] == os_["restarts"], (target, gs, os_)
+        gi, oi = g.iterate(), o.iterate()
+        err = max(rel_inf(a, b) for a, b in zip(gi, oi))
+        assert err <= RTOL, (target, err)
+
+
+@pytest.mark.parametrize("start", [0, 300])
+def test_logistic_iteration_parity(prob, start):
+    """Windows of 32 evaluations (checks every 16) from the cold start and from the
+    oracle's iterate after 300 evaluations."""
+    g = P.Solver(prob, check_period=16)
+    o = oracle.Solver(prob, check_period=16)
+    if start:
+        ref = oracle.Solver(prob)
+        ref.run(start)
+        x, y, _, _ = ref.iterate()
+        om = ref.scalars()["omega"]
+        g.warm_start(x, y, om)
+        o.set_start(x, y, om)
+    _window(g, o, [1, 2, 3, 8, 15, 16, 17, 24, 32])
+    g.close()
+
+
+@pytest.mark.parametrize("precision", [P.PRECISION_FP64, P.PRECISION_FP32])
+def test_logistic_solution_matches_direct_minimisation(prob, precision):
+    fmin, _ = logistic_minimum(prob)
+    g = P.Solver(prob, precision=precision)
+    st, info = g.solve(1e-7, 400_000)
+    assert st == P.OK, info
+    x, y = g.solution()
+    k = oracle.kkt(prob, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1.01e-7, k
+    assert abs(k["pobj"] - fmin) <= 1e-6 * abs(fmin), (k["pobj"], fmin)
+    g.close()
+
+
+def test_logistic_with_learned_exp_start(prob):
+    """A network trained on the plain search's roots only moves the search's starting
+    point: the first evaluations equal the plain solver's to the projection tolerance
+    and the solve reaches the same optimum."""
+    rng = np.random.default_rng(11)
+    v = rng.normal(size=(200_000, 3))
+    d = np.exp(rng.normal(0.0, 0.5, (200_000, 3)))
+    X, t = P.exp_mlp_dataset(v, d)
+    w, _ = P.exp_mlp_train(X, t, P.exp_mlp_init(0), steps=1500, batch=4096, lr=2e-3, seed=5)
+    g0 = P.Solver(prob)
+    g1 = P.Solver(prob, exp_mlp=w)
+    g0.run(1)
+    g1.run(1)
+    assert max(rel_inf(a, b) for a, b in zip(g1.iterate(), g0.iterate())) <= 1e-12
+    g0.close()
+    fmin, _ = logistic_minimum(prob)
+    st, info = g1.solve(1e-7, 400_000)
+    assert st == P.OK, info
+    x, y = g1.solution()
+    k = oracle.kkt(prob, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1.01e-7, k
+    assert abs(k["pobj"] - fmin) <= 1e-6 * abs(fmin)
+    g1.close()
