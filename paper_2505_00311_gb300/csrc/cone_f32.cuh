@@ -144,8 +144,16 @@ __device__ __forceinline__ bool in_kexp_dual_f(float r, float s, float t) {
 // search when the FP32 root search does not give a finite result.
 __device__ inline void exp_project_f32(float r0, float s0, float t0, float dr, float ds, float dt, const float* lg,
                                        float* out, float* L_cache, const float* mlp = nullptr) {
-    if (in_kexp_f(r0 / dr, s0 / ds, t0 / dt)) { out[0] = r0; out[1] = s0; out[2] = t0; return; }
-    if (in_kexp_dual_f(-dr * r0, -ds * s0, -dt * t0)) { out[0] = 0.0f; out[1] = 0.0f; out[2] = 0.0f; return; }
+    // a point within 1e-6 |v| of the cone (of its polar) is taken as inside (see exp_gap_to_cone)
+    const float near = 1e-6f * sqrtf(r0 * r0 + s0 * s0 + t0 * t0);
+    if (in_kexp_f(r0 / dr, s0 / ds, t0 / dt) || exp_gap_to_cone(r0, s0, t0, dr, ds, dt) <= near) {
+        out[0] = r0; out[1] = s0; out[2] = t0;
+        return;
+    }
+    if (in_kexp_dual_f(-dr * r0, -ds * s0, -dt * t0) || exp_gap_to_polar(r0, s0, t0, dr, ds, dt) <= near) {
+        out[0] = 0.0f; out[1] = 0.0f; out[2] = 0.0f;
+        return;
+    }
     if (r0 <= 0.0f && s0 <= 0.0f) { out[0] = r0; out[1] = 0.0f; out[2] = t0 > 0.0f ? t0 : 0.0f; return; }
     ExpCase4T<float> e;
     e.r0 = r0; e.s0 = s0; e.t0 = t0; e.dr = dr; e.ds = ds;

@@ -1143,6 +1143,33 @@ __host__ __device__ __forceinline__ int kexpdual_screen32(float r, float s, floa
     return r > 1e-30f ? -1 : 0;
 }
 
+// Points outside D K_exp (or its polar (D K_exp)° = D^-1 K_exp°) by less than the
+// membership tests resolve: case 4's root then sits at the end of its interval, where the
+// search converges slowly (dual iterates on the boundary of the dual cone at the solution
+// make many such points).  By Moreau, returning v (or 0) errs by dist(v, D K_exp) (or
+// dist(v, polar)); each function bounds it by the distance to a point of the set that
+// differs from v only in t, with t moved past the computed boundary by a slack covering
+// the rounding of the exponent and of exp.  INFINITY where that point does not exist.
+template <typename R> struct ExpGapEps;
+template <> struct ExpGapEps<double> { static constexpr double eps = 2.220446049250313e-16; };
+template <> struct ExpGapEps<float> { static constexpr float eps = 1.1920929e-7f; };
+template <typename R>
+__host__ __device__ __forceinline__ R exp_gap_to_cone(R r0, R s0, R t0, R dr, R ds, R dt) {
+    const R s = s0 / ds, q = (r0 / dr) / s;  // K_exp: s > 0, t >= s e^(r/s)
+    if (!(s > R(0)) || !(fabs(q) < R(80))) return R(INFINITY);
+    const R tb = dt * s * exp(q);
+    const R tq = tb * (R(1) + (R(8) + R(2) * fabs(q)) * ExpGapEps<R>::eps);
+    return t0 >= tq ? R(0) : tq - t0;
+}
+template <typename R>
+__host__ __device__ __forceinline__ R exp_gap_to_polar(R r0, R s0, R t0, R dr, R ds, R dt) {
+    const R a = dr * r0, q = ds * s0 / a - R(1);  // K_exp°: a > 0, c <= -a e^(b/a - 1)
+    if (!(a > R(0)) || !(fabs(q) < R(80))) return R(INFINITY);
+    const R tb = -a * exp(q) / dt;
+    const R tq = tb * (R(1) + (R(8) + R(2) * fabs(q + R(1))) * ExpGapEps<R>::eps);
+    return t0 <= tq ? R(0) : t0 - tq;
+}
+
 // Projection onto D K_exp with precomputed logs of the scales (lg[0..2] = log dr, ds, dt).
 // L_cache (may be null): FP32 copy of the last log-offset of this cone.  mlp (may be
 // null): device weights of the learned starting point, used when there is no cached
@@ -1150,12 +1177,16 @@ __host__ __device__ __forceinline__ int kexpdual_screen32(float r, float s, floa
 __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0, double dr, double ds, double dt,
                                                  const double* lg, double* out, float* L_cache,
                                                  const float* mlp = nullptr, int* ev = nullptr) {
-    // cases 1-3, screened in FP32
+    // cases 1-3, screened in FP32; a point the FP64 test puts outside after an uncertain
+    // screen is taken as inside when it is within 1e-14 |v| of the set (see exp_gap_to_cone)
+    const double near = 1e-14 * sqrt(r0 * r0 + s0 * s0 + t0 * t0);
     int c1 = kexp_screen32((float)r0 / (float)dr, (float)s0 / (float)ds, (float)t0 / (float)dt);
-    if (c1 == 0) c1 = in_kexp(r0 / dr, s0 / ds, t0 / dt) ? 1 : -1;
+    if (c1 == 0) c1 = (in_kexp(r0 / dr, s0 / ds, t0 / dt) || exp_gap_to_cone(r0, s0, t0, dr, ds, dt) <= near) ? 1 : -1;
     if (c1 > 0) { out[0] = r0; out[1] = s0; out[2] = t0; return; }
     int c2 = kexpdual_screen32(-(float)dr * (float)r0, -(float)ds * (float)s0, -(float)dt * (float)t0);
-    if (c2 == 0) c2 = in_kexp_dual(-dr * r0, -ds * s0, -dt * t0) ? 1 : -1;
+    if (c2 == 0)
+        c2 = (in_kexp_dual(-dr * r0, -ds * s0, -dt * t0) || exp_gap_to_polar(r0, s0, t0, dr, ds, dt) <= near) ? 1
+                                                                                                            : -1;
     if (c2 > 0) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
     if (r0 <= 0.0 && s0 <= 0.0) { out[0] = r0; out[1] = 0.0; out[2] = t0 > 0.0 ? t0 : 0.0; return; }
     // case 4: root in FP32
