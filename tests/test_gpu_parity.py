@@ -106,6 +106,30 @@ def test_exp_projection_stressed():
     assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(v)
 
 
+@pytest.mark.parametrize("dual", [0, 1])
+def test_exp_projection_near_the_boundaries(dual):
+    """Points a few ulps to 1e-6 (relative, in t) off the boundary of D K_exp and of its
+    polar, with random scales: the GPU takes points within 1e-14 |v| of either set as
+    inside it, which the oracle's full search must confirm to 1e-12."""
+    rng = np.random.default_rng(21 + dual)
+    n = 20_000
+    d = np.exp(rng.normal(0.0, 1.0, (n, 3)))
+    r, s = rng.normal(0.0, 3.0, n), np.exp(rng.normal(0.0, 1.5, n))
+    a, b = np.exp(rng.normal(0.0, 1.5, n)), rng.normal(0.0, 3.0, n)
+    on_k = np.stack([r, s, s * np.exp(np.clip(r / s, -30, 30))], 1) * d            # boundary of D K
+    on_p = np.stack([a, b, -a * np.exp(np.clip(b / a - 1.0, -30, 30))], 1) / d     # boundary of the polar
+    v = np.where((np.arange(n) % 2 == 0)[:, None], on_k, on_p)
+    k = rng.integers(-1000, 1000, n)
+    rel = 10.0 ** rng.uniform(-12, -6, n) * rng.choice([-1.0, 1.0], n)
+    v[:, 2] += np.where(rng.random(n) < 0.5, k * np.spacing(np.abs(v[:, 2])), v[:, 2] * rel)
+    if dual:  # the same points through the Remark: Proj onto D^-1 K* of w = -v projects v onto D K
+        v = -v
+    got = _gpu_proj(v.ravel(), d.ravel(), np.full(n, 4, np.int32), np.full(n, 3, np.int64), dual).reshape(n, 3)
+    ref = oracle.proj_cones(v.ravel(), np.full(n, 4), np.full(n, 3), d.ravel(), dual=bool(dual)).reshape(n, 3)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(v, axis=1)
+    assert err.max() <= 1e-12, err.max()
+
+
 # ---------------------------------------------------------------------------
 # solver parity
 # ---------------------------------------------------------------------------
