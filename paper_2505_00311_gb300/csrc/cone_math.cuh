@@ -273,13 +273,16 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // when w is null), or formed from the block's scales d as soc_weight<kInv> does.
 struct SocWeightsArray {
     const double* w;
+    const double* wi;  // 1 / w[i] to rounding (may be null: divided out)
     __device__ __forceinline__ double operator()(int i) const { return w ? w[i] : 1.0; }
+    __device__ __forceinline__ double inv(int i) const { return wi ? wi[i] : (w ? 1.0 / w[i] : 1.0); }
 };
 template <bool kInv>
 struct SocWeightsScales {
     const double* d;
     double d0;
     __device__ __forceinline__ double operator()(int i) const { return soc_weight<kInv>(d, d0, i); }
+    __device__ __forceinline__ double inv(int i) const { return soc_weight<!kInv>(d, d0, i); }
 };
 
 // buf[0..dim): the block, projected in place onto E K_soc where the weight of x entry
@@ -289,19 +292,20 @@ __device__ void soc_project_warp_fast(double* buf, WF wf, int dim, float* cache)
     const int lane = threadIdx.x & 31;
     const int nx = dim - 1;
     const double t = buf[0];
-    double xr[R], wr[R];
+    double xr[R], wr[R], wir[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int i = lane + 32 * k;
         const bool in = i < nx;
         xr[k] = in ? buf[1 + i] : 0.0;
         wr[k] = in ? wf(i) : 1.0;
+        wir[k] = in ? wf.inv(i) : 1.0;
     }
     double a = 0.0, b = 0.0;  // ||Dhat x||^2, ||Dhat^{-1} x||^2
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const double x2 = xr[k] * xr[k];
-        a += x2 / wr[k];
+        a += x2 * wir[k];
         b += wr[k] * x2;
     }
     a = warp_sum(a);
@@ -635,11 +639,12 @@ __device__ __forceinline__ void soc_project_wf(double* buf, WF wf, const double*
 
 // Precomputed weights w (w[i] for x entry i, or all ones when null).  scr (may be null):
 // 2 (dim - 1) floats of scratch for blocks beyond the registers (mixed precision there).
+// wi (may be null): precomputed 1 / w[i], saving a division per entry.
 template <bool kInv>
 __device__ __forceinline__ void soc_project_any(double* buf, const double* __restrict__ w,
                                                 const double* __restrict__ d, int dim, bool rot, float* cache,
-                                                float* scr = nullptr) {
-    soc_project_wf<kInv>(buf, SocWeightsArray{w}, d, dim, rot, cache, scr);
+                                                float* scr = nullptr, const double* __restrict__ wi = nullptr) {
+    soc_project_wf<kInv>(buf, SocWeightsArray{w, wi}, d, dim, rot, cache, scr);
 }
 
 // Weights formed from the block's scales d (may be null: D = I) on the fly.
@@ -1023,13 +1028,14 @@ __host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R gues
 // from values given in double (logs of the scales passed in).
 template <typename R>
 __host__ __device__ __forceinline__ void exp_case4_setup(ExpCase4T<R>& e, double r0, double s0, double t0, double dr,
-                                                         double ds, R ldr, R lds, R ldt) {
+                                                         double ds, R ldr, R lds, R ldt, int anchor = 0) {
     e.r0 = R(r0); e.s0 = R(s0); e.t0 = R(t0); e.dr = R(dr); e.ds = R(ds);
     e.tau = R(ds / dr);
     e.ldt = ldt; e.ldr = ldr; e.lds = lds;
     const R ninf = -R(INFINITY);
-    e.lr0 = r0 > 0.0 ? R(log(R(r0))) : ninf;
-    e.ls0 = s0 > 0.0 ? R(log(R(s0))) : ninf;
+    // anchor 3 or 4 (0: both): the evaluation next to that endpoint reads log s0 or log r0 only
+    e.lr0 = (anchor != 3 && r0 > 0.0) ? R(log(R(r0))) : ninf;
+    e.ls0 = (anchor != 4 && s0 > 0.0) ? R(log(R(s0))) : ninf;
     e.lt0 = t0 > 0.0 ? R(log(R(t0))) : (t0 < 0.0 ? R(log(R(-t0))) : ninf);
     e.a3 = (s0 > 0.0) ? R((r0 * ds) / (s0 * dr)) : R(0);
     e.a4 = (r0 > 0.0) ? R(1.0 - (s0 * ds) / (r0 * dr)) : R(0);
@@ -1210,7 +1216,7 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
         // anchor stands when F has the sign beyond the root or is zero to precision;
         // otherwise the root next to it is delta = -F / c, polished by Newton in delta.
         ExpCase4 e;
-        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2]);
+        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2], ef.anchor);
         e.kind = ef.kind;
         e.anchor = ef.anchor;
         e.dir = (double)ef.dir;
@@ -1251,7 +1257,7 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
     if (ok) {
         // FP64 polish from the FP32 root, same branch and anchor
         ExpCase4 e;
-        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2]);
+        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2], ef.anchor);
         e.kind = ef.kind;
         e.anchor = ef.anchor;
         e.dir = (double)ef.dir;
@@ -1268,7 +1274,11 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
                 st = ef.dm ? (st > -1.0 ? log1p(st) : NAN) : st;
                 if (!isfinite(st)) break;
             }
-            if (fabs(st) <= 1e-8) {  // (1e-7 left errors near 1e-12 on stressed inputs)
+            // the neglected second-order terms grow with (step x the log-derivatives of the
+            // output terms A, B, log s_p, log r_d), which reach |rho| when rho is far from 0
+            const double dmax = fmax(fmax(1.0, fmax(fabs(a.dA), fabs(a.dB))),
+                                     fmax(fabs(a.dA - a.drho), fabs(a.dB + a.drho)));
+            if (fabs(st) * dmax <= 1e-8) {  // (1e-7 left errors near 1e-12 on stressed inputs)
                 if (L_cache) *L_cache = (float)(L + st);
                 exp_case4_output_lin(a, st, r0, s0, t0, dr, ds, out);
                 return;

@@ -365,7 +365,8 @@ __device__ __forceinline__ void dual_update_body(const Dev<T>& D, int qidx) {
             __syncwarp();
             if constexpr (sizeof(T) == 8)
                 soc_project_any<true>(D.yh + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, D.soc_lam + cidx,
-                                      reinterpret_cast<float*>(D.scr + o));  // scratch unused during the update
+                                      reinterpret_cast<float*>(D.scr + o),  // scratch unused during the update
+                                      D.soc_wp + o + 1);
             else
                 soc_project_any_f32(D.yh + o, D.soc_w32 + o + 1, D.scr + o, D.dr + o, dim, D.soc_rot[cidx] != 0,
                                     D.soc_lam + cidx);
@@ -494,7 +495,7 @@ __device__ __forceinline__ void cand_dual_body(const Dev<T>& D, int qidx) {
             for (int i = lane; i < dim; i += 32) out[o + i] = val(o + i);
             __syncwarp();
             soc_project_any<true>(out + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, nullptr,
-                                  reinterpret_cast<float*>(D.scr + (size_t)q * D.m + o));
+                                  reinterpret_cast<float*>(D.scr + (size_t)q * D.m + o), D.soc_wp + o + 1);
         }
     } else {
         const int stride = D.nb_exp * D.exp_pb;
@@ -558,7 +559,7 @@ __device__ __forceinline__ void kkt_primal_body(const Dev<T>& D, int qidx) {
             // scaled residual: project v onto Dr K
             for (int i = lane; i < dim; i += 32) s1[o + i] = kx[o + i] - D.h64[o + i];
             __syncwarp();
-            soc_project_any<false>(s1 + o, D.soc_wp + o + 1, D.dr + o, dim, rot, nullptr);
+            soc_project_any<false>(s1 + o, D.soc_wp + o + 1, D.dr + o, dim, rot, nullptr, nullptr, D.soc_w + o + 1);
             for (int i = lane; i < dim; i += 32) {
                 const double v = kx[o + i] - D.h64[o + i];
                 const double r = v - s1[o + i];

@@ -106,6 +106,20 @@ def test_exp_projection_stressed():
     assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(v)
 
 
+def test_exp_projection_wide_scales():
+    """100k N(0,1) x exp(N(0, 3^2)) inputs with scales exp(N(0, 1.5^2)): roots far from 0
+    (|rho| in the thousands), where the first-order output needs a step scaled by the
+    derivatives of its exponents; against the oracle's full search."""
+    rng = np.random.default_rng(99)
+    n = 100_000
+    v = rng.standard_normal((n, 3)) * np.exp(rng.normal(0.0, 3.0, (n, 3)))
+    d = np.exp(rng.normal(0.0, 1.5, (n, 3)))
+    got = _gpu_proj(v.ravel(), d.ravel(), np.full(n, 4, np.int32), np.full(n, 3, np.int64), 0).reshape(n, 3)
+    ref = oracle.proj_cones(v.ravel(), np.full(n, 4), np.full(n, 3), d.ravel()).reshape(n, 3)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(v, axis=1)
+    assert err.max() <= 1e-12, err.max()
+
+
 @pytest.mark.parametrize("dual", [0, 1])
 def test_exp_projection_near_the_boundaries(dual):
     """Points a few ulps to 1e-6 (relative, in t) off the boundary of D K_exp and of its
