@@ -3,7 +3,7 @@
  * solver of "A Practical GPU-Enhanced Matrix-Free Primal-Dual Method for
  * Large-Scale Conic Programs" (PDCS).
  *
- * TEST INFRASTRUCTURE ONLY.  This code is the judge that the CUDA library is
+ * TEST INFRASTRUCTURE ONLY.  This code is the reference that the CUDA library is
  * checked against.  It shares no code, header, helper or constant with the
  * CUDA path; only the test suite, the smoke check and the benchmark's CPU
  * baseline leg may load it.  Everything is single-threaded plain loops in

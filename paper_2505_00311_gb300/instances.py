@@ -231,7 +231,7 @@ def lasso_socp(seed: int = 0, n: int = 200, m: int | None = None, lam: float | N
     (w, r, y) in the rotated SOC ||y||^2 <= 2 w r, objective 2 r + lam 1'(x1 + x2), x1, x2 >= 0,
     w, r, y free.  Data (batched-workload recipe): m = n / 2, A dense N(0, 1), a ground truth
     with 5 % nonzero N(0, 1) entries, b = A x~ + 0.01 N(0, 1), lam ~ U[0.01, 1].  No known
-    optimum: solutions are judged by the KKT evaluator."""
+    optimum: solutions are checked by the KKT evaluator."""
     rng = np.random.default_rng(seed)
     m = max(1, n // 2) if m is None else m
     A = rng.standard_normal((m, n))
@@ -289,7 +289,7 @@ def logistic_exp(seed: int = 2, n_samples: int = 200_000, n_features: int = 2000
     nonnegative rows.  Variables: w+ (p), w- (p), t, u, v (N each).
     Data: each entry of X (N x p) present with probability `density`, N(0, 1) values; labels
     b_i = +-1 with probability 1/2; lam = lam_frac * ||X'b||_inf / 2 (w = 0 is optimal exactly
-    when lam >= ||X'b||_inf / 2).  No known optimum: solutions are judged by the KKT evaluator
+    when lam >= ||X'b||_inf / 2).  No known optimum: solutions are checked by the KKT evaluator
     and, on small instances, by a direct minimisation of the logistic objective."""
     rng = np.random.default_rng(seed)
     N, p = int(n_samples), int(n_features)

@@ -1,6 +1,6 @@
 """FP32-iterate mode: SpMV, updates and cone projections on FP32 iterates, with the
 restart / termination checks (candidates, their products, KKT residuals) and the final
-phase in FP64.  Results are judged by the FP64 oracle's KKT evaluator."""
+phase in FP64.  Results are checked by the FP64 oracle's KKT evaluator."""
 import numpy as np
 import pytest
 
