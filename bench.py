@@ -36,6 +36,9 @@ WORKLOADS = {
     "mixed_cone_1m": "mixed-cone LP/SOCP/exp, n=1,000,000, m=500,000, ~10M nnz, 200k nonneg rows, "
                      "SOC(4-64) on 200k rows, 20k exp cones, 40k zero rows, known optimum, seed 1",
     "small_socp": "random sparse SOCP, n=2,000, m=1,000, 20k nnz, 500 nonneg rows + 50 SOC(10), seed 0",
+    "mixed_cone_literal": "mixed-cone LP/SOCP/exp with the literal cone counts, n=1,000,000, m=2,000,000, ~41M nnz, "
+                          "200k nonneg rows, ~50k SOC(4-64) on 1.7M rows, 20k exp cones, 40k zero rows, known "
+                          "optimum, seed 1",
     "logistic_exp_200k": "l1 logistic regression as an exp-cone program: 200,000 samples x 2,000 features at "
                          "0.5 % density (N(0,1), labels +-1), 400k exp cones + 200k nonneg rows, n=604,000, "
                          "m=1,400,000, ~5.2M nnz, lam = 0.1 ||X'b||_inf / 2, seed 2",
@@ -48,6 +51,8 @@ def make_workload(name):
         return I.mixed_cone(1)
     if name == "small_socp":
         return I.small_socp(0)
+    if name == "mixed_cone_literal":
+        return I.mixed_cone_literal(1)
     if name == "logistic_exp_200k":
         return I.logistic_exp(2)
     raise SystemExit("unknown workload " + name)

@@ -198,6 +198,14 @@ def mixed_cone(seed: int = 1, n: int = 1_000_000, m: int = 500_000, nnz: int = 1
     return _finish(rng, m, n, row_ptr, cols, vals, types, dims, "mixed_cone")
 
 
+def mixed_cone_literal(seed: int = 1):
+    """The mixed-cone recipe with the literal cone counts: 50k SOC blocks of dimension
+    U{4..64} (about 1.7M rows), 200k nonnegative rows, 20k exp cones and 40k zero rows, so
+    m = 2,000,000; n = 1,000,000 and ~41M nonzeros (mean row degree 20.5)."""
+    return mixed_cone(seed=seed, n=1_000_000, m=2_000_000, nnz=41_000_000, n_nonneg=200_000,
+                      soc_rows=1_700_000, n_exp=20_000)
+
+
 def scaled_mixed_cone(seed: int = 1, scale: float = 0.01):
     """The mixed-cone program at a fraction of its size (same recipe)."""
     n = int(1_000_000 * scale)
