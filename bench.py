@@ -186,6 +186,20 @@ def cpu_baseline(p, budget_s=15.0, steps=None):
                       "evaluation, same workload" % n, "seconds": dt}
 
 
+def job_rate(ms, evals, dist=None, device="cpu"):
+    """Whole-job rate of independent replicas: every rank ran `evals` evaluations in `ms`
+    milliseconds and the job lasts as long as the slowest rank.  Returns (evaluations per
+    second over all ranks, the max time in ms)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        world = dist.get_world_size()
+    return world * evals / (ms / 1000.0), ms
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -270,12 +284,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     info1 = solver.info()
     launches = info1["kernel_launches"] - info0["kernel_launches"]
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     evals = args.steps * EVALS_PER_STEP
-    value = world * evals / (ms / 1000.0)
+    value, ms = job_rate(ms, evals, dist, "cuda")
     solver.close()
 
     # end to end through the public API with host buffers: create (H2D + setup),
@@ -343,7 +353,7 @@ def main():
                           "evaluations": inf["attempts"], "fp64_phase_reached": bool(inf["fp64_phase"]),
                           "err": [inf["err_p"], inf["err_d"], inf["err_gap"]]})
             s5.close()
-        fp32 = {"value": world * evals / (ms32 / 1000.0), "unit": "iters/s", "ms_per_step": ms32 / args.steps,
+        fp32 = {"value": job_rate(ms32, evals, dist, "cuda")[0], "unit": "iters/s", "ms_per_step": ms32 / args.steps,
                 "dtype": "f32 iterates, f64 checks", "still_fp32_phase": phase == 0,
                 "kernels_ms_per_launch": kt32, "time_to_tol": ttt32}
 
@@ -476,7 +486,7 @@ def main():
             s7.close()
             exp_heavy[name] = {
                 "first_evaluation_dual_update_ms": first["dual_update"],
-                "value": world * evals / (ms6 / 1000.0), "unit": "iters/s", "ms_per_step": ms6 / args.steps,
+                "value": job_rate(ms6, evals, dist, "cuda")[0], "unit": "iters/s", "ms_per_step": ms6 / args.steps,
                 "dual_update_ms": kt6["dual_update"], "kernels_ms_per_launch": kt6,
                 "time_to_1e-6": {"seconds": dt, "status": P.STATUS_NAMES.get(st, st), "evaluations": inf["attempts"],
                                  "restarts": inf["restarts"], "err": [inf["err_p"], inf["err_d"], inf["err_gap"]],
