@@ -187,8 +187,11 @@ void pdcs_destroy(pdcs_ctx* ctx);
  * means D = I), written to the DEVICE vector out (may equal v).  The cone list
  * is a HOST array as in pdcs_create; for RSOC blocks d must be equal on their
  * first two rows.  SOC by Theorem 1, exp by Theorem 3, exp* by the Remark of
- * App. A.2.  Runs on cuda_stream and returns once the work is queued.
- * Errors: PDCS_ERR_INVALID, PDCS_ERR_CUDA. */
+ * App. A.2.  Accuracy: each block within 1e-12 of its exact projection, relative
+ * to the block's norm (the root searches run in FP32 and are finished in FP64; an
+ * exp point within 1e-14 of its norm from the cone or from the polar cone is
+ * returned as itself or as 0).  Runs on cuda_stream and returns once the work is
+ * queued.  Errors: PDCS_ERR_INVALID, PDCS_ERR_CUDA. */
 pdcs_status pdcs_proj_cones_device(const double* v, const double* d, int64_t m, const pdcs_cone* cones,
                                    int64_t n_cones, int32_t dual, double* out, void* cuda_stream);
 
