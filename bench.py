@@ -149,8 +149,10 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+def ncu_record(kernel, field="bytes_per_launch"):
+    """A per-kernel figure of the committed ncu summary (DRAM bytes per launch, or the
+    FP64-pipe activity in % with field="fp64_pipe_active_pct"), if it was taken on this
+    source; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path))
@@ -158,7 +160,12 @@ def ncu_traffic(kernel):
         return None
     if rec.get("source_hash") != source_hash():
         return None
-    return rec.get("bytes_per_launch", {}).get(kernel)
+    return rec.get(field, {}).get(kernel)
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    return ncu_record(kernel)
 
 
 def measured_peaks():
@@ -503,6 +510,7 @@ def main():
     achieved = alg[dom] / (ktimes[dom] * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if peak else None, "traffic": ncu_traffic(dom),
+            "fp64_pipe_active_pct_ncu": ncu_record(dom, "fp64_pipe_active_pct"),
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak else "unavailable",
             "algorithmic_bytes_per_launch": alg[dom], "ms_per_launch": ktimes[dom],
             "kernels": {k: {"ms_per_launch": ktimes[k], "launches_per_step": kcounts[k],
