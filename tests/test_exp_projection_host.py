@@ -1,0 +1,75 @@
+"""The CUDA path's exponential-cone projection (Theorem 3; FP32 root search, FP64 finish,
+the boundary certificate) built for the host from the same source the kernels compile,
+against the oracle's full search on the CPU: wide-scale random inputs (roots with |rho|
+in the thousands) and points a few ulps to 1e-6 off the boundaries of D K_exp and of its
+polar.  Each result within 1e-12 of the oracle's, relative to the input's norm."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def driver(tmp_path_factory):
+    nvcc = shutil.which(os.environ.get("NVCC", "nvcc"))
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    oracle.build()
+    exe = str(tmp_path_factory.mktemp("hostexp") / "host_exp_projection")
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-x", "cu", os.path.join(HERE, "host_exp_projection.cu"), "-o", exe],
+                   check=True, capture_output=True)
+    return exe
+
+
+def _project(exe, tmp_path, v, d):
+    n = v.shape[0]
+    src, dst = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    with open(src, "wb") as f:
+        np.asarray([n], np.int32).tofile(f)
+        np.concatenate([v, d], axis=1).astype(np.float64).tofile(f)
+    subprocess.run([exe, src, dst], check=True)
+    return np.fromfile(dst, dtype=np.float64).reshape(n, 3)
+
+
+def _check(exe, tmp_path, v, d):
+    got = _project(exe, tmp_path, v, d)
+    n = v.shape[0]
+    ref = oracle.proj_cones(v.ravel(), np.full(n, 4), np.full(n, 3), d.ravel()).reshape(n, 3)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(v, axis=1)
+    assert err.max() <= 1e-12, (err.max(), v[np.argmax(err)], d[np.argmax(err)])
+
+
+# a root at rho ~ 1.65e3 (a3 = r0 ds / (s0 dr)), where a first-order output accepted after
+# a Newton step small in L but not in the exponents erred by 1.3e-12
+FAR_ROOT = ([17.86403990521029, 17.398279345560606, 0.0030304380764708968],
+            [0.1849370054305684, 297.6817719133365, 19.700657216676273])
+
+
+def test_wide_scales(driver, tmp_path):
+    rng = np.random.default_rng(99)
+    n = 60_000
+    v = rng.standard_normal((n, 3)) * np.exp(rng.normal(0.0, 3.0, (n, 3)))
+    d = np.exp(rng.normal(0.0, 1.5, (n, 3)))
+    v[0], d[0] = FAR_ROOT
+    _check(driver, tmp_path, v, d)
+
+
+def test_near_the_boundaries(driver, tmp_path):
+    rng = np.random.default_rng(7)
+    n = 40_000
+    d = np.exp(rng.normal(0.0, 1.0, (n, 3)))
+    r, s = rng.normal(0.0, 3.0, n), np.exp(rng.normal(0.0, 1.5, n))
+    a, b = np.exp(rng.normal(0.0, 1.5, n)), rng.normal(0.0, 3.0, n)
+    on_k = np.stack([r, s, s * np.exp(np.clip(r / s, -30, 30))], 1) * d
+    on_p = np.stack([a, b, -a * np.exp(np.clip(b / a - 1.0, -30, 30))], 1) / d
+    v = np.where((np.arange(n) % 2 == 0)[:, None], on_k, on_p)
+    k = rng.integers(-1000, 1000, n)
+    rel = 10.0 ** rng.uniform(-12, -6, n) * rng.choice([-1.0, 1.0], n)
+    v[:, 2] += np.where(rng.random(n) < 0.5, k * np.spacing(np.abs(v[:, 2])), v[:, 2] * rel)
+    _check(driver, tmp_path, v, d)

@@ -114,6 +114,9 @@ def test_exp_projection_wide_scales():
     n = 100_000
     v = rng.standard_normal((n, 3)) * np.exp(rng.normal(0.0, 3.0, (n, 3)))
     d = np.exp(rng.normal(0.0, 1.5, (n, 3)))
+    # a root at rho ~ 1.65e3 that a first-order output once missed by 1.3e-12
+    v[0] = [17.86403990521029, 17.398279345560606, 0.0030304380764708968]
+    d[0] = [0.1849370054305684, 297.6817719133365, 19.700657216676273]
     got = _gpu_proj(v.ravel(), d.ravel(), np.full(n, 4, np.int32), np.full(n, 3, np.int64), 0).reshape(n, 3)
     ref = oracle.proj_cones(v.ravel(), np.full(n, 4), np.full(n, 3), d.ravel()).reshape(n, 3)
     err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(v, axis=1)
