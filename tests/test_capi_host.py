@@ -95,3 +95,33 @@ def test_validation_rejects_bad_input(lib):
     _bad(p, spmv_lanes=3)
     q = dict(p); q["m"] = 0
     _bad(q)
+
+
+def test_missing_library_fails_loudly():
+    """No CPU fallback: without the CUDA library every entry point raises."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2505_00311_gb300 import pdcs as P, instances as I\n"
+            "P.LIB_PATH = '/nonexistent/libpdcs.so'\n"
+            "try:\n"
+            "    P.Solver(I.small_socp(0))\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "    sys.exit(0)\n"
+            "sys.exit(1)\n") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "missing" in r.stdout
+
+
+def test_product_package_does_not_use_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2505_00311_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
+                assert "pdcs_oracle.h" not in text and "liborc" not in text, f
