@@ -225,7 +225,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256, help="Lasso programs in the batched measurement")
     ap.add_argument("--time-to-tol", default="1e-4,1e-6",
                     help="comma list of tolerances for the time-to-solution runs ('' to skip)")
-    ap.add_argument("--ttt-limit", type=float, default=45.0, help="seconds allowed per time-to-tolerance run")
+    ap.add_argument("--ttt-limit", type=float, default=100.0, help="seconds allowed per time-to-tolerance run")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
