@@ -29,6 +29,11 @@
  *  - the result takes, per coordinate, the smaller of v_p and v_d from its formula
  *    (eq. vpvd_defn) and the other from v0 = v_p + v_d (eq. diagonal_moreau);
  *  - every bisection runs until the midpoint equals an endpoint (FP64 limit).
+ * Accuracy: the bisection settles the root to the last bit of L, so the error of a
+ * result is that of evaluating h and v_p / v_d in FP64.  Where the interval is
+ * narrow (a3 - a4 small) and d~ = rho (rho - 1) + tau^2 cancels, those evaluations
+ * lose digits: among 300k inputs N(0,1) with scales e^N(0, 0.25) one result was
+ * 1.35e-12 (relative to |v0|) from an 80-digit solution, the rest within ~2e-13.
  */
 #include "pdcs_oracle.h"
 #include <math.h>
