@@ -28,12 +28,18 @@
  *    an endpoint, offsets below the smallest double and rho > 709 are handled;
  *  - the result takes, per coordinate, the smaller of v_p and v_d from its formula
  *    (eq. vpvd_defn) and the other from v0 = v_p + v_d (eq. diagonal_moreau);
+ *  - a3 - a4 and d~ = rho (rho - 1) + tau^2 (App. A.2) are evaluated through exact
+ *    identities of their definitions, a3 - a4 = N / (r0 s0), d~(a3) = tau N / s0^2,
+ *    d~(a4) = tau N / r0^2 with N = tau (r0^2 + s0^2) - r0 s0 formed by error-free
+ *    products and sums, and d~(a + dd) = d~(a) + dd (2 a - 1 + dd) at offset dd from
+ *    the anchor a, so that no subtraction cancels where the interval is narrow;
  *  - every bisection runs until the midpoint equals an endpoint (FP64 limit).
  * Accuracy: the bisection settles the root to the last bit of L, so the error of a
- * result is that of evaluating h and v_p / v_d in FP64.  Where the interval is
- * narrow (a3 - a4 small) and d~ = rho (rho - 1) + tau^2 cancels, those evaluations
- * lose digits: among 300k inputs N(0,1) with scales e^N(0, 0.25) one result was
- * 1.35e-12 (relative to |v0|) from an 80-digit solution, the rest within ~2e-13.
+ * result is that of evaluating h and v_p / v_d in FP64: within 1e-13 of a high-
+ * precision solution (relative to |v0|) on 10,000 case-4 inputs chosen for the
+ * cancellation in N (tests/test_oracle_pins.py); the plain differences a3 - a4 and
+ * rho (rho - 1) + tau^2 left up to 7.9e-12 there.  Where |rho| is large, e^rho in
+ * v_p / v_d amplifies the last-bit quantisation of L: ~1e-13 at |rho| ~ 1e4.
  */
 #include "pdcs_oracle.h"
 #include <math.h>
@@ -169,8 +175,48 @@ typedef struct {
     int anchor;  /* 3: rho measured from a3, 4: from a4 */
     double dir;  /* rho = anchor + dir * delta, delta = e^L */
     double w34;  /* a3 - a4 */
+    double dt3, dt4; /* d~ = rho (rho - 1) + tau^2 at rho = a3 and at rho = a4 */
     int kind;    /* 1: r0 > 0, s0 > 0;  2: r0 <= 0, s0 > 0;  3: r0 > 0, s0 <= 0 */
 } exp_ctx;
+
+/* Error-free transformations (Dekker 1971; Knuth, TAOCP vol. 2): a * b = p + e and
+ * a + b = s + e exactly in binary floating point. */
+static double two_prod(double a, double b, double* e) {
+    double p = a * b;
+    *e = fma(a, b, -p);
+    return p;
+}
+static double two_sum(double a, double b, double* e) {
+    double s = a + b, bb = s - a;
+    *e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+/* Theorem 3's endpoint quantities through exact identities of its definitions
+ * (a3 = r0 d_s / (s0 d_r), a4 = 1 - s0 d_s / (r0 d_r), d~(rho) = rho (rho - 1) + tau^2,
+ * tau = d_s / d_r).  With N = tau (r0^2 + s0^2) - r0 s0:
+ *     a3 - a4 = N / (r0 s0),   d~(a3) = tau N / s0^2,   d~(a4) = tau N / r0^2.
+ * When both r0, s0 > 0 the difference in N cancels (the interval (l_rho, u_rho) is then
+ * narrow, or d~ is small on it); N is formed from error-free products and sums of r0, s0
+ * scaled by one power of two (exact), so it is right to its last bits, where the plain
+ * differences a3 - a4 and rho (rho - 1) + tau^2 lose the digits that cancel. */
+static void exp_endpoint_terms(exp_ctx* e) {
+    double r0 = e->r0, s0 = e->s0, tau = e->tau;
+    double mx = fabs(r0) > fabs(s0) ? fabs(r0) : fabs(s0);
+    int k = 0;
+    frexp(mx, &k);
+    double r = ldexp(r0, -k), s = ldexp(s0, -k);
+    double e1, e2, eS, eq, e3, eD;
+    double p1 = two_prod(r, r, &e1), p2 = two_prod(s, s, &e2);
+    double S = two_sum(p1, p2, &eS);
+    double q = two_prod(tau, S, &eq);
+    double p3 = two_prod(r, s, &e3);
+    double D = two_sum(q, -p3, &eD);
+    double N = D + (eD + eq + tau * (eS + e1 + e2) - e3); /* N / 2^(2k) */
+    e->w34 = (r0 > 0.0 && s0 > 0.0) ? N / (r * s) : e->a3 - e->a4;
+    e->dt3 = s0 > 0.0 ? tau * N / (s * s) : 0.0;
+    e->dt4 = r0 > 0.0 ? tau * N / (r * r) : 0.0;
+}
 
 /* rho and the logarithms of s_p, r_d (eq. sp_rd) at log-offset L from the anchor,
  * using s_p = s~ / (d_r d~), r_d = d_s r~ / d~ (App. A.2, eq. tilde_defs).  The
@@ -180,11 +226,10 @@ typedef struct {
  * s_p or r_d (possible only by rounding at the interval ends) gives -inf. */
 static void exp_eval(const exp_ctx* e, double L, double* rho, double* lsp, double* lrd) {
     double delta = exp(L);
-    double rh, rm1, lst, lrt; /* rm1 = rho - 1 from the exact offset */
+    double rh, lst, lrt;
     int sst, srt; /* signs of s~ and r~ */
     if (e->anchor == 4) {
         rh = e->a4 + e->dir * delta;
-        rm1 = e->a4m1 + e->dir * delta;
         lst = log(e->r0) + L;
         sst = e->dir > 0.0 ? 1 : -1;
         double rt = (e->kind == 1) ? e->s0 * (e->w34 - e->dir * delta) : e->tau * e->r0 - rh * e->s0;
@@ -192,14 +237,16 @@ static void exp_eval(const exp_ctx* e, double L, double* rho, double* lsp, doubl
         srt = (rt > 0.0) - (rt < 0.0);
     } else {
         rh = e->a3 + e->dir * delta;
-        rm1 = (e->a3 - 1.0) + e->dir * delta;
         lrt = log(e->s0) + L;
         srt = e->dir < 0.0 ? 1 : -1;
         double st = (e->kind == 1) ? e->r0 * (e->w34 + e->dir * delta) : e->s0 * e->tau - e->r0 + e->r0 * rh;
         lst = log(fabs(st));
         sst = (st > 0.0) - (st < 0.0);
     }
-    double dt_ = rh * rm1 + e->tau * e->tau; /* d~ = rho (rho - 1) + tau^2 */
+    /* d~ = rho (rho - 1) + tau^2 at rho = a + dd: d~(a) + dd (2 a - 1 + dd) */
+    double dd = e->dir * delta;
+    double dt_ = e->anchor == 4 ? e->dt4 + dd * ((2.0 * e->a4m1 + 1.0) + dd)
+                                : e->dt3 + dd * ((2.0 * e->a3 - 1.0) + dd);
     int sdt = (dt_ > 0.0) - (dt_ < 0.0);
     double ldt_ = log(fabs(dt_));
     *rho = rh;
@@ -265,7 +312,7 @@ void orc_proj_exp(const double* v0, const double* d, double* out) {
     e.a3 = (s0 > 0.0) ? (r0 * ds) / (s0 * dr) : 0.0;
     e.a4 = (r0 > 0.0) ? 1.0 - (s0 * ds) / (r0 * dr) : 0.0;
     e.a4m1 = (r0 > 0.0) ? -(s0 * ds) / (r0 * dr) : -1.0;
-    e.w34 = e.a3 - e.a4;
+    exp_endpoint_terms(&e);
     double L;
     if (r0 > 0.0 && s0 > 0.0) {
         e.kind = 1;
@@ -356,9 +403,10 @@ void orc_proj_cones(const double* v, const double* d, int64_t m, const int32_t* 
                 orc_proj_rsoc(vv, dual ? dinv : dd, dim, oo);
                 break;
             case ORC_EXP:
-                if (dual) {
-                    double dinv3[3] = {1.0 / dd[0], 1.0 / dd[1], 1.0 / dd[2]};
-                    orc_proj_exp_dual(vv, dinv3, oo);
+                if (dual) { /* Remark with E = D^-1: Proj_{D^-1 K*}(v) = v + Proj_{D K}(-v) */
+                    double nv[3] = {-vv[0], -vv[1], -vv[2]}, p[3];
+                    orc_proj_exp(nv, dd, p);
+                    for (int i = 0; i < 3; ++i) oo[i] = vv[i] + p[i];
                 } else {
                     orc_proj_exp(vv, dd, oo);
                 }

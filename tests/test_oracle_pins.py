@@ -296,6 +296,76 @@ def test_exp_case4_matches_high_precision():
         n += 1
 
 
+def _case4_pool(seed, n, sd):
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((n, 3))
+    d = np.exp(rng.normal(0.0, sd, (n, 3)))
+    return v, d
+
+
+@pytest.mark.slow
+def test_exp_case4_matches_high_precision_10k():
+    """10,000 case-4 projections against the high-precision solution (tests/exp_high_precision.py),
+    each within 1e-13 of it relative to |v0|: the 4,000 inputs of two 300k pools (v ~ N(0,1),
+    scales e^N(0, 0.25), seeds 5 and 6) whose N = tau (r0^2 + s0^2) - r0 s0 cancels most (narrow
+    intervals, d~ small on them) that fall in case 4, among them input 94805 of seed 5 and 213237
+    of seed 6, where the plain differences a3 - a4 and rho (rho - 1) + tau^2 left 1.35e-12 and
+    7.9e-12, and case-4 inputs with scales e^N(0, 1) (seed 8) up to 10,000 in all."""
+    pytest.importorskip("mpmath")
+    import concurrent.futures as cf
+    import multiprocessing as mpr
+    import os
+    import sys
+    v5, d5 = _case4_pool(5, 300_000, 0.5)
+    v6, d6 = _case4_pool(6, 300_000, 0.5)
+    V, D = np.concatenate([v5, v6]), np.concatenate([d5, d6])
+    r0, s0, tau = V[:, 0], V[:, 1], D[:, 1] / D[:, 0]
+    N = tau * (r0 ** 2 + s0 ** 2) - r0 * s0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = np.where((r0 > 0) & (s0 > 0), (tau * (r0 ** 2 + s0 ** 2) + r0 * s0) / np.abs(N), 0.0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        span = np.maximum(np.where(s0 > 0, np.abs(r0 * tau / s0), 0.0), np.where(r0 > 0, np.abs(1 - s0 * tau / r0), 0.0))
+    ratio[~(span <= 60.0)] = 0.0  # ends beyond |60| need thousands of digits (exp_high_precision.py)
+    pick = list(np.argsort(-ratio)[:4000])
+    assert 94805 in pick and 300_000 + 213237 in pick
+    v8, d8 = _case4_pool(8, 30_000, 1.0)
+    V = np.concatenate([V[pick], v8])
+    D = np.concatenate([D[pick], d8])
+    got = oracle.proj_cones(V.ravel(), np.full(len(V), 4), np.full(len(V), 3), D.ravel()).reshape(-1, 3)
+    t = D[:, 1] / D[:, 0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        span = np.maximum(np.where(V[:, 1] > 0, np.abs(V[:, 0] * t / V[:, 1]), 0.0),
+                          np.where(V[:, 0] > 0, np.abs(1 - V[:, 1] * t / V[:, 0]), 0.0))
+    case4 = ~(np.all(got == V, axis=1) | ~np.any(got, axis=1) | ((V[:, 0] <= 0) & (V[:, 1] <= 0)))
+    case4 &= span <= 60.0
+    idx = np.flatnonzero(case4)
+    first = idx[idx < 4000]
+    idx = np.concatenate([first, idx[idx >= 4000][:10_000 - len(first)]])
+    assert len(idx) == 10_000 and len(first) > 2500
+    assert pick.index(94805) in first and pick.index(300_000 + 213237) in first
+    rows = [(V[i], D[i]) for i in idx]
+    workers = max(1, min(8, os.cpu_count() or 1))
+    chunks = [rows[k::workers] for k in range(workers)]
+    here = os.path.dirname(os.path.abspath(__file__))
+    old = os.environ.get("PYTHONPATH")
+    os.environ["PYTHONPATH"] = here + (os.pathsep + old if old else "")
+    try:
+        sys.path.insert(0, here)
+        import exp_high_precision as hp
+        with cf.ProcessPoolExecutor(workers, mp_context=mpr.get_context("spawn")) as ex:
+            parts = list(ex.map(hp.exp_case4_rows, chunks))
+    finally:
+        if old is None:
+            os.environ.pop("PYTHONPATH", None)
+        else:
+            os.environ["PYTHONPATH"] = old
+    ref = np.empty((len(idx), 3))
+    for k in range(workers):
+        ref[k::workers] = np.array(parts[k])
+    err = np.linalg.norm(got[idx] - ref, axis=1) / np.linalg.norm(V[idx], axis=1)
+    assert err.max() <= 1e-13, (err.max(), V[idx[np.argmax(err)]], D[idx[np.argmax(err)]])
+
+
 def test_exp_certificate_extreme_magnitudes():
     """Moreau certificates with entries spread over many orders of magnitude."""
     rng = np.random.default_rng(99)
