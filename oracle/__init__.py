@@ -89,6 +89,8 @@ def lib():
             L.orc_get_iterate.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
             L.orc_get_solution.argtypes = [ctypes.c_void_p, _dp, _dp]
             L.orc_get_scalars.argtypes = [ctypes.c_void_p, _dp]
+            L.orc_get_state.argtypes = [ctypes.c_void_p] + [_dp] * 9
+            L.orc_set_state.argtypes = [ctypes.c_void_p] + [_dp] * 9
             L.orc_norm2_estimate.argtypes = [ctypes.c_void_p]
             L.orc_norm2_estimate.restype = ctypes.c_double
             _lib = L
@@ -244,3 +246,22 @@ class Solver:
 
     def norm2(self):
         return lib().orc_norm2_estimate(self._h)
+
+    STATE_VECTORS = ["x", "xh", "x0", "xsum", "y", "yh", "y0", "ysum"]
+    STATE_SCALARS = ["eta", "omega", "wsum", "attempts", "accepted", "k", "restarts", "phi0", "phi_prev",
+                     "comp0_rp2", "comp0_rd2", "comp0_gap", "status", "started"]
+
+    def state(self):
+        """Full iterate state in scaled coordinates (dict of arrays and scalars)."""
+        vec = {k: np.empty(self.n if k.startswith("x") else self.m) for k in self.STATE_VECTORS}
+        sc = np.empty(len(self.STATE_SCALARS))
+        lib().orc_get_state(self._h, *[_ptr(vec[k]) for k in self.STATE_VECTORS], _ptr(sc))
+        vec.update(dict(zip(self.STATE_SCALARS, sc.tolist())))
+        return vec
+
+    def set_state(self, st):
+        """Restores a state returned by state() (arrays may be missing: left unchanged)."""
+        vec = [None if st.get(k) is None else _f64(st[k]) for k in self.STATE_VECTORS]
+        cur = self.state()
+        sc = _f64([float(st.get(k, cur[k])) for k in self.STATE_SCALARS])
+        lib().orc_set_state(self._h, *[_ptr(a) for a in vec], _ptr(sc))

@@ -85,6 +85,17 @@ void orc_get_iterate(const orc_solver* s, double* x, double* y, double* xhat, do
 void orc_get_solution(const orc_solver* s, double* x, double* y);
 /* Scalars: [eta, omega, attempts, accepted, restarts, inner_k, status, last err_p, err_d, err_gap, wsum, phi_anchor] */
 void orc_get_scalars(const orc_solver* s, double* out12);
+/* Full iterate state in the solver's scaled coordinates (x~ = x / dc, y~ = y / dr):
+ * the Halpern iterate, the last PDHG output, the anchor of the restart period and the
+ * eta-weighted sums (x: n, y: m), and ORC_STATE_SCALARS scalars
+ * [eta, omega, wsum, attempts, accepted, k, restarts, phi0, phi_prev, comp0[0..2],
+ *  status, started].  NULL arrays are skipped.  orc_set_state restores exactly what
+ * orc_get_state returned, so orc_run continues as if never interrupted. */
+#define ORC_STATE_SCALARS 14
+void orc_get_state(const orc_solver* s, double* x, double* xh, double* x0, double* xsum, double* y, double* yh,
+                   double* y0, double* ysum, double* scalars);
+void orc_set_state(orc_solver* s, const double* x, const double* xh, const double* x0, const double* xsum,
+                   const double* y, const double* yh, const double* y0, const double* ysum, const double* scalars);
 /* ||K~||_2 estimate used by the constant / plain step modes. */
 double orc_norm2_estimate(const orc_solver* s);
 

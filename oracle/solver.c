@@ -581,6 +581,48 @@ void orc_get_scalars(const orc_solver* S, double* o) {
 
 double orc_norm2_estimate(const orc_solver* S) { return S->norm2; }
 
+/* ---- full iterate state (scaled coordinates), for resuming and for parity tests -- */
+void orc_get_state(const orc_solver* S, double* x, double* xh, double* x0, double* xsum, double* y, double* yh,
+                   double* y0, double* ysum, double* sc) {
+    size_t nb = sizeof(double) * (size_t)S->n, mb = sizeof(double) * (size_t)S->m;
+    if (x) memcpy(x, S->x, nb);
+    if (xh) memcpy(xh, S->xh, nb);
+    if (x0) memcpy(x0, S->x0, nb);
+    if (xsum) memcpy(xsum, S->xsum, nb);
+    if (y) memcpy(y, S->y, mb);
+    if (yh) memcpy(yh, S->yh, mb);
+    if (y0) memcpy(y0, S->y0, mb);
+    if (ysum) memcpy(ysum, S->ysum, mb);
+    if (sc) {
+        sc[0] = S->eta; sc[1] = S->omega; sc[2] = S->wsum; sc[3] = (double)S->attempts;
+        sc[4] = (double)S->accepted; sc[5] = (double)S->k; sc[6] = (double)S->restarts;
+        sc[7] = S->phi0; sc[8] = S->phi_prev;
+        sc[9] = S->comp0[0]; sc[10] = S->comp0[1]; sc[11] = S->comp0[2];
+        sc[12] = (double)S->status; sc[13] = (double)S->started;
+    }
+}
+
+void orc_set_state(orc_solver* S, const double* x, const double* xh, const double* x0, const double* xsum,
+                   const double* y, const double* yh, const double* y0, const double* ysum, const double* sc) {
+    size_t nb = sizeof(double) * (size_t)S->n, mb = sizeof(double) * (size_t)S->m;
+    if (x) memcpy(S->x, x, nb);
+    if (xh) memcpy(S->xh, xh, nb);
+    if (x0) memcpy(S->x0, x0, nb);
+    if (xsum) memcpy(S->xsum, xsum, nb);
+    if (y) memcpy(S->y, y, mb);
+    if (yh) memcpy(S->yh, yh, mb);
+    if (y0) memcpy(S->y0, y0, mb);
+    if (ysum) memcpy(S->ysum, ysum, mb);
+    if (sc) {
+        S->eta = sc[0]; S->omega = sc[1]; S->wsum = sc[2]; S->attempts = (int64_t)sc[3];
+        S->accepted = (int64_t)sc[4]; S->k = (int64_t)sc[5]; S->restarts = (int64_t)sc[6];
+        S->phi0 = sc[7]; S->phi_prev = sc[8];
+        S->comp0[0] = sc[9]; S->comp0[1] = sc[10]; S->comp0[2] = sc[11];
+        S->status = (int)sc[12]; S->started = (int)sc[13];
+    }
+}
+
+
 /* ---- KKT of an arbitrary pair for the ORIGINAL program ------------------ */
 int orc_kkt_eval(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                  const double* c, const double* h, const double* lb, const double* ub,

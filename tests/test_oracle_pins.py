@@ -567,6 +567,88 @@ def test_first_pdhg_steps_hand_worked():
     assert yh[0] == pytest.approx(1.0 + eta1, rel=1e-15)
 
 
+def fixed_x_lp():
+    """min x s.t. x >= 0 (one nonnegative row, K = [1], h = 0) with the bound 2 <= x <= 2."""
+    return {"m": 1, "n": 1, "row_ptr": np.array([0, 1]), "col": np.array([0]), "val": np.array([1.0]),
+            "c": np.array([1.0]), "h": np.array([0.0]), "lb": np.array([2.0]), "ub": np.array([2.0]),
+            "cone_types": np.array([oracle.NONNEG]), "cone_dims": np.array([1])}
+
+
+# Hand-worked ReflectedHalpern iterates (Algorithm 1, step 6) on fixed_x_lp from
+# z^{0,0} = (x, y) = (1, 2).  Every PDHG output is the same point: xhat = Proj_[2,2](.) = 2,
+# and yhat = max(y + sigma (0 - (2 xhat - x)), 0) = 0 because y <= 2 and sigma (4 - x) > 2
+# below.  So z^{k+1} = (k+1)/(k+2) ((1 + beta) zhat - beta z^k) + z^0 / (k+2):
+#   beta = 1:   x: 1/2 (4 - 1) + 1/2 = 2;  2/3 (4 - 2) + 1/3 = 5/3;  3/4 (4 - 5/3) + 1/4 = 2;
+#               4/5 (4 - 2) + 1/5 = 9/5
+#               y: 1/2 (0 - 2) + 1 = 0;  2/3 (0 - 0) + 2/3 = 2/3;  3/4 (0 - 2/3) + 1/2 = 0;
+#               4/5 (0 - 0) + 2/5 = 2/5
+#   beta = 1/2: x: 1/2 (3 - 1/2) + 1/2 = 7/4;  2/3 (3 - 7/8) + 1/3 = 7/4;
+#               3/4 (3 - 7/8) + 1/4 = 59/32;  4/5 (3 - 59/64) + 1/5 = 133/80 + 16/80 = 149/80
+#               y: 1/2 (-1) + 1 = 1/2;  2/3 (-1/4) + 2/3 = 1/2;  3/4 (-1/4) + 1/2 = 5/16;
+#               4/5 (-5/32) + 2/5 = -1/8 + 2/5 = 11/40
+HALPERN_STEPS = {
+    1.0: ([2.0, 5 / 3, 2.0, 9 / 5], [0.0, 2 / 3, 0.0, 2 / 5]),
+    0.5: ([7 / 4, 7 / 4, 59 / 32, 149 / 80], [1 / 2, 1 / 2, 5 / 16, 11 / 40]),
+}
+
+
+@pytest.mark.parametrize("beta", [1.0, 0.5])
+def test_reflected_halpern_hand_worked(beta):
+    """Four accepted steps k = 0..3 of the reflected Halpern update with the weights
+    (k+1)/(k+2) and 1/(k+2) and the reflection beta (values worked out above); then the
+    eta-weighted average of Algorithm 1 step 7, sum_i eta_i z^i / sum_i eta_i, with the
+    adaptive step sizes eta_i the oracle used (they vary: 1, 1 - 2^-0.3, ...), so a wrong
+    weight of the average shows.  In this program eta_max = 1.25 > eta at every step, so
+    all four are accepted."""
+    s = oracle.Solver(fixed_x_lp(), rescale=oracle.RESCALE_NONE, beta=beta)
+    s.set_start(np.array([1.0]), np.array([2.0]))
+    xs, ys = HALPERN_STEPS[beta]
+    etas = []
+    for k in range(4):
+        etas.append(s.scalars()["eta"])
+        s.run(1)
+        st = s.state()
+        assert st["xh"][0] == 2.0 and st["yh"][0] == 0.0
+        assert st["accepted"] == k + 1 and st["k"] == k + 1
+        assert st["x"][0] == pytest.approx(xs[k], rel=1e-15, abs=1e-15), (k, st["x"][0], xs[k])
+        assert st["y"][0] == pytest.approx(ys[k], rel=1e-15, abs=1e-15), (k, st["y"][0], ys[k])
+    assert len(set(etas)) == 4  # the step sizes differ, so the weights matter
+    w = np.array(etas)
+    assert st["wsum"] == pytest.approx(w.sum(), rel=1e-15)
+    assert st["xsum"][0] / st["wsum"] == pytest.approx(np.dot(w, xs) / w.sum(), rel=1e-14)
+    assert st["ysum"][0] / st["wsum"] == pytest.approx(np.dot(w, ys) / w.sum(), rel=1e-14)
+    # the unweighted mean differs: the pin above sees the eta weights
+    assert abs(np.mean(xs) - np.dot(w, xs) / w.sum()) > 1e-3
+
+
+def test_constant_step_average_is_the_arithmetic_mean():
+    """SURVEY reading R7: with a constant step every weight of the average is the same, so
+    after four accepted steps it is the plain mean of the hand-worked Halpern iterates,
+    x: (2 + 5/3 + 2 + 9/5) / 4 = 28/15 and y: (0 + 2/3 + 0 + 2/5) / 4 = 4/15."""
+    s = oracle.Solver(fixed_x_lp(), rescale=oracle.RESCALE_NONE, step_mode=oracle.STEP_CONSTANT)
+    s.set_start(np.array([1.0]), np.array([2.0]))
+    s.run(4)
+    st = s.state()
+    assert st["accepted"] == 4
+    assert st["x"][0] == pytest.approx(9 / 5, rel=1e-15)
+    assert st["xsum"][0] / st["wsum"] == pytest.approx(28 / 15, rel=1e-14)
+    assert st["ysum"][0] / st["wsum"] == pytest.approx(4 / 15, rel=1e-14)
+
+
+def test_state_round_trip_resumes_exactly():
+    """orc_set_state(orc_get_state()) on a fresh solver continues bit for bit."""
+    p = I.small_socp(0)
+    a = oracle.Solver(p, check_period=16)
+    a.run(40)
+    b = oracle.Solver(p, check_period=16)
+    b.set_state(a.state())
+    a.run(30)
+    b.run(30)
+    sa, sb = a.state(), b.state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+
+
 @pytest.mark.parametrize("rescale", [oracle.RESCALE_NONE, oracle.RESCALE_COORD])
 def test_known_optimum_is_a_fixed_point(rescale):
     p = I.small_socp(0)
