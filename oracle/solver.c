@@ -34,6 +34,9 @@
  *             SOC / RSOC / exp block shares one factor.
  *   dual obj: h'y + sum_j (l_j mu_j^+ - u_j mu_j^-) with mu = Proj_Lambda(lambda)
  *             and 0 * inf = 0.
+ *   sums    : every sum over a whole vector is compensated (Neumaier), so it is the
+ *             exact sum of its rounded terms to about one rounding; sums along a row
+ *             of K (the matrix-vector products) are plain left-to-right sums.
  */
 #include "pdcs_oracle.h"
 #include <math.h>
@@ -82,10 +85,23 @@ static void spmv(int64_t rows, const int64_t* rp, const int32_t* ci, const doubl
     }
 }
 
+/* Sums over whole vectors (norms, inner products, the KKT and step-size quantities) are
+ * accumulated with Neumaier's compensation (improved Kahan-Babuska summation): the
+ * result is within about one rounding of the exact sum of the (rounded) terms, whatever
+ * the length, where a plain left-to-right sum of 1e6 terms is off by ~1e-14. */
+typedef struct { double s, c; } acc_t;
+static void acc_add(acc_t* a, double v) {
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else a->c += (v - t) + a->s;
+    a->s = t;
+}
+static double acc_val(const acc_t* a) { return a->s + a->c; }
+
 static double dot(int64_t k, const double* a, const double* b) {
-    double s = 0.0;
-    for (int64_t i = 0; i < k; ++i) s += a[i] * b[i];
-    return s;
+    acc_t s = {0.0, 0.0};
+    for (int64_t i = 0; i < k; ++i) acc_add(&s, a[i] * b[i]);
+    return acc_val(&s);
 }
 
 /* Proj onto Lambda_j (eq. defn_Lambda1) */
@@ -125,8 +141,9 @@ static void eval_pair(const orc_solver* S, const double* xt, const double* yt, c
     /* scaled primal residual: v - Proj_{Dr C}(v), v = K~x~ - h~ */
     for (int64_t i = 0; i < m; ++i) v[i] = Kx[i] - S->hs[i];
     orc_proj_cones(v, S->dr, m, S->types, S->dims, S->n_cones, 0, p);
-    double rp2 = 0.0;
-    for (int64_t i = 0; i < m; ++i) rp2 += (v[i] - p[i]) * (v[i] - p[i]);
+    acc_t rp2a = {0.0, 0.0};
+    for (int64_t i = 0; i < m; ++i) acc_add(&rp2a, (v[i] - p[i]) * (v[i] - p[i]));
+    double rp2 = acc_val(&rp2a);
 
     /* unscaled primal residual: K x - h = (K~x~ - h~) / dr, projected onto C */
     for (int64_t i = 0; i < m; ++i) v[i] = v[i] / S->dr[i];
@@ -140,19 +157,21 @@ static void eval_pair(const orc_solver* S, const double* xt, const double* yt, c
     }
 
     /* dual: lambda = c - K'y; scaled lambda~ = dc * lambda */
-    double rd2 = 0.0, dmax = 0.0, cmax = 0.0, ktymax = 0.0, bterm = 0.0, pobj = 0.0;
+    double dmax = 0.0, cmax = 0.0, ktymax = 0.0;
+    acc_t rd2a = {0.0, 0.0}, bterma = {0.0, 0.0}, pobja = {0.0, 0.0};
     for (int64_t j = 0; j < n; ++j) {
         double lam = S->cs[j] - KTy[j];
         double mu = proj_lambda(lam, S->ls[j], S->us[j]);
-        rd2 += (lam - mu) * (lam - mu);
-        bterm += bound_term(S->ls[j], S->us[j], mu);
+        acc_add(&rd2a, (lam - mu) * (lam - mu));
+        acc_add(&bterma, bound_term(S->ls[j], S->us[j], mu));
         double lamu = lam / S->dc[j];
         double muu = proj_lambda(lamu, S->l0[j], S->u0[j]);
         dmax = fmax(dmax, fabs(lamu - muu));
         cmax = fmax(cmax, fabs(S->c0[j]));
         ktymax = fmax(ktymax, fabs(KTy[j] / S->dc[j]));
-        pobj += S->cs[j] * xt[j];
+        acc_add(&pobja, S->cs[j] * xt[j]);
     }
+    double rd2 = acc_val(&rd2a), bterm = acc_val(&bterma), pobj = acc_val(&pobja);
     double dobj = dot(m, S->hs, yt) + bterm;
     double gap = fabs(pobj - dobj);
     r->rp2 = rp2;
@@ -441,8 +460,11 @@ static void check(orc_solver* S, double tol) {
     if (!restart) return;
     /* PrimalWeightUpdate */
     double dx = 0.0, dy = 0.0;
-    for (int64_t j = 0; j < n; ++j) dx += (cx[best][j] - S->x0[j]) * (cx[best][j] - S->x0[j]);
-    for (int64_t i = 0; i < m; ++i) dy += (cy[best][i] - S->y0[i]) * (cy[best][i] - S->y0[i]);
+    acc_t dxa = {0.0, 0.0}, dya = {0.0, 0.0};
+    for (int64_t j = 0; j < n; ++j) acc_add(&dxa, (cx[best][j] - S->x0[j]) * (cx[best][j] - S->x0[j]));
+    for (int64_t i = 0; i < m; ++i) acc_add(&dya, (cy[best][i] - S->y0[i]) * (cy[best][i] - S->y0[i]));
+    dx = acc_val(&dxa);
+    dy = acc_val(&dya);
     dx = sqrt(dx);
     dy = sqrt(dy);
     if (dx > 1e-10 && dy > 1e-10) S->omega = exp(0.5 * log(dy / dx) + 0.5 * log(S->omega));
@@ -496,12 +518,14 @@ static void attempt(orc_solver* S) {
         /* AdaptiveStepPDHG */
         for (int64_t j = 0; j < n; ++j) dxv[j] = S->xh[j] - S->x[j];
         spmv(m, S->rp, S->ci, S->val, dxv, Kdx);
-        double nx = dot(n, dxv, dxv), ny = 0.0, inter = 0.0;
+        double nx = dot(n, dxv, dxv);
+        acc_t nya = {0.0, 0.0}, intera = {0.0, 0.0};
         for (int64_t i = 0; i < m; ++i) {
             double dy = S->yh[i] - S->y[i];
-            ny += dy * dy;
-            inter += dy * Kdx[i];
+            acc_add(&nya, dy * dy);
+            acc_add(&intera, dy * Kdx[i]);
         }
+        double ny = acc_val(&nya), inter = acc_val(&intera);
         inter = fabs(inter);
         double move = S->omega * nx + ny / S->omega;
         double eta_max = inter > 0.0 ? move / (2.0 * inter) : INFINITY;

@@ -635,6 +635,26 @@ def test_constant_step_average_is_the_arithmetic_mean():
     assert st["ysum"][0] / st["wsum"] == pytest.approx(4 / 15, rel=1e-14)
 
 
+def test_vector_sums_are_compensated():
+    """The oracle's sums over whole vectors are within about one rounding of the exact sum:
+    omega_0 = ||c|| / ||h|| on a 400k-row diagonal program (no rescaling) against math.fsum
+    of the same squares (a left-to-right sum of that many terms is off by ~1e-14)."""
+    import math
+    rng = np.random.default_rng(11)
+    m = 400_000
+    c = rng.standard_normal(m) * np.exp(rng.normal(0, 1, m))
+    h = rng.standard_normal(m) * np.exp(rng.normal(0, 1, m))
+    p = {"m": m, "n": m, "row_ptr": np.arange(m + 1), "col": np.arange(m, dtype=np.int32), "val": np.ones(m),
+         "c": c, "h": h, "lb": None, "ub": None, "cone_types": np.array([oracle.ZERO]), "cone_dims": np.array([m])}
+    s = oracle.Solver(p, rescale=oracle.RESCALE_NONE)
+    ref = math.sqrt(math.fsum((c * c).tolist())) / math.sqrt(math.fsum((h * h).tolist()))
+    assert abs(s.scalars()["omega"] - ref) <= 4e-16 * ref
+    seq = 0.0
+    for t in (c * c).tolist():
+        seq += t
+    assert abs(math.sqrt(seq) / math.sqrt(math.fsum((h * h).tolist())) - ref) > 4e-16 * ref  # the plain sum is not
+
+
 def test_state_round_trip_resumes_exactly():
     """orc_set_state(orc_get_state()) on a fresh solver continues bit for bit."""
     p = I.small_socp(0)
