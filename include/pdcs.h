@@ -63,7 +63,8 @@ typedef enum {
     PDCS_ERR_CUDA = 2,           /* a CUDA call failed (text in pdcs_last_error) */
     PDCS_ERR_OOM = 3,            /* device allocation failed */
     PDCS_ERR_NUMERIC = 4,        /* a NaN / Inf appeared in the iterates */
-    PDCS_ERR_DEVICE_TIMEOUT = 5, /* a bounded device wait gave up */
+    PDCS_ERR_DEVICE_TIMEOUT = 5, /* a bounded device wait gave up; reserved: no kernel of this
+                                    version waits on another, so no call returns it */
     PDCS_MAX_ITER = 10,          /* max_iter PDHG evaluations done without reaching tol */
     PDCS_TIME_LIMIT = 11         /* options.time_limit seconds passed without reaching tol */
 } pdcs_status;
@@ -104,6 +105,16 @@ typedef struct {
     int32_t batch_blocks;   /* 0 (default): grids sized per kernel; > 0: every vector / cone kernel
                                of this program runs on exactly this many blocks (needed to join a
                                batch, whose programs share one grid; see pdcs_batch_create) */
+    int32_t spmv_format;    /* storage of K~ and K~' for the SpMV: 1 rows binned by length (one to
+                               32 lanes per row, see spmv_lanes / spmv_autotune); 2 sliced: rows of
+                               at most 256 entries sorted by length in slices of 32, one lane per row
+                               reading its entries in pairs by 128-bit loads, longer rows one warp
+                               each (spmv_autotune then has no effect); 0 (default): 2 for single
+                               programs, 1 when batch_blocks > 0 or spmv_lanes > 0 */
+    int32_t soc_lane_entries; /* FP64 dual update of single programs: each SOC / RSOC cone of at
+                               most 256 rows is projected by a group of S lanes (S a power of two,
+                               the smallest with dim <= S * soc_lane_entries), 32 / S cones per
+                               warp; 0 (default): 4 */
 } pdcs_options;
 
 typedef struct {
@@ -118,7 +129,9 @@ typedef struct {
     int32_t status;               /* pdcs_status of the last pdcs_solve */
     int32_t fp64_phase;           /* 1 once FP32 mode has switched to FP64 polishing */
     int64_t kernel_launches;      /* kernels this context has launched so far (graph nodes included) */
-    int32_t spmv_plan[4];         /* SpMV plans in use: bin shift and unroll of K, then of K' */
+    int32_t spmv_plan[4];         /* SpMV plans in use: bin shift and unroll of K, then of K'
+                                     (binned format) */
+    int32_t spmv_format;          /* SpMV storage in use: 1 binned, 2 sliced */
 } pdcs_info;
 
 typedef struct pdcs_ctx pdcs_ctx;
@@ -160,8 +173,59 @@ pdcs_status pdcs_get_scaling(pdcs_ctx* ctx, double* dr, double* dc);
 pdcs_status pdcs_get_info(pdcs_ctx* ctx, pdcs_info* info);
 
 /* Sets the starting point z^{0,0} = (x, y) (original scaling; NULL means 0) and,
- * when omega > 0, the initial primal weight; resets the counters. */
+ * when omega > 0, the initial primal weight; resets the counters, the restart state and
+ * a NaN / Inf status.  The step size eta is kept (the last one of the previous solve, or
+ * 1 / max |K~ij| after pdcs_create), as the oracle's warm start does. */
 pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y, double omega);
+
+/* Scalars of Algorithm 1 carried by pdcs_get_state / pdcs_set_state. */
+typedef struct {
+    double eta;        /* step size of the next PDHG evaluation */
+    double omega;      /* primal weight */
+    double wsum;       /* sum of the average's weights (step sizes) since the last restart */
+    double phi0;       /* restart metric of the anchor z^{t,0} of the current restart period */
+    double phi_prev;   /* restart metric of the previous check's candidate (INFINITY: none yet) */
+    double comp0[3];   /* ||r_p||^2, ||r_d||^2 and |gap| of the anchor (rescaled program) */
+    int64_t attempts;  /* PDHG evaluations so far (accepted or rejected) */
+    int64_t accepted;  /* accepted steps so far */
+    int64_t k;         /* accepted steps since the last restart (inner index of Algorithm 1) */
+    int64_t restarts;  /* restarts so far */
+    int32_t started;   /* 1 once the first anchor has been evaluated; 0: the next pdcs_solve
+                          evaluates z^{0,0} first, as after pdcs_create */
+    int32_t status;    /* 0 running, 1 converged, 2 NaN / Inf seen */
+} pdcs_state;
+
+/* The vectors of the iterate state, in the coordinates of the rescaled program
+ * (x~ = x / dc, y~ = y / dr with the scalings of pdcs_get_scaling; rows in the original
+ * order).  HOST pointers; any may be NULL. */
+typedef struct {
+    double *x, *xhat, *x0, *xsum;  /* n each: z^{t,k}, last PDHG output, anchor z^{t,0},
+                                      sum of eta_i x^{t,i} (Algorithm 1 steps 6-7) */
+    double *y, *yhat, *y0, *ysum;  /* m each: the same for y */
+    double *kx, *kx0;              /* m each: cached products K~ x, K~ x0 */
+    double *kty, *kty0;            /* n each: cached products K~' y, K~' y0 */
+    float* soc_root;               /* one per SOC / RSOC cone (cone-list order): the last root
+                                      of Theorem 1's search, the next search's starting point */
+    float* exp_root;               /* one per exp cone: the same for Theorem 3's search */
+} pdcs_state_arrays;
+
+/* Checkpoint: copies the whole iterate state of Algorithm 1 into the non-NULL arrays of
+ * *arr and the scalars into *st (may be NULL).  A pending Halpern update of the last
+ * accepted evaluation is applied first (with the arithmetic the next evaluation would use,
+ * so the iterates that follow are unchanged).  FP64 phase only: PDCS_ERR_INVALID while an
+ * FP32-iterate phase runs. */
+pdcs_status pdcs_get_state(pdcs_ctx* ctx, pdcs_state* st, const pdcs_state_arrays* arr);
+
+/* Resume: replaces the iterate state by *st and the arrays of *arr: x, x0, y, y0 are
+ * required; xsum / ysum NULL mean 0; xhat, yhat are ignored (the next evaluation forms
+ * them); when one of kx, kx0, kty, kty0 is NULL the four cached products are recomputed
+ * by the library's SpMV from x, x0, y, y0 (equal to the cached ones up to rounding);
+ * soc_root / exp_root NULL leave the searches' starting points as they are (they change
+ * results only in the last bits); with the products and both of them given, a state from
+ * pdcs_get_state resumes the iteration bit for bit.  The tolerance is set by the next
+ * pdcs_solve.  Afterwards the context runs the FP64 iteration, also in FP32 mode.
+ * Errors: PDCS_ERR_INVALID (NULL or non-finite required data, status outside 0..2). */
+pdcs_status pdcs_set_state(pdcs_ctx* ctx, const pdcs_state* st, const pdcs_state_arrays* arr);
 
 /* Kernel timing for roofline measurements: runs `attempts` more PDHG evaluations
  * (and the checks that fall due) launch by launch, with CUDA events recorded on

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpdcs.so")
-SOURCES = ["solver.cu", "proj.cu", "proj_noalloc.cu", "exp_mlp.cu", "mlp.cu"]
+SOURCES = ["solver.cu", "kern_f64.cu", "kern_f32.cu", "kern_batch.cu", "proj.cu", "proj_noalloc.cu", "exp_mlp.cu",
+           "mlp.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-diag-suppress", "1444"]

@@ -167,6 +167,8 @@ __device__ inline void exp_project_f32(float r0, float s0, float t0, float dr, f
     e.a4m1 = r0 > 0.0f ? -(s0 * ds) / (r0 * dr) : -1.0f;
     e.a4 = r0 > 0.0f ? 1.0f + e.a4m1 : 0.0f;
     e.w34 = e.a3 - e.a4;
+    e.dt3 = s0 > 0.0f ? e.a3 * (e.a3 - 1.0f) + e.tau * e.tau : 0.0f;  // d~ at the interval ends
+    e.dt4 = r0 > 0.0f ? e.a4 * e.a4m1 + e.tau * e.tau : 0.0f;
     int evals = 0;
     float L = 0.0f;
     bool ok = isfinite(e.a3) && isfinite(e.a4) && exp_case4_solve(e, L_cache ? *L_cache : NAN, L, evals, mlp) && !(L != L);

@@ -607,6 +607,187 @@ __device__ void rsoc_project_warp_mp(double* buf, WF wf, const double* __restric
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// Second-order cone by lane groups (segmented warps).  S lanes (a power of two) project
+// one cone staged in shared memory, 32 / S cones side by side in a warp; lane g of a group
+// takes the x entries i = g, g + S, ...  On this GPU an FP64 warp instruction takes the
+// same time whatever lanes are active, so the steps done once per cone (case tests, psi,
+// the Newton steps, square roots) cost 32 / S times less per cone than with a warp per
+// cone, and the sums need log2 S shuffle levels instead of five.  Same mathematics and
+// precision scheme as soc_project_warp_fast: FP32 search, at most three FP64 Newton
+// steps with refined reciprocals, FP64 output; FP64 search as fallback.
+//   v      : the cone's staged rows (t, x_1 .. x_{dim-1}) in shared memory, projected in place
+//   w, wi  : weights of the x entries and their inverses (global memory)
+//   xf, wf : dim - 1 floats each of shared-memory scratch
+//   gmask  : the group's lanes, g: this lane's index in the group
+// ---------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ double seg_sum(double v, unsigned gmask) {
+#pragma unroll
+    for (int o = S / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
+    return v;
+}
+template <int S>
+__device__ __forceinline__ float seg_sum_f(float v, unsigned gmask) {
+#pragma unroll
+    for (int o = S / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
+    return v;
+}
+
+template <int S>
+__device__ void soc_seg_project(double* v, const double* __restrict__ w, const double* __restrict__ wi, float* xf,
+                                float* wf, int dim, bool rot, float* cache, unsigned gmask, int g) {
+    const double r2 = 0.70710678118654752440;
+    if (rot) {
+        if (g == 0) {
+            const double p = v[0], q = v[1];
+            v[0] = (p + q) * r2;
+            v[1] = (p - q) * r2;
+        }
+        __syncwarp(gmask);
+    }
+    const int nx = dim - 1;
+    const double t = v[0];
+    double a = 0.0, b = 0.0;  // ||Dhat x||^2, ||Dhat^{-1} x||^2
+    bool rng = fabs(t) < 1e30 && fabs(t) > 1e-30;
+    for (int i = g; i < nx; i += S) {
+        const double x = v[1 + i], wv = w[i];
+        const double x2 = x * x;
+        a += x2 * wi[i];
+        b += wv * x2;
+        xf[i] = (float)x;
+        wf[i] = (float)wv;
+        rng = rng && wv < 1e30 && wv > 1e-30 && fabs(x) < 1e30;
+    }
+    a = seg_sum<S>(a, gmask);
+    b = seg_sum<S>(b, gmask);
+    if (S > 1) rng = __all_sync(gmask, rng);
+    const double nDx = sqrt(a), nDinvx = sqrt(b);
+    rng = rng && nDinvx < 1e30;
+    double mu = -1.0;  // < 0: v unchanged (case 2)
+    if (t <= 0.0 && nDx <= -t) {
+        mu = 0.0;  // case 1: zero (marked below)
+    } else if (!(nDinvx <= t)) {
+        mu = 1.0;  // case 3 (t == 0)
+        if (t != 0.0) {  // case 4
+            bool known, near = t > 0.0 && soc_cached_near(cache, known);
+            if (t > 0.0 && !known) {  // sign of psi at mu = 1/2
+                if (rng) {
+                    float Sf = 0.0f;
+                    for (int i = g; i < nx; i += S) {
+                        const float r = __frcp_rn(1.0f + 0.5f * wf[i]);
+                        Sf += wf[i] * xf[i] * xf[i] * r * r;
+                    }
+                    near = 0.5f * sqrtf(seg_sum_f<S>(Sf, gmask)) < (float)t;
+                } else {
+                    double Sd = 0.0;
+                    for (int i = g; i < nx; i += S) {
+                        const double x = v[1 + i], r = 1.0 / (1.0 + 0.5 * w[i]);
+                        Sd += w[i] * x * x * r * r;
+                    }
+                    near = 0.5 * sqrt(seg_sum<S>(Sd, gmask)) < t;
+                }
+            }
+            const SocVar<double> V(t, near);
+            const SocVar<float> Vf(V);
+            bool conv = false;
+            double u = 0.0;
+            if (rng) {
+                auto ev32 = [&](float uu, float& ph, float& dph, float& sc) {
+                    float Sf = 0.0f, S2 = 0.0f;
+                    const float m = Vf.mu(uu);
+                    for (int i = g; i < nx; i += S) {
+                        const float r = __frcp_rn(1.0f + m * wf[i]);
+                        const float term = wf[i] * xf[i] * xf[i] * r * r;
+                        Sf += term;
+                        S2 += wf[i] * term * r;
+                    }
+                    Sf = seg_sum_f<S>(Sf, gmask);
+                    S2 = seg_sum_f<S>(S2, gmask);
+                    Vf.psi(uu, sqrtf(Sf), S2, ph, dph, sc);
+                };
+                const float uf = soc_root<float>(ev32, V.tpos, (float)V.guess(t, nDinvx, cache), 2e-6f, 2e-7f, 100);
+                u = (double)uf;
+                if (uf > 0.0f && isfinite(uf)) {
+                    for (int it = 0; it < 3; ++it) {
+                        double Sd = 0.0, S2 = 0.0;
+                        const double m = V.mu(u);
+                        for (int i = g; i < nx; i += S) {
+                            const double x = v[1 + i], wv = w[i];
+                            const double r = rcp_refined(1.0 + m * wv);
+                            const double term = wv * x * x * r * r;
+                            Sd += term;
+                            S2 += wv * term * r;
+                        }
+                        Sd = seg_sum<S>(Sd, gmask);
+                        S2 = seg_sum<S>(S2, gmask);
+                        double ph, dph, sc;
+                        V.psi(u, sqrt(Sd), S2, ph, dph, sc);
+                        if (fabs(ph) <= 1.6e-15 * sc) {  // zero to working precision
+                            u = fmax(u, 0.0);
+                            conv = true;
+                            break;
+                        }
+                        const double step = ph / dph;
+                        if (!isfinite(step)) break;
+                        u -= step;
+                        if (fabs(step) <= (it == 0 ? 1e-7 : RootTolSoc) * (V.tpos ? fmin(u, 1.0 - u) : u)) {
+                            conv = true;
+                            break;
+                        }
+                    }
+                    conv = conv && u >= 0.0 && (!V.tpos || u < 1.0);
+                }
+            }
+            if (!conv) {  // full FP64 safeguarded search
+                auto ev = [&](double uu, double& ph, double& dph, double& sc) {
+                    double Sd = 0.0, S2 = 0.0;
+                    const double m = V.mu(uu);
+                    for (int i = g; i < nx; i += S) {
+                        const double x = v[1 + i], wv = w[i];
+                        const double r = 1.0 / (1.0 + m * wv);
+                        const double term = wv * x * x * r * r;
+                        Sd += term;
+                        S2 += wv * term * r;
+                    }
+                    Sd = seg_sum<S>(Sd, gmask);
+                    S2 = seg_sum<S>(S2, gmask);
+                    V.psi(uu, sqrt(Sd), S2, ph, dph, sc);
+                };
+                u = soc_root<double>(ev, V.tpos, V.guess(t, nDinvx, nullptr), RootTolSoc, 4e-16, 200);
+            }
+            if (cache && g == 0) *cache = V.store(u);
+            mu = V.mu(u);
+        }
+    }
+    if (mu == 0.0) {  // case 1
+        for (int i = g; i < nx; i += S) v[1 + i] = 0.0;
+        __syncwarp(gmask);
+        if (g == 0) v[0] = 0.0;
+    } else if (mu > 0.0) {
+        // y = (I + 2 lambda Dhat^{-2})^{-1} x ;  s = ||Dhat^{-1} y||
+        double s = 0.0;
+        for (int i = g; i < nx; i += S) {
+            const double wv = w[i];
+            const double y = v[1 + i] * rcp_refined(1.0 + mu * wv);
+            s += wv * y * y;
+            v[1 + i] = y;
+        }
+        s = seg_sum<S>(s, gmask);
+        __syncwarp(gmask);
+        if (g == 0) v[0] = sqrt(s);
+    }
+    __syncwarp(gmask);
+    if (rot) {
+        if (g == 0) {
+            const double p = v[0], q = v[1];
+            v[0] = (p + q) * r2;
+            v[1] = (p - q) * r2;
+        }
+        __syncwarp(gmask);
+    }
+}
+
 // Picks the register count for the block (dim - 1 <= 128, weights from wf); larger blocks
 // use the FP64 memory-loop projection with weights formed from the scales d (kInv as there).
 template <bool kInv, typename WF>
@@ -682,6 +863,7 @@ template <> struct RootTol<float> {
 template <typename R>
 struct ExpCase4T {
     R r0, s0, t0, dr, ds, tau, a3, a4, a4m1, w34, ldt, dir, lt0, lr0, ls0, ldr, lds;
+    R dt3, dt4;  // d~ = rho (rho - 1) + tau^2 at rho = a3 and at rho = a4
     int anchor;  // 3 or 4: endpoint rho is measured from
     int slo;     // sign of F next to the anchor when the root is inside the interval
     bool dm;     // F finite at the anchor: affine in delta = e^L next to it
@@ -705,11 +887,10 @@ template <typename R>
 __host__ __device__ __forceinline__ void exp_eval(const ExpCase4T<R>& e, R L, ExpAt<R>& o) {
     const R one = R(1), zero = R(0);
     const R delta = exp(L);
-    R rho, rm1, lst, lrt, dlst, dlrt;  // rm1 = rho - 1 from the exact offset; logs of |s~|, |r~|
+    R rho, lst, lrt, dlst, dlrt;  // logs of |s~|, |r~| and their derivatives
     int sst, srt;
     if (e.anchor == 4) {
         rho = e.a4 + e.dir * delta;
-        rm1 = e.a4m1 + e.dir * delta;
         lst = e.lr0 + L;
         dlst = one;
         sst = e.dir > zero ? 1 : -1;
@@ -719,7 +900,6 @@ __host__ __device__ __forceinline__ void exp_eval(const ExpCase4T<R>& e, R L, Ex
         srt = (rt > zero) - (rt < zero);
     } else {
         rho = e.a3 + e.dir * delta;
-        rm1 = (e.a3 - one) + e.dir * delta;
         lrt = e.ls0 + L;
         dlrt = one;
         srt = e.dir < zero ? 1 : -1;
@@ -728,7 +908,9 @@ __host__ __device__ __forceinline__ void exp_eval(const ExpCase4T<R>& e, R L, Ex
         dlst = (e.r0 / st) * e.dir * delta;
         sst = (st > zero) - (st < zero);
     }
-    const R dt_ = rho * rm1 + e.tau * e.tau;  // d~ = rho (rho - 1) + tau^2
+    // d~ = rho (rho - 1) + tau^2 at rho = anchor + dd, as d~(anchor) + dd (2 anchor - 1 + dd)
+    const R dd = e.dir * delta;
+    const R dt_ = e.anchor == 4 ? e.dt4 + dd * ((R(2) * e.a4m1 + one) + dd) : e.dt3 + dd * ((R(2) * e.a3 - one) + dd);
     const int sdt = (dt_ > zero) - (dt_ < zero);
     const R ldt_ = log(fabs(dt_));
     const R dldt = ((R(2) * rho - one) / dt_) * e.dir * delta;
@@ -1024,11 +1206,58 @@ __host__ __device__ __forceinline__ bool exp_case4_solve(ExpCase4T<R>& e, R gues
     return true;
 }
 
+// Error-free transformations (Dekker 1971; Knuth, TAOCP vol. 2): a * b = p + e and
+// a + b = s + e exactly in binary floating point.
+__host__ __device__ __forceinline__ double two_prod(double a, double b, double& e) {
+    const double p = a * b;
+    e = fma(a, b, -p);
+    return p;
+}
+__host__ __device__ __forceinline__ double two_sum(double a, double b, double& e) {
+    const double s = a + b, bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+// Theorem 3's quantities at the ends of the case-4 interval (a3, a4 of eq. lrho_urho and
+// d~(rho) = rho (rho - 1) + tau^2, tau = ds / dr), in FP64.  With
+// N = tau (r0^2 + s0^2) - r0 s0 they satisfy the exact identities
+//     a3 - a4 = N / (r0 s0),   d~(a3) = tau N / s0^2,   d~(a4) = tau N / r0^2.
+// For r0, s0 > 0 the difference in N cancels exactly where the interval is narrow or d~ is
+// small on it; N is formed from error-free products and sums of r0, s0 scaled by one power
+// of two (exact), so it keeps the digits that a3 - a4 and rho (rho - 1) + tau^2 would lose.
+struct ExpEnds {
+    double a3, a4, a4m1, w34, dt3, dt4;
+};
+__host__ __device__ __forceinline__ ExpEnds exp_ends(double r0, double s0, double dr, double ds) {
+    ExpEnds o;
+    const double tau = ds / dr;
+    o.a3 = (s0 > 0.0) ? (r0 * ds) / (s0 * dr) : 0.0;
+    o.a4m1 = (r0 > 0.0) ? -(s0 * ds) / (r0 * dr) : -1.0;
+    o.a4 = (r0 > 0.0) ? 1.0 + o.a4m1 : 0.0;
+    const double mx = fmax(fabs(r0), fabs(s0));
+    int k = 0;
+    frexp(mx, &k);
+    const double r = ldexp(r0, -k), s = ldexp(s0, -k);
+    double e1, e2, eS, eq, e3, eD;
+    const double p1 = two_prod(r, r, e1), p2 = two_prod(s, s, e2);
+    const double S = two_sum(p1, p2, eS);
+    const double q = two_prod(tau, S, eq);
+    const double p3 = two_prod(r, s, e3);
+    const double Dq = two_sum(q, -p3, eD);
+    const double N = Dq + (eD + eq + tau * (eS + e1 + e2) - e3);  // N / 2^(2k)
+    o.w34 = (r0 > 0.0 && s0 > 0.0) ? N / (r * s) : o.a3 - o.a4;
+    o.dt3 = s0 > 0.0 ? tau * N / (s * s) : 0.0;
+    o.dt4 = r0 > 0.0 ? tau * N / (r * r) : 0.0;
+    return o;
+}
+
 // Fills the case-4 data of v0 = (r0, s0, t0), D = diag(dr, ds, dt), in precision R
-// from values given in double (logs of the scales passed in).
+// from values given in double (logs of the scales and the endpoint quantities passed in).
 template <typename R>
 __host__ __device__ __forceinline__ void exp_case4_setup(ExpCase4T<R>& e, double r0, double s0, double t0, double dr,
-                                                         double ds, R ldr, R lds, R ldt, int anchor = 0) {
+                                                         double ds, R ldr, R lds, R ldt, const ExpEnds& q,
+                                                         int anchor = 0) {
     e.r0 = R(r0); e.s0 = R(s0); e.t0 = R(t0); e.dr = R(dr); e.ds = R(ds);
     e.tau = R(ds / dr);
     e.ldt = ldt; e.ldr = ldr; e.lds = lds;
@@ -1037,10 +1266,12 @@ __host__ __device__ __forceinline__ void exp_case4_setup(ExpCase4T<R>& e, double
     e.lr0 = (anchor != 3 && r0 > 0.0) ? R(log(R(r0))) : ninf;
     e.ls0 = (anchor != 4 && s0 > 0.0) ? R(log(R(s0))) : ninf;
     e.lt0 = t0 > 0.0 ? R(log(R(t0))) : (t0 < 0.0 ? R(log(R(-t0))) : ninf);
-    e.a3 = (s0 > 0.0) ? R((r0 * ds) / (s0 * dr)) : R(0);
-    e.a4 = (r0 > 0.0) ? R(1.0 - (s0 * ds) / (r0 * dr)) : R(0);
-    e.a4m1 = (r0 > 0.0) ? R(-(s0 * ds) / (r0 * dr)) : R(-1);
-    e.w34 = e.a3 - e.a4;
+    e.a3 = R(q.a3);
+    e.a4 = R(q.a4);
+    e.a4m1 = R(q.a4m1);
+    e.w34 = R(q.w34);
+    e.dt3 = R(q.dt3);
+    e.dt4 = R(q.dt4);
 }
 
 // Result of case 4 at the root L (eq. vpvd_defn with v0 = v_p + v_d, eq. diagonal_moreau):
@@ -1097,7 +1328,7 @@ __host__ __device__ inline void exp_project(double r0, double s0, double t0, dou
         return;
     }
     ExpCase4 e;
-    exp_case4_setup(e, r0, s0, t0, dr, ds, log(dr), log(ds), log(dt));
+    exp_case4_setup(e, r0, s0, t0, dr, ds, log(dr), log(ds), log(dt), exp_ends(r0, s0, dr, ds));
     const double guess = L_cache ? *L_cache : NAN;
     double L;
     if (!exp_case4_solve(e, guess, L, evals)) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
@@ -1176,6 +1407,83 @@ __host__ __device__ __forceinline__ R exp_gap_to_polar(R r0, R s0, R t0, R dr, R
     return t0 <= tq ? R(0) : t0 - tq;
 }
 
+// ---------------------------------------------------------------------------
+// Case-4 finish in the linear domain.  Away from the extremes (|rho| < 600, offset from the
+// anchor above 1e-250) h of eq. h_rho and its derivative are formed directly from
+// s~, r~ (eq. tilde_defs) and d~ at the offset delta of rho from the anchor:
+//   h = d_t e^rho s_p - d_t^{-1} e^{-rho} r_d - t0,  s_p = s~ / (d_r d~),  r_d = d_s r~ / d~,
+//   ds_p/drho = (r0 / d_r - s_p (2 rho - 1)) / d~,  dr_d/drho = (-d_s s0 - r_d (2 rho - 1)) / d~,
+// (s~ = r0 (rho - a4) and r~ = s0 (a3 - rho) are affine in rho), one FP64 exp and three
+// divisions per evaluation, where the log-domain evaluation needs five transcendentals.
+// Newton's method in delta from the FP32 root; once a step is below 1e-8 min(1, delta) the
+// result follows from the values at the last point to first order (error of order the
+// step squared), per coordinate the smaller part as in exp_case4_output.
+// ---------------------------------------------------------------------------
+struct ExpLin {
+    double rho, E, iE, sp, rd, sp_r, rd_r, h, dh;  // E = d_t e^rho, iE = 1 / E, *_r: d/drho
+};
+
+__host__ __device__ __forceinline__ bool exp_lin_eval(const ExpCase4& e, double idr, double delta, ExpLin& o) {
+    const double dd = e.dir * delta;  // rho - anchor
+    double rho, st, rt;
+    if (e.anchor == 4) {
+        rho = e.a4 + dd;
+        st = e.r0 * dd;
+        rt = (e.kind == 1) ? e.s0 * (e.w34 - dd) : e.tau * e.r0 - rho * e.s0;
+    } else {
+        rho = e.a3 + dd;
+        rt = -e.s0 * dd;
+        st = (e.kind == 1) ? e.r0 * (e.w34 + dd) : e.s0 * e.tau - e.r0 + e.r0 * rho;
+    }
+    const double dt_ = e.anchor == 4 ? e.dt4 + dd * ((2.0 * e.a4m1 + 1.0) + dd) : e.dt3 + dd * ((2.0 * e.a3 - 1.0) + dd);
+    const double id = 1.0 / dt_;
+    o.rho = rho;
+    o.sp = st * id * idr;
+    o.rd = e.ds * rt * id;
+    o.E = exp(e.ldt + rho);
+    o.iE = 1.0 / o.E;
+    const double g = 2.0 * rho - 1.0;
+    o.sp_r = (e.r0 * idr - o.sp * g) * id;
+    o.rd_r = (-e.ds * e.s0 - o.rd * g) * id;
+    o.h = o.E * o.sp - o.iE * o.rd - e.t0;
+    o.dh = e.dir * (o.E * (o.sp + o.sp_r) + o.iE * (o.rd - o.rd_r));
+    return o.sp > 0.0 && o.rd > 0.0 && o.E > 0.0 && o.E < INFINITY && isfinite(o.h) && isfinite(o.dh) && o.dh != 0.0;
+}
+
+// delta0: offset of the FP32 root; hi: upper end of the offsets (the half interval for
+// r0, s0 > 0, else infinite).  Returns false when the point leaves (0, hi) or does not settle.
+__host__ __device__ __forceinline__ bool exp_lin_polish(const ExpCase4& e, double delta0, double hi, double r0, double s0,
+                                                        double t0, double dr, double ds, double* out, double* L_out,
+                                                        int* ev) {
+    const double idr = 1.0 / dr;
+    double delta = delta0;
+    for (int it = 0; it < 4; ++it) {
+        ExpLin a;
+        if (!exp_lin_eval(e, idr, delta, a)) return false;
+        if (ev) ev[1] += 1;
+        const double s = -a.h / a.dh;
+        if (!isfinite(s)) return false;
+        if (fabs(s) <= 1e-8 * fmin(1.0, delta)) {
+            const double ds_ = e.dir * s;  // change of rho
+            const double rho = a.rho + ds_;
+            const double sp = a.sp + ds_ * a.sp_r, rd = a.rd + ds_ * a.rd_r;
+            const double E = a.E * (1.0 + ds_), iE = a.iE * (1.0 - ds_);
+            const double vp[3] = {dr * rho * sp, ds * sp, E * sp};
+            const double vd[3] = {rd * idr, (1.0 - rho) * rd / ds, -iE * rd};
+            const double v0[3] = {r0, s0, t0};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) out[k] = fabs(vp[k]) <= fabs(vd[k]) ? vp[k] : v0[k] - vd[k];
+            out[2] = t0 >= 0.0 ? t0 - vd[2] : vp[2];
+            if (L_out) *L_out = log(delta + s);
+            return true;
+        }
+        const double nd = delta + s;
+        if (!(nd > 0.0 && nd < hi)) return false;
+        delta = nd;
+    }
+    return false;
+}
+
 // Projection onto D K_exp with precomputed logs of the scales (lg[0..2] = log dr, ds, dt).
 // L_cache (may be null): FP32 copy of the last log-offset of this cone.  mlp (may be
 // null): device weights of the learned starting point, used when there is no cached
@@ -1199,11 +1507,13 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
     const bool in_range = fabs(r0) < 1e30 && fabs(s0) < 1e30 && fabs(t0) < 1e30 && (r0 == 0.0 || fabs(r0) > 1e-30) &&
                           (s0 == 0.0 || fabs(s0) > 1e-30) && (t0 == 0.0 || fabs(t0) > 1e-30);
     ExpCase4T<float> ef;
+    ExpEnds ends;
     float Lf = 0.0f;
     int evals = 0;
     bool ok = in_range;
     if (ok) {
-        exp_case4_setup(ef, r0, s0, t0, dr, ds, (float)lg[0], (float)lg[1], (float)lg[2]);
+        ends = exp_ends(r0, s0, dr, ds);
+        exp_case4_setup(ef, r0, s0, t0, dr, ds, (float)lg[0], (float)lg[1], (float)lg[2], ends);
         // rho (rho - 1) + tau^2 must stay finite in FP32 over the search
         ok = fabsf(ef.a3) < 1e15f && fabsf(ef.a4) < 1e15f && fabsf(ef.tau) < 1e15f &&
              exp_case4_solve(ef, L_cache ? *L_cache : NAN, Lf, evals, mlp) &&
@@ -1216,7 +1526,7 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
         // anchor stands when F has the sign beyond the root or is zero to precision;
         // otherwise the root next to it is delta = -F / c, polished by Newton in delta.
         ExpCase4 e;
-        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2], ef.anchor);
+        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2], ends, ef.anchor);
         e.kind = ef.kind;
         e.anchor = ef.anchor;
         e.dir = (double)ef.dir;
@@ -1257,10 +1567,20 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
     if (ok) {
         // FP64 polish from the FP32 root, same branch and anchor
         ExpCase4 e;
-        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2], ef.anchor);
+        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2], ends, ef.anchor);
         e.kind = ef.kind;
         e.anchor = ef.anchor;
         e.dir = (double)ef.dir;
+        if (Lf > -575.0f) {  // linear domain when rho and the offset are moderate
+            const double delta0 = exp((double)Lf);
+            const double rho0 = (e.anchor == 4 ? e.a4 : e.a3) + e.dir * delta0;
+            const double hi = e.kind == 1 ? 0.5 * fabs(e.w34) : INFINITY;
+            double Lout;
+            if (fabs(rho0) < 600.0 && exp_lin_polish(e, delta0, hi, r0, s0, t0, dr, ds, out, &Lout, ev)) {
+                if (L_cache) *L_cache = (float)Lout;
+                return;
+            }
+        }
         // Newton steps s until one is small enough that the result at L + s follows from
         // the values at L to first order (error of order s^2)
         double L = (double)Lf;

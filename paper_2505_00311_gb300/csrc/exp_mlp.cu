@@ -38,7 +38,7 @@ __global__ void dataset_kernel(long long n, const double* __restrict__ v, const 
             (r0 <= 0.0 && s0 <= 0.0))
             continue;
         ExpCase4 e;
-        exp_case4_setup(e, r0, s0, t0, dr, ds, log(dr), log(ds), log(dt));
+        exp_case4_setup(e, r0, s0, t0, dr, ds, log(dr), log(ds), log(dt), exp_ends(r0, s0, dr, ds));
         double L = 0.0;
         int evals = 0;
         // roots farther than e^-50 from the endpoint (about 2 % of N(0, 1) inputs, with a

@@ -19,87 +19,10 @@
 #include "common.cuh"
 #include "cone_f32.cuh"
 #include "cone_math.cuh"
+#include "dev.h"
 #include "state.h"
 
 namespace pdcs {
-
-// Device view of one problem and its iterate state (passed by value).
-// Rows of a CSR matrix binned by length for the SpMV (see spmv_binned).
-constexpr int kSpmvMaxBins = 6;  // lane counts 32, 16, 8, 4, 2, 1
-struct SpmvBins {
-    int nbins;
-    int blk[kSpmvMaxBins + 1];  // first block of each bin; blk[nbins] = grid size
-    int row[kSpmvMaxBins + 1];  // first entry of each bin in the row list
-    int lanes[kSpmvMaxBins];
-};
-
-template <typename T>
-struct Dev {
-    int m, n;
-    // scaled matrix K~ and its transpose, each stored bin by bin for the SpMV (row
-    // pointer over the binned rows; binned row i is row listK[i] / listKT[i])
-    const int* rp;
-    const int* ci;
-    const T* val;
-    const int* rpT;
-    const int* ciT;
-    const T* valT;
-    // scaled data
-    const T* c;
-    const T* h;
-    const T* l;
-    const T* u;
-    const double* dr;
-    const double* dc;
-    // iterate state
-    T *x, *xh, *x0, *kty, *ktyh, *kty0, *xsum;
-    T *y, *yh, *y0, *kx, *kxh0, *kxh1, *kx0, *ysum;
-    // cone layout (internal row order): [0, m_zero) zero rows, [m_zero, m_scalar)
-    // nonnegative rows, then SOC / RSOC blocks, then exp cones (3 rows each)
-    int m_zero, m_scalar;
-    int n_soc;
-    const int* soc_off;
-    const int* soc_dim;
-    const unsigned char* soc_rot;
-    float* soc_lam;        // last SOC root per cone (FP32 start of the next search)
-    const double* soc_w;   // per SOC row: weight of the dual projection, (dr_row / dr_first)^2
-    const double* soc_wp;  // per SOC row: weight of the primal projection, (dr_first / dr_row)^2
-    int exp_row0, n_exp;
-    float* exp_L;          // last log-offset per exp cone
-    const double* exp_lg;  // per exp cone: log dr of its three rows
-    // blocks of the cone-structured kernels: exp cones in [0, nb_exp), SOC cones in the
-    // next nb_soc, scalar rows in the last nb_scal (the costliest work is dispatched first)
-    int nb_scal, nb_soc, nb_exp;
-    int exp_pb;  // exp cones per exp block (threads beyond it idle): spreads them over all SMs
-    int nb_primal;
-    // reductions and control
-    double* part;
-    PartLayout pl;
-    Ctrl* ctrl;
-    // check buffers (always FP64): candidates, their products, scratch
-    double* xc;    // 2 n
-    double* yc;    // 2 m
-    double* kxc;   // 2 m
-    double* ktyc;  // 2 n
-    double* scr;   // 2 m scratch for projections of residuals
-    // original-scale data for the unscaled KKT (FP64)
-    const double* l_orig;
-    const double* u_orig;
-    // scaled data in FP64 for the checks (equal to c, h, l, u when T is double)
-    const double* c64;
-    const double* h64;
-    const double* l64;
-    const double* u64;
-    // FP32 copies of the SOC weights and exp log-scales (FP32 iterates)
-    const float* soc_w32;
-    const float* exp_lg32;
-    // learned starting point of the exp root search (kExpMlpParams floats), or null
-    const float* exp_mlp;
-    // SpMV plans of K and K': bins and the row each binned row stands for
-    SpmvBins binsK, binsKT;
-    const int* listK;
-    const int* listKT;
-};
 
 // ---------------------------------------------------------------------------
 // SpMV: y = A x.  The rows are grouped in bins by length (host side, once per
@@ -177,6 +100,118 @@ __global__ void __launch_bounds__(kBlock) spmv_binned(SpmvBins B, const int* __r
     }
 }
 
+// ---------------------------------------------------------------------------
+// Sliced SpMV: y = A x with A stored in slices (SlicePlan).  One warp per slice: at each
+// step every lane loads the next pair of entries of its row with one 8-byte (columns) and
+// one 16-byte (FP64 values) load, the warp reading 256 + 512 contiguous bytes, then
+// gathers x for both; a row's S lanes add their partial sums by a shuffle tree (S = 1:
+// one accumulator in the row's order).  Rows longer than kSliceMaxLen come first in the
+// grid, one warp each (lane-strided partial sums, then a shuffle tree).
+// sel / skip as for spmv_binned.
+// ---------------------------------------------------------------------------
+template <typename T> struct Pair2;
+template <> struct Pair2<double> { using type = double2; };
+template <> struct Pair2<float> { using type = float2; };
+
+template <typename T>
+__device__ __forceinline__ T lane_group_sum(T v, int lg) {
+    for (int o = (1 << lg) >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T, typename TO>
+__global__ void __launch_bounds__(kBlock) spmv_sliced(SlicePlan S, const int* __restrict__ ci,
+                                                      const T* __restrict__ val, const T* __restrict__ x, TO* y0,
+                                                      TO* y1, const Ctrl* ctrl, int sel, int skip) {
+    if (skip) {
+        if (ctrl->status != kRunning) return;
+        if (skip == 2 && !ctrl->pending) return;
+    }
+    TO* y = (sel == 1 && (ctrl->attempts & 1)) ? y1 : y0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if ((int)blockIdx.x < S.nb_long) {
+        const int r = (int)blockIdx.x * kWarpsPerBlock + w;
+        if (r >= S.nlong) return;
+        const int b = __ldg(S.long_rp + r), e = __ldg(S.long_rp + r + 1);
+        T acc = T(0);
+        for (int p = b + lane; p < e; p += 32) acc += __ldg(val + p) * __ldg(x + __ldg(ci + p));
+        acc = group_sum<32>(acc);
+        if (lane == 0) y[__ldg(S.long_row + r)] = (TO)acc;
+        return;
+    }
+    using V2 = typename Pair2<T>::type;
+    const int s = ((int)blockIdx.x - S.nb_long) * kWarpsPerBlock + w;
+    if (s >= S.nslices) return;
+    const int base = __ldg(S.slice_off + s);
+    const int steps = (__ldg(S.slice_off + s + 1) - base) >> 6;
+    const int lg = __ldg(S.slice_lg + s);
+    const int2* cp = reinterpret_cast<const int2*>(ci + base) + lane;
+    const V2* vp = reinterpret_cast<const V2*>(val + base) + lane;
+    T acc = T(0);
+    int q = 0;
+    for (; q + 2 <= steps; q += 2) {  // two pairs in flight
+        const int2 c0 = __ldg(cp + 32 * q), c1 = __ldg(cp + 32 * (q + 1));
+        const V2 v0 = __ldg(vp + 32 * q), v1 = __ldg(vp + 32 * (q + 1));
+        const T x0 = c0.x >= 0 ? __ldg(x + c0.x) : T(0);
+        const T x1 = c0.y >= 0 ? __ldg(x + c0.y) : T(0);
+        const T x2 = c1.x >= 0 ? __ldg(x + c1.x) : T(0);
+        const T x3 = c1.y >= 0 ? __ldg(x + c1.y) : T(0);
+        acc += v0.x * x0;
+        acc += v0.y * x1;
+        acc += v1.x * x2;
+        acc += v1.y * x3;
+    }
+    if (q < steps) {
+        const int2 c0 = __ldg(cp + 32 * q);
+        const V2 v0 = __ldg(vp + 32 * q);
+        const T x0 = c0.x >= 0 ? __ldg(x + c0.x) : T(0);
+        const T x1 = c0.y >= 0 ? __ldg(x + c0.y) : T(0);
+        acc += v0.x * x0;
+        acc += v0.y * x1;
+    }
+    acc = lane_group_sum(acc, lg);
+    if ((lane & ((1 << lg) - 1)) == 0) {
+        const int r = __ldg(S.out_row + 32 * s + (lane >> lg));
+        if (r >= 0) y[r] = (TO)acc;
+    }
+}
+
+// Fills the sliced storage of a CSR matrix (rows in order: rp, ci, val) for plan S: one
+// thread per slot (lane of a slice, or long row); values converted to TD; cis or vals may
+// be null.
+template <typename TD>
+__global__ void __launch_bounds__(kBlock) sliced_copy(SlicePlan S, const int* __restrict__ rp,
+                                                      const int* __restrict__ ci, const double* __restrict__ val,
+                                                      int* __restrict__ cis, TD* __restrict__ vals) {
+    const long long slots = 32LL * S.nslices + S.nlong;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < slots;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (t < 32LL * S.nslices) {
+            const int s = (int)(t >> 5), lane = (int)(t & 31);
+            const int lg = S.slice_lg[s], g = lane & ((1 << lg) - 1), j = lane >> lg;
+            const int base = S.slice_off[s], steps = (S.slice_off[s + 1] - base) >> 6;
+            const int r = S.out_row[32 * s + j];
+            const int b = r >= 0 ? rp[r] : 0, len = r >= 0 ? rp[r + 1] - b : 0;
+            for (int q = 0; q < steps; ++q) {
+                const int p = (q << lg) + g;  // pair of the row held at this step
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 2 * p + h;
+                    const long long dst = base + 64LL * q + 2 * lane + h;
+                    if (cis) cis[dst] = k < len ? ci[b + k] : -1;
+                    if (vals) vals[dst] = k < len ? (TD)val[b + k] : TD(0);
+                }
+            }
+        } else {
+            const int jj = (int)(t - 32LL * S.nslices);
+            const int r = S.long_row[jj], b = rp[r], len = rp[r + 1] - b, dst = S.long_rp[jj];
+            for (int k = 0; k < len; ++k) {
+                if (cis) cis[dst + k] = ci[b + k];
+                if (vals) vals[dst + k] = (TD)val[b + k];
+            }
+        }
+    }
+}
+
 // Stores a CSR matrix (rows in order, row pointer rp) bin by bin: binned row i is row
 // list[i]; rpb (the binned row pointer) is given.  One warp per binned row; the
 // entries keep their order within the row.  Values are converted to TD.
@@ -200,16 +235,18 @@ __global__ void __launch_bounds__(kBlock) bin_rows_copy(int rows, const int* __r
 // ---------------------------------------------------------------------------
 // last-block helper: returns true in every thread of the block that finished last
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool last_block(Ctrl* C) {
+// (total: the blocks taking part, possibly spread over several concurrent kernels)
+__device__ __forceinline__ bool last_block(Ctrl* C, unsigned int total) {
     __shared__ unsigned int s_ticket;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_ticket = atomicAdd(&C->ticket, 1u);
     __syncthreads();
-    const bool last = s_ticket == gridDim.x - 1;
+    const bool last = s_ticket == total - 1;
     if (last) __threadfence();
     return last;
 }
+__device__ __forceinline__ bool last_block(Ctrl* C) { return last_block(C, gridDim.x); }
 
 // Deterministic sum of part[0..cnt) by one block (fixed per-thread strides + fixed tree).
 __device__ __forceinline__ double block_reduce_parts(const double* part, int cnt, double (*sm)[kWarpsPerBlock]) {
@@ -324,92 +361,251 @@ __device__ void step_controller(const Dev<T>& D, double (*sm)[kWarpsPerBlock]) {
 
 // ---------------------------------------------------------------------------
 // dual update + projection + step controller
+//
+// Three cone roles over disjoint row ranges: scalar rows (one thread each), SOC / RSOC
+// blocks (one warp each) and exp cones (one thread each).  Each role is a device function
+// of its own; the single-program path launches each as its own kernel (concurrent
+// branches of the evaluation graph, each with the registers it needs), a batch runs them
+// as block ranges of one kernel.  Either way every block writes its partials of
+// ||dy||^2 and dy'(K xhat - K x) to the slot of its global role-block index
+// (exp blocks first, then SOC, then scalar), and the last block to finish, over all roles,
+// runs the step controller: the sums are the same whatever the launch form.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void dual_update_body(const Dev<T>& D, int qidx) {
-    (void)qidx;
-    Ctrl* C = D.ctrl;
-    if (C->status != kRunning) return;
-    __shared__ double sm[2][kWarpsPerBlock];
+struct DualCoef {
+    const T* p;      // K xhat of this evaluation
+    const T* pprev;  // K xhat of the previous one (pending Halpern update of K x)
+    bool pend;
+    T ha, hb, hc, hw, sigma;
+};
+
+template <typename T>
+__device__ __forceinline__ DualCoef<T> dual_coef(const Dev<T>& D) {
+    const Ctrl* C = D.ctrl;
     const long long att = C->attempts;
-    const T* p = (att & 1) ? D.kxh1 : D.kxh0;
-    const T* pprev = (att & 1) ? D.kxh0 : D.kxh1;
-    const bool pend = C->pending != 0;
-    const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw, sigma = (T)C->sigma;
-    T acc_t[2] = {T(0), T(0)};  // per-thread partials in the iterate precision, then FP64
-    const int b = blockIdx.x;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (b >= D.nb_exp + D.nb_soc) {  // scalar rows (blocks dispatched last)
-        const int sb = b - D.nb_exp - D.nb_soc;  // idle beyond this program's split (batches)
-        const int stride = D.nb_scal * blockDim.x;
-        for (int i = sb * blockDim.x + threadIdx.x; sb < D.nb_scal && i < D.m_scalar; i += stride) {
+    DualCoef<T> k;
+    k.p = (att & 1) ? D.kxh1 : D.kxh0;
+    k.pprev = (att & 1) ? D.kxh0 : D.kxh1;
+    k.pend = C->pending != 0;
+    k.ha = (T)C->ha; k.hb = (T)C->hb; k.hc = (T)C->hc; k.hw = (T)C->hw; k.sigma = (T)C->sigma;
+    return k;
+}
+
+// scalar rows [0, m_scalar): block sb of nb_scal
+template <typename T>
+__device__ __forceinline__ void dual_scalar_rows(const Dev<T>& D, const DualCoef<T>& k, int sb, T (&acc)[2]) {
+    const int stride = D.nb_scal * blockDim.x;
+    for (int i = sb * blockDim.x + threadIdx.x; sb < D.nb_scal && i < D.m_scalar; i += stride) {
+        T y, kx;
+        dual_row_halpern(D, i, k.pend, k.ha, k.hb, k.hc, k.hw, k.pprev, y, kx);
+        const T pi = k.p[i];
+        const T v = y + k.sigma * (D.h[i] - T(2) * pi + kx);
+        const T yh = (i < D.m_zero) ? v : fmax(v, T(0));
+        D.yh[i] = yh;
+        const T dy = yh - y;
+        acc[0] += dy * dy;
+        acc[1] += dy * (pi - kx);
+    }
+}
+
+// One SOC / RSOC cone by a whole warp on global memory
+template <typename T>
+__device__ __forceinline__ void dual_soc_cone(const Dev<T>& D, const DualCoef<T>& k, int cidx, T (&acc)[2]) {
+    const int lane = threadIdx.x & 31;
+    {
+        const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
+        for (int i = lane; i < dim; i += 32) {
             T y, kx;
-            dual_row_halpern(D, i, pend, ha, hb, hc, hw, pprev, y, kx);
-            const T pi = p[i];
-            const T v = y + sigma * (D.h[i] - T(2) * pi + kx);
-            const T yh = (i < D.m_zero) ? v : fmax(v, T(0));
-            D.yh[i] = yh;
-            const T dy = yh - y;
-            acc_t[0] += dy * dy;
-            acc_t[1] += dy * (pi - kx);
+            dual_row_halpern(D, o + i, k.pend, k.ha, k.hb, k.hc, k.hw, k.pprev, y, kx);
+            D.yh[o + i] = y + k.sigma * (D.h[o + i] - T(2) * k.p[o + i] + kx);
         }
-    } else if (b >= D.nb_exp) {  // SOC / RSOC blocks
-        const int stride = D.nb_soc * kWarpsPerBlock;
-        for (int cidx = (b - D.nb_exp) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
-            const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
-            for (int i = lane; i < dim; i += 32) {
-                T y, kx;
-                dual_row_halpern(D, o + i, pend, ha, hb, hc, hw, pprev, y, kx);
-                D.yh[o + i] = y + sigma * (D.h[o + i] - T(2) * p[o + i] + kx);
-            }
-            __syncwarp();
-            if constexpr (sizeof(T) == 8)
-                soc_project_any<true>(D.yh + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, D.soc_lam + cidx,
-                                      reinterpret_cast<float*>(D.scr + o),  // scratch unused during the update
-                                      D.soc_wp + o + 1);
-            else
-                soc_project_any_f32(D.yh + o, D.soc_w32 + o + 1, D.scr + o, D.dr + o, dim, D.soc_rot[cidx] != 0,
-                                    D.soc_lam + cidx);
-            for (int i = lane; i < dim; i += 32) {
-                const T dy = D.yh[o + i] - D.y[o + i];
-                acc_t[0] += dy * dy;
-                acc_t[1] += dy * (p[o + i] - D.kx[o + i]);
-            }
-            __syncwarp();
+        __syncwarp();
+        if constexpr (sizeof(T) == 8)
+            soc_project_any<true>(D.yh + o, D.soc_w + o + 1, D.dr + o, dim, D.soc_rot[cidx] != 0, D.soc_lam + cidx,
+                                  reinterpret_cast<float*>(D.scr + o),  // scratch unused during the update
+                                  D.soc_wp + o + 1);
+        else
+            soc_project_any_f32(D.yh + o, D.soc_w32 + o + 1, D.scr + o, D.dr + o, dim, D.soc_rot[cidx] != 0,
+                                D.soc_lam + cidx);
+        for (int i = lane; i < dim; i += 32) {
+            const T dy = D.yh[o + i] - D.y[o + i];
+            acc[0] += dy * dy;
+            acc[1] += dy * (k.p[o + i] - D.kx[o + i]);
         }
-    } else {
-        const int stride = D.nb_exp * D.exp_pb;
-        for (int e = b * D.exp_pb + threadIdx.x; threadIdx.x < D.exp_pb && e < D.n_exp; e += stride) {
-            const int r = D.exp_row0 + 3 * e;
-            T y[3], kx[3], v[3], out[3];
+        __syncwarp();
+    }
+}
+
+// SOC / RSOC blocks: block sb of nb_soc, one warp per cone (batches, FP32 iterates)
+template <typename T>
+__device__ __forceinline__ void dual_soc_blocks(const Dev<T>& D, const DualCoef<T>& k, int sb, T (&acc)[2]) {
+    const int wid = threadIdx.x >> 5;
+    const int stride = D.nb_soc * (blockDim.x >> 5);
+    for (int cidx = sb * (blockDim.x >> 5) + wid; cidx < D.n_soc; cidx += stride) dual_soc_cone(D, k, cidx, acc);
+}
+
+// One tile of cones (tile t, one warp): the pending Halpern update and v of its rows into
+// shared memory (coalesced over the tile's rows), the projections by lane groups of S
+// lanes (soc_seg_project), then yhat and the partials from shared memory.
+template <int S>
+__device__ __forceinline__ void soc_tile_project(const Dev<double>& D, int t, double* sv, const double* sw,
+                                                 const double* swi, float* sxf, float* swf, int lane) {
+    const int c0 = D.tile_cone0[t], nc = D.tile_cone0[t + 1] - c0;
+    const int grp = lane / S, g = lane % S;
+    if (grp >= nc) return;
+    const int so = D.soc_so[c0 + grp];  // staged offset of the group's cone
+    const int cone = D.soc_order[c0 + grp];
+    const int o = D.soc_off[cone], dim = D.soc_dim[cone];
+    const unsigned gmask = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << (grp * S));
+    (void)o;
+    soc_seg_project<S>(sv + so, sw + so + 1, swi + so + 1, sxf + so, swf + so, dim, D.soc_rot[cone] != 0,
+                       D.soc_lam + cone, gmask, g);
+}
+
+__device__ __forceinline__ void dual_soc_tile(const Dev<double>& D, const DualCoef<double>& k, int t,
+                                              double (&acc)[2]) {
+    extern __shared__ double soc_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // per warp: value, weight, inverse weight (doubles), then FP32 copies of value and weight
+    double* sv = soc_smem + (size_t)wid * (kSocTileRows * 4);
+    double* sw = sv + kSocTileRows;
+    double* swi = sw + kSocTileRows;
+    float* sxf = reinterpret_cast<float*>(swi + kSocTileRows);
+    float* swf = sxf + kSocTileRows;
+    const int r0 = D.tile_row0[t], nr = D.tile_row0[t + 1] - r0;
+    for (int q = lane; q < nr; q += 32) {
+        const int i = D.soc_trow[r0 + q];
+        double y, kx;
+        dual_row_halpern(D, i, k.pend, k.ha, k.hb, k.hc, k.hw, k.pprev, y, kx);
+        sv[q] = y + k.sigma * (D.h[i] - 2.0 * k.p[i] + kx);
+        sw[q] = D.soc_w[i];   // weight of the dual projection (1 on a cone's first row, unused)
+        swi[q] = D.soc_wp[i];
+    }
+    __syncwarp();
+    switch (D.tile_lg[t]) {
+        case 0: soc_tile_project<1>(D, t, sv, sw, swi, sxf, swf, lane); break;
+        case 1: soc_tile_project<2>(D, t, sv, sw, swi, sxf, swf, lane); break;
+        case 2: soc_tile_project<4>(D, t, sv, sw, swi, sxf, swf, lane); break;
+        case 3: soc_tile_project<8>(D, t, sv, sw, swi, sxf, swf, lane); break;
+        case 4: soc_tile_project<16>(D, t, sv, sw, swi, sxf, swf, lane); break;
+        default: soc_tile_project<32>(D, t, sv, sw, swi, sxf, swf, lane); break;
+    }
+    __syncwarp();
+    for (int q = lane; q < nr; q += 32) {
+        const int i = D.soc_trow[r0 + q];
+        const double yh = sv[q];
+        D.yh[i] = yh;
+        const double dy = yh - D.y[i];
+        acc[0] += dy * dy;
+        acc[1] += dy * (k.p[i] - D.kx[i]);
+    }
+    __syncwarp();  // the staged rows are read before the next tile overwrites them
+}
+
+// the tiles, dealt round-robin over the tile blocks (block b takes tiles b, b + nb, ...;
+// largest cones first), so every block gets the same share of the work to within a tile
+__device__ __forceinline__ void dual_soc_tiles(const Dev<double>& D, const DualCoef<double>& k, double (&acc)[2]) {
+    const int nb = D.nb_tiles;
+    for (int t = (int)blockIdx.x + (int)(threadIdx.x >> 5) * nb; t < D.n_tiles; t += kWarpsPerBlock * nb)
+        dual_soc_tile(D, k, t, acc);
+}
+
+// the large cones (after the tiles in soc_order), a warp each: block lb of the SOC blocks
+// beyond the tiles
+__device__ __forceinline__ void dual_soc_large(const Dev<double>& D, const DualCoef<double>& k, int lb,
+                                               double (&acc)[2]) {
+    const int wid = threadIdx.x >> 5;
+    const int nbl = D.nb_soc - D.nb_tiles;
+    const int base = D.tile_cone0[D.n_tiles];
+    for (int j = lb * kWarpsPerBlock + wid; j < D.n_large; j += nbl * kWarpsPerBlock)
+        dual_soc_cone(D, k, D.soc_order[base + j], acc);
+}
+
+// exp cones: block b of nb_exp, one thread per cone (exp_pb per block)
+template <typename T>
+__device__ __forceinline__ void dual_exp_cones(const Dev<T>& D, const DualCoef<T>& k, int b, T (&acc)[2]) {
+    const int stride = D.nb_exp * D.exp_pb;
+    for (int e = b * D.exp_pb + threadIdx.x; threadIdx.x < D.exp_pb && e < D.n_exp; e += stride) {
+        const int r = D.exp_row0 + 3 * e;
+        T y[3], kx[3], v[3], out[3];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                dual_row_halpern(D, r + q, pend, ha, hb, hc, hw, pprev, y[q], kx[q]);
-                v[q] = y[q] + sigma * (D.h[r + q] - T(2) * p[r + q] + kx[q]);
-            }
-            if constexpr (sizeof(T) == 8)
-                exp_dual_project_fast(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, out,
-                                      D.exp_L + e, D.exp_mlp);
-            else
-                exp_dual_project_f32(v[0], v[1], v[2], (float)D.dr[r], (float)D.dr[r + 1], (float)D.dr[r + 2],
-                                     D.exp_lg32 + 3 * e, out, D.exp_L + e, D.exp_mlp);
+        for (int q = 0; q < 3; ++q) {
+            dual_row_halpern(D, r + q, k.pend, k.ha, k.hb, k.hc, k.hw, k.pprev, y[q], kx[q]);
+            v[q] = y[q] + k.sigma * (D.h[r + q] - T(2) * k.p[r + q] + kx[q]);
+        }
+        if constexpr (sizeof(T) == 8)
+            exp_dual_project_fast(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, out,
+                                  D.exp_L + e, D.exp_mlp);
+        else
+            exp_dual_project_f32(v[0], v[1], v[2], (float)D.dr[r], (float)D.dr[r + 1], (float)D.dr[r + 2],
+                                 D.exp_lg32 + 3 * e, out, D.exp_L + e, D.exp_mlp);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const T yh = (T)out[q];
-                D.yh[r + q] = yh;
-                const T dy = yh - y[q];
-                acc_t[0] += dy * dy;
-                acc_t[1] += dy * (p[r + q] - kx[q]);
-            }
+        for (int q = 0; q < 3; ++q) {
+            const T yh = (T)out[q];
+            D.yh[r + q] = yh;
+            const T dy = yh - y[q];
+            acc[0] += dy * dy;
+            acc[1] += dy * (k.p[r + q] - kx[q]);
         }
     }
+}
+
+// partials of role-block gb (global index), then the controller in the last block of all
+template <typename T>
+__device__ __forceinline__ void dual_finish(const Dev<T>& D, int gb, const T (&acc_t)[2]) {
+    __shared__ double sm[2][kWarpsPerBlock];
     double acc[2] = {(double)acc_t[0], (double)acc_t[1]};
     block_sum<2>(acc, sm);
     if (threadIdx.x == 0) {
-        D.part[D.pl.off_dy + b] = acc[0];
-        D.part[D.pl.off_dy + D.pl.dual_blocks + b] = acc[1];
+        D.part[D.pl.off_dy + gb] = acc[0];
+        D.part[D.pl.off_dy + D.pl.dual_blocks + gb] = acc[1];
     }
-    if (last_block(C)) step_controller(D, sm);
+    if (last_block(D.ctrl, (unsigned)D.pl.dual_blocks)) step_controller(D, sm);
+}
+
+// all roles as block ranges of one launch (batches): exp blocks, then SOC, then scalar
+template <typename T>
+__device__ __forceinline__ void dual_update_body(const Dev<T>& D, int qidx) {
+    (void)qidx;
+    if (D.ctrl->status != kRunning) return;
+    const DualCoef<T> k = dual_coef(D);
+    T acc[2] = {T(0), T(0)};  // per-thread partials in the iterate precision, then FP64
+    const int b = blockIdx.x;
+    if (b >= D.nb_exp + D.nb_soc) dual_scalar_rows(D, k, b - D.nb_exp - D.nb_soc, acc);
+    else if (b >= D.nb_exp) dual_soc_blocks(D, k, b - D.nb_exp, acc);
+    else dual_exp_cones(D, k, b, acc);
+    dual_finish(D, b, acc);
+}
+
+// one role per kernel (single programs; the three run concurrently)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) dual_scalar(Dev<T> D) {
+    if (D.ctrl->status != kRunning) return;
+    const DualCoef<T> k = dual_coef(D);
+    T acc[2] = {T(0), T(0)};
+    dual_scalar_rows(D, k, blockIdx.x, acc);
+    dual_finish(D, D.nb_exp + D.nb_soc + (int)blockIdx.x, acc);
+}
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 3) dual_soc(Dev<T> D) {
+    if (D.ctrl->status != kRunning) return;
+    const DualCoef<T> k = dual_coef(D);
+    T acc[2] = {T(0), T(0)};
+    if constexpr (sizeof(T) == 8) {  // FP64: tiles by lane groups, then the large cones
+        if ((int)blockIdx.x < D.nb_tiles) dual_soc_tiles(D, k, acc);
+        else dual_soc_large(D, k, (int)blockIdx.x - D.nb_tiles, acc);
+    } else {
+        dual_soc_blocks(D, k, blockIdx.x, acc);
+    }
+    dual_finish(D, D.nb_exp + (int)blockIdx.x, acc);
+}
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 2) dual_exp(Dev<T> D) {
+    if (D.ctrl->status != kRunning) return;
+    const DualCoef<T> k = dual_coef(D);
+    T acc[2] = {T(0), T(0)};
+    dual_exp_cones(D, k, blockIdx.x, acc);
+    dual_finish(D, (int)blockIdx.x, acc);
 }
 
 // ---------------------------------------------------------------------------

@@ -84,19 +84,31 @@ __global__ void scale_rows(int m, const double* __restrict__ dr, const double* _
 }
 
 // Deterministic single-block reductions for setup: kind 0 sum of squares,
-// 1 max |.|, 2 sum x*y.
+// 1 max |.|, 2 sum x*y.  Each thread's long strided sum carries Neumaier's compensation
+// (a plain sum of the ~4,000 terms per thread of a 1M-vector loses ~1e-14).
 __global__ void reduce_small(long long k, const double* __restrict__ a, const double* __restrict__ b, int kind,
                              double* out) {
-    __shared__ double sm[1][kWarpsPerBlock];
-    double v[1] = {0.0};
+    __shared__ double sm[2][kWarpsPerBlock];
+    double v[2] = {0.0, 0.0};  // sum, compensation
     for (long long i = threadIdx.x; i < k; i += blockDim.x) {
         const double x = a[i];
-        if (kind == 0) v[0] += x * x;
-        else if (kind == 1) v[0] = fmax(v[0], fabs(x));
-        else v[0] += x * b[i];
+        if (kind == 1) {
+            v[0] = fmax(v[0], fabs(x));
+            continue;
+        }
+        const double term = kind == 0 ? x * x : x * b[i];
+        const double t = v[0] + term;
+        v[1] += fabs(v[0]) >= fabs(term) ? (v[0] - t) + term : (term - t) + v[0];
+        v[0] = t;
     }
-    if (kind == 1) block_max<1>(v, sm); else block_sum<1>(v, sm);
-    if (threadIdx.x == 0) *out = v[0];
+    if (kind == 1) {
+        double mx[1] = {v[0]};
+        block_max<1>(mx, sm);
+        if (threadIdx.x == 0) *out = mx[0];
+        return;
+    }
+    block_sum<2>(v, sm);
+    if (threadIdx.x == 0) *out = v[0] + v[1];
 }
 
 // v <- u / s (s read from device)

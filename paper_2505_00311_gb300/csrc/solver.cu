@@ -16,7 +16,9 @@
 
 #include "../../include/pdcs.h"
 #include "common.cuh"
-#include "kernels.cuh"
+#include "cone_math.cuh"
+#include "dev.h"
+#include "launch.h"
 #include "setup_kernels.cuh"
 #include "state.h"
 
@@ -55,14 +57,70 @@ struct Arena {
 
 // SpMV plan of one matrix: rows binned by length (see spmv_binned), the matrix
 // stored bin by bin, and the unroll.
+// Or (sliced) the matrix in slices of 32 rows of similar length (see spmv_sliced).
+enum { kFormatBinned = 1, kFormatSliced = 2 };
 struct SpmvPlan {
+    int format = kFormatBinned;
     SpmvBins B{};
     int* list = nullptr;  // device row list, bin by bin: binned row i is row list[i]
     int* rp = nullptr;    // device row pointer over the binned rows
-    int* ci = nullptr;    // device columns, bin by bin
+    int* ci = nullptr;    // device columns, bin by bin (sliced: in the sliced storage)
     int shift = 3;        // lanes = 2^(ceil(log2(length)) - shift), clamped to 1..32
     int unroll = 4;
+    SlicePlan S{};        // sliced format: the plan (device arrays below)
 };
+
+// Host side of a sliced plan: rows of at most kSliceMaxLen entries sorted by length
+// (longest first, then by row), cut into slices whose lanes per row S follow from the
+// slice's first (longest) row; longer rows after them in row order.
+struct SliceHost {
+    std::vector<int> slice_off, out_row, long_row, long_rp;
+    std::vector<unsigned char> slice_lg;
+    long long entries = 0;  // sliced storage size (padding included)
+};
+
+void plan_slices(const std::vector<int>& rp, int rows, SliceHost& H) {
+    std::vector<int> cnt(kSliceMaxLen + 2, 0), shorts;
+    H.long_row.clear();
+    for (int r = 0; r < rows; ++r) {
+        const int len = rp[r + 1] - rp[r];
+        if (len > kSliceMaxLen) H.long_row.push_back(r);
+        else ++cnt[len];
+    }
+    // counting sort by decreasing length, stable in the row index
+    std::vector<int> start(kSliceMaxLen + 2, 0);
+    int acc = 0;
+    for (int len = kSliceMaxLen; len >= 0; --len) { start[len] = acc; acc += cnt[len]; }
+    shorts.assign(acc, 0);
+    for (int r = 0; r < rows; ++r) {
+        const int len = rp[r + 1] - rp[r];
+        if (len <= kSliceMaxLen) shorts[start[len]++] = r;
+    }
+    H.slice_off.clear();
+    H.slice_lg.clear();
+    H.out_row.clear();
+    long long off = 0;
+    for (int i = 0; i < acc;) {
+        const int L = rp[shorts[i] + 1] - rp[shorts[i]];
+        int lg = 0;
+        while (lg < 5 && L > (2 << lg) * kSlicePairsPerLane) ++lg;
+        const int S = 1 << lg, h = 32 >> lg;
+        const int W = (L + 2 * S - 1) / (2 * S) * (2 * S);  // width: a multiple of 2 S
+        H.slice_off.push_back((int)off);
+        H.slice_lg.push_back((unsigned char)lg);
+        for (int j = 0; j < 32; ++j) H.out_row.push_back(j < h && i + j < acc ? shorts[i + j] : -1);
+        off += 32LL * W / S;  // h rows of W entries
+        i += h;
+    }
+    H.slice_off.push_back((int)off);
+    H.long_rp.assign(H.long_row.size() + 1, 0);
+    for (size_t j = 0; j < H.long_row.size(); ++j) {
+        H.long_rp[j] = (int)off;
+        off += rp[H.long_row[j] + 1] - rp[H.long_row[j]];
+    }
+    H.long_rp[H.long_row.size()] = (int)off;
+    H.entries = off;
+}
 
 }  // namespace
 
@@ -103,13 +161,16 @@ struct pdcs_ctx {
     // FP32-iterate mode: FP32 copies of K~, K~', c~, h~, l~, u~ and the iterate state;
     // checks, restarts and the final phase stay FP64 (D)
     Dev<float> DF;
-    float *val_f = nullptr, *valT_f = nullptr;  // bin by bin
+    float *val_f = nullptr, *valT_f = nullptr;  // in the SpMV storage
     bool fp32_active = false;          // the FP32 phase is running
     double fp32_best = INFINITY;       // best relative KKT error seen in the FP32 phase
     int fp32_stall = 0;                // checks since it last improved by 10 %
     int g_vec_n = 0, g_vec_m = 0, g_dual = 0, g_kktd = 0;
 
     cudaGraphExec_t graph = nullptr, graph32 = nullptr;
+    cudaStream_t aux[2] = {nullptr, nullptr};  // helper streams of the concurrent dual-update roles
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    int launches_per_attempt = 4;
     bool started = false;
     double setup_seconds = 0.0, solve_seconds = 0.0;
     double norm2 = 0.0;
@@ -117,6 +178,11 @@ struct pdcs_ctx {
     int last_status = PDCS_OK;
 
     ~pdcs_ctx() {
+        for (int k = 0; k < 2; ++k) {
+            if (aux[k]) cudaStreamDestroy(aux[k]);
+            if (ev_join[k]) cudaEventDestroy(ev_join[k]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
         if (graph) cudaGraphExecDestroy(graph);
         if (graph32) cudaGraphExecDestroy(graph32);
         if (arena.base) cudaFree(arena.base);
@@ -136,16 +202,11 @@ struct pdcs_ctx {
 
 namespace {
 
-template <typename T, typename TO>
-void launch_spmv(const SpmvPlan& P, cudaStream_t s, const int* rp, const int* ci, const T* val, const T* x, TO* y0,
-                 TO* y1, const Ctrl* ctrl, int sel, int skip) {
-    const int grid = P.B.blk[P.B.nbins];
-    if (grid <= 0) return;
-    switch (P.unroll) {
-        case 1: spmv_binned<T, TO, 1><<<grid, kBlock, 0, s>>>(P.B, P.list, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
-        case 4: spmv_binned<T, TO, 4><<<grid, kBlock, 0, s>>>(P.B, P.list, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
-        default: spmv_binned<T, TO, 2><<<grid, kBlock, 0, s>>>(P.B, P.list, rp, ci, val, x, y0, y1, ctrl, sel, skip); break;
-    }
+template <typename T>
+void launch_spmv(const SpmvPlan& P, cudaStream_t s, const int* rp, const int* ci, const T* val, const T* x, T* y0,
+                 T* y1, const Ctrl* ctrl, int sel, int skip) {
+    if (P.format == kFormatSliced) k_spmv_sliced(P.S, s, ci, val, x, y0, y1, ctrl, sel, skip);
+    else k_spmv(P.B, P.unroll, s, P.list, rp, ci, val, x, y0, y1, ctrl, sel, skip);
 }
 
 // Bins of a CSR matrix: lanes per row 2^(ceil(log2(len)) - shift) clamped to 1..32 (or
@@ -257,8 +318,42 @@ cudaError_t store_binned(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp,
     if (e == cudaSuccess) e = cudaMemcpyAsync(P.rp, rpb.data(), sizeof(int) * (rows + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         const long long g = std::min(((long long)rows + kWarpsPerBlock - 1) / kWarpsPerBlock, (long long)ctx->sms * 32);
-        bin_rows_copy<double, TD><<<(int)g, kBlock, 0, s>>>(rows, P.list, drp, dci, dval, P.rp, cols ? P.ci : nullptr,
-                                                             valb);
+        k_bin_rows_copy((int)g, s, rows, P.list, drp, dci, dval, P.rp, cols ? P.ci : nullptr, valb);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors are pageable
+    return e;
+}
+
+// Uploads the sliced plan H of P (arrays taken from the arena beforehand) and fills the
+// sliced storage of a matrix (rows in order: device drp, dci, dval) with values as TD
+// (cols: also the columns into P.ci).
+template <typename TD>
+cudaError_t store_sliced(pdcs_ctx* ctx, SpmvPlan& P, const SliceHost& H, const int* drp, const int* dci,
+                         const double* dval, TD* vals, bool cols) {
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (cols) {
+        unsigned char* slg = const_cast<unsigned char*>(P.S.slice_lg);
+        if (!H.slice_lg.empty())
+            e = cudaMemcpyAsync(slg, H.slice_lg.data(), H.slice_lg.size(), cudaMemcpyHostToDevice, s);
+        int* so = const_cast<int*>(P.S.slice_off);
+        int* orow = const_cast<int*>(P.S.out_row);
+        int* lr = const_cast<int*>(P.S.long_row);
+        int* lrp = const_cast<int*>(P.S.long_rp);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(so, H.slice_off.data(), sizeof(int) * H.slice_off.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !H.out_row.empty())
+            e = cudaMemcpyAsync(orow, H.out_row.data(), sizeof(int) * H.out_row.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !H.long_row.empty())
+            e = cudaMemcpyAsync(lr, H.long_row.data(), sizeof(int) * H.long_row.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(lrp, H.long_rp.data(), sizeof(int) * H.long_rp.size(), cudaMemcpyHostToDevice, s);
+    }
+    const long long slots = 32LL * P.S.nslices + P.S.nlong;
+    if (e == cudaSuccess && slots > 0) {
+        const int g = (int)std::max(1LL, std::min((slots + kBlock - 1) / kBlock, (long long)ctx->sms * 16));
+        k_sliced_copy(P.S, g, s, drp, dci, dval, cols ? P.ci : nullptr, vals);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors are pageable
@@ -297,9 +392,9 @@ cudaError_t tune_spmv(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, in
             for (int un = 1; un <= 4 && e == cudaSuccess; un *= 2) {
                 c.shift = sh;
                 c.unroll = un;
-                for (int r = 0; r < 3; ++r) launch_spmv<T, T>(c, s, P.rp, P.ci, valb, x, y, nullptr, nullptr, 0, 0);
+                for (int r = 0; r < 3; ++r) launch_spmv<T>(c, s, P.rp, P.ci, valb, x, y, nullptr, nullptr, 0, 0);
                 cudaEventRecord(e0, s);
-                for (int r = 0; r < 20; ++r) launch_spmv<T, T>(c, s, P.rp, P.ci, valb, x, y, nullptr, nullptr, 0, 0);
+                for (int r = 0; r < 20; ++r) launch_spmv<T>(c, s, P.rp, P.ci, valb, x, y, nullptr, nullptr, 0, 0);
                 cudaEventRecord(e1, s);
                 e = cudaEventSynchronize(e1);
                 if (e == cudaSuccess) e = cudaGetLastError();
@@ -320,8 +415,38 @@ cudaError_t tune_spmv(pdcs_ctx* ctx, SpmvPlan& P, const std::vector<int>& rp, in
     return store_binned<T>(ctx, P, rp, list, drp, dci, dval, valb, true);
 }
 
-constexpr int kLaunchesPerAttempt = 4;
+constexpr int kLaunchesPerAttempt = 4;  // batches: one dual-update launch per evaluation
 constexpr int kLaunchesPerCheck = 12;
+
+// the dual update: its three cone roles as concurrent kernels (forked from the context's
+// stream onto two helper streams and joined back; captured as parallel graph branches),
+// or one launch over all roles for a program set up to join a batch (its grid includes
+// idle blocks that take part in the step controller's block count)
+template <typename T>
+void enqueue_dual(pdcs_ctx* ctx, const Dev<T>& DT) {
+    cudaStream_t s = ctx->stream;
+    if (ctx->opt.batch_blocks > 0) {
+        k_dual_update(DT, ctx->g_dual, s);
+        return;
+    }
+    const int roles = (DT.nb_scal > 0) + (DT.nb_soc > 0) + (DT.nb_exp > 0);
+    if (roles <= 1) {
+        k_dual_exp(DT, s);
+        k_dual_soc(DT, s);
+        k_dual_scalar(DT, s);
+        return;
+    }
+    cudaEventRecord(ctx->ev_fork, s);
+    cudaStreamWaitEvent(ctx->aux[0], ctx->ev_fork, 0);
+    cudaStreamWaitEvent(ctx->aux[1], ctx->ev_fork, 0);
+    k_dual_soc(DT, ctx->aux[0]);
+    k_dual_scalar(DT, ctx->aux[1]);
+    k_dual_exp(DT, s);
+    cudaEventRecord(ctx->ev_join[0], ctx->aux[0]);
+    cudaEventRecord(ctx->ev_join[1], ctx->aux[1]);
+    cudaStreamWaitEvent(s, ctx->ev_join[0], 0);
+    cudaStreamWaitEvent(s, ctx->ev_join[1], 0);
+}
 
 // one PDHG evaluation on the state DT (FP64, or FP32 in the FP32 phase) with the matrix
 // copies of its precision
@@ -329,15 +454,15 @@ template <typename T>
 void enqueue_attempt_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     cudaStream_t s = ctx->stream;
     if (P) P->mark(0, s);
-    primal_update<T><<<ctx->g_vec_n, kBlock, 0, s>>>(DT);
+    k_primal_update(DT, ctx->g_vec_n, s);
     if (P) { P->mark(0, s); P->mark(1, s); }
-    launch_spmv<T, T>(ctx->pk, s, DT.rp, DT.ci, DT.val, DT.xh, DT.kxh0, DT.kxh1, DT.ctrl, 1, 1);
+    launch_spmv<T>(ctx->pk, s, DT.rp, DT.ci, DT.val, DT.xh, DT.kxh0, DT.kxh1, DT.ctrl, 1, 1);
     if (P) { P->mark(1, s); P->mark(2, s); }
-    dual_update<T><<<ctx->g_dual, kBlock, 0, s>>>(DT);
+    enqueue_dual(ctx, DT);
     if (P) { P->mark(2, s); P->mark(3, s); }
-    launch_spmv<T, T>(ctx->pkt, s, DT.rpT, DT.ciT, DT.valT, DT.yh, DT.ktyh, nullptr, DT.ctrl, 0, 2);
+    launch_spmv<T>(ctx->pkt, s, DT.rpT, DT.ciT, DT.valT, DT.yh, DT.ktyh, nullptr, DT.ctrl, 0, 2);
     if (P) P->mark(3, s);
-    ctx->launches += kLaunchesPerAttempt;
+    ctx->launches += ctx->launches_per_attempt;
 }
 
 // restart / termination check (or the initial evaluation of the anchor): candidates
@@ -350,26 +475,26 @@ void enqueue_check_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     mark(4);
     ctx->launches += kLaunchesPerCheck;
     mark(5);
-    flush_primal<T><<<ctx->g_vec_n, kBlock, 0, s>>>(DT);
-    flush_dual<T><<<ctx->g_vec_m, kBlock, 0, s>>>(DT);
+    k_flush_primal(DT, ctx->g_vec_n, s);
+    k_flush_dual(DT, ctx->g_vec_m, s);
     mark(5); mark(6);
-    cand_primal<T><<<dim3(ctx->g_vec_n, 2), kBlock, 0, s>>>(DT);
+    k_cand_primal(DT, dim3(ctx->g_vec_n, 2), s);
     mark(6); mark(7);
-    cand_dual<T><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(DT);
+    k_cand_dual(DT, dim3(ctx->g_dual, 2), s);
     mark(7); mark(8);
     for (int q = 0; q < 2; ++q) {
-        launch_spmv<double, double>(ctx->pk, s, D.rp, D.ci, D.val, D.xc + (size_t)q * ctx->n,
+        launch_spmv<double>(ctx->pk, s, D.rp, D.ci, D.val, D.xc + (size_t)q * ctx->n,
                                     D.kxc + (size_t)q * ctx->m, nullptr, D.ctrl, 0, 1);
-        launch_spmv<double, double>(ctx->pkt, s, D.rpT, D.ciT, D.valT,
+        launch_spmv<double>(ctx->pkt, s, D.rpT, D.ciT, D.valT,
                                     D.yc + (size_t)q * ctx->m, D.ktyc + (size_t)q * ctx->n, nullptr, D.ctrl, 0, 1);
     }
     mark(8); mark(9);
-    kkt_primal<T><<<dim3(ctx->g_dual, 2), kBlock, 0, s>>>(DT);
+    k_kkt_primal(DT, dim3(ctx->g_dual, 2), s);
     mark(9); mark(10);
-    kkt_dual<T><<<ctx->g_kktd, kBlock, 0, s>>>(DT);
+    k_kkt_dual(DT, ctx->g_kktd, s);
     mark(10); mark(11);
-    restart_primal<T><<<ctx->g_vec_n, kBlock, 0, s>>>(DT);
-    restart_dual<T><<<ctx->g_vec_m, kBlock, 0, s>>>(DT);
+    k_restart_primal(DT, ctx->g_vec_n, s);
+    k_restart_dual(DT, ctx->g_vec_m, s);
     mark(11);
     mark(4);
 }
@@ -477,6 +602,19 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
                 vT[q] = v_i[p];
             }
     }
+    // ---- SpMV storage: sliced (single programs) or binned (batches, fixed lane counts)
+    int fmt = ctx->opt.spmv_format;
+    if (fmt == 0) fmt = (ctx->opt.batch_blocks > 0 || ctx->opt.spmv_lanes != 0) ? kFormatBinned : kFormatSliced;
+    SliceHost hk, hkt;
+    if (fmt == kFormatSliced) {
+        plan_slices(rp_i, m, hk);
+        plan_slices(rpT, n, hkt);
+        if (hk.entries >= 0x7fffffffLL || hkt.entries >= 0x7fffffffLL) fmt = kFormatBinned;
+    }
+    const bool sliced = fmt == kFormatSliced;
+    ctx->pk.format = ctx->pkt.format = fmt;
+    const long long eK = sliced ? std::max(nnz, hk.entries) : nnz;    // storage entries of K~
+    const long long eKT = sliced ? std::max(nnz, hkt.entries) : nnz;  // and of K~'
     std::vector<double> h_i(m), l_h(n), u_h(n);
     for (int r = 0; r < m; ++r) h_i[r] = h[ctx->perm[r]];
     for (int j = 0; j < n; ++j) {
@@ -498,9 +636,57 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     int nb_soc = ctx->n_soc > 0 ? (int)std::min<long long>((ctx->n_soc + kWarpsPerBlock - 1) / kWarpsPerBlock,
                                                            (long long)ctx->sms * 8)
                                 : 0;
+    // SOC tiles of the FP64 dual update: cones sorted by dimension (largest first); a tile
+    // is up to 32 / S cones sharing the lane-group size S of its first cone, S the smallest
+    // power of two with dim <= S kSocLaneEntries and (32 / S) dim <= kSocTileRows; cones
+    // longer than kSocTileRows rows come last
+    std::vector<int> t_cone0, t_row0, t_order, t_trow, t_so;
+    std::vector<unsigned char> t_lg;
+    int n_large = 0;
+    {
+        std::vector<int> ord(ctx->n_soc);
+        for (int k = 0; k < ctx->n_soc; ++k) ord[k] = k;
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return soc_d[a] > soc_d[b]; });
+        std::vector<int> small, large;
+        for (int c : ord) (soc_d[c] > kSocTileRows ? large : small).push_back(c);
+        t_row0.push_back(0);
+        for (size_t i = 0; i < small.size();) {
+            const int d0 = soc_d[small[i]];
+            int lg = 0;
+            const int per_lane = ctx->opt.soc_lane_entries > 0 ? ctx->opt.soc_lane_entries : kSocLaneEntries;
+            while (lg < 5 && ((32 >> lg) * d0 > kSocTileRows || d0 > (1 << lg) * per_lane)) ++lg;
+            t_cone0.push_back((int)t_order.size());
+            t_lg.push_back((unsigned char)lg);
+            const int row0 = (int)t_trow.size();
+            for (int q = 0; q < (32 >> lg) && i < small.size(); ++q, ++i) {
+                const int c = small[i];
+                t_order.push_back(c);
+                t_so.push_back((int)t_trow.size() - row0);
+                for (int r = 0; r < soc_d[c]; ++r) t_trow.push_back(soc_off_i[c] + r);
+            }
+            t_row0.push_back((int)t_trow.size());
+        }
+        t_cone0.push_back((int)t_order.size());  // the large cones start here
+        for (int c : large) t_order.push_back(c);
+        n_large = (int)large.size();
+    }
+    const int n_tiles = (int)t_lg.size();
+    // the tiles are dealt round-robin over at most two blocks per SM (largest cones first),
+    // so the SMs' shares of the FP64 work differ by about one tile
+    const int nb_tiles = (int)std::min<long long>((n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock, 2LL * ctx->sms);
+    if (ctx->opt.batch_blocks == 0 && ctx->n_soc > 0) {
+        const int nb_large =
+            n_large > 0 ? (int)std::min<long long>((n_large + kWarpsPerBlock - 1) / kWarpsPerBlock, (long long)ctx->sms * 8)
+                        : 0;
+        nb_soc = nb_tiles + nb_large;
+    }
     // exp cones: one thread each, at most 256 per block but no fewer blocks than SMs
     // while each keeps a full warp (their FP64 work is bound by each SM's FP64 units)
-    const int exp_pb = (int)std::min<long long>(256, std::max<long long>(32, (ctx->n_exp / std::max(1, ctx->sms)) / 32 * 32));
+    // exp cones: one thread each, whole warps spread evenly over the SMs (their FP64 work is
+    // bound by each SM's FP64 pipe, so the SM with the most warps sets the time): up to
+    // 8 * SMs warps, one block of ceil(warps / SMs) warps per SM; beyond, full blocks
+    const long long exp_warps = (ctx->n_exp + kWarp - 1) / kWarp;
+    const int exp_pb = (int)std::min<long long>(256, kWarp * std::max<long long>(1, (exp_warps + ctx->sms - 1) / ctx->sms));
     int nb_exp = ctx->n_exp > 0 ? (int)std::min<long long>((ctx->n_exp + exp_pb - 1) / exp_pb, (long long)ctx->sms * 8) : 0;
     ctx->g_dual = std::max(1, nb_scal + nb_soc + nb_exp);
     if (ctx->opt.batch_blocks > 0) {
@@ -531,8 +717,14 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     Arena& A = ctx->arena;
     A.reserve<int>(m + 1); A.reserve<int>(nnz); A.reserve<int>(n + 1); A.reserve<int>(nnz);
     A.reserve<int>(m + 1); A.reserve<int>(n + 1);                    // SpMV row lists
-    A.reserve<int>(m + 1); A.reserve<int>(nnz); A.reserve<int>(n + 1); A.reserve<int>(nnz);  // binned rp, ci
-    for (int k = 0; k < 4; ++k) A.reserve<double>(nnz);              // val0, val0T, val, valT
+    A.reserve<int>(m + 1); A.reserve<int>(eK); A.reserve<int>(n + 1); A.reserve<int>(eKT);  // SpMV rp, ci
+    A.reserve<double>(eK); A.reserve<double>(eKT);                   // val0, val0T (then the SpMV values)
+    A.reserve<double>(nnz); A.reserve<double>(nnz);                  // val, valT
+    for (const SliceHost* H : {&hk, &hkt}) {                         // sliced plans
+        A.reserve<int>(H->slice_off.size() + 1); A.reserve<int>(H->out_row.size() + 1);
+        A.reserve<unsigned char>(H->slice_lg.size() + 1);
+        A.reserve<int>(H->long_row.size() + 1); A.reserve<int>(H->long_rp.size() + 1);
+    }
     for (int k = 0; k < 4; ++k) A.reserve<double>(n);                // c0 l0 u0 + cs
     A.reserve<double>(m); A.reserve<double>(m);                      // h0, hs
     A.reserve<double>(n); A.reserve<double>(n);                      // ls us
@@ -540,6 +732,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     A.reserve<int>(ctx->n_soc + 1); A.reserve<int>(ctx->n_soc + 1); A.reserve<unsigned char>(ctx->n_soc + 1);
     A.reserve<int>(ctx->n_tie + 1); A.reserve<int>(ctx->n_tie + 1);
     A.reserve<float>(ctx->n_soc + 1); A.reserve<float>(ctx->n_exp + 1);
+    A.reserve<int>(t_cone0.size() + 1); A.reserve<int>(t_row0.size() + 1); A.reserve<unsigned char>(t_lg.size() + 1);
+    A.reserve<int>(t_order.size() + 1); A.reserve<int>(t_trow.size() + 1); A.reserve<int>(t_so.size() + 1);
     A.reserve<double>(m); A.reserve<double>(m); A.reserve<double>(3LL * ctx->n_exp + 1);
     A.reserve<double>(pl.total);
     A.reserve<Ctrl>(1);
@@ -550,7 +744,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     A.reserve<double>(2LL * m);  // scr
     const bool f32 = ctx->opt.precision == PDCS_PRECISION_FP32;
     if (f32) {
-        A.reserve<float>(nnz); A.reserve<float>(nnz);                    // val_f, valT_f
+        A.reserve<float>(eK); A.reserve<float>(eKT);                     // val_f, valT_f
         for (int k = 0; k < 3; ++k) A.reserve<float>(n);                 // c l u
         A.reserve<float>(m);                                             // h
         for (int k = 0; k < 7; ++k) A.reserve<float>(n);                 // x xh x0 kty ktyh kty0 xsum
@@ -569,10 +763,27 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     ctx->rp = A.take<int>(m + 1); ctx->ci = A.take<int>(nnz);
     ctx->rpT = A.take<int>(n + 1); ctx->ciT = A.take<int>(nnz);
     ctx->pk.list = A.take<int>(m + 1); ctx->pkt.list = A.take<int>(n + 1);
-    ctx->pk.rp = A.take<int>(m + 1); ctx->pk.ci = A.take<int>(nnz);
-    ctx->pkt.rp = A.take<int>(n + 1); ctx->pkt.ci = A.take<int>(nnz);
-    ctx->val0 = A.take<double>(nnz); ctx->val0T = A.take<double>(nnz);
+    ctx->pk.rp = A.take<int>(m + 1); ctx->pk.ci = A.take<int>(eK);
+    ctx->pkt.rp = A.take<int>(n + 1); ctx->pkt.ci = A.take<int>(eKT);
+    ctx->val0 = A.take<double>(eK); ctx->val0T = A.take<double>(eKT);
     ctx->val = A.take<double>(nnz); ctx->valT = A.take<double>(nnz);
+    {
+        SpmvPlan* PP[2] = {&ctx->pk, &ctx->pkt};
+        const SliceHost* HH[2] = {&hk, &hkt};
+        for (int k = 0; k < 2; ++k) {
+            SlicePlan& S = PP[k]->S;
+            const SliceHost& H = *HH[k];
+            S.slice_off = A.take<int>(H.slice_off.size() + 1);
+            S.out_row = A.take<int>(H.out_row.size() + 1);
+            S.slice_lg = A.take<unsigned char>(H.slice_lg.size() + 1);
+            S.long_row = A.take<int>(H.long_row.size() + 1);
+            S.long_rp = A.take<int>(H.long_rp.size() + 1);
+            S.nslices = H.slice_off.empty() ? 0 : (int)H.slice_off.size() - 1;
+            S.nlong = (int)H.long_row.size();
+            S.nb_long = (S.nlong + kWarpsPerBlock - 1) / kWarpsPerBlock;
+            S.grid = S.nb_long + (S.nslices + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        }
+    }
     ctx->c0 = A.take<double>(n); ctx->l0 = A.take<double>(n); ctx->u0 = A.take<double>(n); ctx->cs = A.take<double>(n);
     ctx->h0 = A.take<double>(m); ctx->hs = A.take<double>(m);
     ctx->ls = A.take<double>(n); ctx->us = A.take<double>(n);
@@ -581,6 +792,12 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     ctx->soc_rot = A.take<unsigned char>(ctx->n_soc + 1);
     ctx->tie_off = A.take<int>(ctx->n_tie + 1); ctx->tie_len = A.take<int>(ctx->n_tie + 1);
     ctx->soc_lam = A.take<float>(ctx->n_soc + 1); ctx->exp_L = A.take<float>(ctx->n_exp + 1);
+    int* d_tcone0 = A.take<int>(t_cone0.size() + 1);
+    int* d_trow0 = A.take<int>(t_row0.size() + 1);
+    unsigned char* d_tlg = A.take<unsigned char>(t_lg.size() + 1);
+    int* d_order = A.take<int>(t_order.size() + 1);
+    int* d_trow = A.take<int>(t_trow.size() + 1);
+    int* d_so = A.take<int>(t_so.size() + 1);
     ctx->soc_w = A.take<double>(m); ctx->soc_wp = A.take<double>(m); ctx->exp_lg = A.take<double>(3LL * ctx->n_exp + 1);
     ctx->part = A.take<double>(pl.total);
     ctx->ctrl = A.take<Ctrl>(1);
@@ -595,7 +812,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     Dev<float>& DF = ctx->DF;
     float *c_f = nullptr, *l_f = nullptr, *u_f = nullptr, *h_f = nullptr, *soc_w32 = nullptr, *exp_lg32 = nullptr;
     if (f32) {
-        ctx->val_f = A.take<float>(nnz); ctx->valT_f = A.take<float>(nnz);
+        ctx->val_f = A.take<float>(eK); ctx->valT_f = A.take<float>(eKT);
         c_f = A.take<float>(n); l_f = A.take<float>(n); u_f = A.take<float>(n); h_f = A.take<float>(m);
         DF.x = A.take<float>(n); DF.xh = A.take<float>(n); DF.x0 = A.take<float>(n); DF.kty = A.take<float>(n);
         DF.ktyh = A.take<float>(n); DF.kty0 = A.take<float>(n); DF.xsum = A.take<float>(n);
@@ -623,6 +840,17 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         CK(cudaMemcpyAsync(ctx->soc_off, soc_off_i.data(), sizeof(int) * ctx->n_soc, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->soc_dim, soc_d.data(), sizeof(int) * ctx->n_soc, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->soc_rot, soc_r.data(), ctx->n_soc, cudaMemcpyHostToDevice, s));
+    }
+    {
+        auto up = [&](void* dst, const void* srcp, size_t bytes) {
+            return bytes ? cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+        };
+        CK(up(d_tcone0, t_cone0.data(), sizeof(int) * t_cone0.size()));
+        CK(up(d_trow0, t_row0.data(), sizeof(int) * t_row0.size()));
+        CK(up(d_tlg, t_lg.data(), t_lg.size()));
+        CK(up(d_order, t_order.data(), sizeof(int) * t_order.size()));
+        CK(up(d_trow, t_trow.data(), sizeof(int) * t_trow.size()));
+        CK(up(d_so, t_so.data(), sizeof(int) * t_so.size()));
     }
     if (ctx->n_tie) {
         CK(cudaMemcpyAsync(ctx->tie_off, tie_o.data(), sizeof(int) * ctx->n_tie, cudaMemcpyHostToDevice, s));
@@ -669,8 +897,15 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     // binned FP64 values
     ctx->valb = ctx->val0;
     ctx->valbT = ctx->val0T;
-    const bool tune = ctx->opt.spmv_autotune && ctx->opt.spmv_lanes == 0;
-    if (tune && f32) {
+    const bool tune = ctx->opt.spmv_autotune && ctx->opt.spmv_lanes == 0 && !sliced;
+    if (sliced) {
+        CK(store_sliced<double>(ctx, ctx->pk, hk, ctx->rp, ctx->ci, ctx->val, ctx->valb, true));
+        CK(store_sliced<double>(ctx, ctx->pkt, hkt, ctx->rpT, ctx->ciT, ctx->valT, ctx->valbT, true));
+        if (f32) {
+            CK(store_sliced<float>(ctx, ctx->pk, hk, ctx->rp, ctx->ci, ctx->val, ctx->val_f, false));
+            CK(store_sliced<float>(ctx, ctx->pkt, hkt, ctx->rpT, ctx->ciT, ctx->valT, ctx->valT_f, false));
+        }
+    } else if (tune && f32) {
         CK(tune_spmv<float>(ctx, ctx->pk, rp_i, m, ctx->rp, ctx->ci, ctx->val, ctx->val_f, ctx->DF.x, ctx->DF.kx));
         CK(tune_spmv<float>(ctx, ctx->pkt, rpT, n, ctx->rpT, ctx->ciT, ctx->valT, ctx->valT_f, ctx->DF.y,
                             ctx->DF.kty));
@@ -682,11 +917,11 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         plan_bins(rp_i, m, ctx->pk.shift, 0, ctx->sms, list_k, ctx->pk.B);
         plan_bins(rpT, n, ctx->pkt.shift, 0, ctx->sms, list_kt, ctx->pkt.B);
     }
-    if (!tune || f32) {
+    if (!sliced && (!tune || f32)) {
         CK(store_binned<double>(ctx, ctx->pk, rp_i, list_k, ctx->rp, ctx->ci, ctx->val, ctx->valb, !tune));
         CK(store_binned<double>(ctx, ctx->pkt, rpT, list_kt, ctx->rpT, ctx->ciT, ctx->valT, ctx->valbT, !tune));
     }
-    if (f32 && !tune) {
+    if (!sliced && f32 && !tune) {
         CK(store_binned<float>(ctx, ctx->pk, rp_i, list_k, ctx->rp, ctx->ci, ctx->val, ctx->val_f, false));
         CK(store_binned<float>(ctx, ctx->pkt, rpT, list_kt, ctx->rpT, ctx->ciT, ctx->valT, ctx->valT_f, false));
     }
@@ -703,8 +938,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         CK(cudaStreamSynchronize(s));
         double est = 0.0;
         for (int it = 0; it < ctx->opt.power_iters; ++it) {
-            launch_spmv<double, double>(ctx->pk, s, ctx->pk.rp, ctx->pk.ci, ctx->valb, v, w, nullptr, nullptr, 0, 0);
-            launch_spmv<double, double>(ctx->pkt, s, ctx->pkt.rp, ctx->pkt.ci, ctx->valbT, w, u, nullptr, nullptr, 0,
+            launch_spmv<double>(ctx->pk, s, ctx->pk.rp, ctx->pk.ci, ctx->valb, v, w, nullptr, nullptr, 0, 0);
+            launch_spmv<double>(ctx->pkt, s, ctx->pkt.rp, ctx->pkt.ci, ctx->valbT, w, u, nullptr, nullptr, 0,
                                         0);
             reduce_small<<<1, kBlock, 0, s>>>(n, u, nullptr, 0, ctx->scal + 3);
             double ss;
@@ -735,10 +970,17 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.soc_lam = ctx->soc_lam; D.soc_w = ctx->soc_w; D.soc_wp = ctx->soc_wp; D.exp_lg = ctx->exp_lg;
     D.exp_row0 = ctx->exp_row0; D.n_exp = ctx->n_exp; D.exp_L = ctx->exp_L;
     D.nb_scal = nb_scal; D.nb_soc = nb_soc; D.nb_exp = nb_exp; D.exp_pb = exp_pb; D.nb_primal = ctx->g_vec_n;
+    D.n_tiles = ctx->opt.batch_blocks == 0 ? n_tiles : 0;
+    D.nb_tiles = ctx->opt.batch_blocks == 0 ? nb_tiles : 0;
+    D.n_large = n_large;
+    D.tile_cone0 = d_tcone0; D.tile_row0 = d_trow0; D.tile_lg = d_tlg; D.soc_order = d_order; D.soc_trow = d_trow;
+    D.soc_so = d_so;
     D.part = ctx->part; D.pl = pl; D.ctrl = ctx->ctrl;
     D.l_orig = ctx->l0; D.u_orig = ctx->u0;
     D.exp_mlp = exp_mlp;
     D.binsK = ctx->pk.B; D.binsKT = ctx->pkt.B; D.listK = ctx->pk.list; D.listKT = ctx->pkt.list;
+    ctx->launches_per_attempt =
+        ctx->opt.batch_blocks > 0 ? kLaunchesPerAttempt : 3 + (nb_scal > 0) + (nb_soc > 0) + (nb_exp > 0);
 
     // ---- controller scalars
     Ctrl C;
@@ -804,31 +1046,34 @@ pdcs_status capture_graph(pdcs_ctx* ctx) {
     return PDCS_OK;
 }
 
-// FP32 phase -> FP64 phase: the FP64 state restarts from the check's returned candidate
-// (FP64 values and products), keeping the step size, primal weight and counters; the
-// next check re-evaluates it as the new anchor (as at the start).
+// FP32 phase -> FP64 phase, continuing the same trajectory and restart period: the pending
+// Halpern update is applied in FP32, the iterate, the anchor and the average's sums are
+// widened into the FP64 state, the cached products K~x, K~x0, K~'y, K~'y0 are formed
+// afresh by the FP64 SpMV (the FP32 ones carry FP32 rounding), and every scalar of
+// Algorithm 1 (step size, primal weight, inner index, weights, restart metrics) is kept.
 pdcs_status switch_to_fp64(pdcs_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     Dev<double>& D = ctx->D;
-    const int q = ctx->h_ctrl->sol_cand;
-    const size_t n = ctx->n, m = ctx->m;
-    CK(cudaMemcpyAsync(D.x, D.xc + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(D.x0, D.xc + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(D.kty, D.ktyc + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(D.kty0, D.ktyc + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(D.y, D.yc + q * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(D.y0, D.yc + q * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(D.kx, D.kxc + q * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(D.kx0, D.kxc + q * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(D.xsum, 0, sizeof(double) * n, s));
-    CK(cudaMemsetAsync(D.ysum, 0, sizeof(double) * m, s));
-    Ctrl C = *ctx->h_ctrl;
-    C.pending = 0; C.wsum = 0.0; C.k = 0; C.check_mode = 1; C.phi_prev = INFINITY;
-    *ctx->h_ctrl = C;
-    CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
-    ctx->fp32_active = false;
-    enqueue_check(ctx);  // anchor evaluation in FP64 (may already meet the tolerance)
+    Dev<float>& F = ctx->DF;
+    k_flush_primal(F, ctx->g_vec_n, s);
+    k_flush_dual(F, ctx->g_vec_m, s);
+    clear_pending<<<1, 1, 0, s>>>(ctx->ctrl);
+    const int g = vec_grid(std::max(ctx->m, ctx->n), ctx->sms);
+    const float* fn[3] = {F.x, F.x0, F.xsum};
+    double* dn[3] = {D.x, D.x0, D.xsum};
+    const float* fm[3] = {F.y, F.y0, F.ysum};
+    double* dm[3] = {D.y, D.y0, D.ysum};
+    for (int k = 0; k < 3; ++k) {
+        widen<<<g, kBlock, 0, s>>>(ctx->n, fn[k], dn[k]);
+        widen<<<g, kBlock, 0, s>>>(ctx->m, fm[k], dm[k]);
+    }
+    launch_spmv<double>(ctx->pk, s, D.rp, D.ci, D.val, D.x, D.kx, nullptr, nullptr, 0, 0);
+    launch_spmv<double>(ctx->pk, s, D.rp, D.ci, D.val, D.x0, D.kx0, nullptr, nullptr, 0, 0);
+    launch_spmv<double>(ctx->pkt, s, D.rpT, D.ciT, D.valT, D.y, D.kty, nullptr, nullptr, 0, 0);
+    launch_spmv<double>(ctx->pkt, s, D.rpT, D.ciT, D.valT, D.y0, D.kty0, nullptr, nullptr, 0, 0);
+    ctx->launches += 13;
     CK(cudaGetLastError());
+    ctx->fp32_active = false;
     CK(cudaStreamSynchronize(s));
     return PDCS_OK;
 }
@@ -878,6 +1123,7 @@ void fill_info(pdcs_ctx* ctx, pdcs_info* info) {
     info->spmv_plan[1] = ctx->pk.unroll;
     info->spmv_plan[2] = ctx->pkt.shift;
     info->spmv_plan[3] = ctx->pkt.unroll;
+    info->spmv_format = ctx->pk.format;
 }
 
 __global__ void batch_prepare(Dev<double>* views, int count, double tol, int start) {
@@ -921,26 +1167,26 @@ namespace {
 void batch_attempt(pdcs_batch* b) {
     const int B = (int)b->active.size();
     cudaStream_t s = b->stream;
-    primal_update_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
-    spmv_batch<4><<<dim3(b->g_spmv, 1, B), kBlock, 0, s>>>(b->views, 0);
-    dual_update_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
-    spmv_batch<4><<<dim3(b->g_spmv, 1, B), kBlock, 0, s>>>(b->views, 1);
+    k_batch(kbPrimalUpdate, b->views, dim3(b->G, 1, B), s);
+    k_spmv_batch(b->views, dim3(b->g_spmv, 1, B), 0, s);
+    k_batch(kbDualUpdate, b->views, dim3(b->G, 1, B), s);
+    k_spmv_batch(b->views, dim3(b->g_spmv, 1, B), 1, s);
     for (int i : b->active) b->ctxs[i]->launches += kLaunchesPerAttempt;
 }
 
 void batch_check(pdcs_batch* b) {
     const int B = (int)b->active.size();
     cudaStream_t s = b->stream;
-    flush_primal_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
-    flush_dual_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
-    cand_primal_batch<double><<<dim3(b->G, 2, B), kBlock, 0, s>>>(b->views);
-    cand_dual_batch<double><<<dim3(b->G, 2, B), kBlock, 0, s>>>(b->views);
-    spmv_batch<4><<<dim3(b->g_spmv, 2, B), kBlock, 0, s>>>(b->views, 2);
-    spmv_batch<4><<<dim3(b->g_spmv, 2, B), kBlock, 0, s>>>(b->views, 3);
-    kkt_primal_batch<double><<<dim3(b->G, 2, B), kBlock, 0, s>>>(b->views);
-    kkt_dual_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
-    restart_primal_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
-    restart_dual_batch<double><<<dim3(b->G, 1, B), kBlock, 0, s>>>(b->views);
+    k_batch(kbFlushPrimal, b->views, dim3(b->G, 1, B), s);
+    k_batch(kbFlushDual, b->views, dim3(b->G, 1, B), s);
+    k_batch(kbCandPrimal, b->views, dim3(b->G, 2, B), s);
+    k_batch(kbCandDual, b->views, dim3(b->G, 2, B), s);
+    k_spmv_batch(b->views, dim3(b->g_spmv, 2, B), 2, s);
+    k_spmv_batch(b->views, dim3(b->g_spmv, 2, B), 3, s);
+    k_batch(kbKktPrimal, b->views, dim3(b->G, 2, B), s);
+    k_batch(kbKktDual, b->views, dim3(b->G, 1, B), s);
+    k_batch(kbRestartPrimal, b->views, dim3(b->G, 1, B), s);
+    k_batch(kbRestartDual, b->views, dim3(b->G, 1, B), s);
     for (int i : b->active) b->ctxs[i]->launches += kLaunchesPerCheck;
 }
 
@@ -1012,6 +1258,8 @@ void pdcs_default_options(pdcs_options* o) {
     o->spmv_autotune = 0;
     o->exp_mlp = nullptr;
     o->batch_blocks = 0;
+    o->spmv_format = 0;
+    o->soc_lane_entries = 0;
 }
 
 pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, const double* lb, const double* ub,
@@ -1063,6 +1311,10 @@ pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, con
         return bad("spmv_lanes must be 0 or a power of two <= 32");
     if (o.spmv_autotune != 0 && o.spmv_autotune != 1) return bad("spmv_autotune must be 0 or 1");
     if (o.batch_blocks < 0 || o.batch_blocks > 1 << 20) return bad("batch_blocks must be in [0, 2^20]");
+    if (o.spmv_format < 0 || o.spmv_format > 2) return bad("spmv_format must be 0, 1 or 2");
+    if (o.soc_lane_entries < 0 || o.soc_lane_entries > 256) return bad("soc_lane_entries must be in [0, 256]");
+    if (o.spmv_format == 2 && (o.batch_blocks > 0 || o.spmv_lanes != 0))
+        return bad("the sliced SpMV format serves single programs with spmv_lanes = 0");
 
     pdcs_ctx* ctx = new (std::nothrow) pdcs_ctx();
     if (!ctx) return bad("host allocation failed");
@@ -1082,8 +1334,20 @@ pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, con
         }
     }
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_ctrl, sizeof(Ctrl));
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&ctx->aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         g_create_error = std::string("CUDA setup: ") + cudaGetErrorString(e);
+        delete ctx;
+        return PDCS_ERR_CUDA;
+    }
+    if (e == cudaSuccess) e = k_prepare(static_cast<const Dev<double>*>(nullptr));
+    if (e == cudaSuccess) e = k_prepare(static_cast<const Dev<float>*>(nullptr));
+    if (e != cudaSuccess) {
+        g_create_error = std::string("kernel attributes: ") + cudaGetErrorString(e);
         delete ctx;
         return PDCS_ERR_CUDA;
     }
@@ -1128,7 +1392,7 @@ pdcs_status pdcs_solve(pdcs_ctx* ctx, double tol, int64_t max_iter, pdcs_info* i
                 st = capture_graph(ctx);
                 if (st != PDCS_OK) return st;
                 CK(cudaGraphLaunch(ctx->fp32_active ? ctx->graph32 : ctx->graph, ctx->stream));
-                ctx->launches += (long long)period * kLaunchesPerAttempt + kLaunchesPerCheck;
+                ctx->launches += (long long)period * ctx->launches_per_attempt + kLaunchesPerCheck;
             } else {
                 for (long long a = 0; a < to_b; ++a) enqueue_attempt(ctx);
                 enqueue_check(ctx);
@@ -1204,11 +1468,11 @@ pdcs_status pdcs_get_iterate(pdcs_ctx* ctx, double* x, double* y, double* xhat, 
     if (!ctx) return PDCS_ERR_INVALID;
     // materialise a pending Halpern update (same arithmetic as the next evaluation would apply)
     if (ctx->fp32_active) {
-        flush_primal<float><<<ctx->g_vec_n, kBlock, 0, ctx->stream>>>(ctx->DF);
-        flush_dual<float><<<ctx->g_vec_m, kBlock, 0, ctx->stream>>>(ctx->DF);
+        k_flush_primal(ctx->DF, ctx->g_vec_n, ctx->stream);
+        k_flush_dual(ctx->DF, ctx->g_vec_m, ctx->stream);
     } else {
-        flush_primal<double><<<ctx->g_vec_n, kBlock, 0, ctx->stream>>>(ctx->D);
-        flush_dual<double><<<ctx->g_vec_m, kBlock, 0, ctx->stream>>>(ctx->D);
+        k_flush_primal(ctx->D, ctx->g_vec_n, ctx->stream);
+        k_flush_dual(ctx->D, ctx->g_vec_m, ctx->stream);
     }
     clear_pending<<<1, 1, 0, ctx->stream>>>(ctx->ctrl);
     ctx->launches += 3;
@@ -1268,8 +1532,8 @@ pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y,
     CK(cudaMemcpyAsync(D.y, ys.data(), sizeof(double) * ctx->m, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(D.y0, ys.data(), sizeof(double) * ctx->m, cudaMemcpyHostToDevice, s));
     // cached products of the start: K x, K'y
-    launch_spmv<double, double>(ctx->pk, s, D.rp, D.ci, D.val, D.x, D.kx, nullptr, nullptr, 0, 0);
-    launch_spmv<double, double>(ctx->pkt, s, D.rpT, D.ciT, D.valT, D.y, D.kty, nullptr, nullptr, 0, 0);
+    launch_spmv<double>(ctx->pk, s, D.rp, D.ci, D.val, D.x, D.kx, nullptr, nullptr, 0, 0);
+    launch_spmv<double>(ctx->pkt, s, D.rpT, D.ciT, D.valT, D.y, D.kty, nullptr, nullptr, 0, 0);
     CK(cudaMemcpyAsync(D.kx0, D.kx, sizeof(double) * ctx->m, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(D.kty0, D.kty, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(D.xsum, 0, sizeof(double) * ctx->n, s));
@@ -1305,6 +1569,121 @@ pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y,
     CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     ctx->started = false;
+    return PDCS_OK;
+}
+
+pdcs_status pdcs_get_state(pdcs_ctx* ctx, pdcs_state* st, const pdcs_state_arrays* arr) {
+    if (!ctx) return PDCS_ERR_INVALID;
+    if (ctx->fp32_active) { ctx->err = "pdcs_get_state needs the FP64 phase"; return PDCS_ERR_INVALID; }
+    cudaStream_t s = ctx->stream;
+    Dev<double>& D = ctx->D;
+    // apply a pending Halpern update (the arithmetic of the next evaluation's update)
+    k_flush_primal(D, ctx->g_vec_n, s);
+    k_flush_dual(D, ctx->g_vec_m, s);
+    clear_pending<<<1, 1, 0, s>>>(ctx->ctrl);
+    ctx->launches += 3;
+    CK(cudaGetLastError());
+    pdcs_status r = read_ctrl(ctx);
+    if (r != PDCS_OK) return r;
+    if (arr) {
+        const int n = ctx->n, m = ctx->m;
+        const double* srcn[6] = {D.x, D.xh, D.x0, D.xsum, D.kty, D.kty0};
+        double* dstn[6] = {arr->x, arr->xhat, arr->x0, arr->xsum, arr->kty, arr->kty0};
+        const double* srcm[6] = {D.y, D.yh, D.y0, D.ysum, D.kx, D.kx0};
+        double* dstm[6] = {arr->y, arr->yhat, arr->y0, arr->ysum, arr->kx, arr->kx0};
+        std::vector<double> tmp(m);
+        for (int k = 0; k < 6; ++k)
+            if (dstn[k]) CK(cudaMemcpyAsync(dstn[k], srcn[k], sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < 6; ++k) {
+            if (!dstm[k]) continue;
+            CK(cudaMemcpyAsync(tmp.data(), srcm[k], sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int r2 = 0; r2 < m; ++r2) dstm[k][ctx->perm[r2]] = tmp[r2];
+        }
+        if (arr->soc_root && ctx->n_soc)
+            CK(cudaMemcpyAsync(arr->soc_root, ctx->soc_lam, sizeof(float) * ctx->n_soc, cudaMemcpyDeviceToHost, s));
+        if (arr->exp_root && ctx->n_exp)
+            CK(cudaMemcpyAsync(arr->exp_root, ctx->exp_L, sizeof(float) * ctx->n_exp, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (st) {
+        const Ctrl& C = *ctx->h_ctrl;
+        st->eta = C.eta; st->omega = C.omega; st->wsum = C.wsum; st->phi0 = C.phi0; st->phi_prev = C.phi_prev;
+        for (int k = 0; k < 3; ++k) st->comp0[k] = C.comp0[k];
+        st->attempts = C.attempts; st->accepted = C.accepted; st->k = C.k; st->restarts = C.restarts;
+        st->started = ctx->started ? 1 : 0;
+        st->status = C.status;
+    }
+    return PDCS_OK;
+}
+
+pdcs_status pdcs_set_state(pdcs_ctx* ctx, const pdcs_state* st, const pdcs_state_arrays* arr) {
+    if (!ctx) return PDCS_ERR_INVALID;
+    if (!st || !arr || !arr->x || !arr->x0 || !arr->y || !arr->y0) {
+        ctx->err = "pdcs_set_state needs the scalars and x, x0, y, y0";
+        return PDCS_ERR_INVALID;
+    }
+    if (!(st->eta > 0.0) || !(st->omega > 0.0) || !std::isfinite(st->eta) || !std::isfinite(st->omega) ||
+        st->status < 0 || st->status > 2 || st->attempts < 0 || st->accepted < 0 || st->k < 0 || st->restarts < 0) {
+        ctx->err = "pdcs_set_state: invalid scalars";
+        return PDCS_ERR_INVALID;
+    }
+    const int n = ctx->n, m = ctx->m;
+    const double* inn[4] = {arr->x, arr->x0, arr->xsum, nullptr};
+    const double* inm[4] = {arr->y, arr->y0, arr->ysum, nullptr};
+    for (int k = 0; k < 3; ++k) {
+        if (inn[k]) for (int j = 0; j < n; ++j) if (!std::isfinite(inn[k][j])) { ctx->err = "non-finite state"; return PDCS_ERR_INVALID; }
+        if (inm[k]) for (int i = 0; i < m; ++i) if (!std::isfinite(inm[k][i])) { ctx->err = "non-finite state"; return PDCS_ERR_INVALID; }
+    }
+    cudaStream_t s = ctx->stream;
+    Dev<double>& D = ctx->D;
+    std::vector<double> tmp(m);
+    auto put_n = [&](double* dst, const double* h) -> cudaError_t {
+        if (!h) return cudaMemsetAsync(dst, 0, sizeof(double) * n, s);
+        return cudaMemcpyAsync(dst, h, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    };
+    auto put_m = [&](double* dst, const double* h) -> cudaError_t {
+        if (!h) return cudaMemsetAsync(dst, 0, sizeof(double) * m, s);
+        for (int r = 0; r < m; ++r) tmp[r] = h[ctx->perm[r]];
+        cudaError_t e = cudaMemcpyAsync(dst, tmp.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // tmp is reused (pageable)
+        return e;
+    };
+    CK(put_n(D.x, arr->x)); CK(put_n(D.x0, arr->x0)); CK(put_n(D.xsum, arr->xsum));
+    CK(put_m(D.y, arr->y)); CK(put_m(D.y0, arr->y0)); CK(put_m(D.ysum, arr->ysum));
+    const bool products = arr->kx && arr->kx0 && arr->kty && arr->kty0;
+    if (products) {
+        CK(put_n(D.kty, arr->kty)); CK(put_n(D.kty0, arr->kty0));
+        CK(put_m(D.kx, arr->kx)); CK(put_m(D.kx0, arr->kx0));
+    } else {
+        launch_spmv<double>(ctx->pk, s, D.rp, D.ci, D.val, D.x, D.kx, nullptr, nullptr, 0, 0);
+        launch_spmv<double>(ctx->pk, s, D.rp, D.ci, D.val, D.x0, D.kx0, nullptr, nullptr, 0, 0);
+        launch_spmv<double>(ctx->pkt, s, D.rpT, D.ciT, D.valT, D.y, D.kty, nullptr, nullptr, 0, 0);
+        launch_spmv<double>(ctx->pkt, s, D.rpT, D.ciT, D.valT, D.y0, D.kty0, nullptr, nullptr, 0, 0);
+        ctx->launches += 4;
+        CK(cudaGetLastError());
+    }
+    if (arr->soc_root && ctx->n_soc)
+        CK(cudaMemcpyAsync(ctx->soc_lam, arr->soc_root, sizeof(float) * ctx->n_soc, cudaMemcpyHostToDevice, s));
+    if (arr->exp_root && ctx->n_exp)
+        CK(cudaMemcpyAsync(ctx->exp_L, arr->exp_root, sizeof(float) * ctx->n_exp, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    pdcs_status r = read_ctrl(ctx);
+    if (r != PDCS_OK) return r;
+    Ctrl C = *ctx->h_ctrl;
+    C.eta = st->eta; C.omega = st->omega; C.wsum = st->wsum; C.phi0 = st->phi0; C.phi_prev = st->phi_prev;
+    for (int k = 0; k < 3; ++k) C.comp0[k] = st->comp0[k];
+    C.attempts = st->attempts; C.accepted = st->accepted; C.k = st->k; C.restarts = st->restarts;
+    C.tau = C.eta / C.omega;
+    C.sigma = C.eta * C.omega;
+    C.pending = 0; C.check_mode = 0; C.restart_now = 0; C.ticket = 0;
+    C.status = st->status == 0 ? kRunning : (st->status == 1 ? kConverged : kNumericError);
+    *ctx->h_ctrl = C;
+    CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->started = st->started != 0;
+    ctx->fp32_active = false;
     return PDCS_OK;
 }
 

@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpdcs.so")
 
 CONE_ZERO, CONE_NONNEG, CONE_SOC, CONE_RSOC, CONE_EXP = 0, 1, 2, 3, 4
+SPMV_AUTO, SPMV_BINNED, SPMV_SLICED = 0, 1, 2
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_DEVICE_TIMEOUT, MAX_ITER, TIME_LIMIT = 0, 1, 2, 3, 4, 5, 10, 11
 RESCALE_NONE, RESCALE_COORD, RESCALE_BLOCK = 0, 1, 2
 STEP_ADAPTIVE, STEP_CONSTANT, STEP_PLAIN = 0, 1, 2
@@ -44,7 +45,8 @@ class pdcs_options(ctypes.Structure):
                 ("power_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("fp32_switch_tol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("spmv_lanes", ctypes.c_int32), ("time_limit", ctypes.c_double),
-                ("exp_mlp", ctypes.c_void_p), ("spmv_autotune", ctypes.c_int32), ("batch_blocks", ctypes.c_int32)]
+                ("exp_mlp", ctypes.c_void_p), ("spmv_autotune", ctypes.c_int32), ("batch_blocks", ctypes.c_int32),
+                ("spmv_format", ctypes.c_int32), ("soc_lane_entries", ctypes.c_int32)]
 
 
 class pdcs_info(ctypes.Structure):
@@ -53,11 +55,27 @@ class pdcs_info(ctypes.Structure):
                 ("pobj", ctypes.c_double), ("dobj", ctypes.c_double), ("eta", ctypes.c_double),
                 ("omega", ctypes.c_double), ("setup_seconds", ctypes.c_double),
                 ("solve_seconds", ctypes.c_double), ("status", ctypes.c_int32), ("fp64_phase", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64), ("spmv_plan", ctypes.c_int32 * 4)]
+                ("kernel_launches", ctypes.c_int64), ("spmv_plan", ctypes.c_int32 * 4), ("spmv_format", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if isinstance(getattr(self, k), ctypes.Array) else getattr(self, k))
                 for k, _ in self._fields_}
+
+
+class pdcs_state(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("omega", ctypes.c_double), ("wsum", ctypes.c_double),
+                ("phi0", ctypes.c_double), ("phi_prev", ctypes.c_double), ("comp0", ctypes.c_double * 3),
+                ("attempts", ctypes.c_int64), ("accepted", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("restarts", ctypes.c_int64), ("started", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+STATE_N = ["x", "xhat", "x0", "xsum", "kty", "kty0"]
+STATE_M = ["y", "yhat", "y0", "ysum", "kx", "kx0"]
+
+
+class pdcs_state_arrays(ctypes.Structure):
+    _fields_ = [(k, _dp) for k in ["x", "xhat", "x0", "xsum", "y", "yhat", "y0", "ysum", "kx", "kx0", "kty", "kty0"]] + \
+        [("soc_root", _fp), ("exp_root", _fp)]
 
 
 _lock = threading.Lock()
@@ -76,6 +94,8 @@ SIGNATURES = {
     "pdcs_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pdcs_info)]),
     "pdcs_set_warm_start": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_double]),
     "pdcs_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _dp, _i64p]),
+    "pdcs_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pdcs_state), ctypes.POINTER(pdcs_state_arrays)]),
+    "pdcs_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pdcs_state), ctypes.POINTER(pdcs_state_arrays)]),
     "pdcs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "pdcs_destroy": (None, [ctypes.c_void_p]),
     "pdcs_proj_cones_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -232,6 +252,47 @@ def pdcs_set_warm_start(ctx, x=None, y=None, omega=0.0):
         raise PdcsError(st, pdcs_last_error(ctx))
 
 
+def pdcs_get_state(ctx, m, n, n_soc=0, n_exp=0):
+    """The iterate state in the rescaled program's coordinates: dict of the vectors
+    (x, xhat, x0, xsum, kty, kty0: n; y, yhat, y0, ysum, kx, kx0: m), the root-search
+    starting points (soc_root: n_soc, exp_root: n_exp) and the scalars."""
+    vec = {k: np.empty(n) for k in STATE_N}
+    vec.update({k: np.empty(m) for k in STATE_M})
+    roots = {"soc_root": np.empty(max(n_soc, 1), np.float32), "exp_root": np.empty(max(n_exp, 1), np.float32)}
+    arr = pdcs_state_arrays(**{k: _ptr(v) for k, v in vec.items()},
+                            **{k: _ptr(v, _fp) for k, v in roots.items()})
+    vec["soc_root"], vec["exp_root"] = roots["soc_root"][:n_soc], roots["exp_root"][:n_exp]
+    st = pdcs_state()
+    r = lib().pdcs_get_state(ctx, ctypes.byref(st), ctypes.byref(arr))
+    if r != OK:
+        raise PdcsError(r, pdcs_last_error(ctx))
+    for f, _ in pdcs_state._fields_:
+        v = getattr(st, f)
+        vec[f] = list(v) if isinstance(v, ctypes.Array) else v
+    return vec
+
+
+def pdcs_set_state(ctx, state):
+    """Restores a state (as returned by pdcs_get_state; the product vectors and the sums
+    may be absent: recomputed / zero)."""
+    keep = {k: _f64(state[k]) for k in STATE_N + STATE_M if state.get(k) is not None}
+    roots = {k: np.ascontiguousarray(state[k], np.float32) for k in ("soc_root", "exp_root")
+             if state.get(k) is not None and len(state[k])}
+    arr = pdcs_state_arrays(**{k: _ptr(v) for k, v in keep.items()},
+                            **{k: _ptr(v, _fp) for k, v in roots.items()})
+    st = pdcs_state()
+    for f, _ in pdcs_state._fields_:
+        if f == "comp0":
+            st.comp0[:] = [float(x) for x in state["comp0"]]
+        elif f in ("eta", "omega", "wsum", "phi0", "phi_prev"):
+            setattr(st, f, float(state[f]))
+        else:
+            setattr(st, f, int(state[f]))
+    r = lib().pdcs_set_state(ctx, ctypes.byref(st), ctypes.byref(arr))
+    if r != OK:
+        raise PdcsError(r, pdcs_last_error(ctx))
+
+
 KERNEL_CLASSES = ["primal_update", "spmv_K", "dual_update", "spmv_KT", "check", "check_flush", "check_cand_primal",
                   "check_cand_dual", "check_spmv", "check_kkt_primal", "check_kkt_dual", "check_restart"]
 
@@ -271,6 +332,8 @@ class Solver:
 
     def __init__(self, prob, stream=None, **options):
         self.m, self.n = int(prob["m"]), int(prob["n"])
+        kinds = np.asarray(prob["cone_types"])
+        self.n_soc, self.n_exp = int(np.sum((kinds == CONE_SOC) | (kinds == CONE_RSOC))), int(np.sum(kinds == CONE_EXP))
         mlp = options.pop("exp_mlp", None)
         self.options = pdcs_default_options(**options)
         if mlp is not None:  # weights of the learned exp starting point, copied by pdcs_create
@@ -304,6 +367,12 @@ class Solver:
 
     def warm_start(self, x=None, y=None, omega=0.0):
         pdcs_set_warm_start(self.ctx, x, y, omega)
+
+    def get_state(self):
+        return pdcs_get_state(self.ctx, self.m, self.n, self.n_soc, self.n_exp)
+
+    def set_state(self, state):
+        pdcs_set_state(self.ctx, state)
 
     def close(self):
         if self.ctx:

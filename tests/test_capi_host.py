@@ -39,7 +39,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     """Compile a probe against include/pdcs.h with gcc and compare sizes and offsets."""
     import subprocess
     structs = {"pdcs_csr": P.pdcs_csr, "pdcs_cone": P.pdcs_cone, "pdcs_options": P.pdcs_options,
-               "pdcs_info": P.pdcs_info}
+               "pdcs_info": P.pdcs_info, "pdcs_state": P.pdcs_state, "pdcs_state_arrays": P.pdcs_state_arrays}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdcs.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))

@@ -223,6 +223,62 @@ def test_iteration_parity_from_later_states(prob_name, start):
     g.close()
 
 
+@pytest.mark.parametrize("start", [0, 64, 500, 2000])
+def test_one_evaluation_from_oracle_states(start):
+    """The oracle's full state after `start` evaluations of the 1 % mixed-cone program is
+    loaded into the library (pdcs_set_state; cached products recomputed by the library's
+    SpMV) and both run ONE evaluation: xhat and yhat element by element per cone role, the
+    next Halpern iterate and step size, all within 1e-12.  No feedback through the adaptive
+    step is involved, so this bounds the per-evaluation error directly."""
+    from parity_helpers import one_evaluation
+    p = I.scaled_mixed_cone(1, 0.01)
+    o = oracle.Solver(p, check_period=64)
+    o.run(start)
+    g = P.Solver(p, check_period=64)
+    err, acc = one_evaluation(p, g, o)
+    assert acc[0] == acc[1], (acc, err)
+    assert max(err.values()) <= RTOL, err
+    g.close()
+
+
+@pytest.mark.parametrize("mode", [oracle.STEP_CONSTANT, oracle.STEP_PLAIN])
+def test_one_evaluation_fixed_step_modes(mode):
+    """One evaluation from the oracle's state after 0, 7, 64 and 130 evaluations in the
+    constant and plain PDHG modes, within 1e-12."""
+    from parity_helpers import one_evaluation
+    p = I.small_socp(0)
+    opts = dict(step_mode=mode)
+    if mode == oracle.STEP_PLAIN:
+        opts["rescale"] = oracle.RESCALE_NONE
+    o = oracle.Solver(p, **opts)
+    g = P.Solver(p, **opts)
+    done = 0
+    for k in [0, 7, 64, 130]:
+        o.run(k - done)
+        done = k
+        err, acc = one_evaluation(p, g, o)
+        done += 1
+        assert acc[0] == acc[1] and max(err.values()) <= RTOL, (k, err)
+    g.close()
+
+
+def test_state_round_trip_resumes_bitwise():
+    """pdcs_get_state then pdcs_set_state (with the cached products) on a second context
+    continues exactly as the first."""
+    p = I.scaled_mixed_cone(1, 0.01)
+    a = P.Solver(p, check_period=16)
+    a.run(40)
+    b = P.Solver(p, check_period=16)
+    b.set_state(a.get_state())
+    a.run(37)
+    b.run(37)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ["x", "y", "xhat", "yhat", "xsum", "ysum", "eta", "omega", "restarts", "accepted"]:
+        assert np.array_equal(sa[k], sb[k]), k
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("mode", [oracle.STEP_CONSTANT, oracle.STEP_PLAIN])
 def test_fixed_step_modes_parity(mode):
     p = I.small_socp(0)
@@ -326,9 +382,61 @@ def test_spmv_plans_agree_with_oracle(prob_name):
     computes the same products up to the order of summation: 16 evaluations stay at
     the oracle to the iteration-parity tolerance."""
     p = I.small_socp(0) if prob_name == "small_socp" else I.scaled_mixed_cone(1, 0.01)
-    for opts in [dict(spmv_lanes=1), dict(spmv_lanes=32), dict(spmv_autotune=1)]:
+    for opts in [dict(spmv_lanes=1), dict(spmv_lanes=32), dict(spmv_autotune=1), dict(spmv_format=P.SPMV_BINNED),
+                 dict(spmv_format=P.SPMV_SLICED)]:
         g, o = _pair(p, check_period=16, **opts)
         g.run(16)
         o.run(16)
         assert _compare_iterates(g, o) <= RTOL, opts
         g.close()
+
+
+def _ragged_lp(seed=3, m=3000, n=2500):
+    """An LP whose rows and columns span every SpMV path: empty rows, short rows of 1-7
+    entries, rows around the sliced limit (255-257 entries) and rows of 4,000 entries;
+    columns of K' from empty to ~1,000 entries."""
+    rng = np.random.default_rng(seed)
+    lens = rng.choice([0, 1, 2, 3, 7, 20, 64, 255, 256, 257], m, p=[.05, .1, .1, .1, .15, .2, .2, .04, .03, .03])
+    lens[rng.choice(m, 6, replace=False)] = 4000
+    hot = rng.choice(n, 40, replace=False)  # popular columns: long rows of K'
+    cols = []
+    for k in lens:
+        c = rng.choice(n, size=int(k), replace=False) if k < n else np.arange(n)
+        c[: min(int(k), 3)] = rng.choice(hot, min(int(k), 3), replace=False)
+        cols.append(np.unique(c))
+    row_ptr = np.concatenate([[0], np.cumsum([len(c) for c in cols])])
+    col = np.concatenate(cols).astype(np.int32)
+    val = rng.standard_normal(col.size)
+    return {"m": m, "n": n, "row_ptr": row_ptr, "col": col, "val": val, "c": rng.standard_normal(n),
+            "h": rng.standard_normal(m), "lb": None, "ub": None,
+            "cone_types": np.array([P.CONE_NONNEG]), "cone_dims": np.array([m])}
+
+
+@pytest.mark.parametrize("fmt", [1, 2])
+def test_spmv_formats_match_host_products(fmt):
+    """The cached products that pdcs_set_state recomputes with the library's SpMV (K~x,
+    K~x0, K~'y, K~'y0) against the products formed on the host from the same scaled
+    matrix, for the binned and the sliced storage, on rows from empty to 4,000 entries:
+    each within 1e-14 of sum_j |K~ij x_j|."""
+    import scipy.sparse as sp
+    p = _ragged_lp()
+    g = P.Solver(p, spmv_format=fmt)
+    assert g.info()["spmv_format"] == fmt
+    dr, dc = g.scaling()
+    K = sp.csr_matrix((p["val"], p["col"], p["row_ptr"]), shape=(p["m"], p["n"]))
+    Ks = sp.diags(dr) @ K @ sp.diags(dc)
+    rng = np.random.default_rng(1)
+    st = g.get_state()
+    for k in ["x", "x0"]:
+        st[k] = rng.standard_normal(p["n"]) * np.exp(rng.normal(0, 2, p["n"]))
+    for k in ["y", "y0"]:
+        st[k] = rng.standard_normal(p["m"]) * np.exp(rng.normal(0, 2, p["m"]))
+    for k in ["kx", "kx0", "kty", "kty0", "xsum", "ysum", "soc_root", "exp_root"]:
+        st.pop(k)
+    g.set_state(st)
+    got = g.get_state()
+    for prod, vec, A in [("kx", "x", Ks), ("kx0", "x0", Ks), ("kty", "y", Ks.T.tocsr()), ("kty0", "y0", Ks.T.tocsr())]:
+        ref = A @ st[vec]
+        bound = abs(A) @ np.abs(st[vec])
+        assert np.all(np.abs(got[prod] - ref) <= 1e-14 * bound + 1e-300), prod
+    g.close()
