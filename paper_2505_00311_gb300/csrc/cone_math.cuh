@@ -1254,18 +1254,25 @@ __host__ __device__ __forceinline__ ExpEnds exp_ends(double r0, double s0, doubl
 
 // Fills the case-4 data of v0 = (r0, s0, t0), D = diag(dr, ds, dt), in precision R
 // from values given in double (logs of the scales and the endpoint quantities passed in).
+// Logarithms of the data used by the log-domain evaluation (exp_eval); anchor 3 or 4 (0:
+// both): the evaluation next to that endpoint reads log s0 or log r0 only.
 template <typename R>
-__host__ __device__ __forceinline__ void exp_case4_setup(ExpCase4T<R>& e, double r0, double s0, double t0, double dr,
-                                                         double ds, R ldr, R lds, R ldt, const ExpEnds& q,
-                                                         int anchor = 0) {
-    e.r0 = R(r0); e.s0 = R(s0); e.t0 = R(t0); e.dr = R(dr); e.ds = R(ds);
-    e.tau = R(ds / dr);
-    e.ldt = ldt; e.ldr = ldr; e.lds = lds;
+__host__ __device__ __forceinline__ void exp_case4_logs(ExpCase4T<R>& e, double r0, double s0, double t0, int anchor) {
     const R ninf = -R(INFINITY);
-    // anchor 3 or 4 (0: both): the evaluation next to that endpoint reads log s0 or log r0 only
     e.lr0 = (anchor != 3 && r0 > 0.0) ? R(log(R(r0))) : ninf;
     e.ls0 = (anchor != 4 && s0 > 0.0) ? R(log(R(s0))) : ninf;
     e.lt0 = t0 > 0.0 ? R(log(R(t0))) : (t0 < 0.0 ? R(log(R(-t0))) : ninf);
+}
+
+// (logs = false: without the logarithms of the data; exp_case4_logs adds them)
+template <typename R>
+__host__ __device__ __forceinline__ void exp_case4_setup(ExpCase4T<R>& e, double r0, double s0, double t0, double dr,
+                                                         double ds, R ldr, R lds, R ldt, const ExpEnds& q,
+                                                         int anchor = 0, bool logs = true) {
+    e.r0 = R(r0); e.s0 = R(s0); e.t0 = R(t0); e.dr = R(dr); e.ds = R(ds);
+    e.tau = R(ds / dr);
+    e.ldt = ldt; e.ldr = ldr; e.lds = lds;
+    if (logs) exp_case4_logs(e, r0, s0, t0, anchor);
     e.a3 = R(q.a3);
     e.a4 = R(q.a4);
     e.a4m1 = R(q.a4m1);
@@ -1474,7 +1481,10 @@ __host__ __device__ __forceinline__ bool exp_lin_polish(const ExpCase4& e, doubl
 #pragma unroll
             for (int k = 0; k < 2; ++k) out[k] = fabs(vp[k]) <= fabs(vd[k]) ? vp[k] : v0[k] - vd[k];
             out[2] = t0 >= 0.0 ? t0 - vd[2] : vp[2];
-            if (L_out) *L_out = log(delta + s);
+            if (L_out) {  // the next search's starting point: FP32 precision is enough
+                const double d1 = delta + s;
+                *L_out = d1 > 1e-30 ? (double)logf((float)d1) : log(d1);
+            }
             return true;
         }
         const double nd = delta + s;
@@ -1493,14 +1503,14 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
                                                  const float* mlp = nullptr, int* ev = nullptr) {
     // cases 1-3, screened in FP32; a point the FP64 test puts outside after an uncertain
     // screen is taken as inside when it is within 1e-14 |v| of the set (see exp_gap_to_cone)
-    const double near = 1e-14 * sqrt(r0 * r0 + s0 * s0 + t0 * t0);
+    auto near = [&]() { return 1e-14 * sqrt(r0 * r0 + s0 * s0 + t0 * t0); };
     int c1 = kexp_screen32((float)r0 / (float)dr, (float)s0 / (float)ds, (float)t0 / (float)dt);
-    if (c1 == 0) c1 = (in_kexp(r0 / dr, s0 / ds, t0 / dt) || exp_gap_to_cone(r0, s0, t0, dr, ds, dt) <= near) ? 1 : -1;
+    if (c1 == 0) c1 = (in_kexp(r0 / dr, s0 / ds, t0 / dt) || exp_gap_to_cone(r0, s0, t0, dr, ds, dt) <= near()) ? 1 : -1;
     if (c1 > 0) { out[0] = r0; out[1] = s0; out[2] = t0; return; }
     int c2 = kexpdual_screen32(-(float)dr * (float)r0, -(float)ds * (float)s0, -(float)dt * (float)t0);
     if (c2 == 0)
-        c2 = (in_kexp_dual(-dr * r0, -ds * s0, -dt * t0) || exp_gap_to_polar(r0, s0, t0, dr, ds, dt) <= near) ? 1
-                                                                                                            : -1;
+        c2 = (in_kexp_dual(-dr * r0, -ds * s0, -dt * t0) || exp_gap_to_polar(r0, s0, t0, dr, ds, dt) <= near()) ? 1
+                                                                                                              : -1;
     if (c2 > 0) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
     if (r0 <= 0.0 && s0 <= 0.0) { out[0] = r0; out[1] = 0.0; out[2] = t0 > 0.0 ? t0 : 0.0; return; }
     // case 4: root in FP32
@@ -1567,12 +1577,12 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
     if (ok) {
         // FP64 polish from the FP32 root, same branch and anchor
         ExpCase4 e;
-        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2], ends, ef.anchor);
+        exp_case4_setup(e, r0, s0, t0, dr, ds, lg[0], lg[1], lg[2], ends, ef.anchor, false);
         e.kind = ef.kind;
         e.anchor = ef.anchor;
         e.dir = (double)ef.dir;
         if (Lf > -575.0f) {  // linear domain when rho and the offset are moderate
-            const double delta0 = exp((double)Lf);
+            const double delta0 = Lf > -80.0f ? (double)expf(Lf) : exp((double)Lf);  // a starting point
             const double rho0 = (e.anchor == 4 ? e.a4 : e.a3) + e.dir * delta0;
             const double hi = e.kind == 1 ? 0.5 * fabs(e.w34) : INFINITY;
             double Lout;
@@ -1581,6 +1591,7 @@ __host__ __device__ inline void exp_project_fast(double r0, double s0, double t0
                 return;
             }
         }
+        exp_case4_logs(e, r0, s0, t0, ef.anchor);
         // Newton steps s until one is small enough that the result at L + s follows from
         // the values at L to first order (error of order s^2)
         double L = (double)Lf;

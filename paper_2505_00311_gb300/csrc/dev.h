@@ -38,10 +38,9 @@ struct SlicePlan {
 };
 
 // Rows of one SOC tile staged in shared memory (32 bytes each: the FP64 value, its weight
-// and inverse weight, FP32 copies of the entry and of the weight), per warp; lanes per cone
-// are chosen so that each lane takes about kSocLaneEntries entries of its cone.
+// and inverse weight, FP32 copies of the entry and of the weight), per warp
+// (pdcs_options.soc_lane_entries > 0).
 constexpr int kSocTileRows = 256;
-constexpr int kSocLaneEntries = 4;
 
 template <typename T>
 struct Dev {

@@ -149,6 +149,26 @@ __global__ void __launch_bounds__(kBlock) spmv_sliced(SlicePlan S, const int* __
     const V2* vp = reinterpret_cast<const V2*>(val + base) + lane;
     T acc = T(0);
     int q = 0;
+    for (; q + 4 <= steps; q += 4) {  // four pairs in flight
+        int2 c[4];
+        V2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = __ldg(cp + 32 * (q + u));
+            v[u] = __ldg(vp + 32 * (q + u));
+        }
+        T xv[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            xv[2 * u] = c[u].x >= 0 ? __ldg(x + c[u].x) : T(0);
+            xv[2 * u + 1] = c[u].y >= 0 ? __ldg(x + c[u].y) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            acc += v[u].x * xv[2 * u];
+            acc += v[u].y * xv[2 * u + 1];
+        }
+    }
     for (; q + 2 <= steps; q += 2) {  // two pairs in flight
         const int2 c0 = __ldg(cp + 32 * q), c1 = __ldg(cp + 32 * (q + 1));
         const V2 v0 = __ldg(vp + 32 * q), v1 = __ldg(vp + 32 * (q + 1));

@@ -275,9 +275,9 @@ int spmv_grid(int rows, int G, int sms) {
     return (int)std::max(1LL, std::min(g, (long long)sms * 32));
 }
 
-int vec_grid(long long k, int sms) {
+int vec_grid(long long k, int sms, int per_sm = 8) {
     long long g = (k + kBlock - 1) / kBlock;
-    return (int)std::max(1LL, std::min(g, (long long)sms * 8));
+    return (int)std::max(1LL, std::min(g, (long long)sms * per_sm));
 }
 
 
@@ -636,10 +636,10 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     int nb_soc = ctx->n_soc > 0 ? (int)std::min<long long>((ctx->n_soc + kWarpsPerBlock - 1) / kWarpsPerBlock,
                                                            (long long)ctx->sms * 8)
                                 : 0;
-    // SOC tiles of the FP64 dual update: cones sorted by dimension (largest first); a tile
-    // is up to 32 / S cones sharing the lane-group size S of its first cone, S the smallest
-    // power of two with dim <= S kSocLaneEntries and (32 / S) dim <= kSocTileRows; cones
-    // longer than kSocTileRows rows come last
+    // SOC tiles of the FP64 dual update (soc_lane_entries = E > 0): cones sorted by dimension
+    // (largest first); a tile is up to 32 / S cones sharing the lane-group size S of its first
+    // cone, S the smallest power of two with dim <= S E and (32 / S) dim <= kSocTileRows;
+    // cones longer than kSocTileRows rows (all cones when E = 0) come last, a warp each
     std::vector<int> t_cone0, t_row0, t_order, t_trow, t_so;
     std::vector<unsigned char> t_lg;
     int n_large = 0;
@@ -648,12 +648,13 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         for (int k = 0; k < ctx->n_soc; ++k) ord[k] = k;
         std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return soc_d[a] > soc_d[b]; });
         std::vector<int> small, large;
-        for (int c : ord) (soc_d[c] > kSocTileRows ? large : small).push_back(c);
+        const bool tiles = ctx->opt.soc_lane_entries > 0;  // 0: a warp per cone throughout
+        for (int c : ord) (!tiles || soc_d[c] > kSocTileRows ? large : small).push_back(c);
         t_row0.push_back(0);
         for (size_t i = 0; i < small.size();) {
             const int d0 = soc_d[small[i]];
             int lg = 0;
-            const int per_lane = ctx->opt.soc_lane_entries > 0 ? ctx->opt.soc_lane_entries : kSocLaneEntries;
+            const int per_lane = ctx->opt.soc_lane_entries;
             while (lg < 5 && ((32 >> lg) * d0 > kSocTileRows || d0 > (1 << lg) * per_lane)) ++lg;
             t_cone0.push_back((int)t_order.size());
             t_lg.push_back((unsigned char)lg);
@@ -1368,7 +1369,13 @@ pdcs_status pdcs_solve(pdcs_ctx* ctx, double tol, int64_t max_iter, pdcs_info* i
     const double t0 = now_s();
     pdcs_status st = read_ctrl(ctx);
     if (st != PDCS_OK) return st;
-    if (ctx->h_ctrl->status != kRunning) {  // a converged solver stays converged
+    if (ctx->h_ctrl->status == kConverged && tol > 0.0 && tol < ctx->h_ctrl->tol) {
+        // converged to a looser tolerance: continue from the same state towards the new one
+        const int running = kRunning;
+        CK(cudaMemcpyAsync(&ctx->ctrl->status, &running, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        ctx->h_ctrl->status = kRunning;
+    }
+    if (ctx->h_ctrl->status != kRunning) {  // otherwise a converged solver stays converged
         ctx->last_status = status_of(*ctx->h_ctrl);
         if (info) fill_info(ctx, info);
         return (pdcs_status)ctx->last_status;

@@ -241,6 +241,23 @@ def test_one_evaluation_from_oracle_states(start):
     g.close()
 
 
+@pytest.mark.parametrize("lane_entries", [1, 4, 16])
+def test_one_evaluation_soc_lane_groups(lane_entries):
+    """The SOC cones projected by lane groups in shared memory (soc_lane_entries > 0) give
+    the same evaluation as the oracle, from its states after 0 and 64 evaluations."""
+    from parity_helpers import one_evaluation
+    p = I.scaled_mixed_cone(1, 0.01)
+    o = oracle.Solver(p, check_period=64)
+    g = P.Solver(p, check_period=64, soc_lane_entries=lane_entries)
+    done = 0
+    for start in [0, 64]:
+        o.run(start - done)
+        err, acc = one_evaluation(p, g, o)
+        done = start + 1
+        assert acc[0] == acc[1] and max(err.values()) <= RTOL, (start, err)
+    g.close()
+
+
 @pytest.mark.parametrize("mode", [oracle.STEP_CONSTANT, oracle.STEP_PLAIN])
 def test_one_evaluation_fixed_step_modes(mode):
     """One evaluation from the oracle's state after 0, 7, 64 and 130 evaluations in the
