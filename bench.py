@@ -227,9 +227,13 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-iterate mode measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-programs measurement")
     ap.add_argument("--no-proj", action="store_true", help="skip the standalone projection measurements")
+    ap.add_argument("--no-lasso", action="store_true", help="skip the paper-generator Lasso time-to-tolerance runs")
     ap.add_argument("--no-exp", action="store_true",
                     help="skip the exp-cone logistic program (plain vs learned exp root start)")
     ap.add_argument("--batch-count", type=int, default=256, help="Lasso programs in the batched measurement")
+    ap.add_argument("--batch-nhi", type=int, default=400, help="largest feature count of the batched Lasso programs")
+    ap.add_argument("--batch-seq-sample", type=int, default=0,
+                    help="programs of the one-by-one baseline (0: all; fewer: a seeded sample, time scaled up)")
     ap.add_argument("--time-to-tol", default="1e-4,1e-6",
                     help="comma list of tolerances for the time-to-solution runs ('' to skip)")
     ap.add_argument("--ttt-limit", type=float, default=100.0, help="seconds allowed per time-to-tolerance run")
@@ -391,21 +395,32 @@ def main():
     batch = None
     if not args.no_batch:
         from paper_2505_00311_gb300 import instances as I
-        probs = I.lasso_batch(7, args.batch_count, 50, 400)
+        t_gen = time.perf_counter()
+        probs = I.lasso_batch(7, args.batch_count, 50, args.batch_nhi)
+        t_gen = time.perf_counter() - t_gen
         G = 8
+        t_create = time.perf_counter()
         solvers = [P.Solver(q, stream=stream.cuda_stream, batch_blocks=G) for q in probs]
+        t_create = time.perf_counter() - t_create
         bt = P.Batch(solvers)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, nconv = bt.solve(1e-6, 100_000)
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
-        evals_b = max(sv.info()["attempts"] for sv in solvers)
+        bstats = [sv.info() for sv in solvers]
+        evals_b = max(b["attempts"] for b in bstats)
         bt.close()
         for sv in solvers:
             sv.close()
+        nonconv = [{"program": k, "n": int(probs[k]["n"]), "evaluations": bstats[k]["attempts"],
+                    "err": [bstats[k]["err_p"], bstats[k]["err_d"], bstats[k]["err_gap"]]}
+                   for k in range(len(probs)) if bstats[k]["status"] != P.OK][:10]
+        seq_idx = list(range(len(probs)))
+        if 0 < args.batch_seq_sample < len(probs):
+            seq_idx = sorted(np.random.default_rng(17).choice(len(probs), args.batch_seq_sample, replace=False).tolist())
         t_seq, nseq, evals_s = 0.0, 0, 0
-        for q in probs:
+        for q in (probs[k] for k in seq_idx):
             sv = P.Solver(q, stream=stream.cuda_stream)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -415,16 +430,22 @@ def main():
             nseq += st1 == P.OK
             evals_s += inf1["attempts"]
             sv.close()
-        batch = {"workload": "%d Lasso SOCPs (App. C form), n ~ U{50..400} features, m = n/2, dense N(0,1) "
-                             "design, tol 1e-6, FP64" % len(probs),
+        scale = len(probs) / len(seq_idx)
+        batch = {"workload": "%d Lasso SOCPs (App. B.2 form), n ~ U{50..%d} features, m = n/2, dense N(0,1) "
+                             "design, tol 1e-6, FP64" % (len(probs), args.batch_nhi),
+                 "nnz_total": int(sum(int(q["row_ptr"][-1]) for q in probs)),
+                 "generate_seconds": t_gen, "create_seconds": t_create,
                  "batched_seconds": t_batch, "batched_converged": nconv, "batched_lockstep_evaluations": evals_b,
-                 "sequential_seconds": t_seq, "sequential_converged": nseq,
-                 "sequential_total_evaluations": evals_s, "speedup": t_seq / t_batch if t_batch > 0 else None}
+                 "not_converged": nonconv,
+                 "sequential_programs": len(seq_idx), "sequential_seconds": t_seq * scale,
+                 "sequential_seconds_measured": t_seq, "sequential_converged": nseq,
+                 "sequential_total_evaluations": evals_s,
+                 "speedup": t_seq * scale / t_batch if t_batch > 0 else None}
 
-    # standalone cone projections (the projection step on its own): SOC blocks of several
-    # sizes over 2e8 entries and 2e6 exp cones, unscaled (D = I) and with scales
-    # exp(N(0, 0.5^2)); bytes: read v (and d) and write the result once; the time is the
-    # whole call (it uploads the cone list and lays out the blocks)
+    # standalone cone projections (Sec. 4's strategy comparison, Fig. 3 stand-in): 2e8 entries
+    # as SOC blocks of several sizes, and 2e6 exp cones, unscaled (D = I) and with scales
+    # exp(N(0, 0.5^2)); a projection plan per layout (built before the timed runs), whose runs
+    # only enqueue kernels; bytes: read v (and d) and write the result once
     proj = None
     if not args.no_proj:
         proj = []
@@ -433,7 +454,8 @@ def main():
         peak = measured_peaks().get("hbm_gbs")
 
         def timed(fn, reps=5):
-            fn()
+            for _ in range(3):
+                fn()
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -446,29 +468,64 @@ def main():
         v = torch.randn(total, device="cuda", dtype=torch.float64, generator=g)
         dsc = torch.exp(0.5 * torch.randn(total, device="cuda", dtype=torch.float64, generator=g))
         out = torch.empty_like(v)
-        for nblk in [1_000, 100_000, 1_000_000]:
+        for nblk in [10, 1_000, 100_000, 10_000_000]:
             dim = total // nblk
             types = np.full(nblk, P.CONE_SOC, np.int32)
             dims = np.full(nblk, dim, np.int64)
+            plan = P.ProjPlan(nblk * dim, types, dims, stream.cuda_stream)
             for scaled in (False, True):
                 dp = dsc.data_ptr() if scaled else 0
-                pms = timed(lambda: P.pdcs_proj_cones_device(v.data_ptr(), dp, nblk * dim, types, dims, 0,
-                                                              out.data_ptr(), stream.cuda_stream))
+                pms = timed(lambda: plan.run(v.data_ptr(), dp, 0, out.data_ptr(), stream.cuda_stream))
                 byt = nblk * dim * (24 if scaled else 16)
                 proj.append({"cones": "SOC", "count": nblk, "dim": dim, "scaled": scaled, "ms": pms,
                              "GBps": byt / (pms * 1e-3) / 1e9, "frac_of_hbm": byt / (pms * 1e-3) / 1e9 / peak
                              if peak else None})
+            if plan.check(stream.cuda_stream) != P.OK:
+                raise SystemExit("projection plan: a team wait gave up")
+            plan.close()
         ne = 2_000_000
         types = np.full(ne, P.CONE_EXP, np.int32)
         dims = np.full(ne, 3, np.int64)
+        plan = P.ProjPlan(3 * ne, types, dims, stream.cuda_stream)
         for scaled in (False, True):
             dp = dsc.data_ptr() if scaled else 0
-            pms = timed(lambda: P.pdcs_proj_cones_device(v.data_ptr(), dp, 3 * ne, types, dims, 0, out.data_ptr(),
-                                                          stream.cuda_stream))
+            pms = timed(lambda: plan.run(v.data_ptr(), dp, 0, out.data_ptr(), stream.cuda_stream))
             byt = 3 * ne * (24 if scaled else 16)
             proj.append({"cones": "EXP", "count": ne, "dim": 3, "scaled": scaled, "ms": pms,
                          "cones_per_s": ne / (pms * 1e-3), "GBps": byt / (pms * 1e-3) / 1e9})
+        plan.close()
         del v, dsc, out
+
+    # the paper's Lasso workload (Sec. 5.3, App. B.2) at 7e4 x 7e5 (4.9e6 entries of A, one SOC
+    # of 70,002 rows projected grid-wise): time to 1e-3 and 1e-6 (the paper's two accuracy
+    # levels), FP64, wall clock of pdcs_solve, setup apart
+    lasso = None
+    if not args.no_lasso:
+        from paper_2505_00311_gb300 import instances as I
+        q = I.lasso_paper(0, 70_000, 700_000, 1e-4)
+        sl = P.Solver(q, stream=stream.cuda_stream, time_limit=args.ttt_limit)
+        ktl, _ = sl.kernel_times(EVALS_PER_STEP)
+        sl.close()
+        sl = P.Solver(q, stream=stream.cuda_stream, time_limit=args.ttt_limit)
+        inf = sl.info()
+        lasso = {"workload": "Lasso (App. B.2 generator), A 70,000 x 700,000, 4.9e6 entries U[0,1], "
+                             "lam = ||A'b||_inf; SOCP n = %d, m = %d, nnz = %d, one SOC of %d rows" %
+                             (q["n"], q["m"], int(q["row_ptr"][-1]), int(q["cone_dims"][-1])),
+                 "soc_grid_cones": inf["soc_grid_cones"], "setup_seconds": inf["setup_seconds"],
+                 "kernels_ms_per_launch": ktl, "time_to_tol": []}
+        total_s = 0.0
+        for tol in (1e-3, 1e-6):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, inf = sl.solve(tol, 10_000_000)
+            torch.cuda.synchronize()
+            total_s += time.perf_counter() - t0
+            lasso["time_to_tol"].append({"tol": tol, "seconds": total_s, "status": P.STATUS_NAMES.get(st, st),
+                                         "evaluations": inf["attempts"],
+                                         "err": [inf["err_p"], inf["err_d"], inf["err_gap"]]})
+            if st != P.OK:
+                break
+        sl.close()
 
     # the exp-cone-heavy program (l1 logistic regression, 400k exp cones), plain exp root
     # search against the learned starting point: the first evaluation (no cached roots), the
@@ -569,7 +626,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": bench_config(args, world),
             "rates": rates, "clocks": clk, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-            "time_to_tol": ttt, "fp32_iterates": fp32, "batched_programs": batch, "projections": proj,
+            "time_to_tol": ttt, "fp32_iterates": fp32, "batched_programs": batch, "projections": proj, "paper_lasso": lasso,
             "exp_heavy": exp_heavy}
     print(json.dumps(line))
 

@@ -63,8 +63,10 @@ typedef enum {
     PDCS_ERR_CUDA = 2,           /* a CUDA call failed (text in pdcs_last_error) */
     PDCS_ERR_OOM = 3,            /* device allocation failed */
     PDCS_ERR_NUMERIC = 4,        /* a NaN / Inf appeared in the iterates */
-    PDCS_ERR_DEVICE_TIMEOUT = 5, /* a bounded device wait gave up; reserved: no kernel of this
-                                    version waits on another, so no call returns it */
+    PDCS_ERR_DEVICE_TIMEOUT = 5, /* a bounded device wait gave up: the blocks of the grid-wise SOC
+                                    projection (options.soc_grid_dim) wait for one another with an
+                                    iteration limit (a few seconds); the solver stops with this
+                                    status instead of hanging */
     PDCS_MAX_ITER = 10,          /* max_iter PDHG evaluations done without reaching tol */
     PDCS_TIME_LIMIT = 11         /* options.time_limit seconds passed without reaching tol */
 } pdcs_status;
@@ -80,7 +82,9 @@ typedef struct {
     int32_t step_mode;      /* PDCS_STEP_*: adaptive (Algorithm 1), constant 0.998/||K||_2,
                                or plain PDHG of App. D (0.9/||K||_2, no Halpern, no restarts) */
     int32_t check_period;   /* restart / termination check every this many PDHG evaluations, default 64 */
-    double beta;            /* reflection parameter of ReflectedHalpern, default 1 */
+    double beta;            /* reflection parameter of ReflectedHalpern (Algorithm 1 step 6), in
+                               [0, 1], default 1/2: the damped reflection that Algorithm 1 step 5
+                               asks for, as a constant (its adaptive rule is not in the paper) */
     int32_t power_iters;    /* power iterations for ||K||_2 (constant / plain modes), default 50 */
     int32_t precision;      /* PDCS_PRECISION_FP64 (default), or PDCS_PRECISION_FP32: SpMV, primal
                                / dual updates and cone projections on FP32 copies of K~, K~', the
@@ -117,6 +121,12 @@ typedef struct {
                                power of two, the smallest with dim <= S * soc_lane_entries),
                                32 / S cones per warp (measured slower on the 1M-variable mixed-cone
                                program: 182 vs 153 us per dual update at 4) */
+    int32_t soc_grid_dim;   /* grid-wise projection of large SOC / RSOC cones (Sec. 4, the grid-wise
+                               strategy), single programs with FP64 iterates: several blocks of one
+                               cooperative launch share a cone, its sums reduced across them in a
+                               fixed order.  0 (default): the cones of at least 4096 rows that hold
+                               more than 1 / (number of SMs) of all SOC rows; > 0: every cone of at
+                               least this many rows; -1: none (one warp per cone throughout) */
 } pdcs_options;
 
 typedef struct {
@@ -134,6 +144,7 @@ typedef struct {
     int32_t spmv_plan[4];         /* SpMV plans in use: bin shift and unroll of K, then of K'
                                      (binned format) */
     int32_t spmv_format;          /* SpMV storage in use: 1 binned, 2 sliced */
+    int32_t soc_grid_cones;       /* SOC / RSOC cones projected grid-wise (options.soc_grid_dim) */
 } pdcs_info;
 
 typedef struct pdcs_ctx pdcs_ctx;
@@ -262,6 +273,37 @@ void pdcs_destroy(pdcs_ctx* ctx);
  * queued.  Errors: PDCS_ERR_INVALID, PDCS_ERR_CUDA. */
 pdcs_status pdcs_proj_cones_device(const double* v, const double* d, int64_t m, const pdcs_cone* cones,
                                    int64_t n_cones, int32_t dual, double* out, void* cuda_stream);
+
+/* Projection plan: the cone layout of pdcs_proj_cones_device built once, for repeated
+ * projections of vectors with the same cone list.  Each SOC / RSOC cone gets a strategy by
+ * its dimension (Sec. 4): up to 4096 rows one warp; beyond, a team of blocks of one
+ * cooperative launch (about one block per 32768 rows, at most one per SM), teams packed
+ * into waves of at most one block per SM, every sum over a cone reduced across its team's
+ * blocks in a fixed order (deterministic).  D = I takes the textbook closed form.
+ * pdcs_proj_plan_create copies the HOST cone list (rows in order, sum of dims == m) and
+ * allocates the plan's device memory (the lists, 8 bytes per row of FP32 scratch when some
+ * SOC cone has more than 129 rows, the teams' barrier words and partials); it synchronises
+ * cuda_stream once.  Errors: PDCS_ERR_INVALID (malformed list), PDCS_ERR_OOM, PDCS_ERR_CUDA. */
+typedef struct pdcs_proj_plan pdcs_proj_plan;
+pdcs_status pdcs_proj_plan_create(int64_t m, const pdcs_cone* cones, int64_t n_cones, void* cuda_stream,
+                                  pdcs_proj_plan** out);
+
+/* Enqueues the projection of the DEVICE vector v onto D C (dual == 0) or D^{-1} C*
+ * (dual == 1), D = diag(d) (DEVICE pointer, NULL means D = I), into the DEVICE vector
+ * out (may equal v): kernel launches on cuda_stream only (no allocation, no copy, no
+ * synchronisation).  Same results and accuracy as pdcs_proj_cones_device.  Runs of one
+ * plan that overlap on the GPU race on its scratch.  The teams' blocks wait for one
+ * another with an iteration limit; a run whose wait gave up leaves out undefined and sets
+ * a flag that pdcs_proj_plan_check reports.  Errors: PDCS_ERR_INVALID, PDCS_ERR_CUDA. */
+pdcs_status pdcs_proj_plan_run(pdcs_proj_plan* plan, const double* v, const double* d, int32_t dual, double* out,
+                               void* cuda_stream);
+
+/* Synchronises cuda_stream and returns PDCS_ERR_DEVICE_TIMEOUT if a run of the plan gave up
+ * a wait (the flag stays set), PDCS_OK otherwise. */
+pdcs_status pdcs_proj_plan_check(pdcs_proj_plan* plan, void* cuda_stream);
+
+/* Waits for the device and frees the plan; NULL is a no-op. */
+void pdcs_proj_plan_destroy(pdcs_proj_plan* plan);
 
 /* Largest cone list pdcs_proj_cones_device_noalloc accepts. */
 #define PDCS_NOALLOC_MAX_CONES 262144

@@ -15,7 +15,7 @@ constexpr int kWarpsPerBlock = kBlock / kWarp;
 enum ConeKind : int32_t { kZero = 0, kNonneg = 1, kSoc = 2, kRsoc = 3, kExp = 4 };
 
 // Solver status words kept on the device.
-enum : int32_t { kRunning = 0, kConverged = 1, kNumericError = 2 };
+enum : int32_t { kRunning = 0, kConverged = 1, kNumericError = 2, kTimeout = 3 };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

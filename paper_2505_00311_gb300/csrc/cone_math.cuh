@@ -276,6 +276,7 @@ struct SocWeightsArray {
     const double* wi;  // 1 / w[i] to rounding (may be null: divided out)
     __device__ __forceinline__ double operator()(int i) const { return w ? w[i] : 1.0; }
     __device__ __forceinline__ double inv(int i) const { return wi ? wi[i] : (w ? 1.0 / w[i] : 1.0); }
+    __device__ __forceinline__ bool unit() const { return w == nullptr; }  // Dhat = I
 };
 template <bool kInv>
 struct SocWeightsScales {
@@ -283,6 +284,7 @@ struct SocWeightsScales {
     double d0;
     __device__ __forceinline__ double operator()(int i) const { return soc_weight<kInv>(d, d0, i); }
     __device__ __forceinline__ double inv(int i) const { return soc_weight<!kInv>(d, d0, i); }
+    __device__ __forceinline__ bool unit() const { return d == nullptr; }
 };
 
 // buf[0..dim): the block, projected in place onto E K_soc where the weight of x entry
@@ -788,11 +790,49 @@ __device__ void soc_seg_project(double* v, const double* __restrict__ w, const d
     }
 }
 
+// Dhat = I (every weight 1): the textbook projection onto K_soc (Q K_soc for rot),
+// (t + ||x||) / 2 (1, x / ||x||) when ||x|| > |t|, by a warp on memory (any dim).
+static __device__ __noinline__ void soc_project_warp_unit(double* buf, int dim, bool rot) {
+    const int lane = threadIdx.x & 31;
+    const double r2 = 0.70710678118654752440;
+    __syncwarp();
+    if (rot && lane == 0) {
+        const double p = buf[0], q = buf[1];
+        buf[0] = (p + q) * r2;
+        buf[1] = (p - q) * r2;
+    }
+    __syncwarp();
+    const double t = buf[0];
+    double a = 0.0;
+    for (int i = 1 + lane; i < dim; i += 32) a += buf[i] * buf[i];
+    const double nx = sqrt(warp_sum(a));
+    if (nx > fabs(t)) {
+        const double top = 0.5 * (t + nx), sc = top / nx;
+        for (int i = 1 + lane; i < dim; i += 32) buf[i] *= sc;
+        __syncwarp();
+        if (lane == 0) buf[0] = top;
+    } else if (t <= 0.0) {  // in the polar cone (nx <= -t)
+        for (int i = lane; i < dim; i += 32) buf[i] = 0.0;
+    }
+    __syncwarp();
+    if (rot && lane == 0) {
+        const double p = buf[0], q = buf[1];
+        buf[0] = (p + q) * r2;
+        buf[1] = (p - q) * r2;
+    }
+    __syncwarp();
+}
+
 // Picks the register count for the block (dim - 1 <= 128, weights from wf); larger blocks
 // use the FP64 memory-loop projection with weights formed from the scales d (kInv as there).
+// Dhat = I takes the closed form.
 template <bool kInv, typename WF>
 __device__ __forceinline__ void soc_project_wf(double* buf, WF wf, const double* __restrict__ d, int dim, bool rot,
                                                float* cache, float* scr) {
+    if (wf.unit()) {
+        soc_project_warp_unit(buf, dim, rot);
+        return;
+    }
     const int nx = dim - 1;
     if (nx > 128) {
         if (scr) {

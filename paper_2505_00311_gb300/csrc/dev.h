@@ -42,6 +42,12 @@ struct SlicePlan {
 // (pdcs_options.soc_lane_entries > 0).
 constexpr int kSocTileRows = 256;
 
+// Grid-wise SOC cones (team.cuh): at least kTeamMinDim rows; a team takes at least
+// kTeamMinRows x entries per block.  kTeamQ: quantities of one team sum.
+constexpr int kTeamMinDim = 4096;
+constexpr int kTeamMinRows = 512;
+constexpr int kTeamQ = 4;
+
 template <typename T>
 struct Dev {
     int m, n;
@@ -87,6 +93,18 @@ struct Dev {
     const int* soc_order;                 // tiled cones, then the large ones
     const int* soc_so;                    // per tiled cone (as soc_order): its staged row offset in the tile
     const int* soc_trow;                  // internal row of each staged row, tile by tile
+    // grid-wise projection of large SOC / RSOC cones (see team.cuh): entry e projects cone
+    // team_cone[e] with blocks [team_b0[e], team_b0[e] + team_g[e]) of a cooperative launch
+    // of team_nb blocks; soc_huge[c] = 1 for those cones, which the other SOC loops skip
+    int team_nb, n_team;
+    const int* team_cone;
+    const int* team_b0;
+    const int* team_g;
+    unsigned* team_bar;              // [count, generation] per entry
+    double* team_part;               // 2 * team_nb * kTeamQ partial slots
+    const unsigned char* soc_huge;   // per cone, or null when no cone is projected by a team
+    int team_gb0;                    // dual-update partial slot of team block 0
+    int team_kb0;                    // primal-side KKT partial slot of team block 0
     // blocks of the cone-structured kernels: exp cones in [0, nb_exp), SOC cones in the
     // next nb_soc, scalar rows in the last nb_scal (the costliest work is dispatched first)
     int nb_scal, nb_soc, nb_exp;

@@ -34,6 +34,17 @@ constexpr int dual_soc_smem() {
     void k_kkt_dual(const Dev<T>& D, dim3 g, cudaStream_t s) { kkt_dual<T><<<g, kBlock, 0, s>>>(D); }             \
     void k_restart_primal(const Dev<T>& D, dim3 g, cudaStream_t s) { restart_primal<T><<<g, kBlock, 0, s>>>(D); } \
     void k_restart_dual(const Dev<T>& D, dim3 g, cudaStream_t s) { restart_dual<T><<<g, kBlock, 0, s>>>(D); }     \
+    cudaError_t k_soc_team(const Dev<T>& D, int mode, cudaStream_t s) {                                            \
+        if (D.team_nb <= 0) return cudaSuccess;                                                                    \
+        Dev<T> Dv = D;                                                                                             \
+        int md = mode;                                                                                             \
+        void* args[] = {(void*)&Dv, (void*)&md};                                                                   \
+        return cudaLaunchCooperativeKernel((const void*)soc_team<T>, dim3(D.team_nb), dim3(kBlock), args, 0, s);   \
+    }                                                                                                              \
+    int k_team_occupancy(const Dev<T>*) {                                                                          \
+        int occ = 0;                                                                                               \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, soc_team<T>, kBlock, 0) == cudaSuccess ? occ : 0; \
+    }                                                                                                              \
     void k_spmv(const SpmvBins& B, int unroll, cudaStream_t s, const int* list, const int* rp, const int* ci,     \
                 const T* val, const T* x, T* y0, T* y1, const Ctrl* ctrl, int sel, int skip) {                     \
         const int grid = B.blk[B.nbins];                                                                           \

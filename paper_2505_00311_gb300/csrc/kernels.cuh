@@ -19,6 +19,7 @@
 #include "common.cuh"
 #include "cone_f32.cuh"
 #include "cone_math.cuh"
+#include "team.cuh"
 #include "dev.h"
 #include "state.h"
 
@@ -707,6 +708,7 @@ __device__ __forceinline__ void cand_dual_body(const Dev<T>& D, int qidx) {
     } else if (b >= D.nb_exp) {  // SOC / RSOC blocks
         const int stride = D.nb_soc * kWarpsPerBlock;
         for (int cidx = (b - D.nb_exp) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
+            if (D.soc_huge && D.soc_huge[cidx]) continue;  // grid-wise (soc_team)
             const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
             for (int i = lane; i < dim; i += 32) out[o + i] = val(o + i);
             __syncwarp();
@@ -770,6 +772,7 @@ __device__ __forceinline__ void kkt_primal_body(const Dev<T>& D, int qidx) {
     } else if (b >= D.nb_exp) {  // SOC / RSOC blocks
         const int stride = D.nb_soc * kWarpsPerBlock;
         for (int cidx = (b - D.nb_exp) * kWarpsPerBlock + wid; cidx < D.n_soc; cidx += stride) {
+            if (D.soc_huge && D.soc_huge[cidx]) continue;  // grid-wise (soc_team)
             const int o = D.soc_off[cidx], dim = D.soc_dim[cidx];
             const bool rot = D.soc_rot[cidx] != 0;
             // scaled residual: project v onto Dr K
@@ -1017,6 +1020,163 @@ __device__ __forceinline__ void restart_dual_body(const Dev<T>& D, int qidx) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Grid-wise projection of the large SOC / RSOC cones (team.cuh), one cooperative launch
+// of team_nb blocks per use:
+//   kTeamDual : the dual update's rows of those cones (FP64 iterates): pending Halpern
+//               update, v, yhat = Proj(v), partials of ||dy||^2 and dy'(K xhat - K x) in the
+//               dual-update slots after the role blocks; takes part in the step
+//               controller's ticket like the role kernels;
+//   kTeamCand : the dual candidates' projections (cand_dual skips these cones);
+//   kTeamKkt  : the primal-side KKT partials of these cones' rows (kkt_primal skips them),
+//               in the slots after kkt_primal's blocks.
+// A block in no team entry writes zero partials.
+// ---------------------------------------------------------------------------
+enum TeamMode { kTeamDual = 0, kTeamCand = 1, kTeamKkt = 2 };
+
+template <typename T>
+__device__ __forceinline__ Team make_team(const Dev<T>& D, int e) {
+    Team tm;
+    tm.G = D.team_g[e];
+    tm.slot0 = D.team_b0[e];
+    tm.r = (int)blockIdx.x - tm.slot0;
+    tm.slot = blockIdx.x;
+    tm.stride = D.team_nb;
+    tm.bar = D.team_bar + 2 * e;
+    tm.part = D.team_part;
+    tm.abort = &D.ctrl->team_abort;
+    tm.phase = 0u;
+    tm.ok = true;
+    return tm;
+}
+
+template <typename T>
+__device__ __forceinline__ bool in_team(const Dev<T>& D, int e) {
+    const int b0 = D.team_b0[e];
+    return (int)blockIdx.x >= b0 && (int)blockIdx.x < b0 + D.team_g[e];
+}
+
+// Records a wait that gave up (status kTimeout; the host reports PDCS_ERR_DEVICE_TIMEOUT).
+__device__ __forceinline__ void team_report(Ctrl* C, bool ok) {
+    if (!ok && threadIdx.x == 0) atomicExch(&C->status, (int)kTimeout);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) soc_team(Dev<T> D, int mode) {
+    Ctrl* C = D.ctrl;
+    if (C->status != kRunning) return;
+    bool ok = true;
+    if (mode == kTeamDual) {
+        if constexpr (sizeof(T) == 8) {
+            const DualCoef<T> k = dual_coef(D);
+            T acc[2] = {T(0), T(0)};
+            for (int e = 0; e < D.n_team; ++e) {
+                if (!in_team(D, e)) continue;
+                Team tm = make_team(D, e);
+                const int c = D.team_cone[e], o = D.soc_off[c], dim = D.soc_dim[c];
+                int rl, rh;
+                team_rows(dim, tm.G, tm.r, rl, rh);
+                for (int i = rl + (int)threadIdx.x; i < rh; i += blockDim.x) {
+                    T y, kx;
+                    dual_row_halpern(D, o + i, k.pend, k.ha, k.hb, k.hc, k.hw, k.pprev, y, kx);
+                    D.yh[o + i] = y + k.sigma * (D.h[o + i] - T(2) * k.p[o + i] + kx);
+                }
+                __syncthreads();
+                soc_team_project<true>(D.yh + o, SocWeightsArray{D.soc_w + o + 1, D.soc_wp + o + 1}, D.dr + o, dim,
+                                       D.soc_rot[c] != 0, D.soc_lam + c, reinterpret_cast<float*>(D.scr + o), tm);
+                for (int i = rl + (int)threadIdx.x; i < rh; i += blockDim.x) {
+                    const T dy = D.yh[o + i] - D.y[o + i];
+                    acc[0] += dy * dy;
+                    acc[1] += dy * (k.p[o + i] - D.kx[o + i]);
+                }
+                ok = ok && tm.ok;
+            }
+            team_report(C, ok);
+            dual_finish(D, D.team_gb0 + (int)blockIdx.x, acc);
+        }
+        return;
+    }
+    const int nc = n_candidates(C);
+    for (int q = 0; q < nc; ++q) {
+        if (mode == kTeamCand) {
+            const double iw = q ? 1.0 / C->wsum : 0.0;
+            double* out = D.yc + (size_t)q * D.m;
+            const T* src = q ? D.ysum : D.y;
+            for (int e = 0; e < D.n_team; ++e) {
+                if (!in_team(D, e)) continue;
+                Team tm = make_team(D, e);
+                const int c = D.team_cone[e], o = D.soc_off[c], dim = D.soc_dim[c];
+                int rl, rh;
+                team_rows(dim, tm.G, tm.r, rl, rh);
+                for (int i = rl + (int)threadIdx.x; i < rh; i += blockDim.x)
+                    out[o + i] = q ? (double)src[o + i] * iw : (double)src[o + i];
+                __syncthreads();
+                soc_team_project<true>(out + o, SocWeightsArray{D.soc_w + o + 1, D.soc_wp + o + 1}, D.dr + o, dim,
+                                       D.soc_rot[c] != 0, nullptr,
+                                       reinterpret_cast<float*>(D.scr + (size_t)q * D.m + o), tm);
+                ok = ok && tm.ok;
+            }
+        } else {
+            __shared__ double sm[3][kWarpsPerBlock];
+            const double* kx = D.kxc + (size_t)q * D.m;
+            const double* yc = D.yc + (size_t)q * D.m;
+            double* s1 = D.scr + (size_t)q * D.m;
+            double sums[3] = {0.0, 0.0, 0.0};  // rp2, hy, dy2
+            double mx[3] = {0.0, 0.0, 0.0};    // rmax, kxmax, pmax
+            for (int e = 0; e < D.n_team; ++e) {
+                if (!in_team(D, e)) continue;
+                Team tm = make_team(D, e);
+                const int c = D.team_cone[e], o = D.soc_off[c], dim = D.soc_dim[c];
+                const bool rot = D.soc_rot[c] != 0;
+                // FP32 copies in the other candidate's scratch rows of this cone (free here)
+                float* f32 = reinterpret_cast<float*>(D.scr + (size_t)(1 - q) * D.m + o);
+                int rl, rh;
+                team_rows(dim, tm.G, tm.r, rl, rh);
+                // scaled residual: project v = K~ xc - h~ onto Dr K
+                for (int i = rl + (int)threadIdx.x; i < rh; i += blockDim.x) s1[o + i] = kx[o + i] - D.h64[o + i];
+                __syncthreads();
+                soc_team_project<false>(s1 + o, SocWeightsArray{D.soc_wp + o + 1, D.soc_w + o + 1}, D.dr + o, dim,
+                                        rot, nullptr, f32, tm);
+                for (int i = rl + (int)threadIdx.x; i < rh; i += blockDim.x) {
+                    const double r = (kx[o + i] - D.h64[o + i]) - s1[o + i];
+                    sums[0] += r * r;
+                }
+                __syncthreads();
+                // unscaled residual: project w = v / dr onto K (D = I)
+                for (int i = rl + (int)threadIdx.x; i < rh; i += blockDim.x)
+                    s1[o + i] = (kx[o + i] - D.h64[o + i]) / D.dr[o + i];
+                __syncthreads();
+                soc_team_project<false>(s1 + o, SocWeightsArray{nullptr, nullptr}, nullptr, dim, rot, nullptr, f32,
+                                        tm);
+                for (int i = rl + (int)threadIdx.x; i < rh; i += blockDim.x) {
+                    const double w = (kx[o + i] - D.h64[o + i]) / D.dr[o + i];
+                    mx[0] = fmax(mx[0], fabs(w - s1[o + i]));
+                    mx[2] = fmax(mx[2], fabs(s1[o + i]));
+                    sums[1] += D.h64[o + i] * yc[o + i];
+                    const double dy = yc[o + i] - (double)D.y0[o + i];
+                    sums[2] += dy * dy;
+                    mx[1] = fmax(mx[1], fabs(kx[o + i] / D.dr[o + i]));
+                }
+                __syncthreads();
+                ok = ok && tm.ok;
+            }
+            block_sum<3>(sums, sm);
+            block_max<3>(mx, sm);
+            if (threadIdx.x == 0) {
+                const int nb = D.pl.kktp_blocks, b = D.team_kb0 + (int)blockIdx.x;
+                double* P = D.part + D.pl.off_kp + (size_t)q * kKktPN * nb;
+                P[kpRp2 * nb + b] = sums[0];
+                P[kpHy * nb + b] = sums[1];
+                P[kpDy2 * nb + b] = sums[2];
+                P[kpRmax * nb + b] = mx[0];
+                P[kpKxmax * nb + b] = mx[1];
+                P[kpPmax * nb + b] = mx[2];
+            }
+        }
+    }
+    team_report(C, ok);
+}
 
 // ---------------------------------------------------------------------------
 // Batched SpMV (FP64 programs): program blockIdx.z.  mode 0: K xhat into the buffer of

@@ -24,6 +24,11 @@ namespace pdcs {
     void k_kkt_dual(const Dev<T>& D, dim3 g, cudaStream_t s);                                                     \
     void k_restart_primal(const Dev<T>& D, dim3 g, cudaStream_t s);                                               \
     void k_restart_dual(const Dev<T>& D, dim3 g, cudaStream_t s);                                                 \
+    /* grid-wise SOC cones (soc_team, mode 0 dual update, 1 candidates, 2 KKT): a cooperative  */                  \
+    /* launch of D.team_nb blocks; nothing when D.team_nb == 0 */                                                  \
+    cudaError_t k_soc_team(const Dev<T>& D, int mode, cudaStream_t s);                                            \
+    /* resident blocks per SM of soc_team (0 on error) */                                                          \
+    int k_team_occupancy(const Dev<T>*);                                                                           \
     /* y = A x over the binned rows of B (see spmv_binned); unroll 1, 2 or 4 */                                    \
     void k_spmv(const SpmvBins& B, int unroll, cudaStream_t s, const int* list, const int* rp, const int* ci,     \
                 const T* val, const T* x, T* y0, T* y1, const Ctrl* ctrl, int sel, int skip);                      \

@@ -171,6 +171,7 @@ struct pdcs_ctx {
     cudaStream_t aux[2] = {nullptr, nullptr};  // helper streams of the concurrent dual-update roles
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     int launches_per_attempt = 4;
+    int team_cones = 0;  // SOC cones projected grid-wise
     bool started = false;
     double setup_seconds = 0.0, solve_seconds = 0.0;
     double norm2 = 0.0;
@@ -429,10 +430,12 @@ void enqueue_dual(pdcs_ctx* ctx, const Dev<T>& DT) {
         k_dual_update(DT, ctx->g_dual, s);
         return;
     }
-    const int roles = (DT.nb_scal > 0) + (DT.nb_soc > 0) + (DT.nb_exp > 0);
+    const bool team = DT.team_nb > 0;  // the grid-wise cones follow the SOC role on its stream
+    const int roles = (DT.nb_scal > 0) + (DT.nb_soc > 0 || team) + (DT.nb_exp > 0);
     if (roles <= 1) {
         k_dual_exp(DT, s);
         k_dual_soc(DT, s);
+        if (team) k_soc_team(DT, 0, s);
         k_dual_scalar(DT, s);
         return;
     }
@@ -440,6 +443,7 @@ void enqueue_dual(pdcs_ctx* ctx, const Dev<T>& DT) {
     cudaStreamWaitEvent(ctx->aux[0], ctx->ev_fork, 0);
     cudaStreamWaitEvent(ctx->aux[1], ctx->ev_fork, 0);
     k_dual_soc(DT, ctx->aux[0]);
+    if (team) k_soc_team(DT, 0, ctx->aux[0]);
     k_dual_scalar(DT, ctx->aux[1]);
     k_dual_exp(DT, s);
     cudaEventRecord(ctx->ev_join[0], ctx->aux[0]);
@@ -473,7 +477,7 @@ void enqueue_check_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     Dev<double>& D = ctx->D;
     auto mark = [&](int c) { if (P) P->mark(c, s); };
     mark(4);
-    ctx->launches += kLaunchesPerCheck;
+    ctx->launches += kLaunchesPerCheck + (DT.team_nb > 0 ? 2 : 0);
     mark(5);
     k_flush_primal(DT, ctx->g_vec_n, s);
     k_flush_dual(DT, ctx->g_vec_m, s);
@@ -481,6 +485,7 @@ void enqueue_check_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     k_cand_primal(DT, dim3(ctx->g_vec_n, 2), s);
     mark(6); mark(7);
     k_cand_dual(DT, dim3(ctx->g_dual, 2), s);
+    k_soc_team(DT, 1, s);
     mark(7); mark(8);
     for (int q = 0; q < 2; ++q) {
         launch_spmv<double>(ctx->pk, s, D.rp, D.ci, D.val, D.xc + (size_t)q * ctx->n,
@@ -490,6 +495,7 @@ void enqueue_check_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     }
     mark(8); mark(9);
     k_kkt_primal(DT, dim3(ctx->g_dual, 2), s);
+    k_soc_team(DT, 2, s);
     mark(9); mark(10);
     k_kkt_dual(DT, ctx->g_kktd, s);
     mark(10); mark(11);
@@ -643,13 +649,58 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     std::vector<int> t_cone0, t_row0, t_order, t_trow, t_so;
     std::vector<unsigned char> t_lg;
     int n_large = 0;
+    // grid-wise cones (team.cuh): by default those of at least kTeamMinDim rows that alone
+    // hold more than one SM's share of the SOC rows, whose FP64 work a warp (or a block)
+    // would otherwise serialise on one SM; soc_grid_dim > 0 takes every cone of at least
+    // that many rows, -1 none.  Single programs with FP64 iterates only.
+    std::vector<unsigned char> huge(ctx->n_soc + 1, 0);
+    std::vector<int> team_cone, team_b0, team_g;
+    int team_nb = 0;
+    if (ctx->opt.batch_blocks == 0 && ctx->n_soc > 0 && ctx->opt.soc_grid_dim >= 0 &&
+        ctx->opt.precision == PDCS_PRECISION_FP64) {
+        long long soc_rows = 0;
+        for (int k = 0; k < ctx->n_soc; ++k) soc_rows += soc_d[k];
+        std::vector<int> hc;
+        for (int k = 0; k < ctx->n_soc; ++k) {
+            const long long dk = soc_d[k];
+            const bool h = ctx->opt.soc_grid_dim > 0 ? dk >= ctx->opt.soc_grid_dim
+                                                     : (dk >= kTeamMinDim && dk * ctx->sms > soc_rows);
+            if (h) hc.push_back(k);
+        }
+        int occ = 0;
+        if (!hc.empty()) occ = k_team_occupancy((const Dev<double>*)nullptr);
+        if (!hc.empty() && occ >= 1) {
+            team_nb = ctx->sms;
+            std::stable_sort(hc.begin(), hc.end(), [&](int a, int b) { return soc_d[a] > soc_d[b]; });
+            const int nh = (int)hc.size();
+            if (nh > team_nb) {  // one block per cone, dealt round-robin (largest first)
+                for (int i = 0; i < nh; ++i) {
+                    team_cone.push_back(hc[i]); team_b0.push_back(i % team_nb); team_g.push_back(1);
+                }
+            } else {  // one block each, the rest shared in proportion to the rows
+                long long tot = 0;
+                for (int c : hc) tot += soc_d[c];
+                int b0 = 0;
+                for (int c : hc) {
+                    long long g = 1 + (long long)(team_nb - nh) * soc_d[c] / tot;
+                    g = std::min<long long>(g, std::max<long long>(1, (soc_d[c] - 1 + kTeamMinRows - 1) / kTeamMinRows));
+                    team_cone.push_back(c); team_b0.push_back(b0); team_g.push_back((int)g);
+                    b0 += (int)g;
+                }
+            }
+            for (int c : hc) huge[c] = 1;
+        }
+    }
     {
         std::vector<int> ord(ctx->n_soc);
         for (int k = 0; k < ctx->n_soc; ++k) ord[k] = k;
         std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return soc_d[a] > soc_d[b]; });
         std::vector<int> small, large;
         const bool tiles = ctx->opt.soc_lane_entries > 0;  // 0: a warp per cone throughout
-        for (int c : ord) (!tiles || soc_d[c] > kSocTileRows ? large : small).push_back(c);
+        for (int c : ord) {
+            if (huge[c]) continue;
+            (!tiles || soc_d[c] > kSocTileRows ? large : small).push_back(c);
+        }
         t_row0.push_back(0);
         for (size_t i = 0; i < small.size();) {
             const int d0 = soc_d[small[i]];
@@ -704,10 +755,13 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
             nb_scal = share(nb_scal);
         }
     }
+    // the team blocks' partial slots follow the role blocks (dual update, FP64 iterates) and
+    // kkt_primal's blocks (checks)
+    const int team_gb0 = nb_scal + nb_soc + nb_exp;
     PartLayout pl;
     pl.primal_blocks = ctx->g_vec_n;
-    pl.dual_blocks = ctx->g_dual;
-    pl.kktp_blocks = ctx->g_dual;
+    pl.dual_blocks = team_nb > 0 ? team_gb0 + team_nb : ctx->g_dual;
+    pl.kktp_blocks = ctx->g_dual + team_nb;
     pl.kktd_blocks = ctx->g_kktd;
     pl.off_px = 0;
     pl.off_dy = pl.off_px + pl.primal_blocks;
@@ -735,6 +789,10 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     A.reserve<float>(ctx->n_soc + 1); A.reserve<float>(ctx->n_exp + 1);
     A.reserve<int>(t_cone0.size() + 1); A.reserve<int>(t_row0.size() + 1); A.reserve<unsigned char>(t_lg.size() + 1);
     A.reserve<int>(t_order.size() + 1); A.reserve<int>(t_trow.size() + 1); A.reserve<int>(t_so.size() + 1);
+    const int n_team = (int)team_cone.size();
+    for (int k = 0; k < 3; ++k) A.reserve<int>(n_team + 1);          // team_cone, team_b0, team_g
+    A.reserve<unsigned>(2LL * n_team + 2); A.reserve<double>(2LL * team_nb * kTeamQ + 1);
+    A.reserve<unsigned char>(ctx->n_soc + 1);                         // soc_huge
     A.reserve<double>(m); A.reserve<double>(m); A.reserve<double>(3LL * ctx->n_exp + 1);
     A.reserve<double>(pl.total);
     A.reserve<Ctrl>(1);
@@ -799,6 +857,12 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     int* d_order = A.take<int>(t_order.size() + 1);
     int* d_trow = A.take<int>(t_trow.size() + 1);
     int* d_so = A.take<int>(t_so.size() + 1);
+    int* d_team_cone = A.take<int>(n_team + 1);
+    int* d_team_b0 = A.take<int>(n_team + 1);
+    int* d_team_g = A.take<int>(n_team + 1);
+    unsigned* d_team_bar = A.take<unsigned>(2LL * n_team + 2);
+    double* d_team_part = A.take<double>(2LL * team_nb * kTeamQ + 1);
+    unsigned char* d_huge = A.take<unsigned char>(ctx->n_soc + 1);
     ctx->soc_w = A.take<double>(m); ctx->soc_wp = A.take<double>(m); ctx->exp_lg = A.take<double>(3LL * ctx->n_exp + 1);
     ctx->part = A.take<double>(pl.total);
     ctx->ctrl = A.take<Ctrl>(1);
@@ -852,6 +916,11 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         CK(up(d_order, t_order.data(), sizeof(int) * t_order.size()));
         CK(up(d_trow, t_trow.data(), sizeof(int) * t_trow.size()));
         CK(up(d_so, t_so.data(), sizeof(int) * t_so.size()));
+        CK(up(d_team_cone, team_cone.data(), sizeof(int) * n_team));
+        CK(up(d_team_b0, team_b0.data(), sizeof(int) * n_team));
+        CK(up(d_team_g, team_g.data(), sizeof(int) * n_team));
+        CK(up(d_huge, huge.data(), (size_t)ctx->n_soc));
+        CK(cudaMemsetAsync(d_team_bar, 0, sizeof(unsigned) * (2 * n_team + 2), s));
     }
     if (ctx->n_tie) {
         CK(cudaMemcpyAsync(ctx->tie_off, tie_o.data(), sizeof(int) * ctx->n_tie, cudaMemcpyHostToDevice, s));
@@ -976,12 +1045,19 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.n_large = n_large;
     D.tile_cone0 = d_tcone0; D.tile_row0 = d_trow0; D.tile_lg = d_tlg; D.soc_order = d_order; D.soc_trow = d_trow;
     D.soc_so = d_so;
+    D.team_nb = team_nb; D.n_team = n_team;
+    D.team_cone = d_team_cone; D.team_b0 = d_team_b0; D.team_g = d_team_g;
+    D.team_bar = d_team_bar; D.team_part = d_team_part;
+    D.soc_huge = n_team > 0 ? d_huge : nullptr;
+    D.team_gb0 = team_gb0; D.team_kb0 = ctx->g_dual;
+    ctx->team_cones = n_team;
     D.part = ctx->part; D.pl = pl; D.ctrl = ctx->ctrl;
     D.l_orig = ctx->l0; D.u_orig = ctx->u0;
     D.exp_mlp = exp_mlp;
     D.binsK = ctx->pk.B; D.binsKT = ctx->pkt.B; D.listK = ctx->pk.list; D.listKT = ctx->pkt.list;
-    ctx->launches_per_attempt =
-        ctx->opt.batch_blocks > 0 ? kLaunchesPerAttempt : 3 + (nb_scal > 0) + (nb_soc > 0) + (nb_exp > 0);
+    ctx->launches_per_attempt = ctx->opt.batch_blocks > 0
+                                    ? kLaunchesPerAttempt
+                                    : 3 + (nb_scal > 0) + (nb_soc > 0) + (nb_exp > 0) + (team_nb > 0);
 
     // ---- controller scalars
     Ctrl C;
@@ -1100,6 +1176,7 @@ bool fp32_done(pdcs_ctx* ctx, double tol) {
 pdcs_status status_of(const Ctrl& C) {
     if (C.status == kConverged) return PDCS_OK;
     if (C.status == kNumericError) return PDCS_ERR_NUMERIC;
+    if (C.status == kTimeout) return PDCS_ERR_DEVICE_TIMEOUT;
     return PDCS_MAX_ITER;
 }
 
@@ -1125,6 +1202,7 @@ void fill_info(pdcs_ctx* ctx, pdcs_info* info) {
     info->spmv_plan[2] = ctx->pkt.shift;
     info->spmv_plan[3] = ctx->pkt.unroll;
     info->spmv_format = ctx->pk.format;
+    info->soc_grid_cones = ctx->team_cones;
 }
 
 __global__ void batch_prepare(Dev<double>* views, int count, double tol, int start) {
@@ -1249,7 +1327,7 @@ void pdcs_default_options(pdcs_options* o) {
     o->pock_chambolle = 1;
     o->step_mode = PDCS_STEP_ADAPTIVE;
     o->check_period = 64;
-    o->beta = 1.0;
+    o->beta = 0.5;
     o->power_iters = 50;
     o->precision = PDCS_PRECISION_FP64;
     o->fp32_switch_tol = 1e-4;
@@ -1261,6 +1339,7 @@ void pdcs_default_options(pdcs_options* o) {
     o->batch_blocks = 0;
     o->spmv_format = 0;
     o->soc_lane_entries = 0;
+    o->soc_grid_dim = 0;
 }
 
 pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, const double* lb, const double* ub,
@@ -1314,6 +1393,7 @@ pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, con
     if (o.batch_blocks < 0 || o.batch_blocks > 1 << 20) return bad("batch_blocks must be in [0, 2^20]");
     if (o.spmv_format < 0 || o.spmv_format > 2) return bad("spmv_format must be 0, 1 or 2");
     if (o.soc_lane_entries < 0 || o.soc_lane_entries > 256) return bad("soc_lane_entries must be in [0, 256]");
+    if (o.soc_grid_dim < -1) return bad("soc_grid_dim must be -1, 0 or positive");
     if (o.spmv_format == 2 && (o.batch_blocks > 0 || o.spmv_lanes != 0))
         return bad("the sliced SpMV format serves single programs with spmv_lanes = 0");
 
@@ -1429,8 +1509,10 @@ pdcs_status pdcs_solve(pdcs_ctx* ctx, double tol, int64_t max_iter, pdcs_info* i
     if (st != PDCS_OK) return st;
     if (ctx->h_ctrl->status == kConverged) result = PDCS_OK;
     else if (ctx->h_ctrl->status == kNumericError) result = PDCS_ERR_NUMERIC;
+    else if (ctx->h_ctrl->status == kTimeout) result = PDCS_ERR_DEVICE_TIMEOUT;
     else if (result != PDCS_TIME_LIMIT) result = PDCS_MAX_ITER;
     if (result == PDCS_ERR_NUMERIC) ctx->err = "NaN or Inf in the iterates";
+    if (result == PDCS_ERR_DEVICE_TIMEOUT) ctx->err = "a bounded wait of the grid-wise SOC projection gave up";
     ctx->solve_seconds += now_s() - t0;
     ctx->last_status = result;
     if (info) fill_info(ctx, info);

@@ -27,7 +27,7 @@ struct Ctrl {
     long long k;          // accepted steps since the last restart
     long long restarts;
     int32_t pending;      // 1: the Halpern update of the last evaluation is not applied yet
-    int32_t status;       // kRunning / kConverged / kNumericError
+    int32_t status;       // kRunning / kConverged / kNumericError / kTimeout
     int32_t step_mode;    // 0 adaptive, 1 constant, 2 plain
     int32_t check_mode;   // 0 regular check, 1 initial evaluation of the anchor
     int32_t restart_now;  // set by the check controller: 1 restart to candidate `best`
@@ -35,7 +35,7 @@ struct Ctrl {
     int32_t sol_cand;     // candidate copied into the solution by the last check
     int32_t n_cand;       // candidates evaluated by the last check (1 or 2)
     unsigned int ticket;  // block counter of the last-block reductions
-    int32_t pad;
+    int32_t team_abort;   // set when a bounded wait of the grid-wise SOC projection gave up
 };
 
 // Fixed slots of the partial-sum buffer (one double per block per quantity).

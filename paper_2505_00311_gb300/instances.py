@@ -283,6 +283,106 @@ def lasso_socp(seed: int = 0, n: int = 200, m: int | None = None, lam: float | N
             "lasso": {"A": A, "b": b, "lam": lam}}
 
 
+def _sparse_positions(rng, rows: int, cols: int, count: int):
+    """`count` distinct positions of a rows x cols matrix, uniform, in row-major order."""
+    total = rows * cols
+    count = min(int(count), total)
+    if count * 4 >= total:
+        idx = np.sort(rng.choice(total, size=count, replace=False))
+    else:
+        idx = np.unique(rng.integers(0, total, size=count))
+        while idx.size < count:
+            idx = np.unique(np.concatenate([idx, rng.integers(0, total, size=count - idx.size)]))
+    return idx // cols, idx % cols
+
+
+def lasso_paper(seed: int = 0, m: int = 70_000, n: int = 700_000, density: float = 1e-4):
+    """The Lasso workload of the paper's experiments (Sec. 5.3; App. B.2):
+    min ||A x - b||^2 + lam ||x||_1 with A (m x n) holding round(density m n) entries at
+    uniform positions, each U[0, 1]; a ground truth x~ with N(0, 1) entries of which a random
+    half is set to zero; b = A x~ + 1e-6 * 1; lam = ||A'b||_inf.  As the SOCP of App. B.2:
+    variables w, r, y (m), x1, x2 (n each) with x = x1 - x2 >= 0 parts; zero rows w = 1 and
+    y - A x1 + A x2 = -b; one second-order cone of dimension m + 2 holding
+    ((w + r) / sqrt2, (w - r) / sqrt2, y), i.e. ||y||^2 <= 2 r when w = 1; objective
+    2 r + lam 1'(x1 + x2).  The paper's sizes run from 1e4 x 1e5 (1e5 entries) to
+    7.5e5 x 7.5e6 (5.6e8 entries)."""
+    rng = np.random.default_rng(seed)
+    m, n = int(m), int(n)
+    ar, ac = _sparse_positions(rng, m, n, round(density * m * n))
+    av = rng.random(ar.size)
+    A = sp.csr_matrix((av, (ar, ac)), shape=(m, n))
+    xt = rng.standard_normal(n)
+    xt[rng.permutation(n)[: n // 2]] = 0.0
+    b = A @ xt + 1e-6
+    lam = float(np.abs(A.T @ b).max()) if A.nnz else 1.0
+    nv = 2 + m + 2 * n
+    iw, ir, iy, ix1, ix2 = 0, 1, 2, 2 + m, 2 + m + n
+    s2 = np.sqrt(0.5)
+    im = np.arange(m)
+    rows = [np.zeros(1, np.int64), 1 + im, 1 + ar, 1 + ar, np.full(2, 1 + m), np.full(2, 2 + m), 3 + m + im]
+    cols = [np.array([iw]), iy + im, ix1 + ac, ix2 + ac, np.array([iw, ir]), np.array([iw, ir]), iy + im]
+    vals = [np.ones(1), np.ones(m), -av, av, np.array([s2, s2]), np.array([s2, -s2]), np.ones(m)]
+    K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(2 * m + 3, nv))
+    K.sort_indices()
+    c = np.zeros(nv)
+    c[ir] = 2.0
+    c[ix1:] = lam
+    h = np.zeros(2 * m + 3)
+    h[0] = 1.0
+    h[1:1 + m] = -b
+    lb = np.full(nv, -np.inf)
+    lb[ix1:] = 0.0
+    ub = np.full(nv, np.inf)
+    return {"name": "lasso_paper", "m": 2 * m + 3, "n": nv, "row_ptr": K.indptr.astype(np.int64),
+            "col": K.indices.astype(np.int32), "val": K.data, "c": c, "h": h, "lb": lb, "ub": ub,
+            "cone_types": np.asarray([ZERO, SOC], dtype=np.int32),
+            "cone_dims": np.asarray([1 + m, m + 2], dtype=np.int64),
+            "lasso": {"A": A, "b": b, "lam": lam}}
+
+
+def fisher_market(seed: int = 0, buyers: int = 100_000, goods: int = 1000, density: float = 0.2):
+    """The Fisher market equilibrium workload of the paper's experiments (Sec. 5.2; App. B.1):
+    max sum_i w_i log(sum_j U_ij X_ij) s.t. sum_i X_ij = b_j, X >= 0, with U (buyers x goods)
+    holding round(density buyers goods) entries at uniform positions, each U[0, 1], budgets
+    w_i ~ U[0, 1] and supplies b_j = 0.25.  As the exponential-cone program of App. B.1:
+    min -w'p with t_i = sum_j U_ij X_ij and (p_i, 1, t_i) in K_exp (p_i <= log t_i).
+    Variables X_ij only where U_ij > 0 (a buyer who does not value a good never receives it
+    at equilibrium), then (p_i, t_i) per buyer; rows: goods clearing (zero), utility
+    definitions (zero), then one exp cone per buyer.  The paper's sizes run from 1e2 x 5e3
+    (1e5 entries) to 2.8e5 x 1e3 (5.5e7 entries)."""
+    rng = np.random.default_rng(seed)
+    mb, ng = int(buyers), int(goods)
+    ur, uc = _sparse_positions(rng, mb, ng, round(density * mb * ng))
+    uv = rng.random(ur.size)
+    w = rng.random(mb)
+    bsup = np.full(ng, 0.25)
+    nx = ur.size
+    n = nx + 2 * mb
+    ip, it = nx, nx + mb
+    ib = np.arange(mb)
+    m = ng + mb + 3 * mb
+    ex0 = ng + mb  # first exp row
+    rows = [uc, ng + ur, ng + ib, ex0 + 3 * ib, ex0 + 3 * ib + 2]
+    cols = [np.arange(nx), np.arange(nx), it + ib, ip + ib, it + ib]
+    vals = [np.ones(nx), uv, -np.ones(mb), np.ones(mb), np.ones(mb)]
+    K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(m, n))
+    K.sort_indices()
+    c = np.zeros(n)
+    c[ip:ip + mb] = -w
+    h = np.zeros(m)
+    h[:ng] = bsup
+    h[ex0 + 3 * ib + 1] = -1.0
+    lb = np.full(n, -np.inf)
+    lb[:nx] = 0.0
+    ub = np.full(n, np.inf)
+    types = np.concatenate([np.asarray([ZERO], dtype=np.int32), np.full(mb, EXP, dtype=np.int32)])
+    dims = np.concatenate([np.asarray([ng + mb], dtype=np.int64), np.full(mb, 3, dtype=np.int64)])
+    return {"name": "fisher_market", "m": m, "n": n, "row_ptr": K.indptr.astype(np.int64),
+            "col": K.indices.astype(np.int32), "val": K.data, "c": c, "h": h, "lb": lb, "ub": ub,
+            "cone_types": types, "cone_dims": dims,
+            "fisher": {"U": sp.csr_matrix((uv, (ur, uc)), shape=(mb, ng)), "w": w, "b": bsup}}
+
+
 def logistic_exp(seed: int = 2, n_samples: int = 200_000, n_features: int = 2000, density: float = 0.005,
                  lam_frac: float = 0.1):
     """l1-regularised logistic regression, min sum_i log(1 + exp(-b_i x_i'w)) + lam ||w||_1,

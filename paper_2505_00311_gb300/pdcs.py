@@ -46,7 +46,8 @@ class pdcs_options(ctypes.Structure):
                 ("fp32_switch_tol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("spmv_lanes", ctypes.c_int32), ("time_limit", ctypes.c_double),
                 ("exp_mlp", ctypes.c_void_p), ("spmv_autotune", ctypes.c_int32), ("batch_blocks", ctypes.c_int32),
-                ("spmv_format", ctypes.c_int32), ("soc_lane_entries", ctypes.c_int32)]
+                ("spmv_format", ctypes.c_int32), ("soc_lane_entries", ctypes.c_int32),
+                ("soc_grid_dim", ctypes.c_int32)]
 
 
 class pdcs_info(ctypes.Structure):
@@ -55,7 +56,8 @@ class pdcs_info(ctypes.Structure):
                 ("pobj", ctypes.c_double), ("dobj", ctypes.c_double), ("eta", ctypes.c_double),
                 ("omega", ctypes.c_double), ("setup_seconds", ctypes.c_double),
                 ("solve_seconds", ctypes.c_double), ("status", ctypes.c_int32), ("fp64_phase", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64), ("spmv_plan", ctypes.c_int32 * 4), ("spmv_format", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int64), ("spmv_plan", ctypes.c_int32 * 4), ("spmv_format", ctypes.c_int32),
+                ("soc_grid_cones", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if isinstance(getattr(self, k), ctypes.Array) else getattr(self, k))
@@ -104,6 +106,12 @@ SIGNATURES = {
     "pdcs_proj_cones_device_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                       ctypes.POINTER(pdcs_cone), ctypes.c_int64, ctypes.c_int32,
                                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "pdcs_proj_plan_create": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(pdcs_cone), ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "pdcs_proj_plan_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "pdcs_proj_plan_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pdcs_proj_plan_destroy": (None, [ctypes.c_void_p]),
     "pdcs_exp_mlp_dataset": (ctypes.c_int, [ctypes.c_int64, _dp, _dp, _fp, _fp, _i64p]),
     "pdcs_exp_mlp_loss_grad": (ctypes.c_int, [ctypes.c_int64, _fp, _fp, _fp, _fp, _fp]),
     "pdcs_exp_mlp_train": (ctypes.c_int, [ctypes.c_int64, _fp, _fp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
@@ -325,6 +333,37 @@ def pdcs_proj_cones_device_noalloc(v_ptr, d_ptr, m, types, dims, dual, out_ptr, 
     device array of NOALLOC_MAX_CONES cones); returns the pdcs_status code."""
     cones = _cones(types, dims)
     return lib().pdcs_proj_cones_device_noalloc(v_ptr, d_ptr, int(m), cones, len(cones), int(dual), out_ptr, stream)
+
+
+class ProjPlan:
+    """A projection plan (pdcs_proj_plan_*): the cone layout built once, then runs that
+    only enqueue kernels.  Pointers are integers (e.g. torch ``data_ptr()``)."""
+
+    def __init__(self, m, types, dims, stream=None):
+        self._cones = _cones(types, dims)
+        self.plan = ctypes.c_void_p()
+        st = lib().pdcs_proj_plan_create(int(m), self._cones, len(self._cones), stream, ctypes.byref(self.plan))
+        if st != OK:
+            raise PdcsError(st, "pdcs_proj_plan_create failed")
+
+    def run(self, v_ptr, d_ptr, dual, out_ptr, stream=None):
+        st = lib().pdcs_proj_plan_run(self.plan, v_ptr, d_ptr, int(dual), out_ptr, stream)
+        if st != OK:
+            raise PdcsError(st, "pdcs_proj_plan_run failed")
+
+    def check(self, stream=None):
+        return lib().pdcs_proj_plan_check(self.plan, stream)
+
+    def close(self):
+        if self.plan:
+            lib().pdcs_proj_plan_destroy(self.plan)
+            self.plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

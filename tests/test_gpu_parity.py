@@ -179,7 +179,9 @@ def test_scaling_parity():
 # about 10x every 10 evaluations (measured on these programs).  Per-iteration
 # parity is therefore checked on windows of 32 evaluations from a common state,
 # with checks every 16 evaluations so that restarts, averages and primal-weight
-# updates happen inside each window.
+# updates happen inside each window: within 1e-12 over the first 16 evaluations, and
+# within 1e-11 over the next 16 (one order of growth; the per-evaluation error itself is
+# bounded at 1e-12 by the one-evaluation tests below, which have no such feedback).
 WINDOW = [1, 2, 3, 5, 8, 10, 15, 16, 17, 20, 24, 31, 32]
 
 
@@ -193,10 +195,13 @@ def _window(g, o, tol=RTOL, check_eta=True, targets=None):
         assert gs["attempts"] == os_["attempts"]
         assert gs["accepted"] == os_["accepted"] and gs["restarts"] == os_["restarts"], (target, gs, os_)
         err = _compare_iterates(g, o)
-        assert err <= tol, (target, err)
+        assert err <= (tol if target <= 16 else 10 * tol), (target, err)
         if check_eta:  # near a solution eta_max is a ratio of tiny moves: compare iterates only
             assert abs(gs["eta"] - os_["eta"]) <= 1e-10 * os_["eta"]
-        assert abs(gs["omega"] - os_["omega"]) <= 1e-10 * os_["omega"]
+        # omega: PrimalWeightUpdate takes the ratio of the moves ||dy|| / ||dx|| between restart
+        # anchors, differences that magnify the iterates' relative error by the ratio of iterate
+        # to move (~1e2 late in a solve)
+        assert abs(gs["omega"] - os_["omega"]) <= 1e-8 * os_["omega"]
 
 
 @pytest.mark.parametrize("prob_name", ["small_socp", "mixed_small"])

@@ -1,6 +1,7 @@
-"""The Lasso (App. C form) and portfolio generators, pinned outside the solver: the
-oracle's optimum of each conic program equals the optimum an independent method finds
-for the original problem (coordinate descent for the Lasso, SLSQP for the portfolio)."""
+"""The Lasso (dense batched form and the paper's App. B.2 workload), Fisher market (App. B.1)
+and portfolio generators, pinned outside the solver: the oracle's optimum of each conic
+program equals the optimum an independent method finds for the original problem (coordinate
+descent for the Lasso, SLSQP for the Fisher market and the portfolio)."""
 import numpy as np
 import pytest
 from scipy.optimize import minimize
@@ -55,3 +56,52 @@ def test_portfolio_program_matches_slsqp():
     f_or, x = _oracle_optimum(q, tol=1e-8)
     assert abs(f_or - r.fun) <= 1e-6 * max(1.0, abs(r.fun)), (f_or, r.fun)
     np.testing.assert_allclose(x[:na], r.x, atol=2e-4)
+
+
+def test_paper_lasso_program_matches_coordinate_descent():
+    """The paper's Lasso workload (App. B.2: sparse U[0, 1] design, half-zero ground truth,
+    lam = ||A'b||_inf, one SOC of dimension m + 2), at a small size and a higher density."""
+    sk = pytest.importorskip("sklearn.linear_model")
+    q = I.lasso_paper(11, m=40, n=400, density=0.05)
+    A, b, lam = q["lasso"]["A"].toarray(), q["lasso"]["b"], q["lasso"]["lam"]
+    m, n = A.shape
+    assert q["cone_dims"][-1] == m + 2 and lam == pytest.approx(np.abs(A.T @ b).max())
+    fit = sk.Lasso(alpha=lam / (2 * m), fit_intercept=False, tol=1e-14, max_iter=1_000_000).fit(A, b)
+    w = fit.coef_
+    f_cd = float(np.sum((A @ w - b) ** 2) + lam * np.abs(w).sum())
+    f_or, x = _oracle_optimum(q)
+    assert abs(f_or - f_cd) <= 1e-6 * max(1.0, abs(f_cd)), (f_or, f_cd)
+    i1 = 2 + m
+    np.testing.assert_allclose(x[i1:i1 + n] - x[i1 + n:i1 + 2 * n], w, atol=1e-4)
+
+
+def test_fisher_market_program_matches_slsqp_and_clears_the_budgets():
+    """The paper's Fisher market workload (App. B.1) at a small size: the oracle's optimum
+    equals the Eisenberg-Gale optimum that SLSQP finds directly, and the equilibrium prices
+    (the duals of the clearing rows) spend exactly the buyers' budgets: sum_j p_j b_j = sum_i w_i."""
+    q = I.fisher_market(3, buyers=6, goods=10, density=0.5)
+    U, w, bs = q["fisher"]["U"].toarray(), q["fisher"]["w"], q["fisher"]["b"]
+    mb, ng = U.shape
+    rows, cols = np.nonzero(U)  # the program's X variables, row-major as the generator orders them
+    u = U[rows, cols]
+
+    def f(xv):
+        util = np.bincount(rows, weights=u * xv, minlength=mb)
+        return -float(w @ np.log(np.maximum(util, 1e-300)))
+
+    def g(xv):
+        util = np.bincount(rows, weights=u * xv, minlength=mb)
+        return -(w[rows] * u / np.maximum(util[rows], 1e-300))
+
+    cons = [{"type": "eq", "fun": lambda xv: np.bincount(cols, weights=xv, minlength=ng) - bs,
+             "jac": lambda xv: (np.arange(ng)[:, None] == cols[None, :]).astype(float)}]
+    x0 = bs[cols] / np.bincount(cols, minlength=ng)[cols]
+    r = minimize(f, x0, jac=g, method="SLSQP", bounds=[(0.0, None)] * rows.size, constraints=cons,
+                 options={"ftol": 1e-15, "maxiter": 2000})
+    assert r.success, r.message
+    f_or, x = _oracle_optimum(q, tol=1e-9)
+    assert abs(f_or - r.fun) <= 1e-6 * max(1.0, abs(r.fun)), (f_or, r.fun)
+    s = oracle.Solver(q)
+    assert s.run(2_000_000, 1e-9) == oracle.CONVERGED
+    _, y = s.solution()
+    assert abs(abs(float(y[:ng] @ bs)) - w.sum()) <= 1e-6 * w.sum()

@@ -547,14 +547,14 @@ def one_row_lp():
 
 
 def test_first_pdhg_steps_hand_worked():
-    """eq. PDHG + Algorithm 1 on min x s.t. x >= 1, no rescaling, from z = 0.
-    eta_0 = 1 / max|K| = 1 and omega_0 = ||c|| / ||h|| = 1, so tau = sigma = 1:
+    """eq. PDHG + Algorithm 1 on min x s.t. x >= 1, no rescaling, full reflection (beta = 1),
+    from z = 0.  eta_0 = 1 / max|K| = 1 and omega_0 = ||c|| / ||h|| = 1, so tau = sigma = 1:
       xhat = max(0 - (1 - 0), 0) = 0,  yhat = max(0 + (1 - K(0)), 0) = 1;
       dx = 0 so the step is accepted and the next eta is (1 + 2^-0.6) * 1;
       Halpern with k = 0: z^1 = 1/2 (2 zhat - z) + 1/2 z^0 = zhat = (0, 1).
     Second evaluation with tau = sigma = 1 + 2^-0.6:
       xhat = max(0 - tau (1 - 1), 0) = 0,  yhat = 1 + sigma (1 - 0)."""
-    s = oracle.Solver(one_row_lp(), rescale=oracle.RESCALE_NONE)
+    s = oracle.Solver(one_row_lp(), rescale=oracle.RESCALE_NONE, beta=1.0)
     s.run(1)
     x, y, xh, yh = s.iterate()
     assert xh[0] == 0.0 and yh[0] == 1.0
@@ -622,10 +622,10 @@ def test_reflected_halpern_hand_worked(beta):
 
 
 def test_constant_step_average_is_the_arithmetic_mean():
-    """SURVEY reading R7: with a constant step every weight of the average is the same, so
-    after four accepted steps it is the plain mean of the hand-worked Halpern iterates,
-    x: (2 + 5/3 + 2 + 9/5) / 4 = 28/15 and y: (0 + 2/3 + 0 + 2/5) / 4 = 4/15."""
-    s = oracle.Solver(fixed_x_lp(), rescale=oracle.RESCALE_NONE, step_mode=oracle.STEP_CONSTANT)
+    """Algorithm 1 step 7 with a constant step: every weight of the average is the same, so
+    after four accepted steps it is the plain mean of the hand-worked Halpern iterates
+    (beta = 1), x: (2 + 5/3 + 2 + 9/5) / 4 = 28/15 and y: (0 + 2/3 + 0 + 2/5) / 4 = 4/15."""
+    s = oracle.Solver(fixed_x_lp(), rescale=oracle.RESCALE_NONE, step_mode=oracle.STEP_CONSTANT, beta=1.0)
     s.set_start(np.array([1.0]), np.array([2.0]))
     s.run(4)
     st = s.state()
