@@ -83,8 +83,9 @@ typedef struct {
                                or plain PDHG of App. D (0.9/||K||_2, no Halpern, no restarts) */
     int32_t check_period;   /* restart / termination check every this many PDHG evaluations, default 64 */
     double beta;            /* reflection parameter of ReflectedHalpern (Algorithm 1 step 6), in
-                               [0, 1], default 1/2: the damped reflection that Algorithm 1 step 5
-                               asks for, as a constant (its adaptive rule is not in the paper) */
+                               [0, 1], default 1 (constant: the adaptive rule of Algorithm 1 step 5
+                               is not in the paper); 1/2 converges in fewer evaluations on small
+                               programs, in more on the 1M-variable and 7,000 x 70,000 Lasso ones */
     int32_t power_iters;    /* power iterations for ||K||_2 (constant / plain modes), default 50 */
     int32_t precision;      /* PDCS_PRECISION_FP64 (default), or PDCS_PRECISION_FP32: SpMV, primal
                                / dual updates and cone projections on FP32 copies of K~, K~', the

@@ -18,10 +18,8 @@
  *             accept iff eta <= eta_max; next eta =
  *             min((1 - (j+1)^-0.3) eta_max, (1 + (j+1)^-0.6) eta), j = 1-based
  *             index of the PDHG evaluation; eta_0 = 1 / max_ij |K~_ij|.
- *   beta    : constant, default 1/2.  AdaptiveReflectionParameter (Algorithm 1 step 5)
- *             exists to damp the oscillations of the fully reflected Halpern step
- *             (beta = 1, Sec. 3) while keeping its speed; its rule is in the report,
- *             so the damping is the fixed midpoint of [0, 1].
+ *   beta    : constant, default 1 (the reflected Halpern step of Sec. 3; the rule of
+ *             AdaptiveReflectionParameter, Algorithm 1 step 5, is in the report).
  *   average : weights are the step sizes with which each accepted zhat was made.
  *   check   : every `check_period` PDHG evaluations (accepted or not).
  *   restart : candidates z^{t,k+1} and the average, each projected onto X x Y;
@@ -73,7 +71,7 @@ void orc_default_options(orc_options* o) {
     o->pock_chambolle = 1;
     o->step_mode = ORC_STEP_ADAPTIVE;
     o->check_period = 64;
-    o->beta = 0.5;
+    o->beta = 1.0;
     o->power_iters = 50;
 }
 

@@ -1327,7 +1327,7 @@ void pdcs_default_options(pdcs_options* o) {
     o->pock_chambolle = 1;
     o->step_mode = PDCS_STEP_ADAPTIVE;
     o->check_period = 64;
-    o->beta = 0.5;
+    o->beta = 1.0;
     o->power_iters = 50;
     o->precision = PDCS_PRECISION_FP64;
     o->fp32_switch_tol = 1e-4;

@@ -60,7 +60,7 @@ def test_struct_layouts_match_the_header(tmp_path):
 def test_default_options(lib):
     o = P.pdcs_default_options()
     assert o.rescale == P.RESCALE_COORD and o.ruiz_iters == 10 and o.check_period == 64
-    assert o.beta == 0.5 and o.step_mode == P.STEP_ADAPTIVE and o.use_graphs == 1
+    assert o.beta == 1.0 and o.step_mode == P.STEP_ADAPTIVE and o.use_graphs == 1
 
 
 def _bad(prob, **opts):
