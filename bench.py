@@ -42,6 +42,10 @@ WORKLOADS = {
     "logistic_exp_200k": "l1 logistic regression as an exp-cone program: 200,000 samples x 2,000 features at "
                          "0.5 % density (N(0,1), labels +-1), 400k exp cones + 200k nonneg rows, n=604,000, "
                          "m=1,400,000, ~5.2M nnz, lam = 0.1 ||X'b||_inf / 2, seed 2",
+    "lasso_paper_70k": "Lasso (App. B.2 generator): A 70,000 x 700,000 with 4.9e6 entries U[0,1], lam = "
+                       "||A'b||_inf; SOCP n=1,470,002, m=140,003, ~9.9M nnz, one SOC of 70,002 rows, seed 0",
+    "fisher_100k": "Fisher market (App. B.1 generator): 100,000 buyers x 1,000 goods, U at 20 % density "
+                   "U[0,1]; exp-cone program n=20,200,000, m=401,000, ~40M nnz, 100k exp cones, seed 0",
 }
 
 
@@ -55,6 +59,10 @@ def make_workload(name):
         return I.mixed_cone_literal(1)
     if name == "logistic_exp_200k":
         return I.logistic_exp(2)
+    if name == "lasso_paper_70k":
+        return I.lasso_paper(0, 70_000, 700_000, 1e-4)
+    if name == "fisher_100k":
+        return I.fisher_market(0, 100_000, 1000, 0.2)
     raise SystemExit("unknown workload " + name)
 
 

@@ -287,7 +287,7 @@ def _sparse_positions(rng, rows: int, cols: int, count: int):
     """`count` distinct positions of a rows x cols matrix, uniform, in row-major order."""
     total = rows * cols
     count = min(int(count), total)
-    if count * 4 >= total:
+    if count * 4 >= total or (count * 100 >= total and total <= 1 << 31):
         idx = np.sort(rng.choice(total, size=count, replace=False))
     else:
         idx = np.unique(rng.integers(0, total, size=count))
@@ -362,11 +362,36 @@ def fisher_market(seed: int = 0, buyers: int = 100_000, goods: int = 1000, densi
     ib = np.arange(mb)
     m = ng + mb + 3 * mb
     ex0 = ng + mb  # first exp row
-    rows = [uc, ng + ur, ng + ib, ex0 + 3 * ib, ex0 + 3 * ib + 2]
-    cols = [np.arange(nx), np.arange(nx), it + ib, ip + ib, it + ib]
-    vals = [np.ones(nx), uv, -np.ones(mb), np.ones(mb), np.ones(mb)]
-    K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(m, n))
-    K.sort_indices()
+    # K row by row, built directly in CSR: goods j (the X_ij of every buyer i that values j,
+    # in buyer order), buyers i (their X_ij in good order, then -t_i), then per buyer the exp
+    # rows p_i, (empty), t_i
+    xid = np.arange(nx, dtype=np.int64)
+    by_good = np.argsort(uc, kind="stable")
+    cnt_g = np.bincount(uc, minlength=ng).astype(np.int64)
+    cnt_b = np.bincount(ur, minlength=mb).astype(np.int64)
+    lens = np.concatenate([cnt_g, cnt_b + 1, np.tile(np.array([1, 0, 1], np.int64), mb)])
+    indptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(lens, out=indptr[1:])
+    indices = np.empty(indptr[-1], dtype=np.int64)
+    data = np.empty(indptr[-1])
+    nb = int(indptr[ng])
+    indices[:nb] = xid[by_good]
+    data[:nb] = 1.0
+    # buyer rows: entries of buyer i at indptr[ng + i] .. (cnt_b[i] X entries, then t_i)
+    start = indptr[ng:ng + mb]
+    pos_x = np.repeat(start, cnt_b) + (xid - np.repeat(np.cumsum(cnt_b) - cnt_b, cnt_b))
+    indices[pos_x] = xid
+    data[pos_x] = uv
+    pos_t = start + cnt_b
+    indices[pos_t] = it + ib
+    data[pos_t] = -1.0
+    e0 = indptr[ex0 + 3 * ib]
+    indices[e0] = ip + ib
+    data[e0] = 1.0
+    e2 = indptr[ex0 + 3 * ib + 2]
+    indices[e2] = it + ib
+    data[e2] = 1.0
+    K = sp.csr_matrix((data, indices.astype(np.int32), indptr), shape=(m, n))
     c = np.zeros(n)
     c[ip:ip + mb] = -w
     h = np.zeros(m)
@@ -380,7 +405,8 @@ def fisher_market(seed: int = 0, buyers: int = 100_000, goods: int = 1000, densi
     return {"name": "fisher_market", "m": m, "n": n, "row_ptr": K.indptr.astype(np.int64),
             "col": K.indices.astype(np.int32), "val": K.data, "c": c, "h": h, "lb": lb, "ub": ub,
             "cone_types": types, "cone_dims": dims,
-            "fisher": {"U": sp.csr_matrix((uv, (ur, uc)), shape=(mb, ng)), "w": w, "b": bsup}}
+            "fisher": {"U": sp.csr_matrix((uv, uc.astype(np.int32), np.concatenate([[0], np.cumsum(cnt_b)])),
+                                          shape=(mb, ng)), "w": w, "b": bsup}}
 
 
 def logistic_exp(seed: int = 2, n_samples: int = 200_000, n_features: int = 2000, density: float = 0.005,
