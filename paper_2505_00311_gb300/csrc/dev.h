@@ -66,8 +66,10 @@ struct Dev {
     const T* u;
     const double* dr;
     const double* dc;
-    // iterate state
+    // iterate state (xh and xh1: the two x-hat buffers, Ctrl::xsel picks the current one)
     T *x, *xh, *x0, *kty, *ktyh, *kty0, *xsum;
+    T* xh1;
+    int px_f0;  // first primal partial slot of the fused K' product's blocks (= primal_update's grid)
     T *y, *yh, *y0, *kx, *kxh0, *kxh1, *kx0, *ysum;
     // cone layout (internal row order): [0, m_zero) zero rows, [m_zero, m_scalar)
     // nonnegative rows, then SOC / RSOC blocks, then exp cones (3 rows each)

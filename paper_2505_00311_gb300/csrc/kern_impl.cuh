@@ -56,8 +56,11 @@ constexpr int dual_soc_smem() {
         }                                                                                                          \
     }                                                                                                              \
     void k_spmv_sliced(const SlicePlan& S, cudaStream_t s, const int* ci, const T* val, const T* x, T* y0, T* y1, \
-                       const Ctrl* ctrl, int sel, int skip) {                                                      \
-        if (S.grid > 0) spmv_sliced<T, T><<<S.grid, kBlock, 0, s>>>(S, ci, val, x, y0, y1, ctrl, sel, skip);      \
+                       const Ctrl* ctrl, int sel, int skip, const T* xalt) {                                       \
+        if (S.grid > 0) spmv_sliced<T, T><<<S.grid, kBlock, 0, s>>>(S, ci, val, x, y0, y1, ctrl, sel, skip, xalt); \
+    }                                                                                                              \
+    void k_spmv_kt_primal(const SlicePlan& S, cudaStream_t s, const int* ci, const T* val, const Dev<T>& D) {     \
+        if (S.grid > 0) spmv_kt_primal<T><<<S.grid, kBlock, 0, s>>>(S, ci, val, D);                               \
     }                                                                                                              \
     void k_sliced_copy(const SlicePlan& S, int grid, cudaStream_t s, const int* rp, const int* ci,                \
                        const double* val, int* cis, T* vals) {                                                     \

@@ -120,14 +120,18 @@ __device__ __forceinline__ T lane_group_sum(T v, int lg) {
     return v;
 }
 
+// xalt (may be null): the second x-hat buffer; with it x is the buffer Ctrl::xsel ^ xnext
+// names (the iteration's K x-hat, see spmv_kt_primal)
 template <typename T, typename TO>
 __global__ void __launch_bounds__(kBlock) spmv_sliced(SlicePlan S, const int* __restrict__ ci,
                                                       const T* __restrict__ val, const T* __restrict__ x, TO* y0,
-                                                      TO* y1, const Ctrl* ctrl, int sel, int skip) {
+                                                      TO* y1, const Ctrl* ctrl, int sel, int skip,
+                                                      const T* __restrict__ xalt) {
     if (skip) {
         if (ctrl->status != kRunning) return;
         if (skip == 2 && !ctrl->pending) return;
     }
+    if (xalt && (ctrl->xsel ^ ctrl->xnext)) x = xalt;
     TO* y = (sel == 1 && (ctrl->attempts & 1)) ? y1 : y0;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if ((int)blockIdx.x < S.nb_long) {
@@ -194,6 +198,112 @@ __global__ void __launch_bounds__(kBlock) spmv_sliced(SlicePlan S, const int* __
     if ((lane & ((1 << lg) - 1)) == 0) {
         const int r = __ldg(S.out_row + 32 * s + (lane >> lg));
         if (r >= 0) y[r] = (TO)acc;
+    }
+}
+
+// K' y-hat fused with the next primal update (the epilogue of row j of K' is variable j):
+// after an accepted step, the pending reflected-Halpern update of x_j and K'y_j (with this
+// product as K' y-hat) and the average, then the next evaluation's
+// x-hat_j = Proj_[l,u](x_j - tau (c_j - K'y_j)) with the controller's new tau, into the other
+// x-hat buffer, and per-block partials of ||x-hat - x||^2 in the slots after primal_update's.
+// The same arithmetic as primal_update_body, element by element.  Skipped (like the plain
+// K' product) when the step was rejected; block 0 sets Ctrl::xnext.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) spmv_kt_primal(SlicePlan S, const int* __restrict__ ci,
+                                                         const T* __restrict__ val, Dev<T> D) {
+    Ctrl* C = D.ctrl;
+    if (C->status != kRunning || !C->pending) return;
+    __shared__ double sm[1][kWarpsPerBlock];
+    const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw, tau = (T)C->tau;
+    const T* xcur = C->xsel ? D.xh1 : D.xh;
+    T* xnew = C->xsel ? D.xh : D.xh1;
+    const T* __restrict__ yh = D.yh;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T dx2 = T(0);
+    auto epilogue = [&](int j, T ktyh) {
+        T x = D.x[j], kty = D.kty[j];
+        x = ha * xcur[j] + hb * x + hc * D.x0[j];
+        kty = ha * ktyh + hb * kty + hc * D.kty0[j];
+        D.x[j] = x;
+        D.kty[j] = kty;
+        if (hw != T(0)) D.xsum[j] += hw * x;
+        const T xh = fmin(fmax(x - tau * (D.c[j] - kty), D.l[j]), D.u[j]);
+        xnew[j] = xh;
+        const T dx = xh - x;
+        dx2 += dx * dx;
+    };
+    if ((int)blockIdx.x < S.nb_long) {
+        const int r = (int)blockIdx.x * kWarpsPerBlock + w;
+        if (r < S.nlong) {
+            const int b = __ldg(S.long_rp + r), e = __ldg(S.long_rp + r + 1);
+            T acc = T(0);
+            for (int p = b + lane; p < e; p += 32) acc += __ldg(val + p) * __ldg(yh + __ldg(ci + p));
+            acc = group_sum<32>(acc);
+            if (lane == 0) epilogue(__ldg(S.long_row + r), acc);
+        }
+    } else {
+        using V2 = typename Pair2<T>::type;
+        const int s = ((int)blockIdx.x - S.nb_long) * kWarpsPerBlock + w;
+        if (s < S.nslices) {
+            const int base = __ldg(S.slice_off + s);
+            const int steps = (__ldg(S.slice_off + s + 1) - base) >> 6;
+            const int lg = __ldg(S.slice_lg + s);
+            const int2* cp = reinterpret_cast<const int2*>(ci + base) + lane;
+            const V2* vp = reinterpret_cast<const V2*>(val + base) + lane;
+            T acc = T(0);
+            int q = 0;
+            for (; q + 4 <= steps; q += 4) {
+                int2 c[4];
+                V2 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    c[u] = __ldg(cp + 32 * (q + u));
+                    v[u] = __ldg(vp + 32 * (q + u));
+                }
+                T xv[8];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    xv[2 * u] = c[u].x >= 0 ? __ldg(yh + c[u].x) : T(0);
+                    xv[2 * u + 1] = c[u].y >= 0 ? __ldg(yh + c[u].y) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    acc += v[u].x * xv[2 * u];
+                    acc += v[u].y * xv[2 * u + 1];
+                }
+            }
+            for (; q + 2 <= steps; q += 2) {
+                const int2 c0 = __ldg(cp + 32 * q), c1 = __ldg(cp + 32 * (q + 1));
+                const V2 v0 = __ldg(vp + 32 * q), v1 = __ldg(vp + 32 * (q + 1));
+                const T x0 = c0.x >= 0 ? __ldg(yh + c0.x) : T(0);
+                const T x1 = c0.y >= 0 ? __ldg(yh + c0.y) : T(0);
+                const T x2 = c1.x >= 0 ? __ldg(yh + c1.x) : T(0);
+                const T x3 = c1.y >= 0 ? __ldg(yh + c1.y) : T(0);
+                acc += v0.x * x0;
+                acc += v0.y * x1;
+                acc += v1.x * x2;
+                acc += v1.y * x3;
+            }
+            if (q < steps) {
+                const int2 c0 = __ldg(cp + 32 * q);
+                const V2 v0 = __ldg(vp + 32 * q);
+                const T x0 = c0.x >= 0 ? __ldg(yh + c0.x) : T(0);
+                const T x1 = c0.y >= 0 ? __ldg(yh + c0.y) : T(0);
+                acc += v0.x * x0;
+                acc += v0.y * x1;
+            }
+            acc = lane_group_sum(acc, lg);
+            if ((lane & ((1 << lg) - 1)) == 0) {
+                const int r = __ldg(S.out_row + 32 * s + (lane >> lg));
+                if (r >= 0) epilogue(r, acc);
+            }
+        }
+    }
+    double a[1] = {(double)dx2};
+    block_sum<1>(a, sm);
+    if (threadIdx.x == 0) {
+        D.part[D.pl.off_px + D.px_f0 + blockIdx.x] = a[0];
+        if (blockIdx.x == 0) C->xnext = 1;
     }
 }
 
@@ -292,22 +402,29 @@ __device__ __forceinline__ void primal_update_body(const Dev<T>& D, int qidx) {
     (void)qidx;
     Ctrl* C = D.ctrl;
     if (C->status != kRunning) return;
+    if (C->xnext) {  // formed by the previous evaluation's K' product (spmv_kt_primal)
+        if (threadIdx.x == 0) D.part[D.pl.off_px + blockIdx.x] = 0.0;
+        return;
+    }
     __shared__ double sm[1][kWarpsPerBlock];
     const bool pend = C->pending != 0;
     const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw, tau = (T)C->tau;
+    T* xhat = C->xsel ? D.xh1 : D.xh;
+    if (threadIdx.x == 0)  // the fused product's slots hold an earlier evaluation's partials
+        for (int b = D.px_f0 + (int)blockIdx.x; b < D.pl.primal_blocks; b += gridDim.x) D.part[D.pl.off_px + b] = 0.0;
     T acc_t = T(0);  // per-thread partial in the iterate precision, then FP64 across threads
     const int stride = gridDim.x * blockDim.x;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
         T x = D.x[j], kty = D.kty[j];
         if (pend) {
-            x = ha * D.xh[j] + hb * x + hc * D.x0[j];
+            x = ha * xhat[j] + hb * x + hc * D.x0[j];
             kty = ha * D.ktyh[j] + hb * kty + hc * D.kty0[j];
             D.x[j] = x;
             D.kty[j] = kty;
             if (hw != T(0)) D.xsum[j] += hw * x;
         }
         T xh = fmin(fmax(x - tau * (D.c[j] - kty), D.l[j]), D.u[j]);
-        D.xh[j] = xh;
+        xhat[j] = xh;
         const T dx = xh - x;
         acc_t += dx * dx;
     }
@@ -341,6 +458,10 @@ __device__ void step_controller(const Dev<T>& D, double (*sm)[kWarpsPerBlock]) {
     if (threadIdx.x != 0) return;
     C->ticket = 0;
     C->attempts += 1;
+    if (C->xnext) {  // this evaluation's x-hat was the precomputed one: it is now the current
+        C->xsel ^= 1;
+        C->xnext = 0;
+    }
     if (!isfinite(nx2) || !isfinite(ny2) || !isfinite(itr)) {
         C->status = kNumericError;
         C->pending = 0;
@@ -636,11 +757,12 @@ template <typename T>
 __device__ __forceinline__ void flush_primal_body(const Dev<T>& D, int qidx) {
     (void)qidx;
     Ctrl* C = D.ctrl;
-    if (C->status != kRunning || !C->pending) return;
+    if (C->status != kRunning || !C->pending || C->xnext) return;  // xnext: applied already
     const T ha = (T)C->ha, hb = (T)C->hb, hc = (T)C->hc, hw = (T)C->hw;
+    const T* xhat = C->xsel ? D.xh1 : D.xh;
     const int stride = gridDim.x * blockDim.x;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
-        const T x = ha * D.xh[j] + hb * D.x[j] + hc * D.x0[j];
+        const T x = ha * xhat[j] + hb * D.x[j] + hc * D.x0[j];
         D.x[j] = x;
         D.kty[j] = ha * D.ktyh[j] + hb * D.kty[j] + hc * D.kty0[j];
         if (hw != T(0)) D.xsum[j] += hw * x;
@@ -884,6 +1006,7 @@ __device__ void check_controller(const Dev<T>& D, double (*sm)[kWarpsPerBlock]) 
     }
     C->restart_now = 0;
     C->pending = 0;
+    C->xnext = 0;  // a restart may move x: the next primal update forms x-hat again
     C->n_cand = nc;
     if (!finite) { C->status = kNumericError; return; }
     // solution = the better candidate of this check (current first)

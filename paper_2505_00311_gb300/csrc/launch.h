@@ -34,7 +34,9 @@ namespace pdcs {
                 const T* val, const T* x, T* y0, T* y1, const Ctrl* ctrl, int sel, int skip);                      \
     /* y = A x in the sliced storage of plan S (see spmv_sliced) */                                                 \
     void k_spmv_sliced(const SlicePlan& S, cudaStream_t s, const int* ci, const T* val, const T* x, T* y0, T* y1, \
-                       const Ctrl* ctrl, int sel, int skip);                                                       \
+                       const Ctrl* ctrl, int sel, int skip, const T* xalt);                                        \
+    /* K' y-hat in the sliced storage of S with the next primal update in its epilogue (spmv_kt_primal) */        \
+    void k_spmv_kt_primal(const SlicePlan& S, cudaStream_t s, const int* ci, const T* val, const Dev<T>& D);      \
     /* a CSR matrix (rows in order, FP64 values) in the sliced storage of S, values as T (vals may be null) */     \
     void k_sliced_copy(const SlicePlan& S, int grid, cudaStream_t s, const int* rp, const int* ci,                \
                        const double* val, int* cis, T* vals);                                                      \

@@ -172,6 +172,7 @@ struct pdcs_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     int launches_per_attempt = 4;
     int team_cones = 0;  // SOC cones projected grid-wise
+    bool fuse_primal = false;  // the K' product forms the next primal update (spmv_kt_primal)
     bool started = false;
     double setup_seconds = 0.0, solve_seconds = 0.0;
     double norm2 = 0.0;
@@ -205,8 +206,8 @@ namespace {
 
 template <typename T>
 void launch_spmv(const SpmvPlan& P, cudaStream_t s, const int* rp, const int* ci, const T* val, const T* x, T* y0,
-                 T* y1, const Ctrl* ctrl, int sel, int skip) {
-    if (P.format == kFormatSliced) k_spmv_sliced(P.S, s, ci, val, x, y0, y1, ctrl, sel, skip);
+                 T* y1, const Ctrl* ctrl, int sel, int skip, const T* xalt = nullptr) {
+    if (P.format == kFormatSliced) k_spmv_sliced(P.S, s, ci, val, x, y0, y1, ctrl, sel, skip, xalt);
     else k_spmv(P.B, P.unroll, s, P.list, rp, ci, val, x, y0, y1, ctrl, sel, skip);
 }
 
@@ -460,11 +461,12 @@ void enqueue_attempt_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     if (P) P->mark(0, s);
     k_primal_update(DT, ctx->g_vec_n, s);
     if (P) { P->mark(0, s); P->mark(1, s); }
-    launch_spmv<T>(ctx->pk, s, DT.rp, DT.ci, DT.val, DT.xh, DT.kxh0, DT.kxh1, DT.ctrl, 1, 1);
+    launch_spmv<T>(ctx->pk, s, DT.rp, DT.ci, DT.val, DT.xh, DT.kxh0, DT.kxh1, DT.ctrl, 1, 1, DT.xh1);
     if (P) { P->mark(1, s); P->mark(2, s); }
     enqueue_dual(ctx, DT);
     if (P) { P->mark(2, s); P->mark(3, s); }
-    launch_spmv<T>(ctx->pkt, s, DT.rpT, DT.ciT, DT.valT, DT.yh, DT.ktyh, nullptr, DT.ctrl, 0, 2);
+    if (ctx->fuse_primal) k_spmv_kt_primal(ctx->pkt.S, s, DT.ciT, DT.valT, DT);  // + next primal update
+    else launch_spmv<T>(ctx->pkt, s, DT.rpT, DT.ciT, DT.valT, DT.yh, DT.ktyh, nullptr, DT.ctrl, 0, 2);
     if (P) P->mark(3, s);
     ctx->launches += ctx->launches_per_attempt;
 }
@@ -515,7 +517,19 @@ void enqueue_check(pdcs_ctx* ctx, Prof* P = nullptr) {
     else enqueue_check_t<double>(ctx, ctx->D, P);
 }
 
-__global__ void clear_pending(Ctrl* C) { C->pending = 0; }
+// After a flush: no pending update, no precomputed x-hat, and x-hat in the first buffer
+// (xhat_first copies it there first).
+__global__ void clear_pending(Ctrl* C) {
+    C->pending = 0;
+    C->xnext = 0;
+    C->xsel = 0;
+}
+
+template <typename T>
+__global__ void xhat_first(int n, T* xh, const T* __restrict__ xh1, const Ctrl* C) {
+    if (!C->xsel) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) xh[j] = xh1[j];
+}
 
 __global__ void widen(int k, const float* __restrict__ in, double* out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) out[i] = (double)in[i];
@@ -758,8 +772,13 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     // the team blocks' partial slots follow the role blocks (dual update, FP64 iterates) and
     // kkt_primal's blocks (checks)
     const int team_gb0 = nb_scal + nb_soc + nb_exp;
+    // the K' product with the primal update's epilogue (sliced storage, single programs):
+    // its blocks write their ||dx||^2 partials after primal_update's
+    ctx->fuse_primal = sliced && ctx->opt.batch_blocks == 0 && ctx->opt.fuse_primal != 0;
+    const int kt_grid = (int)((hkt.long_row.size() + kWarpsPerBlock - 1) / kWarpsPerBlock +
+                              (std::max<size_t>(hkt.slice_off.size(), 1) - 1 + kWarpsPerBlock - 1) / kWarpsPerBlock);
     PartLayout pl;
-    pl.primal_blocks = ctx->g_vec_n;
+    pl.primal_blocks = ctx->g_vec_n + (ctx->fuse_primal ? kt_grid : 0);
     pl.dual_blocks = team_nb > 0 ? team_gb0 + team_nb : ctx->g_dual;
     pl.kktp_blocks = ctx->g_dual + team_nb;
     pl.kktd_blocks = ctx->g_kktd;
@@ -797,7 +816,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     A.reserve<double>(pl.total);
     A.reserve<Ctrl>(1);
     A.reserve<double>(16);
-    for (int k = 0; k < 7; ++k) A.reserve<double>(n);  // x xh x0 kty ktyh kty0 xsum
+    for (int k = 0; k < 8; ++k) A.reserve<double>(n);  // x xh x0 kty ktyh kty0 xsum xh1
     for (int k = 0; k < 8; ++k) A.reserve<double>(m);  // y yh y0 kx kxh0 kxh1 kx0 ysum
     A.reserve<double>(2LL * n); A.reserve<double>(2LL * m); A.reserve<double>(2LL * m); A.reserve<double>(2LL * n);
     A.reserve<double>(2LL * m);  // scr
@@ -806,7 +825,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         A.reserve<float>(eK); A.reserve<float>(eKT);                     // val_f, valT_f
         for (int k = 0; k < 3; ++k) A.reserve<float>(n);                 // c l u
         A.reserve<float>(m);                                             // h
-        for (int k = 0; k < 7; ++k) A.reserve<float>(n);                 // x xh x0 kty ktyh kty0 xsum
+        for (int k = 0; k < 8; ++k) A.reserve<float>(n);                 // x xh x0 kty ktyh kty0 xsum xh1
         for (int k = 0; k < 8; ++k) A.reserve<float>(m);                 // y yh y0 kx kxh0 kxh1 kx0 ysum
         A.reserve<float>(m); A.reserve<float>(3LL * ctx->n_exp + 1);      // soc_w32, exp_lg32
     }
@@ -869,7 +888,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     ctx->scal = A.take<double>(16);
     Dev<double>& D = ctx->D;
     D.x = A.take<double>(n); D.xh = A.take<double>(n); D.x0 = A.take<double>(n); D.kty = A.take<double>(n);
-    D.ktyh = A.take<double>(n); D.kty0 = A.take<double>(n); D.xsum = A.take<double>(n);
+    D.ktyh = A.take<double>(n); D.kty0 = A.take<double>(n); D.xsum = A.take<double>(n); D.xh1 = A.take<double>(n);
     D.y = A.take<double>(m); D.yh = A.take<double>(m); D.y0 = A.take<double>(m); D.kx = A.take<double>(m);
     D.kxh0 = A.take<double>(m); D.kxh1 = A.take<double>(m); D.kx0 = A.take<double>(m); D.ysum = A.take<double>(m);
     D.xc = A.take<double>(2LL * n); D.yc = A.take<double>(2LL * m); D.kxc = A.take<double>(2LL * m);
@@ -880,7 +899,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         ctx->val_f = A.take<float>(eK); ctx->valT_f = A.take<float>(eKT);
         c_f = A.take<float>(n); l_f = A.take<float>(n); u_f = A.take<float>(n); h_f = A.take<float>(m);
         DF.x = A.take<float>(n); DF.xh = A.take<float>(n); DF.x0 = A.take<float>(n); DF.kty = A.take<float>(n);
-        DF.ktyh = A.take<float>(n); DF.kty0 = A.take<float>(n); DF.xsum = A.take<float>(n);
+        DF.ktyh = A.take<float>(n); DF.kty0 = A.take<float>(n); DF.xsum = A.take<float>(n); DF.xh1 = A.take<float>(n);
         DF.y = A.take<float>(m); DF.yh = A.take<float>(m); DF.y0 = A.take<float>(m); DF.kx = A.take<float>(m);
         DF.kxh0 = A.take<float>(m); DF.kxh1 = A.take<float>(m); DF.kx0 = A.take<float>(m); DF.ysum = A.take<float>(m);
         soc_w32 = A.take<float>(m); exp_lg32 = A.take<float>(3LL * ctx->n_exp + 1);
@@ -1050,6 +1069,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.team_bar = d_team_bar; D.team_part = d_team_part;
     D.soc_huge = n_team > 0 ? d_huge : nullptr;
     D.team_gb0 = team_gb0; D.team_kb0 = ctx->g_dual;
+    D.px_f0 = ctx->g_vec_n;
     ctx->team_cones = n_team;
     D.part = ctx->part; D.pl = pl; D.ctrl = ctx->ctrl;
     D.l_orig = ctx->l0; D.u_orig = ctx->u0;
@@ -1087,14 +1107,15 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         cast_vec<float><<<g, kBlock, 0, s>>>(m, ctx->soc_w, soc_w32);
         cast_vec<float><<<g, kBlock, 0, s>>>(3LL * ctx->n_exp, ctx->exp_lg, exp_lg32);
         // the FP32 view: FP32 matrix, data and state; everything else shared with D
-        float *x = DF.x, *xh = DF.xh, *x0 = DF.x0, *kty = DF.kty, *ktyh = DF.ktyh, *kty0 = DF.kty0, *xsum = DF.xsum;
+        float *x = DF.x, *xh = DF.xh, *x0 = DF.x0, *kty = DF.kty, *ktyh = DF.ktyh, *kty0 = DF.kty0, *xsum = DF.xsum,
+              *xh1 = DF.xh1;
         float *y = DF.y, *yh = DF.yh, *y0 = DF.y0, *kx = DF.kx, *kxh0 = DF.kxh0, *kxh1 = DF.kxh1, *kx0 = DF.kx0,
               *ysum = DF.ysum;
         static_assert(sizeof(Dev<float>) == sizeof(Dev<double>), "Dev layouts differ only in pointee types");
         std::memcpy(static_cast<void*>(&DF), static_cast<const void*>(&D), sizeof(Dev<float>));
         DF.val = ctx->val_f; DF.valT = ctx->valT_f;
         DF.c = c_f; DF.h = h_f; DF.l = l_f; DF.u = u_f;
-        DF.x = x; DF.xh = xh; DF.x0 = x0; DF.kty = kty; DF.ktyh = ktyh; DF.kty0 = kty0; DF.xsum = xsum;
+        DF.x = x; DF.xh = xh; DF.x0 = x0; DF.kty = kty; DF.ktyh = ktyh; DF.kty0 = kty0; DF.xsum = xsum; DF.xh1 = xh1;
         DF.y = y; DF.yh = yh; DF.y0 = y0; DF.kx = kx; DF.kxh0 = kxh0; DF.kxh1 = kxh1; DF.kx0 = kx0; DF.ysum = ysum;
         DF.soc_w32 = soc_w32; DF.exp_lg32 = exp_lg32;
         ctx->fp32_active = true;
@@ -1134,7 +1155,7 @@ pdcs_status switch_to_fp64(pdcs_ctx* ctx) {
     Dev<float>& F = ctx->DF;
     k_flush_primal(F, ctx->g_vec_n, s);
     k_flush_dual(F, ctx->g_vec_m, s);
-    clear_pending<<<1, 1, 0, s>>>(ctx->ctrl);
+    clear_pending<<<1, 1, 0, s>>>(ctx->ctrl);  // the FP64 primal update forms x-hat afresh
     const int g = vec_grid(std::max(ctx->m, ctx->n), ctx->sms);
     const float* fn[3] = {F.x, F.x0, F.xsum};
     double* dn[3] = {D.x, D.x0, D.xsum};
@@ -1203,6 +1224,7 @@ void fill_info(pdcs_ctx* ctx, pdcs_info* info) {
     info->spmv_plan[3] = ctx->pkt.unroll;
     info->spmv_format = ctx->pk.format;
     info->soc_grid_cones = ctx->team_cones;
+    info->fuse_primal = ctx->fuse_primal ? 1 : 0;
 }
 
 __global__ void batch_prepare(Dev<double>* views, int count, double tol, int start) {
@@ -1340,6 +1362,7 @@ void pdcs_default_options(pdcs_options* o) {
     o->spmv_format = 0;
     o->soc_lane_entries = 0;
     o->soc_grid_dim = 0;
+    o->fuse_primal = 0;
 }
 
 pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, const double* lb, const double* ub,
@@ -1394,6 +1417,7 @@ pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, con
     if (o.spmv_format < 0 || o.spmv_format > 2) return bad("spmv_format must be 0, 1 or 2");
     if (o.soc_lane_entries < 0 || o.soc_lane_entries > 256) return bad("soc_lane_entries must be in [0, 256]");
     if (o.soc_grid_dim < -1) return bad("soc_grid_dim must be -1, 0 or positive");
+    if (o.fuse_primal != 0 && o.fuse_primal != 1) return bad("fuse_primal must be 0 or 1");
     if (o.spmv_format == 2 && (o.batch_blocks > 0 || o.spmv_lanes != 0))
         return bad("the sliced SpMV format serves single programs with spmv_lanes = 0");
 
@@ -1559,9 +1583,11 @@ pdcs_status pdcs_get_iterate(pdcs_ctx* ctx, double* x, double* y, double* xhat, 
     if (ctx->fp32_active) {
         k_flush_primal(ctx->DF, ctx->g_vec_n, ctx->stream);
         k_flush_dual(ctx->DF, ctx->g_vec_m, ctx->stream);
+        xhat_first<float><<<ctx->g_vec_n, kBlock, 0, ctx->stream>>>(ctx->n, ctx->DF.xh, ctx->DF.xh1, ctx->ctrl);
     } else {
         k_flush_primal(ctx->D, ctx->g_vec_n, ctx->stream);
         k_flush_dual(ctx->D, ctx->g_vec_m, ctx->stream);
+        xhat_first<double><<<ctx->g_vec_n, kBlock, 0, ctx->stream>>>(ctx->n, ctx->D.xh, ctx->D.xh1, ctx->ctrl);
     }
     clear_pending<<<1, 1, 0, ctx->stream>>>(ctx->ctrl);
     ctx->launches += 3;
@@ -1654,6 +1680,7 @@ pdcs_status pdcs_set_warm_start(pdcs_ctx* ctx, const double* x, const double* y,
     C.sigma = C.eta * C.omega;
     C.pending = 0; C.wsum = 0.0; C.k = 0; C.accepted = 0; C.attempts = 0; C.restarts = 0;
     C.status = kRunning; C.check_mode = 0; C.phi_prev = INFINITY;
+    C.xnext = 0;  // the next primal update forms x-hat from the new start
     *ctx->h_ctrl = C;
     CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
@@ -1669,8 +1696,9 @@ pdcs_status pdcs_get_state(pdcs_ctx* ctx, pdcs_state* st, const pdcs_state_array
     // apply a pending Halpern update (the arithmetic of the next evaluation's update)
     k_flush_primal(D, ctx->g_vec_n, s);
     k_flush_dual(D, ctx->g_vec_m, s);
+    xhat_first<double><<<ctx->g_vec_n, kBlock, 0, s>>>(ctx->n, D.xh, D.xh1, ctx->ctrl);
     clear_pending<<<1, 1, 0, s>>>(ctx->ctrl);
-    ctx->launches += 3;
+    ctx->launches += 4;
     CK(cudaGetLastError());
     pdcs_status r = read_ctrl(ctx);
     if (r != PDCS_OK) return r;
@@ -1767,6 +1795,7 @@ pdcs_status pdcs_set_state(pdcs_ctx* ctx, const pdcs_state* st, const pdcs_state
     C.tau = C.eta / C.omega;
     C.sigma = C.eta * C.omega;
     C.pending = 0; C.check_mode = 0; C.restart_now = 0; C.ticket = 0;
+    C.xsel = 0; C.xnext = 0;
     C.status = st->status == 0 ? kRunning : (st->status == 1 ? kConverged : kNumericError);
     *ctx->h_ctrl = C;
     CK(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));

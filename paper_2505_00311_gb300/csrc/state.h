@@ -36,6 +36,11 @@ struct Ctrl {
     int32_t n_cand;       // candidates evaluated by the last check (1 or 2)
     unsigned int ticket;  // block counter of the last-block reductions
     int32_t team_abort;   // set when a bounded wait of the grid-wise SOC projection gave up
+    // x-hat buffers (fused K' product + primal update, see spmv_kt_primal): xsel names the
+    // buffer holding the x-hat of the current / last evaluation; xnext = 1 when the next
+    // evaluation's x-hat (and the accepted step's update of x, K'y, xsum) was already formed,
+    // in the other buffer, by the K' product's epilogue
+    int32_t xsel, xnext;
 };
 
 // Fixed slots of the partial-sum buffer (one double per block per quantity).

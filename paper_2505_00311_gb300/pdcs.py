@@ -47,7 +47,7 @@ class pdcs_options(ctypes.Structure):
                 ("spmv_lanes", ctypes.c_int32), ("time_limit", ctypes.c_double),
                 ("exp_mlp", ctypes.c_void_p), ("spmv_autotune", ctypes.c_int32), ("batch_blocks", ctypes.c_int32),
                 ("spmv_format", ctypes.c_int32), ("soc_lane_entries", ctypes.c_int32),
-                ("soc_grid_dim", ctypes.c_int32)]
+                ("soc_grid_dim", ctypes.c_int32), ("fuse_primal", ctypes.c_int32)]
 
 
 class pdcs_info(ctypes.Structure):
@@ -57,7 +57,7 @@ class pdcs_info(ctypes.Structure):
                 ("omega", ctypes.c_double), ("setup_seconds", ctypes.c_double),
                 ("solve_seconds", ctypes.c_double), ("status", ctypes.c_int32), ("fp64_phase", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int64), ("spmv_plan", ctypes.c_int32 * 4), ("spmv_format", ctypes.c_int32),
-                ("soc_grid_cones", ctypes.c_int32)]
+                ("soc_grid_cones", ctypes.c_int32), ("fuse_primal", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if isinstance(getattr(self, k), ctypes.Array) else getattr(self, k))

@@ -462,3 +462,31 @@ def test_spmv_formats_match_host_products(fmt):
         bound = abs(A) @ np.abs(st[vec])
         assert np.all(np.abs(got[prod] - ref) <= 1e-14 * bound + 1e-300), prod
     g.close()
+
+
+def test_fused_primal_update_matches_separate_kernels():
+    """The K' product with the primal update in its row epilogue (fuse_primal = 1, sliced
+    storage) against the separate primal-update kernel, from the same start, checks
+    every 16 evaluations: equal counters, iterates within 1e-12 over 16 evaluations and 1e-11
+    over 48 (the two differ only in the order of the ||x-hat - x||^2 sum, which the adaptive step
+    feeds back), and both equal to the oracle over the first 16."""
+    p = I.scaled_mixed_cone(1, 0.01)
+    a = P.Solver(p, check_period=16, fuse_primal=1)
+    b = P.Solver(p, check_period=16, fuse_primal=0)
+    o = oracle.Solver(p, check_period=16)
+    assert a.info()["fuse_primal"] == 1 and b.info()["fuse_primal"] == 0
+    done = 0
+    for target in [1, 2, 3, 8, 16, 17, 32, 48]:
+        a.run(target - done)
+        b.run(target - done)
+        if target <= 16:
+            o.run(target - done)
+        done = target
+        ia, ib = a.info(), b.info()
+        assert (ia["attempts"], ia["accepted"], ia["restarts"]) == (ib["attempts"], ib["accepted"], ib["restarts"])
+        err = _compare_iterates(a, b)
+        assert err <= (RTOL if target <= 16 else 10 * RTOL), (target, err)
+        if target <= 16:
+            assert _compare_iterates(a, o) <= RTOL, target
+    a.close()
+    b.close()
