@@ -429,6 +429,13 @@ int64_t pdcs_mlp_params(int32_t n_layers, const int32_t* sizes);
 pdcs_status pdcs_mlp_forward(int32_t n_layers, const int32_t* sizes, int64_t n, const float* X, const float* W,
                              float* Y);
 
+/* The same outputs with every layer's product on the tensor cores: the rows and weights are
+ * rounded to BF16 as they are loaded and multiplied by mma.sync m16n8k16 tiles with FP32
+ * accumulation; bias and ReLU in FP32.  Error against the FP32 forward: about 2^-8 relative
+ * to sum |W| |x| per layer (BF16 operands). */
+pdcs_status pdcs_mlp_forward_bf16(int32_t n_layers, const int32_t* sizes, int64_t n, const float* X,
+                                  const float* W, float* Y);
+
 /* Loss on the n rows (targets T, n x sizes[n_layers]) and its gradient (layout of W). */
 pdcs_status pdcs_mlp_loss_grad(int32_t n_layers, const int32_t* sizes, int64_t n, const float* X, const float* T,
                                const float* W, float* grad, float* loss);

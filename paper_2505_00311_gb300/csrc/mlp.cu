@@ -3,6 +3,7 @@
 // of parametric program families (initial dual iterate and primal weight from a summary
 // of the instance data).  Offline entry points: host arrays in and out, device memory
 // allocated per call.  FP32 throughout with sums in a fixed order (deterministic).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,6 +50,53 @@ __global__ void dense_fwd(int B, int din, int dout, const float* __restrict__ X,
     for (int i = 0; i < din; ++i) a = fmaf(w[i], x[i], a);
     Z[t] = a;
     Y[t] = relu ? fmaxf(a, 0.0f) : a;
+}
+
+// The same layer on the tensor cores: X and W rounded to BF16 as they are loaded, products
+// accumulated in FP32 by mma.sync m16n8k16 tiles (one warp per 16 x 8 tile of Z, K in steps of
+// 16, zero padding past din), bias and ReLU in FP32.  Fragment layout of the PTX ISA for
+// m16n8k16 with 16-bit operands: lane = 4 g + t; A rows g and g + 8, columns 2t, 2t + 1 and
+// 8 + 2t, 9 + 2t; B (k x n, "col") columns n = g, rows 2t, 2t + 1 and 8 + 2t, 9 + 2t;
+// C rows g and g + 8, columns 2t, 2t + 1.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__global__ void dense_fwd_bf16(int B, int din, int dout, const float* __restrict__ X, const float* __restrict__ W,
+                               const float* __restrict__ b, float* Z, float* Y, int relu) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int tn = (dout + 7) / 8;
+    if (warp >= (long long)((B + 15) / 16) * tn) return;  // whole warps
+    const int m0 = (int)(warp / tn) * 16, n0 = (int)(warp % tn) * 8;
+    const int g = lane >> 2, t = lane & 3;
+    auto xa = [&](int r, int k) { return (r < B && k < din) ? X[(size_t)r * din + k] : 0.0f; };
+    auto wb = [&](int n, int k) { return (n < dout && k < din) ? W[(size_t)n * din + k] : 0.0f; };
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int k0 = 0; k0 < din; k0 += 16) {
+        const int ka = k0 + 2 * t, kb = k0 + 8 + 2 * t;
+        const uint32_t a0 = pack_bf16(xa(m0 + g, ka), xa(m0 + g, ka + 1));
+        const uint32_t a1 = pack_bf16(xa(m0 + g + 8, ka), xa(m0 + g + 8, ka + 1));
+        const uint32_t a2 = pack_bf16(xa(m0 + g, kb), xa(m0 + g, kb + 1));
+        const uint32_t a3 = pack_bf16(xa(m0 + g + 8, kb), xa(m0 + g + 8, kb + 1));
+        const uint32_t b0 = pack_bf16(wb(n0 + g, ka), wb(n0 + g, ka + 1));
+        const uint32_t b1 = pack_bf16(wb(n0 + g, kb), wb(n0 + g, kb + 1));
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+            "{%0, %1, %2, %3};"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = m0 + g + (q >= 2 ? 8 : 0), n = n0 + 2 * t + (q & 1);
+        if (r < B && n < dout) {
+            const float z = c[q] + b[n];
+            Z[(size_t)r * dout + n] = z;
+            Y[(size_t)r * dout + n] = relu ? fmaxf(z, 0.0f) : z;
+        }
+    }
 }
 
 // output error: dZ = 2 (Y - T) / (B dout), squared errors for the loss
@@ -169,6 +217,17 @@ void forward(const Net& N, int B, const float* X, const float* W, Work& w) {
     }
 }
 
+// the forward pass with every layer on the tensor cores (dense_fwd_bf16)
+void forward_bf16(const Net& N, int B, const float* X, const float* W, Work& w) {
+    const float* in = X;
+    for (int l = 0; l < N.L; ++l) {
+        const long long tiles = (long long)((B + 15) / 16) * ((N.sz[l + 1] + 7) / 8);
+        dense_fwd_bf16<<<blocks(tiles * 32), 256>>>(B, N.sz[l], N.sz[l + 1], in, W + N.wo[l], W + N.bo[l],
+                                                    w.Z[l + 1], w.Y[l + 1], l + 1 < N.L);
+        in = w.Y[l + 1];
+    }
+}
+
 // loss and gradient of B rows (targets T indexed by idx, or in order when idx is null)
 void loss_grad(const Net& N, int B, const float* X, const float* T, const long long* idx, const float* W, Work& w) {
     forward(N, B, X, W, w);
@@ -216,6 +275,25 @@ pdcs_status pdcs_mlp_forward(int32_t n_layers, const int32_t* sizes, int64_t n, 
     CKM(cudaMemcpy(dX, X, sizeof(float) * B * N.sz[0], cudaMemcpyHostToDevice));
     CKM(cudaMemcpy(dW, W, sizeof(float) * N.params, cudaMemcpyHostToDevice));
     forward(N, B, dX, dW, w);
+    CKM(cudaGetLastError());
+    CKM(cudaMemcpy(Y, w.Y[N.L], sizeof(float) * B * N.sz[N.L], cudaMemcpyDeviceToHost));
+    return PDCS_OK;
+}
+
+pdcs_status pdcs_mlp_forward_bf16(int32_t n_layers, const int32_t* sizes, int64_t n, const float* X, const float* W,
+                                  float* Y) {
+    Net N;
+    if (!N.init(n_layers, sizes) || n < 1 || n > (1 << 24) || !X || !W || !Y) return PDCS_ERR_INVALID;
+    const int B = (int)n;
+    DevMem M;
+    Work w;
+    cudaError_t e = w.alloc(M, N, B);
+    float* dX = M.get<float>((size_t)B * N.sz[0], e);
+    float* dW = M.get<float>(N.params, e);
+    CKM(e);
+    CKM(cudaMemcpy(dX, X, sizeof(float) * B * N.sz[0], cudaMemcpyHostToDevice));
+    CKM(cudaMemcpy(dW, W, sizeof(float) * N.params, cudaMemcpyHostToDevice));
+    forward_bf16(N, B, dX, dW, w);
     CKM(cudaGetLastError());
     CKM(cudaMemcpy(Y, w.Y[N.L], sizeof(float) * B * N.sz[N.L], cudaMemcpyDeviceToHost));
     return PDCS_OK;

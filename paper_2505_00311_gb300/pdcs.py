@@ -124,6 +124,7 @@ SIGNATURES = {
     "pdcs_batch_destroy": (None, [ctypes.c_void_p]),
     "pdcs_mlp_params": (ctypes.c_int64, [ctypes.c_int32, _i32p]),
     "pdcs_mlp_forward": (ctypes.c_int, [ctypes.c_int32, _i32p, ctypes.c_int64, _fp, _fp, _fp]),
+    "pdcs_mlp_forward_bf16": (ctypes.c_int, [ctypes.c_int32, _i32p, ctypes.c_int64, _fp, _fp, _fp]),
     "pdcs_mlp_loss_grad": (ctypes.c_int, [ctypes.c_int32, _i32p, ctypes.c_int64, _fp, _fp, _fp, _fp, _fp]),
     "pdcs_mlp_train": (ctypes.c_int, [ctypes.c_int32, _i32p, ctypes.c_int64, _fp, _fp, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _fp, _fp]),
@@ -549,6 +550,15 @@ def mlp_forward(sizes, X, W):
     sz, X, W = _sizes(sizes), _f32(X), _f32(W)
     Y = np.empty((X.shape[0], sz[-1]), dtype=np.float32)
     _check(lib().pdcs_mlp_forward(sz.size - 1, _ptr(sz, _i32p), X.shape[0], _ptr(X, _fp), _ptr(W, _fp), _ptr(Y, _fp)))
+    return Y
+
+
+def mlp_forward_bf16(sizes, X, W):
+    """mlp_forward with the layers' products on the tensor cores (BF16 operands, FP32 sums)."""
+    sz, X, W = _sizes(sizes), _f32(X), _f32(W)
+    Y = np.empty((X.shape[0], sz[-1]), dtype=np.float32)
+    _check(lib().pdcs_mlp_forward_bf16(sz.size - 1, _ptr(sz, _i32p), X.shape[0], _ptr(X, _fp), _ptr(W, _fp),
+                                       _ptr(Y, _fp)))
     return Y
 
 

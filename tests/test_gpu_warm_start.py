@@ -34,6 +34,47 @@ def test_gpu_network_loss_and_gradient_match_the_reference():
     np.testing.assert_allclose(Y, N.forward(sizes, W.astype(np.float64), X), rtol=1e-4, atol=1e-5)
 
 
+def _bf16(a):
+    """Round to the nearest BF16 (ties to even), in FP64: the top 16 bits of the FP32 value."""
+    f = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    f = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000
+    return f.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_tensor_core_forward_matches_the_reference():
+    """pdcs_mlp_forward_bf16 (mma.sync m16n8k16 tiles, BF16 operands, FP32 accumulation) on the
+    warm-start network's shape and on ragged sizes (rows, inputs and outputs that are not
+    multiples of the tile): against the FP64 forward of oracle/mlp.py with the same BF16
+    roundings of the rows, weights and hidden activations, within 1e-4 of the scale of each
+    layer's products, and against the FP32 forward within the BF16 rounding."""
+    rng = np.random.default_rng(4)
+    for sizes, n in (([17, 256, 256, 23], 1000), ([9, 40, 13], 37), ([5, 3], 1)):
+        W = P.mlp_init(sizes, 5).astype(np.float32)
+        X = rng.normal(size=(n, sizes[0])).astype(np.float32)
+        Y = P.mlp_forward_bf16(sizes, X, W)
+        # reference: layer by layer, the products of BF16-rounded operands in FP64
+        h = X.astype(np.float64)
+        off = 0
+        scale = 0.0
+        for l in range(len(sizes) - 1):
+            din, dout = sizes[l], sizes[l + 1]
+            Wl = W[off:off + din * dout].reshape(dout, din).astype(np.float64)
+            off += din * dout
+            bl = W[off:off + dout].astype(np.float64)
+            off += dout
+            prod = _bf16(h) @ _bf16(Wl).T
+            scale = np.abs(_bf16(h)) @ np.abs(_bf16(Wl)).T
+            h = prod + bl
+            if l + 1 < len(sizes) - 1:
+                h = np.maximum(h, 0.0)
+        # the last layer's inputs differ from the reference only by FP32 sums (and, rarely, by
+        # the BF16 rounding of an activation they moved across a tie)
+        assert np.max(np.abs(Y - h) / (scale + 1e-30)) <= 1e-2
+        assert np.median(np.abs(Y - h) / (scale + 1e-30)) <= 1e-5
+        Y32 = P.mlp_forward(sizes, X, W)
+        assert np.max(np.abs(Y - Y32) / (scale + 1e-30)) <= 4e-2
+
+
 FAM_ASSETS, FAM_FACTORS = 400, 10
 SIZES = [FAM_FACTORS + 7, 256, 256, 1 + 2 * FAM_FACTORS + 2]
 
