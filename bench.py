@@ -236,6 +236,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-programs measurement")
     ap.add_argument("--no-proj", action="store_true", help="skip the standalone projection measurements")
     ap.add_argument("--no-lasso", action="store_true", help="skip the paper-generator Lasso time-to-tolerance runs")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start measurement")
     ap.add_argument("--no-exp", action="store_true",
                     help="skip the exp-cone logistic program (plain vs learned exp root start)")
     ap.add_argument("--batch-count", type=int, default=256, help="Lasso programs in the batched measurement")
@@ -507,6 +508,65 @@ def main():
         plan.close()
         del v, dsc, out
 
+    # learned warm start on a parametric portfolio family (400 assets, 10 factors): a network
+    # trained on 160 batched solves predicts (log omega, y) from a summary of the returns; 24
+    # held-out instances solved to 1e-6 cold and warm, one at a time (wall clock of pdcs_solve,
+    # prediction time included in the warm arm), with FP32 and BF16 tensor-core predictions
+    warm = None
+    if not args.no_warm:
+        from paper_2505_00311_gb300 import instances as I
+        fam = I.portfolio_family(0, 400, 10)
+        sizes = [17, 256, 256, 23]
+
+        def solve_batch(seeds):
+            svs = [P.Solver(I.portfolio_socp(fam, I.portfolio_mu(fam, sd)), stream=stream.cuda_stream, batch_blocks=4)
+                   for sd in seeds]
+            bt = P.Batch(svs)
+            bt.solve(1e-6, 200_000)
+            out = [(sv.solution(), sv.info()) for sv in svs]
+            bt.close()
+            for sv in svs:
+                sv.close()
+            return out
+
+        train = list(range(160))
+        t0 = time.perf_counter()
+        res = solve_batch(train)
+        t_data = time.perf_counter() - t0
+        Xtr = np.stack([I.portfolio_features(fam, I.portfolio_mu(fam, sd)) for sd in train])
+        Ytr = np.stack([np.concatenate([[np.log(inf["omega"])], y]) for (x, y), inf in res])
+        mu_x, sd_x = Xtr.mean(axis=0), Xtr.std(axis=0) + 1e-12
+        mu_y, sd_y = Ytr.mean(axis=0), Ytr.std(axis=0) + 1e-12
+        t0 = time.perf_counter()
+        Wn, _ = P.mlp_train(sizes, (Xtr - mu_x) / sd_x, (Ytr - mu_y) / sd_y, P.mlp_init(sizes, 0), steps=3000,
+                            batch=64, lr=1e-3, seed=7)
+        t_train = time.perf_counter() - t0
+        held = list(range(1000, 1024))
+        arms = {}
+        for arm in ("cold", "warm_fp32", "warm_bf16"):
+            secs, evals, conv = 0.0, 0, 0
+            for sd in held:
+                q = I.portfolio_socp(fam, I.portfolio_mu(fam, sd))
+                sv = P.Solver(q, stream=stream.cuda_stream)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if arm != "cold":
+                    f = ((I.portfolio_features(fam, I.portfolio_mu(fam, sd)) - mu_x) / sd_x)[None, :]
+                    fwd = P.mlp_forward if arm == "warm_fp32" else P.mlp_forward_bf16
+                    pr = fwd(sizes, f, Wn)[0] * sd_y + mu_y
+                    sv.warm_start(None, pr[1:].astype(np.float64), float(np.exp(pr[0])))
+                st1, inf1 = sv.solve(1e-6, 200_000)
+                torch.cuda.synchronize()
+                secs += time.perf_counter() - t0
+                evals += inf1["attempts"]
+                conv += st1 == P.OK
+                sv.close()
+            arms[arm] = {"seconds": secs, "evaluations": evals, "converged": conv}
+        warm = {"workload": "portfolio SOCP family, 400 assets, 10 factors (budget, box, ||F'x|| <= gamma), "
+                            "24 held-out instances to 1e-6 one at a time; network 17-256-256-23 trained on 160 "
+                            "batched solves", "training_solves_seconds": t_data, "training_seconds": t_train,
+                **arms}
+
     # the paper's Lasso workload (Sec. 5.3, App. B.2) at 7e4 x 7e5 (4.9e6 entries of A, one SOC
     # of 70,002 rows projected grid-wise): time to 1e-3 and 1e-6 (the paper's two accuracy
     # levels), FP64, wall clock of pdcs_solve, setup apart
@@ -640,7 +700,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": bench_config(args, world),
             "rates": rates, "clocks": clk, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-            "time_to_tol": ttt, "fp32_iterates": fp32, "batched_programs": batch, "projections": proj, "paper_lasso": lasso,
+            "time_to_tol": ttt, "fp32_iterates": fp32, "batched_programs": batch, "projections": proj, "paper_lasso": lasso, "warm_start": warm,
             "exp_heavy": exp_heavy}
     print(json.dumps(line))
 
