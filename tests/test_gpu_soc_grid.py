@@ -100,3 +100,23 @@ def test_lasso_solve_passes_the_oracle_evaluator():
                    options={"maxiter": 20000, "ftol": 1e-15, "gtol": 1e-12})
     assert abs(k["pobj"] - res.fun) <= 1e-4 * max(1.0, abs(res.fun)), (k["pobj"], res.fun)
     g.close()
+
+
+def test_one_evaluation_rotated_cone_across_blocks():
+    """A rotated SOC (the dense Lasso's (w, r, y) block of 1,502 rows) split over a team of three
+    blocks (soc_grid_dim forces it): the Q transform of the first two rows happens in the first
+    block while the others hold the rest of the cone; one evaluation from the oracle's states
+    after 0 and 64 evaluations within 1e-12."""
+    from parity_helpers import one_evaluation
+    p = I.lasso_socp(6, 3000)
+    assert p["cone_types"][-1] == 3 and p["cone_dims"][-1] == 1502
+    o = oracle.Solver(p, check_period=64)
+    g = P.Solver(p, check_period=64, soc_grid_dim=1024)
+    assert g.info()["soc_grid_cones"] == 1
+    done = 0
+    for start in [0, 64]:
+        o.run(start - done)
+        err, acc = one_evaluation(p, g, o)
+        done = start + 1
+        assert acc[0] == acc[1] and max(err.values()) <= RTOL, (start, err)
+    g.close()
