@@ -34,18 +34,22 @@ extern "C" {
 
 /* Cone kinds (Sec. 1 notation): ZERO {0}^d; NONNEG R_+^d; SOC {(t, x): ||x|| <= t};
  * RSOC {(x, y, z): ||z||^2 <= 2xy, x, y >= 0}; EXP the closure of
- * {(r, s, t): s > 0, t >= s exp(r / s)} (dim must be 3). */
+ * {(r, s, t): s > 0, t >= s exp(r / s)} (dim must be 3); EXP_DUAL its dual cone K_exp^*,
+ * the closure of {(r, s, t): r < 0, -r exp(s / r) <= e t} (dim 3; a dual-cone row block of
+ * the problem of Sec. 2, projected through the Remark of App. A.2; y of such a block lies
+ * in K_exp). */
 typedef enum {
     PDCS_CONE_ZERO = 0,
     PDCS_CONE_NONNEG = 1,
     PDCS_CONE_SOC = 2,
     PDCS_CONE_RSOC = 3,
-    PDCS_CONE_EXP = 4
+    PDCS_CONE_EXP = 4,
+    PDCS_CONE_EXP_DUAL = 5
 } pdcs_cone_type;
 
 typedef struct {
     int32_t type; /* pdcs_cone_type */
-    int64_t dim;  /* rows covered; SOC >= 1, RSOC >= 2, EXP == 3; the dims sum to m */
+    int64_t dim;  /* rows covered; SOC >= 1, RSOC >= 2, EXP and EXP_DUAL == 3; the dims sum to m */
 } pdcs_cone;
 
 /* CSR matrix in host memory: row_ptr[m + 1] (row_ptr[0] == 0, nondecreasing),
@@ -276,8 +280,8 @@ void pdcs_destroy(pdcs_ctx* ctx);
  * onto (D C)* = D^{-1} C* (dual == 1), D = diag(d) (DEVICE pointer, d > 0; NULL
  * means D = I), written to the DEVICE vector out (may equal v).  The cone list
  * is a HOST array as in pdcs_create; for RSOC blocks d must be equal on their
- * first two rows.  SOC by Theorem 1, exp by Theorem 3, exp* by the Remark of
- * App. A.2.  Accuracy: each block within 1e-12 of its exact projection, relative
+ * first two rows.  SOC by Theorem 1, exp by Theorem 3, exp* (the dual side of an EXP
+ * block, and the primal side of an EXP_DUAL block) by the Remark of App. A.2.  Accuracy: each block within 1e-12 of its exact projection, relative
  * to the block's norm (the root searches run in FP32 and are finished in FP64; an
  * exp point within 1e-14 of its norm from the cone or from the polar cone is
  * returned as itself or as 0).  Runs on cuda_stream and returns once the work is
@@ -335,6 +339,7 @@ void pdcs_proj_plan_destroy(pdcs_proj_plan* plan);
  *   - The array is shared by all calls and keeps the last call's contents; every
  *     entry a call reads is written by the same call first.  Calls that overlap on
  *     the GPU (different streams, no ordering between them) race on it.
+ *   - EXP_DUAL blocks are not accepted (PDCS_ERR_INVALID); the other cone kinds are.
  *   - Arguments and layout as pdcs_proj_cones_device: v, d (may be NULL), out are
  *     DEVICE pointers, cones a HOST array that must stay unchanged until the queued
  *     work has run.  Returns PDCS_ERR_INVALID for a malformed cone list or

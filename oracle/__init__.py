@@ -25,7 +25,7 @@ _SOURCES = ["cones.c", "solver.c"]
 _lock = threading.Lock()
 _lib = None
 
-ZERO, NONNEG, SOC, RSOC, EXP = 0, 1, 2, 3, 4
+ZERO, NONNEG, SOC, RSOC, EXP, EXP_DUAL = 0, 1, 2, 3, 4, 5
 RESCALE_NONE, RESCALE_COORD, RESCALE_BLOCK = 0, 1, 2
 STEP_ADAPTIVE, STEP_CONSTANT, STEP_PLAIN = 0, 1, 2
 RUNNING, CONVERGED, MAX_ITER = 0, 1, 2

@@ -374,7 +374,9 @@ void orc_proj_exp_dual(const double* v0, const double* d, double* out) {
 
 /* Blockwise projection, eq. multi_cone_proj.  dual == 0: onto D C.
  * dual == 1: onto (D C)^* = D^{-1} C^*, where zero^* = R, nonneg, SOC and RSOC
- * are self-dual and exp^* is handled by the Remark. */
+ * are self-dual and exp^* is handled by the Remark.  An EXP_DUAL block is K_exp^*
+ * itself (the dual-cone row blocks of the problem of Sec. 2): D K_exp^* by the Remark,
+ * its dual D^{-1} K_exp directly. */
 void orc_proj_cones(const double* v, const double* d, int64_t m, const int32_t* types,
                     const int64_t* dims, int64_t n_cones, int dual, double* out) {
     (void)m;
@@ -385,7 +387,7 @@ void orc_proj_cones(const double* v, const double* d, int64_t m, const int32_t* 
         const double* dd = d + o;
         double* oo = out + o;
         double* dinv = NULL;
-        if (dual && (types[k] == ORC_SOC || types[k] == ORC_RSOC)) {
+        if ((dual && (types[k] == ORC_SOC || types[k] == ORC_RSOC)) || types[k] == ORC_EXP_DUAL) {
             dinv = (double*)malloc(sizeof(double) * (size_t)dim);
             for (int64_t i = 0; i < dim; ++i) dinv[i] = 1.0 / dd[i];
         }
@@ -409,6 +411,15 @@ void orc_proj_cones(const double* v, const double* d, int64_t m, const int32_t* 
                     for (int i = 0; i < 3; ++i) oo[i] = vv[i] + p[i];
                 } else {
                     orc_proj_exp(vv, dd, oo);
+                }
+                break;
+            case ORC_EXP_DUAL: /* the block is D K_exp*; its dual cone is D^-1 K_exp */
+                if (dual) {
+                    orc_proj_exp(vv, dinv, oo);
+                } else { /* Remark with E = D: Proj_{D K*}(v) = v + Proj_{D^-1 K}(-v) */
+                    double nv[3] = {-vv[0], -vv[1], -vv[2]}, p[3];
+                    orc_proj_exp(nv, dinv, p);
+                    for (int i = 0; i < 3; ++i) oo[i] = vv[i] + p[i];
                 }
                 break;
             default:

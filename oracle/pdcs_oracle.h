@@ -23,7 +23,7 @@
 extern "C" {
 #endif
 
-enum { ORC_ZERO = 0, ORC_NONNEG = 1, ORC_SOC = 2, ORC_RSOC = 3, ORC_EXP = 4 };
+enum { ORC_ZERO = 0, ORC_NONNEG = 1, ORC_SOC = 2, ORC_RSOC = 3, ORC_EXP = 4, ORC_EXP_DUAL = 5 };
 enum { ORC_RESCALE_NONE = 0, ORC_RESCALE_COORD = 1, ORC_RESCALE_BLOCK = 2 };
 enum { ORC_STEP_ADAPTIVE = 0, ORC_STEP_CONSTANT = 1, ORC_STEP_PLAIN = 2 };
 enum { ORC_RUNNING = 0, ORC_CONVERGED = 1, ORC_MAX_ITER = 2 };

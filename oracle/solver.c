@@ -207,7 +207,8 @@ static void tie_rows(const orc_solver* S, double* rn, int use_max) {
         int64_t g = 0;
         if (S->opt.rescale == ORC_RESCALE_COORD && S->types[k] == ORC_RSOC) g = 2;
         if (S->opt.rescale == ORC_RESCALE_BLOCK &&
-            (S->types[k] == ORC_SOC || S->types[k] == ORC_RSOC || S->types[k] == ORC_EXP)) g = dim;
+            (S->types[k] == ORC_SOC || S->types[k] == ORC_RSOC || S->types[k] == ORC_EXP ||
+             S->types[k] == ORC_EXP_DUAL)) g = dim;
         if (g < 2) continue;
         double mx = 0.0;
         for (int64_t i = 0; i < g; ++i) mx = fmax(mx, rn[o + i]);
@@ -301,9 +302,9 @@ orc_solver* orc_create(int64_t m, int64_t n, const int64_t* row_ptr, const int32
     int64_t tot = 0;
     for (int64_t k = 0; k < n_cones; ++k) {
         if (dims[k] < 1) return NULL;
-        if (types[k] == ORC_EXP && dims[k] != 3) return NULL;
+        if ((types[k] == ORC_EXP || types[k] == ORC_EXP_DUAL) && dims[k] != 3) return NULL;
         if (types[k] == ORC_RSOC && dims[k] < 2) return NULL;
-        if (types[k] < ORC_ZERO || types[k] > ORC_EXP) return NULL;
+        if (types[k] < ORC_ZERO || types[k] > ORC_EXP_DUAL) return NULL;
         tot += dims[k];
     }
     if (tot != m) return NULL;

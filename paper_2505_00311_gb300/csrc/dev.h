@@ -82,6 +82,7 @@ struct Dev {
     const double* soc_w;   // per SOC row: weight of the dual projection, (dr_row / dr_first)^2
     const double* soc_wp;  // per SOC row: weight of the primal projection, (dr_first / dr_row)^2
     int exp_row0, n_exp;
+    const unsigned char* exp_kind;  // per exp-region block: 1 for K_exp^* (EXP_DUAL); null when none
     float* exp_L;          // last log-offset per exp cone
     const double* exp_lg;  // per exp cone: log dr of its three rows
     // SOC tiles of the FP64 dual update (see dual_soc_tiles): the cones sorted by dimension

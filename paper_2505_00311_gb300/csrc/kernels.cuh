@@ -663,6 +663,39 @@ __device__ __forceinline__ void dual_soc_large(const Dev<double>& D, const DualC
         dual_soc_cone(D, k, D.soc_order[base + j], acc);
 }
 
+// Exponential-family blocks of the exp region: kind 0 is K_exp, kind 1 (EXP_DUAL) is K_exp^*.
+// For scales D (row scales d, logs lg) and v, the projections onto D C_e (primal side) and
+// onto (D C_e)^* (dual side):
+//   K_exp  : D K_exp directly, D^{-1} K_exp^* by the Remark (v + Proj_{D K_exp}(-v));
+//   K_exp^*: D K_exp^* = (D^{-1})^{-1} K_exp^* by the Remark with the inverse scales, and
+//            (D K_exp^*)^* = D^{-1} K_exp directly with the inverse scales.
+__device__ __forceinline__ void exp_block_project(bool kdual, bool dual_side, double r, double s, double t,
+                                                  double d0, double d1, double d2, const double* lg, double* out,
+                                                  float* cache, const float* mlp) {
+    if (!kdual) {
+        if (dual_side) exp_dual_project_fast(r, s, t, d0, d1, d2, lg, out, cache, mlp);
+        else exp_project_fast(r, s, t, d0, d1, d2, lg, out, cache, mlp);
+        return;
+    }
+    const double li[3] = {-lg[0], -lg[1], -lg[2]};
+    if (dual_side) exp_project_fast(r, s, t, 1.0 / d0, 1.0 / d1, 1.0 / d2, li, out, cache, mlp);
+    else exp_dual_project_fast(r, s, t, 1.0 / d0, 1.0 / d1, 1.0 / d2, li, out, cache, mlp);
+}
+__device__ __forceinline__ void exp_block_project_f32(bool kdual, float r, float s, float t, float d0, float d1,
+                                                      float d2, const float* lg, float* out, float* cache,
+                                                      const float* mlp) {  // dual side
+    if (!kdual) {
+        exp_dual_project_f32(r, s, t, d0, d1, d2, lg, out, cache, mlp);
+        return;
+    }
+    const float li[3] = {-lg[0], -lg[1], -lg[2]};
+    exp_project_f32(r, s, t, 1.0f / d0, 1.0f / d1, 1.0f / d2, li, out, cache, mlp);
+}
+template <typename T>
+__device__ __forceinline__ bool exp_kind_dual(const Dev<T>& D, int e) {
+    return D.exp_kind != nullptr && D.exp_kind[e] != 0;
+}
+
 // exp cones: block b of nb_exp, one thread per cone (exp_pb per block)
 template <typename T>
 __device__ __forceinline__ void dual_exp_cones(const Dev<T>& D, const DualCoef<T>& k, int b, T (&acc)[2]) {
@@ -675,12 +708,13 @@ __device__ __forceinline__ void dual_exp_cones(const Dev<T>& D, const DualCoef<T
             dual_row_halpern(D, r + q, k.pend, k.ha, k.hb, k.hc, k.hw, k.pprev, y[q], kx[q]);
             v[q] = y[q] + k.sigma * (D.h[r + q] - T(2) * k.p[r + q] + kx[q]);
         }
+        const bool kd = exp_kind_dual(D, e);
         if constexpr (sizeof(T) == 8)
-            exp_dual_project_fast(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, out,
-                                  D.exp_L + e, D.exp_mlp);
+            exp_block_project(kd, true, v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, out,
+                              D.exp_L + e, D.exp_mlp);
         else
-            exp_dual_project_f32(v[0], v[1], v[2], (float)D.dr[r], (float)D.dr[r + 1], (float)D.dr[r + 2],
-                                 D.exp_lg32 + 3 * e, out, D.exp_L + e, D.exp_mlp);
+            exp_block_project_f32(kd, v[0], v[1], v[2], (float)D.dr[r], (float)D.dr[r + 1], (float)D.dr[r + 2],
+                                  D.exp_lg32 + 3 * e, out, D.exp_L + e, D.exp_mlp);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const T yh = (T)out[q];
@@ -842,8 +876,8 @@ __device__ __forceinline__ void cand_dual_body(const Dev<T>& D, int qidx) {
         for (int e = b * D.exp_pb + threadIdx.x; threadIdx.x < D.exp_pb && e < D.n_exp; e += stride) {
             const int r = D.exp_row0 + 3 * e;
             double o3[3];
-            exp_dual_project_fast(val(r), val(r + 1), val(r + 2), D.dr[r], D.dr[r + 1], D.dr[r + 2],
-                                  D.exp_lg + 3 * e, o3, nullptr, D.exp_mlp);
+            exp_block_project(exp_kind_dual(D, e), true, val(r), val(r + 1), val(r + 2), D.dr[r], D.dr[r + 1],
+                              D.dr[r + 2], D.exp_lg + 3 * e, o3, nullptr, D.exp_mlp);
             out[r] = o3[0];
             out[r + 1] = o3[1];
             out[r + 2] = o3[2];
@@ -929,9 +963,10 @@ __device__ __forceinline__ void kkt_primal_body(const Dev<T>& D, int qidx) {
                 w[k] = v[k] / D.dr[r + k];
             }
             const double lg0[3] = {0.0, 0.0, 0.0};
-            exp_project_fast(v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, ps, nullptr,
-                             D.exp_mlp);
-            exp_project_fast(w[0], w[1], w[2], 1.0, 1.0, 1.0, lg0, pu, nullptr, D.exp_mlp);
+            const bool kd = exp_kind_dual(D, e);
+            exp_block_project(kd, false, v[0], v[1], v[2], D.dr[r], D.dr[r + 1], D.dr[r + 2], D.exp_lg + 3 * e, ps,
+                              nullptr, D.exp_mlp);
+            exp_block_project(kd, false, w[0], w[1], w[2], 1.0, 1.0, 1.0, lg0, pu, nullptr, D.exp_mlp);
             for (int k = 0; k < 3; ++k) {
                 const double rs = v[k] - ps[k];
                 sums[0] += rs * rs;

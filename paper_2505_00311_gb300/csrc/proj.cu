@@ -56,7 +56,10 @@ __global__ void proj_soc(int nc, const int* __restrict__ off, const int* __restr
     }
 }
 
-__global__ void proj_exp(int ne, const int* __restrict__ off, const double* v, const double* d, int dual, double* out) {
+// kind (may be null): 1 for a K_exp^* (EXP_DUAL) block, projected with the inverse scales
+// (D K_exp^* by the Remark, its dual D^{-1} K_exp directly)
+__global__ void proj_exp(int ne, const int* __restrict__ off, const unsigned char* __restrict__ kind, const double* v,
+                         const double* d, int dual, double* out) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ne; k += stride) {
         const int o = off[k];
@@ -65,8 +68,15 @@ __global__ void proj_exp(int ne, const int* __restrict__ off, const double* v, c
         const double lg[3] = {d ? log(dr) : 0.0, d ? log(ds) : 0.0, d ? log(dt) : 0.0};
         double p[3];
         // the solver's mixed-precision search (FP32 screening and root, FP64 result)
-        if (dual) exp_dual_project_fast(r, s, t, dr, ds, dt, lg, p, nullptr);
-        else exp_project_fast(r, s, t, dr, ds, dt, lg, p, nullptr);
+        if (kind && kind[k]) {
+            const double li[3] = {-lg[0], -lg[1], -lg[2]};
+            if (dual) exp_project_fast(r, s, t, 1.0 / dr, 1.0 / ds, 1.0 / dt, li, p, nullptr);
+            else exp_dual_project_fast(r, s, t, 1.0 / dr, 1.0 / ds, 1.0 / dt, li, p, nullptr);
+        } else if (dual) {
+            exp_dual_project_fast(r, s, t, dr, ds, dt, lg, p, nullptr);
+        } else {
+            exp_project_fast(r, s, t, dr, ds, dt, lg, p, nullptr);
+        }
         out[o] = p[0];
         out[o + 1] = p[1];
         out[o + 2] = p[2];
@@ -79,18 +89,19 @@ extern "C" pdcs_status pdcs_proj_cones_device(const double* v, const double* d, 
                                               int64_t n_cones, int32_t dual, double* out, void* cuda_stream) {
     if (!v || !out || !cones || n_cones < 1 || m < 1 || m > 0x7fffffff) return PDCS_ERR_INVALID;
     std::vector<int> s_off, s_dim, soc_off, soc_dim, exp_off;
-    std::vector<unsigned char> s_type, soc_rot;
+    std::vector<unsigned char> s_type, soc_rot, exp_kind;
     long long o = 0;
     for (int64_t k = 0; k < n_cones; ++k) {
         const int t = cones[k].type;
         const long long dm = cones[k].dim;
-        if (t < PDCS_CONE_ZERO || t > PDCS_CONE_EXP || dm < 1 || (t == PDCS_CONE_EXP && dm != 3) ||
-            (t == PDCS_CONE_RSOC && dm < 2))
+        const bool ex = t == PDCS_CONE_EXP || t == PDCS_CONE_EXP_DUAL;
+        if (t < PDCS_CONE_ZERO || t > PDCS_CONE_EXP_DUAL || dm < 1 || (ex && dm != 3) || (t == PDCS_CONE_RSOC && dm < 2))
             return PDCS_ERR_INVALID;
         if (t == PDCS_CONE_ZERO || t == PDCS_CONE_NONNEG) {
             s_off.push_back((int)o); s_dim.push_back((int)dm); s_type.push_back((unsigned char)t);
-        } else if (t == PDCS_CONE_EXP) {
+        } else if (ex) {
             exp_off.push_back((int)o);
+            exp_kind.push_back(t == PDCS_CONE_EXP_DUAL);
         } else {
             soc_off.push_back((int)o); soc_dim.push_back((int)dm); soc_rot.push_back(t == PDCS_CONE_RSOC);
         }
@@ -99,7 +110,7 @@ extern "C" pdcs_status pdcs_proj_cones_device(const double* v, const double* d, 
     if (o != m) return PDCS_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const size_t ns = s_off.size(), nc = soc_off.size(), ne = exp_off.size();
-    const size_t bytes = sizeof(int) * (2 * ns + 2 * nc + ne) + ns + nc + 64;
+    const size_t bytes = sizeof(int) * (2 * ns + 2 * nc + ne) + ns + nc + ne + 64;
     char* buf = nullptr;
     if (cudaMallocAsync(&buf, bytes, s) != cudaSuccess) return PDCS_ERR_CUDA;
     std::vector<char> host(bytes, 0);
@@ -109,6 +120,7 @@ extern "C" pdcs_status pdcs_proj_cones_device(const double* v, const double* d, 
     const size_t o_coff = put(soc_off.data(), sizeof(int) * nc), o_cdim = put(soc_dim.data(), sizeof(int) * nc);
     const size_t o_eoff = put(exp_off.data(), sizeof(int) * ne);
     const size_t o_styp = put(s_type.data(), ns), o_crot = put(soc_rot.data(), nc);
+    const size_t o_ekind = put(exp_kind.data(), ne);
     cudaError_t e = cudaMemcpyAsync(buf, host.data(), bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging buffer is pageable and local
     int sms = 152, dev = 0;
@@ -131,7 +143,8 @@ extern "C" pdcs_status pdcs_proj_cones_device(const double* v, const double* d, 
     if (scr) cudaFreeAsync(scr, s);
     if (e == cudaSuccess && ne) {
         const int g = (int)std::min<long long>((ne + kBlock - 1) / kBlock, (long long)sms * 16);
-        proj_exp<<<g, kBlock, 0, s>>>((int)ne, (int*)(buf + o_eoff), v, d, dual, out);
+        proj_exp<<<g, kBlock, 0, s>>>((int)ne, (int*)(buf + o_eoff), (unsigned char*)(buf + o_ekind), v, d, dual,
+                                      out);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     cudaFreeAsync(buf, s);
@@ -246,7 +259,7 @@ struct pdcs_proj_plan {
     int sms = 152;
     int ns = 0, nc = 0, ne = 0;
     int *s_off = nullptr, *s_dim = nullptr, *c_off = nullptr, *c_dim = nullptr, *e_off = nullptr;
-    unsigned char *s_type = nullptr, *c_rot = nullptr;
+    unsigned char *s_type = nullptr, *c_rot = nullptr, *e_kind = nullptr;
     bool big_warp = false;  // a warp cone beyond the registers (FP32 copies in scr)
     int nsl = 0;            // lane-group slices of the warp cones (D = I runs)
     int* sl_c0 = nullptr;
@@ -262,20 +275,22 @@ extern "C" pdcs_status pdcs_proj_plan_create(int64_t m, const pdcs_cone* cones, 
     *out = nullptr;
     if (!cones || n_cones < 1 || m < 1 || m > 0x7fffffff) return PDCS_ERR_INVALID;
     std::vector<int> s_off, s_dim, c_off, c_dim, e_off, big;
-    std::vector<unsigned char> s_type, c_rot;
+    std::vector<unsigned char> s_type, c_rot, e_kind;
     std::vector<long long> offs(n_cones);
     long long o = 0, soc_rows = 0;
     for (int64_t k = 0; k < n_cones; ++k) {
         const int t = cones[k].type;
         const long long dm = cones[k].dim;
-        if (t < PDCS_CONE_ZERO || t > PDCS_CONE_EXP || dm < 1 || (t == PDCS_CONE_EXP && dm != 3) ||
+        const bool ex = t == PDCS_CONE_EXP || t == PDCS_CONE_EXP_DUAL;
+        if (t < PDCS_CONE_ZERO || t > PDCS_CONE_EXP_DUAL || dm < 1 || (ex && dm != 3) ||
             (t == PDCS_CONE_RSOC && dm < 2) || o + dm > m)
             return PDCS_ERR_INVALID;
         offs[k] = o;
         if (t == PDCS_CONE_ZERO || t == PDCS_CONE_NONNEG) {
             s_off.push_back((int)o); s_dim.push_back((int)dm); s_type.push_back((unsigned char)t);
-        } else if (t == PDCS_CONE_EXP) {
+        } else if (ex) {
             e_off.push_back((int)o);
+            e_kind.push_back(t == PDCS_CONE_EXP_DUAL);
         } else if (dm > kTeamMinDim) {
             big.push_back((int)k);
             soc_rows += dm;
@@ -358,7 +373,7 @@ extern "C" pdcs_status pdcs_proj_plan_create(int64_t m, const pdcs_cone* cones, 
     auto take = [&](size_t sz) { size_t q = bytes; bytes += (sz + 255) / 256 * 256; return q; };
     const size_t o_soff = take(sizeof(int) * P->ns), o_sdim = take(sizeof(int) * P->ns), o_styp = take(P->ns);
     const size_t o_coff = take(sizeof(int) * P->nc), o_cdim = take(sizeof(int) * P->nc), o_crot = take(P->nc);
-    const size_t o_eoff = take(sizeof(int) * P->ne);
+    const size_t o_eoff = take(sizeof(int) * P->ne), o_ekind = take(P->ne);
     const size_t o_slc0 = take(sizeof(int) * (P->nsl + 1)), o_sllg = take(P->nsl);
     const size_t o_toff = take(sizeof(int) * nt), o_tdim = take(sizeof(int) * nt), o_trot = take(nt);
     const size_t o_tb0 = take(sizeof(int) * nt), o_tg = take(sizeof(int) * nt);
@@ -377,7 +392,7 @@ extern "C" pdcs_status pdcs_proj_plan_create(int64_t m, const pdcs_cone* cones, 
     put(o_styp, s_type.data(), P->ns);
     put(o_coff, c_off.data(), sizeof(int) * P->nc); put(o_cdim, c_dim.data(), sizeof(int) * P->nc);
     put(o_crot, c_rot.data(), P->nc);
-    put(o_eoff, e_off.data(), sizeof(int) * P->ne);
+    put(o_eoff, e_off.data(), sizeof(int) * P->ne); put(o_ekind, e_kind.data(), P->ne);
     put(o_slc0, sl_c0.data(), sizeof(int) * (P->nsl + 1)); put(o_sllg, sl_lg.data(), P->nsl);
     put(o_toff, t_off.data(), sizeof(int) * nt); put(o_tdim, t_dim.data(), sizeof(int) * nt);
     put(o_trot, t_rot.data(), nt); put(o_tb0, t_b0.data(), sizeof(int) * nt); put(o_tg, t_g.data(), sizeof(int) * nt);
@@ -390,7 +405,7 @@ extern "C" pdcs_status pdcs_proj_plan_create(int64_t m, const pdcs_cone* cones, 
     }
     P->s_off = (int*)(b + o_soff); P->s_dim = (int*)(b + o_sdim); P->s_type = (unsigned char*)(b + o_styp);
     P->c_off = (int*)(b + o_coff); P->c_dim = (int*)(b + o_cdim); P->c_rot = (unsigned char*)(b + o_crot);
-    P->e_off = (int*)(b + o_eoff);
+    P->e_off = (int*)(b + o_eoff); P->e_kind = (unsigned char*)(b + o_ekind);
     P->sl_c0 = (int*)(b + o_slc0); P->sl_lg = (unsigned char*)(b + o_sllg);
     P->T.n_team = nt; P->T.nb = NB;
     P->T.off = (int*)(b + o_toff); P->T.dim = (int*)(b + o_tdim); P->T.rot = (unsigned char*)(b + o_trot);
@@ -428,7 +443,7 @@ extern "C" pdcs_status pdcs_proj_plan_run(pdcs_proj_plan* P, const double* v, co
     }
     if (P->ne) {
         const int g = (int)std::min<long long>((P->ne + kBlock - 1) / kBlock, (long long)sms * 16);
-        proj_exp<<<g, kBlock, 0, s>>>(P->ne, P->e_off, v, d, dual, out);
+        proj_exp<<<g, kBlock, 0, s>>>(P->ne, P->e_off, P->e_kind, v, d, dual, out);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? PDCS_OK : PDCS_ERR_CUDA;

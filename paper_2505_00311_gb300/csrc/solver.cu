@@ -554,7 +554,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     const long long nnz = ctx->nnz;
     // ---- row grouping: zero rows, nonnegative rows, SOC/RSOC blocks, exp cones
     std::vector<int> zero_rows, nonneg_rows, soc_o, soc_d, exp_o;
-    std::vector<unsigned char> soc_r;
+    std::vector<unsigned char> soc_r, exp_k;  // exp_k: 1 for a K_exp^* (EXP_DUAL) block
     {
         long long o = 0;
         for (int64_t k = 0; k < n_cones; ++k) {
@@ -564,7 +564,10 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
             else if (t == PDCS_CONE_NONNEG) for (long long i = 0; i < d; ++i) nonneg_rows.push_back((int)(o + i));
             else if (t == PDCS_CONE_SOC || t == PDCS_CONE_RSOC) {
                 soc_o.push_back((int)o); soc_d.push_back((int)d); soc_r.push_back(t == PDCS_CONE_RSOC);
-            } else exp_o.push_back((int)o);
+            } else {
+                exp_o.push_back((int)o);
+                exp_k.push_back(t == PDCS_CONE_EXP_DUAL);
+            }
             o += d;
         }
     }
@@ -812,6 +815,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     for (int k = 0; k < 3; ++k) A.reserve<int>(n_team + 1);          // team_cone, team_b0, team_g
     A.reserve<unsigned>(2LL * n_team + 2); A.reserve<double>(2LL * team_nb * kTeamQ + 1);
     A.reserve<unsigned char>(ctx->n_soc + 1);                         // soc_huge
+    A.reserve<unsigned char>(ctx->n_exp + 1);                         // exp_kind
     A.reserve<double>(m); A.reserve<double>(m); A.reserve<double>(3LL * ctx->n_exp + 1);
     A.reserve<double>(pl.total);
     A.reserve<Ctrl>(1);
@@ -882,6 +886,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     unsigned* d_team_bar = A.take<unsigned>(2LL * n_team + 2);
     double* d_team_part = A.take<double>(2LL * team_nb * kTeamQ + 1);
     unsigned char* d_huge = A.take<unsigned char>(ctx->n_soc + 1);
+    unsigned char* d_exp_kind = A.take<unsigned char>(ctx->n_exp + 1);
     ctx->soc_w = A.take<double>(m); ctx->soc_wp = A.take<double>(m); ctx->exp_lg = A.take<double>(3LL * ctx->n_exp + 1);
     ctx->part = A.take<double>(pl.total);
     ctx->ctrl = A.take<Ctrl>(1);
@@ -939,6 +944,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         CK(up(d_team_b0, team_b0.data(), sizeof(int) * n_team));
         CK(up(d_team_g, team_g.data(), sizeof(int) * n_team));
         CK(up(d_huge, huge.data(), (size_t)ctx->n_soc));
+        CK(up(d_exp_kind, exp_k.data(), exp_k.size()));
         CK(cudaMemsetAsync(d_team_bar, 0, sizeof(unsigned) * (2 * n_team + 2), s));
     }
     if (ctx->n_tie) {
@@ -1058,6 +1064,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.n_soc = ctx->n_soc; D.soc_off = ctx->soc_off; D.soc_dim = ctx->soc_dim; D.soc_rot = ctx->soc_rot;
     D.soc_lam = ctx->soc_lam; D.soc_w = ctx->soc_w; D.soc_wp = ctx->soc_wp; D.exp_lg = ctx->exp_lg;
     D.exp_row0 = ctx->exp_row0; D.n_exp = ctx->n_exp; D.exp_L = ctx->exp_L;
+    D.exp_kind = std::find(exp_k.begin(), exp_k.end(), (unsigned char)1) != exp_k.end() ? d_exp_kind : nullptr;
     D.nb_scal = nb_scal; D.nb_soc = nb_soc; D.nb_exp = nb_exp; D.exp_pb = exp_pb; D.nb_primal = ctx->g_vec_n;
     D.n_tiles = ctx->opt.batch_blocks == 0 ? n_tiles : 0;
     D.nb_tiles = ctx->opt.batch_blocks == 0 ? nb_tiles : 0;
@@ -1396,8 +1403,8 @@ pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, con
     for (int64_t k = 0; k < n_cones; ++k) {
         const int t = cones[k].type;
         const long long d = cones[k].dim;
-        if (t < PDCS_CONE_ZERO || t > PDCS_CONE_EXP) return bad("unknown cone type");
-        if (d < 1 || (t == PDCS_CONE_EXP && d != 3) || (t == PDCS_CONE_RSOC && d < 2))
+        if (t < PDCS_CONE_ZERO || t > PDCS_CONE_EXP_DUAL) return bad("unknown cone type");
+        if (d < 1 || ((t == PDCS_CONE_EXP || t == PDCS_CONE_EXP_DUAL) && d != 3) || (t == PDCS_CONE_RSOC && d < 2))
             return bad("bad cone dimension");
         tot += d;
     }

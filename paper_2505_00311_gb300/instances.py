@@ -22,7 +22,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-ZERO, NONNEG, SOC, RSOC, EXP = 0, 1, 2, 3, 4
+ZERO, NONNEG, SOC, RSOC, EXP, EXP_DUAL = 0, 1, 2, 3, 4, 5
 
 
 def _unique_cols(rng, row_ptr, n):
@@ -131,6 +131,8 @@ def _finish(rng, m, n, row_ptr, cols, vals, cone_types, cone_dims, name, lb=None
             s[o:o + d], y[o:o + d] = ss, yy
         elif t == EXP:
             s[o:o + 3], y[o:o + 3] = _exp_pair(rng)
+        elif t == EXP_DUAL:  # the block is K_exp^*: the pair with the roles of the cones swapped
+            y[o:o + 3], s[o:o + 3] = _exp_pair(rng)
         else:
             raise ValueError("unsupported cone in the known-optimum construction")
         o += d
@@ -213,6 +215,25 @@ def scaled_mixed_cone(seed: int = 1, scale: float = 0.01):
     return mixed_cone(seed=seed, n=n, m=m, nnz=int(10_000_000 * scale),
                       n_nonneg=int(200_000 * scale), soc_rows=int(200_000 * scale),
                       n_exp=int(20_000 * scale), scalar_chunk=max(1, int(1000 * scale)))
+
+
+def dual_exp_program(seed: int = 3, n: int = 800, row_nnz: int = 10):
+    """Random sparse program with exponential-cone blocks and dual-exponential-cone blocks
+    (rows constrained to K_exp^*, the dual-cone row blocks of the problem of Sec. 2) beside
+    zero, nonnegative and SOC rows: 100 zero, 200 nonneg, 20 SOC(5), 30 EXP, 70 EXP_DUAL
+    (m = 700), 10 uniform columns per row, N(0,1) values, known optimum (an EXP_DUAL block
+    takes the exp pair with s* in K_exp^* and y* in K_exp)."""
+    rng = np.random.default_rng(seed)
+    types = [ZERO, NONNEG] + [SOC] * 20 + [EXP] * 30 + [EXP_DUAL] * 70
+    dims = [100, 200] + [5] * 20 + [3] * 30 + [3] * 70
+    order = rng.permutation(len(types) - 2) + 2  # interleave the cone blocks after the scalar rows
+    types = types[:2] + [types[k] for k in order]
+    dims = dims[:2] + [dims[k] for k in order]
+    m = int(sum(dims))
+    row_ptr = np.arange(m + 1, dtype=np.int64) * row_nnz
+    cols = _unique_cols(rng, row_ptr, n)
+    vals = rng.standard_normal(int(row_ptr[-1]))
+    return _finish(rng, m, n, row_ptr, cols, vals, types, dims, "dual_exp_program")
 
 
 def edge_cases(seed: int = 5, m: int = 40, n: int = 30):

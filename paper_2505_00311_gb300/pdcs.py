@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpdcs.so")
 
-CONE_ZERO, CONE_NONNEG, CONE_SOC, CONE_RSOC, CONE_EXP = 0, 1, 2, 3, 4
+CONE_ZERO, CONE_NONNEG, CONE_SOC, CONE_RSOC, CONE_EXP, CONE_EXP_DUAL = 0, 1, 2, 3, 4, 5
 SPMV_AUTO, SPMV_BINNED, SPMV_SLICED = 0, 1, 2
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_DEVICE_TIMEOUT, MAX_ITER, TIME_LIMIT = 0, 1, 2, 3, 4, 5, 10, 11
 RESCALE_NONE, RESCALE_COORD, RESCALE_BLOCK = 0, 1, 2
@@ -373,7 +373,7 @@ class Solver:
     def __init__(self, prob, stream=None, **options):
         self.m, self.n = int(prob["m"]), int(prob["n"])
         kinds = np.asarray(prob["cone_types"])
-        self.n_soc, self.n_exp = int(np.sum((kinds == CONE_SOC) | (kinds == CONE_RSOC))), int(np.sum(kinds == CONE_EXP))
+        self.n_soc, self.n_exp = int(np.sum((kinds == CONE_SOC) | (kinds == CONE_RSOC))), int(np.sum((kinds == CONE_EXP) | (kinds == CONE_EXP_DUAL)))
         mlp = options.pop("exp_mlp", None)
         self.options = pdcs_default_options(**options)
         if mlp is not None:  # weights of the learned exp starting point, copied by pdcs_create

@@ -8,7 +8,7 @@ def role_masks(prob):
     m = int(prob["m"])
     kinds = np.repeat(np.asarray(prob["cone_types"]), np.asarray(prob["cone_dims"]))
     assert kinds.size == m
-    return {"scalar": kinds <= 1, "soc": (kinds == 2) | (kinds == 3), "exp": kinds == 4}
+    return {"scalar": kinds <= 1, "soc": (kinds == 2) | (kinds == 3), "exp": kinds >= 4}
 
 
 def _rel(a, b, mask=None):

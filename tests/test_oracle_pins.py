@@ -728,3 +728,56 @@ def test_ruiz_equilibrates():
     s0 = oracle.Solver(p, rescale=oracle.RESCALE_NONE)
     dr0, dc0 = s0.scaling()
     assert np.all(dr0 == 1) and np.all(dc0 == 1)
+
+
+def test_dual_exp_block_projections_satisfy_moreau():
+    """EXP_DUAL blocks (rows in K_exp^*): the oracle's projection p of v onto D K_exp^* and the
+    rest v - p satisfy the Moreau decomposition (Lemma moreau_decomp) for the pair
+    (D K_exp^*, its polar -D^{-1} K_exp): D^{-1} p in K_exp^*, -D (v - p) in K_exp, <p, v - p> = 0;
+    the dual-side projection is the plain exp projection onto D^{-1} K_exp."""
+    rng = np.random.default_rng(41)
+    n = 3000
+    v = rng.standard_normal(3 * n) * np.exp(rng.normal(0, 1.0, 3 * n))
+    d = np.exp(rng.normal(0, 0.7, 3 * n))
+    types, dims = np.full(n, oracle.EXP_DUAL), np.full(n, 3)
+    p = oracle.proj_cones(v, types, dims, d, dual=False)
+    for k in range(n):
+        b = slice(3 * k, 3 * k + 3)
+        vv, pp, dd = v[b], p[b], d[b]
+        q = vv - pp
+        sc = np.linalg.norm(vv)
+        assert abs(pp @ q) <= 1e-12 * sc * sc
+        # memberships to rounding: the scaled coordinates carry |v| eps / min(d) or |v| eps max(d)
+        tp, tq = 1e-11 * sc / dd.min(), 1e-11 * sc * dd.max()
+        r, s_, t = pp / dd  # in K_exp^*: r < 0, -r e^(s/r) <= e t, or r = 0, s, t >= 0
+        if r < 0:  # -r e^(s/r) <= e t, directly or in logs (first-order effect of perturbations tp)
+            slack = tp * (1.0 / abs(r) + abs(s_) / r ** 2) + (tp / t if t > 0 else np.inf)
+            direct = r < 0 and s_ / r < 700 and -r * np.exp(s_ / r) <= np.e * t + tp
+            logs = r < 0 and t > 0 and np.log(-r) + s_ / r <= 1.0 + np.log(t) + slack + 1e-12
+            assert direct or logs or (abs(r) <= tp and s_ >= -tp and t >= -tp), (k, r, s_, t)
+        else:  # the face r = 0: s, t >= 0
+            assert r <= tp and s_ >= -tp and t >= -tp
+        r, s_, t = -dd * q  # in K_exp: s > 0, s e^(r/s) <= t, or (r <= 0, s = 0, t >= 0)
+        if s_ > 0 and r / s_ < 700 and s_ * np.exp(r / s_) <= t * (1 + 1e-10) + tq:
+            pass  # s e^(r/s) <= t
+        elif s_ > 0 and t > 0 and np.log(s_) + r / s_ <= np.log(t) + tq * (1 / s_ + abs(r) / s_ ** 2 + 1 / t) + 1e-12:
+            pass  # the same compared in logs, with the first-order effect of perturbations of size tq
+        else:
+            assert r <= tq and abs(s_) <= tq and t >= -tq, (k, r, s_, t)
+    pd = oracle.proj_cones(v, types, dims, d, dual=True)
+    pe = oracle.proj_cones(v, np.full(n, oracle.EXP), dims, 1.0 / d, dual=False)
+    np.testing.assert_array_equal(pd, pe)
+
+
+def test_known_optimum_with_dual_exp_blocks():
+    """The known optimum of the program with EXP and EXP_DUAL blocks is a KKT point, and the
+    oracle's solve reaches its optimal value."""
+    q = I.dual_exp_program(3)
+    k = oracle.kkt(q, q["x_star"], q["y_star"])
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) < 1e-13
+    s = oracle.Solver(q)
+    assert s.run(400_000, 1e-6) == oracle.CONVERGED
+    x, y = s.solution()
+    kk = oracle.kkt(q, x, y)
+    assert max(kk["err_p"], kk["err_d"], kk["err_gap"]) <= 1e-6
+    assert kk["pobj"] == pytest.approx(q["obj_star"], rel=1e-5, abs=1e-5)
