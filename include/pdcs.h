@@ -3,8 +3,8 @@
  *
  * Solves   min c'x   s.t.   K x - h in C,   l <= x <= u
  * (the conic program of Sec. 2, eq. prob_cp, with no primal cone block), where
- * C is a product of zero, nonnegative, second-order, rotated second-order and
- * exponential cones listed in row order (eq. multi_cone_proj).  The dual is
+ * C is a product of zero, nonnegative, second-order, rotated second-order,
+ * exponential and dual exponential cones listed in row order (eq. multi_cone_proj).  The dual is
  * eq. dual_conic: y in C*, lambda = c - K'y in Lambda (eq. defn_Lambda1).
  * The method is PDCS, Algorithm 1 of the paper: adaptive-step PDHG (eq. PDHG)
  * on the diagonally rescaled program, reflected Halpern iteration, the
