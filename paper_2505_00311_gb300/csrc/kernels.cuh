@@ -669,27 +669,38 @@ __device__ __forceinline__ void dual_soc_large(const Dev<double>& D, const DualC
 //   K_exp  : D K_exp directly, D^{-1} K_exp^* by the Remark (v + Proj_{D K_exp}(-v));
 //   K_exp^*: D K_exp^* = (D^{-1})^{-1} K_exp^* by the Remark with the inverse scales, and
 //            (D K_exp^*)^* = D^{-1} K_exp directly with the inverse scales.
-__device__ __forceinline__ void exp_block_project(bool kdual, bool dual_side, double r, double s, double t,
-                                                  double d0, double d1, double d2, const double* lg, double* out,
-                                                  float* cache, const float* mlp) {
-    if (!kdual) {
-        if (dual_side) exp_dual_project_fast(r, s, t, d0, d1, d2, lg, out, cache, mlp);
-        else exp_project_fast(r, s, t, d0, d1, d2, lg, out, cache, mlp);
-        return;
-    }
+// (the K_exp^* blocks in a call of their own, so that the K_exp path compiles as before)
+static __device__ __noinline__ void exp_block_project_inv(bool dual_side, double r, double s, double t, double d0,
+                                                          double d1, double d2, const double* lg, double* out,
+                                                          float* cache, const float* mlp) {
     const double li[3] = {-lg[0], -lg[1], -lg[2]};
     if (dual_side) exp_project_fast(r, s, t, 1.0 / d0, 1.0 / d1, 1.0 / d2, li, out, cache, mlp);
     else exp_dual_project_fast(r, s, t, 1.0 / d0, 1.0 / d1, 1.0 / d2, li, out, cache, mlp);
 }
+__device__ __forceinline__ void exp_block_project(bool kdual, bool dual_side, double r, double s, double t,
+                                                  double d0, double d1, double d2, const double* lg, double* out,
+                                                  float* cache, const float* mlp) {
+    if (kdual) {
+        exp_block_project_inv(dual_side, r, s, t, d0, d1, d2, lg, out, cache, mlp);
+        return;
+    }
+    if (dual_side) exp_dual_project_fast(r, s, t, d0, d1, d2, lg, out, cache, mlp);
+    else exp_project_fast(r, s, t, d0, d1, d2, lg, out, cache, mlp);
+}
+static __device__ __noinline__ void exp_block_project_inv_f32(float r, float s, float t, float d0, float d1, float d2,
+                                                              const float* lg, float* out, float* cache,
+                                                              const float* mlp) {
+    const float li[3] = {-lg[0], -lg[1], -lg[2]};
+    exp_project_f32(r, s, t, 1.0f / d0, 1.0f / d1, 1.0f / d2, li, out, cache, mlp);
+}
 __device__ __forceinline__ void exp_block_project_f32(bool kdual, float r, float s, float t, float d0, float d1,
                                                       float d2, const float* lg, float* out, float* cache,
                                                       const float* mlp) {  // dual side
-    if (!kdual) {
-        exp_dual_project_f32(r, s, t, d0, d1, d2, lg, out, cache, mlp);
+    if (kdual) {
+        exp_block_project_inv_f32(r, s, t, d0, d1, d2, lg, out, cache, mlp);
         return;
     }
-    const float li[3] = {-lg[0], -lg[1], -lg[2]};
-    exp_project_f32(r, s, t, 1.0f / d0, 1.0f / d1, 1.0f / d2, li, out, cache, mlp);
+    exp_dual_project_f32(r, s, t, d0, d1, d2, lg, out, cache, mlp);
 }
 template <typename T>
 __device__ __forceinline__ bool exp_kind_dual(const Dev<T>& D, int e) {
