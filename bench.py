@@ -544,7 +544,7 @@ def main():
         held = list(range(1000, 1024))
         arms = {}
         for arm in ("cold", "warm_fp32", "warm_bf16"):
-            secs, evals, conv = 0.0, 0, 0
+            w_secs, w_evals, w_conv = 0.0, 0, 0
             for sd in held:
                 q = I.portfolio_socp(fam, I.portfolio_mu(fam, sd))
                 sv = P.Solver(q, stream=stream.cuda_stream)
@@ -557,11 +557,11 @@ def main():
                     sv.warm_start(None, pr[1:].astype(np.float64), float(np.exp(pr[0])))
                 st1, inf1 = sv.solve(1e-6, 200_000)
                 torch.cuda.synchronize()
-                secs += time.perf_counter() - t0
-                evals += inf1["attempts"]
-                conv += st1 == P.OK
+                w_secs += time.perf_counter() - t0
+                w_evals += inf1["attempts"]
+                w_conv += st1 == P.OK
                 sv.close()
-            arms[arm] = {"seconds": secs, "evaluations": evals, "converged": conv}
+            arms[arm] = {"seconds": w_secs, "evaluations": w_evals, "converged": w_conv}
         warm = {"workload": "portfolio SOCP family, 400 assets, 10 factors (budget, box, ||F'x|| <= gamma), "
                             "24 held-out instances to 1e-6 one at a time; network 17-256-256-23 trained on 160 "
                             "batched solves", "training_solves_seconds": t_data, "training_seconds": t_train,
