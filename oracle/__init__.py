@@ -50,7 +50,8 @@ def build(force: bool = False) -> str:
 class _Options(ctypes.Structure):
     _fields_ = [("rescale", ctypes.c_int), ("ruiz_iters", ctypes.c_int), ("pock_chambolle", ctypes.c_int),
                 ("step_mode", ctypes.c_int), ("check_period", ctypes.c_int), ("beta", ctypes.c_double),
-                ("power_iters", ctypes.c_int)]
+                ("power_iters", ctypes.c_int), ("pc_types", ctypes.POINTER(ctypes.c_int32)),
+                ("pc_dims", ctypes.POINTER(ctypes.c_int64)), ("n_pc", ctypes.c_int64), ("pc_start", ctypes.c_int64)]
 
 
 class _Kkt(ctypes.Structure):
@@ -78,6 +79,10 @@ def lib():
             L.orc_kkt_eval.argtypes = [ctypes.c_int64, ctypes.c_int64, _i64p, _i32p, _dp, _dp, _dp, _dp, _dp,
                                        _i32p, _i64p, ctypes.c_int64, _dp, _dp, ctypes.POINTER(_Kkt)]
             L.orc_kkt_eval.restype = ctypes.c_int
+            L.orc_kkt_eval_pc.argtypes = [ctypes.c_int64, ctypes.c_int64, _i64p, _i32p, _dp, _dp, _dp, _dp, _dp,
+                                          _i32p, _i64p, ctypes.c_int64, _i32p, _i64p, ctypes.c_int64,
+                                          ctypes.c_int64, _dp, _dp, ctypes.POINTER(_Kkt)]
+            L.orc_kkt_eval_pc.restype = ctypes.c_int
             L.orc_create.argtypes = [ctypes.c_int64, ctypes.c_int64, _i64p, _i32p, _dp, _dp, _dp, _dp, _dp,
                                      _i32p, _i64p, ctypes.c_int64, ctypes.POINTER(_Options)]
             L.orc_create.restype = ctypes.c_void_p
@@ -171,15 +176,25 @@ def _problem_arrays(prob):
     return rp, ci, val, c, h, lb, ub, types, dims
 
 
+def _pc_arrays(prob):
+    """Primal cone blocks of a problem dict (keys pcone_types, pcone_dims, pcone_start; absent:
+    none): types (int32), sizes (int64), first variable."""
+    t = np.ascontiguousarray(prob.get("pcone_types", []), dtype=np.int32)
+    d = np.ascontiguousarray(prob.get("pcone_dims", []), dtype=np.int64)
+    return t, d, int(prob.get("pcone_start", 0))
+
+
 def kkt(prob, x, y):
     """Relative KKT errors (eq. PDCS_terminate_tolerance) of (x, y) for the original program."""
     rp, ci, val, c, h, lb, ub, types, dims = _problem_arrays(prob)
+    pt, pd, ps = _pc_arrays(prob)
     x = _f64(x)
     y = _f64(y)
     out = _Kkt()
-    rc = lib().orc_kkt_eval(prob["m"], prob["n"], _ptr(rp, _i64p), _ptr(ci, _i32p), _ptr(val), _ptr(c), _ptr(h),
-                            _ptr(lb), _ptr(ub), _ptr(types, _i32p), _ptr(dims, _i64p), types.size,
-                            _ptr(x), _ptr(y), ctypes.byref(out))
+    rc = lib().orc_kkt_eval_pc(prob["m"], prob["n"], _ptr(rp, _i64p), _ptr(ci, _i32p), _ptr(val), _ptr(c),
+                               _ptr(h), _ptr(lb), _ptr(ub), _ptr(types, _i32p), _ptr(dims, _i64p), types.size,
+                               _ptr(pt if pt.size else None, _i32p), _ptr(pd if pd.size else None, _i64p),
+                               pt.size, ps, _ptr(x), _ptr(y), ctypes.byref(out))
     if rc != 0:
         raise ValueError("invalid problem")
     return {"err_p": out.err_p, "err_d": out.err_d, "err_gap": out.err_gap, "pobj": out.pobj, "dobj": out.dobj}
@@ -201,6 +216,12 @@ class Solver:
         rp, ci, val, c, h, lb, ub, types, dims = self._arrs
         self.m, self.n = int(prob["m"]), int(prob["n"])
         self._opt = default_options(**opts)
+        self._pc = _pc_arrays(prob)
+        if self._pc[0].size:
+            self._opt.pc_types = self._pc[0].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            self._opt.pc_dims = self._pc[1].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+            self._opt.n_pc = self._pc[0].size
+            self._opt.pc_start = self._pc[2]
         self._h = lib().orc_create(self.m, self.n, _ptr(rp, _i64p), _ptr(ci, _i32p), _ptr(val), _ptr(c), _ptr(h),
                                    _ptr(lb), _ptr(ub), _ptr(types, _i32p), _ptr(dims, _i64p), types.size,
                                    ctypes.byref(self._opt))

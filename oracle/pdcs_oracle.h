@@ -14,6 +14,10 @@
  * C a product of zero, nonnegative, second-order, rotated second-order and
  * exponential cones in row order.  Dual (eq. dual_conic): y in C*,
  * lambda = c - K'y in Lambda (eq. defn_Lambda1).
+ * Optionally (orc_options.n_pc > 0) a contiguous range of variables forms
+ * primal cone blocks x2 in K_p (eq. prob_cp with n2 > 0), K_p a product of
+ * second-order and rotated second-order cones; their reduced costs then lie
+ * in K_p* instead of Lambda.
  */
 #ifndef PDCS_ORACLE_H
 #define PDCS_ORACLE_H
@@ -36,6 +40,13 @@ typedef struct {
     int check_period;   /* restart / termination check every this many PDHG evaluations */
     double beta;        /* reflection parameter of the reflected Halpern step */
     int power_iters;    /* power iterations for ||K~||_2 (constant / plain step modes) */
+    /* primal cone blocks: variables pc_start, pc_start + 1, ... grouped in order into n_pc
+     * cones of types pc_types (ORC_SOC or ORC_RSOC) and sizes pc_dims; their bounds must be
+     * (-inf, +inf).  The arrays are copied at create.  n_pc = 0: none. */
+    const int32_t* pc_types;
+    const int64_t* pc_dims;
+    int64_t n_pc;
+    int64_t pc_start;
 } orc_options;
 
 typedef struct {
@@ -65,6 +76,13 @@ int orc_kkt_eval(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* co
                  const double* c, const double* h, const double* lb, const double* ub,
                  const int32_t* types, const int64_t* dims, int64_t n_cones,
                  const double* x, const double* y, orc_kkt* out);
+
+/* The same with primal cone blocks (see orc_options; n_pc = 0: none). */
+int orc_kkt_eval_pc(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                    const double* c, const double* h, const double* lb, const double* ub,
+                    const int32_t* types, const int64_t* dims, int64_t n_cones,
+                    const int32_t* pc_types, const int64_t* pc_dims, int64_t n_pc, int64_t pc_start,
+                    const double* x, const double* y, orc_kkt* out);
 
 /* ---- solver ------------------------------------------------------------- */
 /* Copies every input.  lb / ub may be NULL (then l = 0, u = +inf).  Returns NULL on invalid input. */

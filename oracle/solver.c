@@ -63,6 +63,11 @@ struct orc_solver {
     double phi0, phi_prev, comp0[3];
     int status, started;
     double last_err[3];
+    /* primal cone blocks x2 in K_p: types, sizes, first variable of each, a vector of ones */
+    int64_t n_pc, pc_lo, pc_hi; /* the blocks cover variables [pc_lo, pc_hi) */
+    int32_t* pct;
+    int64_t *pcd, *pco;
+    double* ones_n;
 };
 
 void orc_default_options(orc_options* o) {
@@ -73,7 +78,27 @@ void orc_default_options(orc_options* o) {
     o->check_period = 64;
     o->beta = 1.0;
     o->power_iters = 50;
+    o->pc_types = NULL;
+    o->pc_dims = NULL;
+    o->n_pc = 0;
+    o->pc_start = 0;
 }
+
+/* Projection of the variables of the primal cone blocks onto K_p (dual == 0) or K_p^*
+ * (dual == 1; the SOC and the rotated SOC are self-dual, so both are the same set).  Their
+ * column scales are tied within each block, so Dc^{-1} K_p = K_p and D = I takes the
+ * textbook projection.  Entries outside the blocks are left as they are. */
+static void proj_pc(const struct orc_solver* S, const double* v, double* out) {
+    for (int64_t k = 0; k < S->n_pc; ++k) {
+        int64_t o = S->pco[k], d = S->pcd[k];
+        if (S->pct[k] == ORC_SOC)
+            orc_proj_soc(v[o], v + o + 1, S->ones_n, d - 1, out + o, out + o + 1);
+        else
+            orc_proj_rsoc(v + o, S->ones_n, d, out + o);
+    }
+}
+
+static int in_pc(const struct orc_solver* S, int64_t j) { return j >= S->pc_lo && j < S->pc_hi; }
 
 /* ---- small helpers ---------------------------------------------------- */
 static double* dalloc(int64_t k) { return (double*)calloc((size_t)(k > 0 ? k : 1), sizeof(double)); }
@@ -157,16 +182,30 @@ static void eval_pair(const orc_solver* S, const double* xt, const double* yt, c
         pmax = fmax(pmax, fabs(p[i]));
     }
 
-    /* dual: lambda = c - K'y; scaled lambda~ = dc * lambda */
+    /* dual: lambda = c - K'y; scaled lambda~ = dc * lambda.  Box variables: mu = Proj_Lambda;
+     * primal cone blocks: mu = Proj_{K_p^*}(lambda) per block, and no bound term (the infimum
+     * of mu'x over x in K_p is 0 for mu in K_p^*). */
+    double* lam_s = dalloc(n);
+    double* mu_s = dalloc(n);
+    double* lam_u = dalloc(n);
+    double* mu_u = dalloc(n);
+    for (int64_t j = 0; j < n; ++j) {
+        lam_s[j] = S->cs[j] - KTy[j];
+        lam_u[j] = lam_s[j] / S->dc[j];
+        mu_s[j] = proj_lambda(lam_s[j], S->ls[j], S->us[j]);
+        mu_u[j] = proj_lambda(lam_u[j], S->l0[j], S->u0[j]);
+    }
+    proj_pc(S, lam_s, mu_s);
+    proj_pc(S, lam_u, mu_u);
     double dmax = 0.0, cmax = 0.0, ktymax = 0.0;
     acc_t rd2a = {0.0, 0.0}, bterma = {0.0, 0.0}, pobja = {0.0, 0.0};
     for (int64_t j = 0; j < n; ++j) {
-        double lam = S->cs[j] - KTy[j];
-        double mu = proj_lambda(lam, S->ls[j], S->us[j]);
+        double lam = lam_s[j];
+        double mu = mu_s[j];
         acc_add(&rd2a, (lam - mu) * (lam - mu));
-        acc_add(&bterma, bound_term(S->ls[j], S->us[j], mu));
-        double lamu = lam / S->dc[j];
-        double muu = proj_lambda(lamu, S->l0[j], S->u0[j]);
+        if (!in_pc(S, j)) acc_add(&bterma, bound_term(S->ls[j], S->us[j], mu));
+        double lamu = lam_u[j];
+        double muu = mu_u[j];
         dmax = fmax(dmax, fabs(lamu - muu));
         cmax = fmax(cmax, fabs(S->c0[j]));
         ktymax = fmax(ktymax, fabs(KTy[j] / S->dc[j]));
@@ -184,6 +223,7 @@ static void eval_pair(const orc_solver* S, const double* xt, const double* yt, c
     r->err_d = dmax / (1.0 + fmax(cmax, ktymax));
     r->err_gap = gap / (1.0 + fmax(fabs(pobj), fabs(dobj)));
     free(Kx); free(KTy); free(v); free(p); free(ones);
+    free(lam_s); free(mu_s); free(lam_u); free(mu_u);
 }
 
 static double phi_of(const double comp[3], double omega) {
@@ -193,6 +233,7 @@ static double phi_of(const double comp[3], double omega) {
 /* ---- projections onto X = [l~, u~] and Y = Dr^{-1} C^* ------------------ */
 static void proj_X(const orc_solver* S, const double* x, double* out) {
     for (int64_t j = 0; j < S->n; ++j) out[j] = fmin(fmax(x[j], S->ls[j]), S->us[j]);
+    proj_pc(S, x, out);
 }
 static void proj_Y(const orc_solver* S, const double* y, double* out) {
     orc_proj_cones(y, S->dr, S->m, S->types, S->dims, S->n_cones, 1, out);
@@ -243,6 +284,11 @@ static void rescale(orc_solver* S, const double* val0) {
                 else { rn[i] = fmax(rn[i], a); cn[j] = fmax(cn[j], a); }
             }
         tie_rows(S, rn, 1);
+        for (int64_t k = 0; k < S->n_pc; ++k) { /* one factor per primal cone block */
+            double mx = 0.0;
+            for (int64_t j = S->pco[k]; j < S->pco[k] + S->pcd[k]; ++j) mx = fmax(mx, cn[j]);
+            for (int64_t j = S->pco[k]; j < S->pco[k] + S->pcd[k]; ++j) cn[j] = mx;
+        }
         for (int64_t i = 0; i < m; ++i) if (rn[i] > 0.0) S->dr[i] = S->dr[i] / sqrt(rn[i]);
         for (int64_t j = 0; j < n; ++j) if (cn[j] > 0.0) S->dc[j] = S->dc[j] / sqrt(cn[j]);
         apply_scale_values(S, val0);
@@ -309,6 +355,19 @@ orc_solver* orc_create(int64_t m, int64_t n, const int64_t* row_ptr, const int32
     }
     if (tot != m) return NULL;
     if (lb && ub) for (int64_t j = 0; j < n; ++j) if (lb[j] > ub[j]) return NULL;
+    int64_t npc = opt ? opt->n_pc : 0, pcs = opt ? opt->pc_start : 0, pctot = 0;
+    if (npc < 0) return NULL;
+    if (npc > 0) {
+        if (!opt->pc_types || !opt->pc_dims || pcs < 0) return NULL;
+        for (int64_t k = 0; k < npc; ++k) {
+            if (opt->pc_types[k] != ORC_SOC && opt->pc_types[k] != ORC_RSOC) return NULL;
+            if (opt->pc_dims[k] < (opt->pc_types[k] == ORC_RSOC ? 2 : 1)) return NULL;
+            pctot += opt->pc_dims[k];
+        }
+        if (pcs + pctot > n) return NULL;
+        for (int64_t j = pcs; j < pcs + pctot; ++j) /* cone variables carry no bounds */
+            if (!lb || !ub || lb[j] != -INFINITY || ub[j] != INFINITY) return NULL;
+    }
 
     orc_solver* S = (orc_solver*)calloc(1, sizeof(orc_solver));
     S->m = m; S->n = n; S->nnz = nnz; S->n_cones = n_cones;
@@ -342,6 +401,24 @@ orc_solver* orc_create(int64_t m, int64_t n, const int64_t* row_ptr, const int32
     }
     S->dr = dalloc(m);
     S->dc = dalloc(n);
+    S->opt.pc_types = NULL; /* the caller's arrays are copied, not kept */
+    S->opt.pc_dims = NULL;
+    S->n_pc = npc;
+    S->pc_lo = pcs;
+    S->pc_hi = pcs + pctot;
+    S->pct = (int32_t*)malloc(sizeof(int32_t) * (size_t)(npc > 0 ? npc : 1));
+    S->pcd = (int64_t*)malloc(sizeof(int64_t) * (size_t)(npc > 0 ? npc : 1));
+    S->pco = (int64_t*)malloc(sizeof(int64_t) * (size_t)(npc > 0 ? npc : 1));
+    int64_t maxd = 1;
+    for (int64_t k = 0, o2 = pcs; k < npc; ++k) {
+        S->pct[k] = opt->pc_types[k];
+        S->pcd[k] = opt->pc_dims[k];
+        S->pco[k] = o2;
+        o2 += opt->pc_dims[k];
+        if (opt->pc_dims[k] > maxd) maxd = opt->pc_dims[k];
+    }
+    S->ones_n = dalloc(maxd);
+    for (int64_t i = 0; i < maxd; ++i) S->ones_n[i] = 1.0;
 
     build_transpose(S);
     rescale(S, val);
@@ -382,7 +459,7 @@ void orc_destroy(orc_solver* S) {
     void* ps[] = {S->rp, S->rpT, S->ci, S->ciT, S->val, S->valT, S->c0, S->h0, S->l0, S->u0,
                   S->cs, S->hs, S->ls, S->us, S->types, S->dims, S->offs, S->dr, S->dc,
                   S->x, S->y, S->xh, S->yh, S->x0, S->y0, S->xsum, S->ysum, S->solx, S->soly,
-                  S->tm, S->tn, S->tm2, S->tn2, S->tm3, S->tn3};
+                  S->tm, S->tn, S->tm2, S->tn2, S->tm3, S->tn3, S->pct, S->pcd, S->pco, S->ones_n};
     for (size_t i = 0; i < sizeof(ps) / sizeof(ps[0]); ++i) free(ps[i]);
     free(S);
 }
@@ -499,6 +576,7 @@ static void attempt(orc_solver* S) {
         double g = S->cs[j] - KTy[j];
         S->xh[j] = fmin(fmax(S->x[j] - tau * g, S->ls[j]), S->us[j]);
     }
+    proj_pc(S, S->xh, S->xh); /* x2 blocks: Proj_{K_p} of the same gradient step */
     /* yhat = Proj_Y(y + sigma (h - K(2 xhat - x))) */
     for (int64_t j = 0; j < n; ++j) dxv[j] = 2.0 * S->xh[j] - S->x[j];
     spmv(m, S->rp, S->ci, S->val, dxv, Kv);
@@ -654,9 +732,22 @@ int orc_kkt_eval(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* co
                  const double* c, const double* h, const double* lb, const double* ub,
                  const int32_t* types, const int64_t* dims, int64_t n_cones,
                  const double* x, const double* y, orc_kkt* out) {
+    return orc_kkt_eval_pc(m, n, row_ptr, col, val, c, h, lb, ub, types, dims, n_cones, NULL, NULL, 0, 0,
+                           x, y, out);
+}
+
+int orc_kkt_eval_pc(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                    const double* c, const double* h, const double* lb, const double* ub,
+                    const int32_t* types, const int64_t* dims, int64_t n_cones,
+                    const int32_t* pc_types, const int64_t* pc_dims, int64_t n_pc, int64_t pc_start,
+                    const double* x, const double* y, orc_kkt* out) {
     orc_options o;
     orc_default_options(&o);
     o.rescale = ORC_RESCALE_NONE;
+    o.pc_types = pc_types;
+    o.pc_dims = pc_dims;
+    o.n_pc = n_pc;
+    o.pc_start = pc_start;
     orc_solver* S = orc_create(m, n, row_ptr, col, val, c, h, lb, ub, types, dims, n_cones, &o);
     if (!S) return 1;
     cand_eval ev;

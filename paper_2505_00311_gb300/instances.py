@@ -236,6 +236,52 @@ def dual_exp_program(seed: int = 3, n: int = 800, row_nnz: int = 10):
     return _finish(rng, m, n, row_ptr, cols, vals, types, dims, "dual_exp_program")
 
 
+def primal_cone_program(seed: int = 4, n_before: int = 300, pcone_dims=(5, 40, 2, 120, 9),
+                        pcone_types=None, n_after: int = 200, m: int = 400, row_nnz: int = 8):
+    """A program with primal cone blocks x2 in K_p (Sec. 2, eq. prob_cp with n2 > 0) and a known
+    optimum: variables [n_before box | the cone blocks | n_after box], the box variables in
+    [0, +inf), the cone variables free of bounds and grouped into SOC / RSOC blocks (types
+    alternate SOC, RSOC unless given); rows: a quarter zero, a quarter nonneg, the rest SOC
+    blocks of 10 rows; row_nnz N(0, 1) entries per row at uniform columns.  The optimal pair
+    follows the construction of the module docstring, with each cone block of x* and its reduced
+    cost lambda* drawn as a complementary (s*, y*) pair of that cone (K_p^* = K_p)."""
+    rng = np.random.default_rng(seed)
+    pcone_dims = [int(d) for d in pcone_dims]
+    if pcone_types is None:
+        pcone_types = [SOC if k % 2 == 0 else RSOC for k in range(len(pcone_dims))]
+    n_pc = sum(pcone_dims)
+    n = n_before + n_pc + n_after
+    row_ptr = np.arange(m + 1, dtype=np.int64) * row_nnz
+    cols = _unique_cols(rng, row_ptr, n)
+    vals = rng.standard_normal(m * row_nnz)
+    mz, mn = m // 4, m // 4
+    n_soc = (m - mz - mn) // 10
+    types = [ZERO, NONNEG] + [SOC] * n_soc
+    dims = [mz, mn + (m - mz - mn - 10 * n_soc)] + [10] * n_soc
+    lb = np.zeros(n)
+    ub = np.full(n, np.inf)
+    lb[n_before:n_before + n_pc] = -np.inf
+    p = _finish(rng, m, n, row_ptr, cols, vals, types, dims, "primal_cone_program", lb=lb, ub=ub)
+    x, lam = p["x_star"], p["lambda_star"]
+    o = n_before
+    for t, d in zip(pcone_types, pcone_dims):
+        xs, ls = (_soc_pair(rng, d) if d >= 2 else (np.array([rng.uniform(0.1, 1.0)]), np.zeros(1)))
+        if t == RSOC:
+            for v in (xs, ls):
+                a, b = v[0], v[1]
+                v[0], v[1] = (a + b) / np.sqrt(2.0), (a - b) / np.sqrt(2.0)
+        x[o:o + d], lam[o:o + d] = xs, ls
+        o += d
+    K = sp.csr_matrix((vals, cols, row_ptr), shape=(m, n))
+    p["c"] = K.T @ p["y_star"] + lam
+    p["h"] = K @ x - p["s_star"]
+    p["obj_star"] = float(p["c"] @ x)
+    p["pcone_types"] = np.asarray(pcone_types, dtype=np.int32)
+    p["pcone_dims"] = np.asarray(pcone_dims, dtype=np.int64)
+    p["pcone_start"] = n_before
+    return p
+
+
 def edge_cases(seed: int = 5, m: int = 40, n: int = 30):
     """Small program with every cone kind (zero, nonneg, RSOC, SOC, exp), empty rows,
     two empty columns, finite boxes, one-sided bounds and free variables; known optimum."""
@@ -359,6 +405,29 @@ def lasso_paper(seed: int = 0, m: int = 70_000, n: int = 700_000, density: float
             "cone_types": np.asarray([ZERO, SOC], dtype=np.int32),
             "cone_dims": np.asarray([1 + m, m + 2], dtype=np.int64),
             "lasso": {"A": A, "b": b, "lam": lam}}
+
+
+def lasso_paper_kp(seed: int = 0, m: int = 70_000, n: int = 700_000, density: float = 1e-4):
+    """The same Lasso as lasso_paper (App. B.2), in the form the appendix writes it: the cone
+    constraint on the variables themselves.  ((w + r)/sqrt2, (w - r)/sqrt2, y) in K_soc is
+    (w, r, y) in K_rsoc (2 w r >= ||y||^2), a primal cone block x2 in K_p of m + 2 variables at
+    the front; the rows are only the zero rows w = 1 and y - A x1 + A x2 = -b."""
+    q = lasso_paper(seed, m, n, density)
+    A, b = q["lasso"]["A"], q["lasso"]["b"]
+    m, n = A.shape
+    nv = 2 + m + 2 * n
+    top = sp.csr_matrix((np.ones(1), (np.zeros(1, np.int64), np.zeros(1, np.int64))), shape=(1, nv))
+    bot = sp.hstack([sp.csr_matrix((m, 2)), sp.identity(m, format="csr"), -A, A], format="csr")
+    K = sp.vstack([top, bot], format="csr")
+    K.sort_indices()
+    h = np.concatenate([[1.0], -b])
+    lb = q["lb"].copy()
+    lb[:2] = -np.inf
+    return {"name": "lasso_paper_kp", "m": 1 + m, "n": nv, "row_ptr": K.indptr.astype(np.int64),
+            "col": K.indices.astype(np.int32), "val": K.data, "c": q["c"], "h": h, "lb": lb, "ub": q["ub"],
+            "cone_types": np.asarray([ZERO], dtype=np.int32), "cone_dims": np.asarray([1 + m], dtype=np.int64),
+            "pcone_types": np.asarray([RSOC], dtype=np.int32), "pcone_dims": np.asarray([m + 2], dtype=np.int64),
+            "pcone_start": 0, "lasso": q["lasso"]}
 
 
 def fisher_market(seed: int = 0, buyers: int = 100_000, goods: int = 1000, density: float = 0.2):

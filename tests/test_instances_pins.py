@@ -105,3 +105,24 @@ def test_fisher_market_program_matches_slsqp_and_clears_the_budgets():
     assert s.run(2_000_000, 1e-9) == oracle.CONVERGED
     _, y = s.solution()
     assert abs(abs(float(y[:ng] @ bs)) - w.sum()) <= 1e-6 * w.sum()
+
+
+def test_paper_lasso_with_a_primal_cone_matches_coordinate_descent():
+    """The same Lasso with the cone on the variables (the appendix's own form: (w, r, y) in
+    K_rsoc as a primal cone block, only the zero rows left): the same optimum."""
+    sk = pytest.importorskip("sklearn.linear_model")
+    q = I.lasso_paper_kp(11, m=40, n=400, density=0.05)
+    A, b, lam = q["lasso"]["A"].toarray(), q["lasso"]["b"], q["lasso"]["lam"]
+    m, n = A.shape
+    assert q["m"] == m + 1 and q["pcone_dims"][0] == m + 2
+    fit = sk.Lasso(alpha=lam / (2 * m), fit_intercept=False, tol=1e-14, max_iter=1_000_000).fit(A, b)
+    w = fit.coef_
+    f_cd = float(np.sum((A @ w - b) ** 2) + lam * np.abs(w).sum())
+    s = oracle.Solver(q, beta=0.5)
+    assert s.run(2_000_000, 1e-9) == oracle.CONVERGED
+    x, y = s.solution()
+    k = oracle.kkt(q, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1e-9
+    assert abs(k["pobj"] - f_cd) <= 1e-6 * max(1.0, abs(f_cd)), (k["pobj"], f_cd)
+    i1 = 2 + m
+    np.testing.assert_allclose(x[i1:i1 + n] - x[i1 + n:i1 + 2 * n], w, atol=1e-4)

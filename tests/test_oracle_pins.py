@@ -781,3 +781,90 @@ def test_known_optimum_with_dual_exp_blocks():
     kk = oracle.kkt(q, x, y)
     assert max(kk["err_p"], kk["err_d"], kk["err_gap"]) <= 1e-6
     assert kk["pobj"] == pytest.approx(q["obj_star"], rel=1e-5, abs=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# primal cone blocks x2 in K_p (Sec. 2, eq. prob_cp with n2 > 0)
+# ---------------------------------------------------------------------------
+def test_primal_cone_known_optimum_has_zero_kkt_error():
+    """At the constructed optimum every residual vanishes; moving one cone block off its
+    complementary pair (or reading its reduced cost as a free variable's, which must be 0)
+    does not."""
+    p = I.primal_cone_program()
+    k = oracle.kkt(p, p["x_star"], p["y_star"])
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1e-14
+    assert k["pobj"] == pytest.approx(p["obj_star"], rel=1e-14)
+    o = p["pcone_start"]
+    d0 = int(p["pcone_dims"][0])
+    assert np.abs(p["lambda_star"][o:o + d0]).max() > 0.0 or np.abs(p["lambda_star"][o:]).max() > 0.0
+    q = dict(p)
+    q.pop("pcone_types"); q.pop("pcone_dims"); q.pop("pcone_start")  # cone variables as free ones
+    k2 = oracle.kkt(q, p["x_star"], p["y_star"])
+    assert k2["err_d"] > 1e-3
+    x = p["x_star"].copy()
+    x[o] -= 1.0  # first entry of the first SOC block: leaves the cone
+    assert oracle.kkt(p, x, p["y_star"])["err_gap"] > 1e-3
+
+
+def test_primal_cone_first_step_projects_onto_the_cone():
+    """One evaluation from zero without rescaling: x-hat = Proj_X(-tau c) with the cone blocks
+    projected by the textbook SOC / rotated SOC projection and the box entries clamped."""
+    p = I.primal_cone_program(seed=7, n_before=6, pcone_dims=(4, 5), n_after=3, m=16, row_nnz=4)
+    s = oracle.Solver(p, rescale=oracle.RESCALE_NONE)
+    sc0 = s.scalars()
+    s.run(1)
+    _, _, xh, _ = s.iterate()
+    tau = sc0["eta"] / sc0["omega"]
+    g = -tau * p["c"]
+    want = np.maximum(g, 0.0)
+    o = p["pcone_start"]
+    want[o:o + 4] = textbook_soc(g[o:o + 4])
+    r = g[o + 4:o + 9]
+    q = r.copy()
+    q[0], q[1] = (r[0] + r[1]) / np.sqrt(2.0), (r[0] - r[1]) / np.sqrt(2.0)
+    pq = textbook_soc(q)
+    want[o + 4:o + 9] = pq
+    want[o + 4], want[o + 5] = (pq[0] + pq[1]) / np.sqrt(2.0), (pq[0] - pq[1]) / np.sqrt(2.0)
+    np.testing.assert_allclose(xh, want, rtol=1e-13, atol=1e-15)
+
+
+def test_primal_cone_scales_are_tied_per_block():
+    p = I.primal_cone_program()
+    s = oracle.Solver(p)
+    _, dc = s.scaling()
+    o = p["pcone_start"]
+    for d in p["pcone_dims"]:
+        d = int(d)
+        assert np.all(dc[o:o + d] == dc[o])
+        o += d
+    assert np.unique(dc[:p["pcone_start"]]).size > 1  # box columns keep their own factors
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_primal_cone_solve_reaches_known_optimum(seed):
+    p = I.primal_cone_program(seed=seed)
+    s = oracle.Solver(p, beta=0.5)
+    assert s.run(100_000, 1e-6) == oracle.CONVERGED
+    x, y = s.solution()
+    k = oracle.kkt(p, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1e-6
+    assert k["pobj"] == pytest.approx(p["obj_star"], rel=1e-5)
+    o = p["pcone_start"]
+    for t, d in zip(p["pcone_types"], p["pcone_dims"]):  # the cone blocks are in their cones
+        v = x[o:o + int(d)]
+        if t == I.RSOC:
+            assert v[0] >= -1e-12 and v[1] >= -1e-12 and v[2:] @ v[2:] <= 2 * v[0] * v[1] + 1e-9
+        else:
+            assert np.linalg.norm(v[1:]) <= v[0] + 1e-9
+        o += int(d)
+
+
+def test_primal_cone_validation():
+    p = I.primal_cone_program(seed=7, n_before=6, pcone_dims=(4, 5), n_after=3, m=16, row_nnz=4)
+    bad = dict(p, lb=np.zeros(p["n"]))  # bounded cone variables
+    with pytest.raises(ValueError):
+        oracle.Solver(bad)
+    with pytest.raises(ValueError):
+        oracle.Solver(dict(p, pcone_types=np.array([I.SOC, I.EXP], np.int32)))
+    with pytest.raises(ValueError):
+        oracle.Solver(dict(p, pcone_start=p["n"] - 3))
