@@ -141,6 +141,20 @@ typedef struct {
                                mixed program (2,729 vs 2,960 evaluations/s): the slices hold the rows
                                sorted by length, so the epilogue's 13 accesses per variable scatter
                                (102.8 us for the fused product against 51.3 + 37.4 us) */
+    /* Primal cone blocks x2 in K_p (Sec. 2, eq. prob_cp with n2 > 0): variables
+     * primal_cone_start, primal_cone_start + 1, ... taken in order by n_primal_cones cones of
+     * the given types (PDCS_CONE_SOC with dim >= 1, PDCS_CONE_RSOC with dim >= 2) and sizes;
+     * their bounds must be lb = -inf, ub = +inf.  x-hat projects these blocks onto K_p, the
+     * checks project the candidates onto them and the reduced costs lambda = c - K'y of their
+     * variables onto K_p^* (both cones are self-dual), with no bound term in the dual
+     * objective.  The columns of a block share one scale factor (the largest of their norms in
+     * each rescaling pass), so D^{-1} K_p = K_p and the projection is the textbook one.  Host
+     * array, copied at create; NULL / 0 (default): none.  Single programs with FP64 iterates
+     * and separate primal updates only (PDCS_ERR_INVALID with precision FP32, batch_blocks > 0
+     * or fuse_primal). */
+    const pdcs_cone* primal_cones;
+    int64_t n_primal_cones;
+    int64_t primal_cone_start;
 } pdcs_options;
 
 typedef struct {

@@ -48,6 +48,11 @@ constexpr int kTeamMinDim = 4096;
 constexpr int kTeamMinRows = 512;
 constexpr int kTeamQ = 4;
 
+// Primal cone blocks (x2 in K_p): one block of pc_reduce / pc_apply per kPcChunk variables
+// of a cone.
+constexpr int kPcChunk = 1024;
+enum PcMode { kPcHat = 0, kPcCand = 1, kPcLam = 2 };  // sources of pc_reduce / pc_apply
+
 template <typename T>
 struct Dev {
     int m, n;
@@ -136,6 +141,19 @@ struct Dev {
     const float* exp_lg32;
     // learned starting point of the exp root search (kExpMlpParams floats), or null
     const float* exp_mlp;
+    // primal cone blocks x2 in K_p (FP64 single programs): variables [pc_lo, pc_lo + pc_len)
+    // in n_pc SOC / RSOC cones (first variable pc_off[k], size pc_dim[k], pc_rot[k] = 1 for
+    // RSOC), pc_nch chunks of kPcChunk for the largest; scratch per source q (x-hat, or the
+    // two candidates): pc_ss[(q n_pc + k) pc_nch + b] sums of squares, pc_t[q n_pc + k] first
+    // entries, pc_mu[q pc_len + j - pc_lo] the projected reduced costs; pc_slot0: first
+    // ||dx||^2 partial slot of pc_apply (n_pc pc_nch slots after primal_update's)
+    int n_pc, pc_lo, pc_len, pc_nch, pc_slot0;
+    const int* pc_off;
+    const int* pc_dim;
+    const unsigned char* pc_rot;
+    double* pc_ss;
+    double* pc_t;
+    double* pc_mu;
     // SpMV plans of K and K': bins and the row each binned row stands for
     SpmvBins binsK, binsKT;
     const int* listK;

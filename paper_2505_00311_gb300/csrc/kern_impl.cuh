@@ -41,6 +41,12 @@ constexpr int dual_soc_smem() {
         void* args[] = {(void*)&Dv, (void*)&md};                                                                   \
         return cudaLaunchCooperativeKernel((const void*)soc_team<T>, dim3(D.team_nb), dim3(kBlock), args, 0, s);   \
     }                                                                                                              \
+    void k_pc(const Dev<T>& D, int mode, int nq, cudaStream_t s) {                                                 \
+        if (D.n_pc <= 0) return;                                                                                   \
+        const dim3 g(D.n_pc, D.pc_nch, nq);                                                                        \
+        pc_reduce<T><<<g, kBlock, 0, s>>>(D, mode);                                                                \
+        pc_apply<T><<<g, kBlock, 0, s>>>(D, mode);                                                                 \
+    }                                                                                                              \
     int k_team_occupancy(const Dev<T>*) {                                                                          \
         int occ = 0;                                                                                               \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, soc_team<T>, kBlock, 0) == cudaSuccess ? occ : 0; \

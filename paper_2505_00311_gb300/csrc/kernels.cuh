@@ -426,7 +426,7 @@ __device__ __forceinline__ void primal_update_body(const Dev<T>& D, int qidx) {
         T xh = fmin(fmax(x - tau * (D.c[j] - kty), D.l[j]), D.u[j]);
         xhat[j] = xh;
         const T dx = xh - x;
-        acc_t += dx * dx;
+        if ((unsigned)(j - D.pc_lo) >= (unsigned)D.pc_len) acc_t += dx * dx;  // cone blocks: pc_apply
     }
     double acc[1] = {(double)acc_t};
     block_sum<1>(acc, sm);
@@ -1129,15 +1129,18 @@ __device__ __forceinline__ void kkt_dual_body(const Dev<T>& D, int qidx) {
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D.n; j += stride) {
             const double ls = D.l64[j], us = D.u64[j];
             const double lam = D.c64[j] - kty[j];
-            const double mu = proj_lambda(lam, ls, us);
+            // a primal cone block's reduced costs were projected onto K_p^* by pc_apply; its
+            // variables add no bound term (the infimum of mu'x over K_p is 0)
+            const bool in_pc = (unsigned)(j - D.pc_lo) < (unsigned)D.pc_len;
+            const double mu = in_pc ? D.pc_mu[(size_t)q * D.pc_len + (j - D.pc_lo)] : proj_lambda(lam, ls, us);
             sums[0] += (lam - mu) * (lam - mu);
             sums[1] += D.c64[j] * xc[j];
-            if (mu > 0.0) sums[2] += ls * mu;
-            if (mu < 0.0) sums[2] += us * mu;
+            if (!in_pc && mu > 0.0) sums[2] += ls * mu;
+            if (!in_pc && mu < 0.0) sums[2] += us * mu;
             const double dx = xc[j] - (double)D.x0[j];
             sums[3] += dx * dx;
             const double lu = lam / D.dc[j];
-            mx[0] = fmax(mx[0], fabs(lu - proj_lambda(lu, D.l_orig[j], D.u_orig[j])));
+            mx[0] = fmax(mx[0], fabs(lu - (in_pc ? mu / D.dc[j] : proj_lambda(lu, D.l_orig[j], D.u_orig[j]))));
             mx[1] = fmax(mx[1], fabs(kty[j] / D.dc[j]));
         }
         block_sum<4>(sums, sm);
@@ -1384,6 +1387,120 @@ __global__ void __launch_bounds__(kBlock) spmv_batch(const Dev<double>* __restri
         case 8: spmv_bin_rows<double, double, 8, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
         case 16: spmv_bin_rows<double, double, 16, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
         default: spmv_bin_rows<double, double, 32, U>(l, cnt, wb, nwb, rp, ci, val, x, y); break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Primal cone blocks x2 in K_p (Sec. 2, eq. prob_cp with n2 > 0): SOC / RSOC cones over
+// variables.  Their column scales are tied per block, so D^{-1} K_p = K_p and the projection
+// is the textbook one: (t, x) -> itself if ||x|| <= t, 0 if ||x|| <= -t, else
+// a (1, x / ||x||) with a = (t + ||x||) / 2; an RSOC block is rotated by
+// Q = [[1, 1], [1, -1]] / sqrt2 (+) I first and back after.  Two launches over the grid
+// (cone k = blockIdx.x, chunk b = blockIdx.y, source q = blockIdx.z): pc_reduce writes each
+// chunk's sum of squares of the (rotated) x part and, from chunk 0, the (rotated) first entry;
+// pc_apply sums a cone's chunk partials in a fixed order (the same in every block of the cone)
+// and projects its chunk.  Sources: kPcHat the x-hat of this evaluation, projected in place,
+// with the cone variables' ||x-hat - x||^2 partials (primal_update leaves them out) in the
+// primal slots after primal_update's; kPcCand the candidates, in place; kPcLam the candidates'
+// reduced costs lambda = c - K'y, projected onto K_p^* (= K_p) into pc_mu for kkt_dual.
+// ---------------------------------------------------------------------------
+constexpr double kSqrtHalf = 0.70710678118654752440;
+
+template <typename T>
+__device__ __forceinline__ bool pc_active(const Dev<T>& D, int mode, int q) {
+    const Ctrl* C = D.ctrl;
+    if (C->status != kRunning) return false;
+    if (mode == kPcHat) return C->xnext == 0;
+    return q < n_candidates(C);
+}
+
+// entry j (a variable of a cone block) of source q
+template <typename T>
+__device__ __forceinline__ double pc_src(const Dev<T>& D, int mode, int q, int j) {
+    if (mode == kPcHat) return (double)(D.ctrl->xsel ? D.xh1 : D.xh)[j];
+    if (mode == kPcCand) return D.xc[(size_t)q * D.n + j];
+    return D.c64[j] - D.ktyc[(size_t)q * D.n + j];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) pc_reduce(Dev<T> D, int mode) {
+    const int k = blockIdx.x, b = blockIdx.y, q = blockIdx.z;
+    if (!pc_active(D, mode, q)) return;
+    __shared__ double sm[1][kWarpsPerBlock];
+    const int o = D.pc_off[k], d = D.pc_dim[k];
+    const bool rot = D.pc_rot[k] != 0;
+    const int i0 = b * kPcChunk, i1 = min(d, i0 + kPcChunk);
+    double acc[1] = {0.0};
+    for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) {
+        if (i == 0) continue;  // t
+        const double v = pc_src(D, mode, q, o + i);
+        const double w = (rot && i == 1) ? (pc_src(D, mode, q, o) - v) * kSqrtHalf : v;
+        acc[0] += w * w;
+    }
+    block_sum<1>(acc, sm);
+    if (threadIdx.x == 0) {
+        D.pc_ss[((size_t)q * D.n_pc + k) * D.pc_nch + b] = acc[0];
+        if (b == 0) {
+            const double v0 = pc_src(D, mode, q, o);
+            D.pc_t[(size_t)q * D.n_pc + k] = rot ? (v0 + pc_src(D, mode, q, o + 1)) * kSqrtHalf : v0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) pc_apply(Dev<T> D, int mode) {
+    const int k = blockIdx.x, b = blockIdx.y, q = blockIdx.z;
+    if (!pc_active(D, mode, q)) return;
+    __shared__ double sm[1][kWarpsPerBlock];
+    __shared__ double s_t, s_sc;
+    const int o = D.pc_off[k], d = D.pc_dim[k];
+    const bool rot = D.pc_rot[k] != 0;
+    const int i0 = b * kPcChunk, i1 = min(d, i0 + kPcChunk);
+    double* slot = D.part + D.pl.off_px + D.pc_slot0 + (size_t)k * D.pc_nch + b;
+    if (i0 >= i1) {
+        if (mode == kPcHat && threadIdx.x == 0) *slot = 0.0;
+        return;
+    }
+    const double ss = block_reduce_parts(D.pc_ss + ((size_t)q * D.n_pc + k) * D.pc_nch, D.pc_nch, sm);
+    if (threadIdx.x == 0) {
+        const double t = D.pc_t[(size_t)q * D.n_pc + k], nx = sqrt(ss);
+        if (nx <= t) { s_t = t; s_sc = 1.0; }
+        else if (nx <= -t) { s_t = 0.0; s_sc = 0.0; }
+        else { const double a = 0.5 * (t + nx); s_t = a; s_sc = a / nx; }
+    }
+    __syncthreads();
+    const double tn = s_t, sc = s_sc;
+    T* xhat = D.ctrl->xsel ? D.xh1 : D.xh;
+    double acc[1] = {0.0};
+    auto put = [&](int j, double val) {
+        if (mode == kPcHat) {
+            xhat[j] = (T)val;
+            const double dx = (double)(T)val - (double)D.x[j];
+            acc[0] += dx * dx;
+        } else if (mode == kPcCand) {
+            D.xc[(size_t)q * D.n + j] = val;
+        } else {
+            D.pc_mu[(size_t)q * D.pc_len + (j - D.pc_lo)] = val;
+        }
+    };
+    for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) {
+        if (rot && i == 1) continue;  // written with entry 0
+        if (i == 0) {
+            if (rot) {
+                const double p1 = sc * ((pc_src(D, mode, q, o) - pc_src(D, mode, q, o + 1)) * kSqrtHalf);
+                const double e0 = (tn + p1) * kSqrtHalf, e1 = (tn - p1) * kSqrtHalf;
+                put(o, e0);
+                put(o + 1, e1);
+            } else {
+                put(o, tn);
+            }
+        } else {
+            put(o + i, sc * pc_src(D, mode, q, o + i));
+        }
+    }
+    if (mode == kPcHat) {
+        block_sum<1>(acc, sm);
+        if (threadIdx.x == 0) *slot = acc[0];
     }
 }
 

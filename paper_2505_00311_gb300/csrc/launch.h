@@ -27,6 +27,9 @@ namespace pdcs {
     /* grid-wise SOC cones (soc_team, mode 0 dual update, 1 candidates, 2 KKT): a cooperative  */                  \
     /* launch of D.team_nb blocks; nothing when D.team_nb == 0 */                                                  \
     cudaError_t k_soc_team(const Dev<T>& D, int mode, cudaStream_t s);                                            \
+    /* primal cone blocks (pc_reduce then pc_apply; mode kPcHat, kPcCand or kPcLam over nq sources); */            \
+    /* nothing when D.n_pc == 0 */                                                                                 \
+    void k_pc(const Dev<T>& D, int mode, int nq, cudaStream_t s);                                                 \
     /* resident blocks per SM of soc_team (0 on error) */                                                          \
     int k_team_occupancy(const Dev<T>*);                                                                           \
     /* y = A x over the binned rows of B (see spmv_binned); unroll 1, 2 or 4 */                                    \

@@ -157,6 +157,8 @@ struct pdcs_ctx {
     Ctrl* h_ctrl = nullptr;  // pinned host mirror
 
     Dev<double> D;
+    std::vector<pdcs_cone> pcones;  // primal cone blocks (options.primal_cones, copied)
+    long long pc_start = 0;
     SpmvPlan pk, pkt;  // K (m rows) and K' (n rows)
     // FP32-iterate mode: FP32 copies of K~, K~', c~, h~, l~, u~ and the iterate state;
     // checks, restarts and the final phase stay FP64 (D)
@@ -460,6 +462,7 @@ void enqueue_attempt_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     cudaStream_t s = ctx->stream;
     if (P) P->mark(0, s);
     k_primal_update(DT, ctx->g_vec_n, s);
+    k_pc(DT, kPcHat, 1, s);  // primal cone blocks of x-hat
     if (P) { P->mark(0, s); P->mark(1, s); }
     launch_spmv<T>(ctx->pk, s, DT.rp, DT.ci, DT.val, DT.xh, DT.kxh0, DT.kxh1, DT.ctrl, 1, 1, DT.xh1);
     if (P) { P->mark(1, s); P->mark(2, s); }
@@ -479,12 +482,13 @@ void enqueue_check_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     Dev<double>& D = ctx->D;
     auto mark = [&](int c) { if (P) P->mark(c, s); };
     mark(4);
-    ctx->launches += kLaunchesPerCheck + (DT.team_nb > 0 ? 2 : 0);
+    ctx->launches += kLaunchesPerCheck + (DT.team_nb > 0 ? 2 : 0) + (DT.n_pc > 0 ? 4 : 0);
     mark(5);
     k_flush_primal(DT, ctx->g_vec_n, s);
     k_flush_dual(DT, ctx->g_vec_m, s);
     mark(5); mark(6);
     k_cand_primal(DT, dim3(ctx->g_vec_n, 2), s);
+    k_pc(DT, kPcCand, 2, s);
     mark(6); mark(7);
     k_cand_dual(DT, dim3(ctx->g_dual, 2), s);
     k_soc_team(DT, 1, s);
@@ -499,6 +503,7 @@ void enqueue_check_t(pdcs_ctx* ctx, Dev<T>& DT, Prof* P) {
     k_kkt_primal(DT, dim3(ctx->g_dual, 2), s);
     k_soc_team(DT, 2, s);
     mark(9); mark(10);
+    k_pc(DT, kPcLam, 2, s);  // the candidates' reduced costs on the primal cone blocks
     k_kkt_dual(DT, ctx->g_kktd, s);
     mark(10); mark(11);
     k_restart_primal(DT, ctx->g_vec_n, s);
@@ -597,6 +602,22 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
             for (int e = 0; e < ctx->n_exp; ++e) { tie_o.push_back(ctx->exp_row0 + 3 * e); tie_l.push_back(3); }
     }
     ctx->n_tie = (int)tie_o.size();
+    // primal cone blocks: first variable, size and rotation of each, chunks of the largest
+    const int n_pc = (int)ctx->pcones.size();
+    std::vector<int> pc_o(n_pc + 1, 0), pc_dd(n_pc + 1, 0);
+    std::vector<unsigned char> pc_r(n_pc + 1, 0);
+    int pc_len = 0, pc_nch = 1;
+    for (int k = 0; k < n_pc; ++k) {
+        pc_o[k] = (int)ctx->pc_start + pc_len;
+        pc_dd[k] = (int)ctx->pcones[k].dim;
+        pc_r[k] = ctx->pcones[k].type == PDCS_CONE_RSOC;
+        pc_len += pc_dd[k];
+        pc_nch = std::max(pc_nch, (pc_dd[k] + kPcChunk - 1) / kPcChunk);
+    }
+    if (n_pc > 0 && (long long)n_pc * pc_nch > (1LL << 24)) {
+        ctx->err = "too many primal cone blocks for one launch";
+        return PDCS_ERR_INVALID;
+    }
 
     // ---- internal K (rows permuted) and K' by counting sort (host, once)
     std::vector<int> rp_i(m + 1), ci_i((size_t)nnz);
@@ -781,7 +802,7 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     const int kt_grid = (int)((hkt.long_row.size() + kWarpsPerBlock - 1) / kWarpsPerBlock +
                               (std::max<size_t>(hkt.slice_off.size(), 1) - 1 + kWarpsPerBlock - 1) / kWarpsPerBlock);
     PartLayout pl;
-    pl.primal_blocks = ctx->g_vec_n + (ctx->fuse_primal ? kt_grid : 0);
+    pl.primal_blocks = ctx->g_vec_n + (ctx->fuse_primal ? kt_grid : 0) + (n_pc > 0 ? n_pc * pc_nch : 0);
     pl.dual_blocks = team_nb > 0 ? team_gb0 + team_nb : ctx->g_dual;
     pl.kktp_blocks = ctx->g_dual + team_nb;
     pl.kktd_blocks = ctx->g_kktd;
@@ -834,6 +855,9 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         A.reserve<float>(m); A.reserve<float>(3LL * ctx->n_exp + 1);      // soc_w32, exp_lg32
     }
     if (ctx->opt.exp_mlp) A.reserve<float>(kExpMlpParams);
+    A.reserve<int>(n_pc + 1); A.reserve<int>(n_pc + 1); A.reserve<unsigned char>(n_pc + 1);  // pc_off dim rot
+    A.reserve<double>(2LL * n_pc * pc_nch + 1); A.reserve<double>(2LL * n_pc + 1);            // pc_ss, pc_t
+    A.reserve<double>(2LL * pc_len + 1);                                                       // pc_mu
     {
         cudaError_t e = cudaMalloc(&A.base, A.plan);
         if (e != cudaSuccess) {
@@ -898,6 +922,15 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.kxh0 = A.take<double>(m); D.kxh1 = A.take<double>(m); D.kx0 = A.take<double>(m); D.ysum = A.take<double>(m);
     D.xc = A.take<double>(2LL * n); D.yc = A.take<double>(2LL * m); D.kxc = A.take<double>(2LL * m);
     D.ktyc = A.take<double>(2LL * n); D.scr = A.take<double>(2LL * m);
+    int* d_pc_off = A.take<int>(n_pc + 1);
+    int* d_pc_dim = A.take<int>(n_pc + 1);
+    unsigned char* d_pc_rot = A.take<unsigned char>(n_pc + 1);
+    D.pc_ss = A.take<double>(2LL * n_pc * pc_nch + 1);
+    D.pc_t = A.take<double>(2LL * n_pc + 1);
+    D.pc_mu = A.take<double>(2LL * pc_len + 1);
+    D.pc_off = d_pc_off; D.pc_dim = d_pc_dim; D.pc_rot = d_pc_rot;
+    D.n_pc = n_pc; D.pc_lo = n_pc > 0 ? pc_o[0] : 0; D.pc_len = pc_len; D.pc_nch = pc_nch;
+    D.pc_slot0 = ctx->g_vec_n;
     Dev<float>& DF = ctx->DF;
     float *c_f = nullptr, *l_f = nullptr, *u_f = nullptr, *h_f = nullptr, *soc_w32 = nullptr, *exp_lg32 = nullptr;
     if (f32) {
@@ -951,6 +984,11 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
         CK(cudaMemcpyAsync(ctx->tie_off, tie_o.data(), sizeof(int) * ctx->n_tie, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->tie_len, tie_l.data(), sizeof(int) * ctx->n_tie, cudaMemcpyHostToDevice, s));
     }
+    if (n_pc > 0) {
+        CK(cudaMemcpyAsync(d_pc_off, pc_o.data(), sizeof(int) * n_pc, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_pc_dim, pc_dd.data(), sizeof(int) * n_pc, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_pc_rot, pc_r.data(), (size_t)n_pc, cudaMemcpyHostToDevice, s));
+    }
     // the host copies above are pageable: wait before the vectors go out of scope
     CK(cudaStreamSynchronize(s));
 
@@ -967,6 +1005,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
             scaled_row_norms<<<gr, kBlock, 0, s>>>(m, ctx->rp, ctx->ci, ctx->val0, ctx->dr, ctx->dc, 1, kind, ctx->rn);
             scaled_row_norms<<<gc, kBlock, 0, s>>>(n, ctx->rpT, ctx->ciT, ctx->val0T, ctx->dc, ctx->dr, 0, kind, ctx->cn);
             if (ctx->n_tie) tie_groups<<<(ctx->n_tie + 255) / 256, 256, 0, s>>>(ctx->n_tie, ctx->tie_off, ctx->tie_len, ctx->rn);
+            // the columns of a primal cone block share one factor (D^{-1} K_p = K_p)
+            if (n_pc) tie_groups<<<(n_pc + 255) / 256, 256, 0, s>>>(n_pc, d_pc_off, d_pc_dim, ctx->cn);
             apply_norm<<<(m + 255) / 256, 256, 0, s>>>(m, ctx->rn, ctx->dr);
             apply_norm<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->cn, ctx->dc);
         }
@@ -1084,7 +1124,8 @@ pdcs_status build(pdcs_ctx* ctx, const pdcs_csr* K, const double* c, const doubl
     D.binsK = ctx->pk.B; D.binsKT = ctx->pkt.B; D.listK = ctx->pk.list; D.listKT = ctx->pkt.list;
     ctx->launches_per_attempt = ctx->opt.batch_blocks > 0
                                     ? kLaunchesPerAttempt
-                                    : 3 + (nb_scal > 0) + (nb_soc > 0) + (nb_exp > 0) + (team_nb > 0);
+                                    : 3 + (nb_scal > 0) + (nb_soc > 0) + (nb_exp > 0) + (team_nb > 0) +
+                                          (n_pc > 0 ? 2 : 0);
 
     // ---- controller scalars
     Ctrl C;
@@ -1370,6 +1411,9 @@ void pdcs_default_options(pdcs_options* o) {
     o->soc_lane_entries = 0;
     o->soc_grid_dim = 0;
     o->fuse_primal = 0;
+    o->primal_cones = nullptr;
+    o->n_primal_cones = 0;
+    o->primal_cone_start = 0;
 }
 
 pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, const double* lb, const double* ub,
@@ -1427,10 +1471,30 @@ pdcs_status pdcs_create(const pdcs_csr* K, const double* c, const double* h, con
     if (o.fuse_primal != 0 && o.fuse_primal != 1) return bad("fuse_primal must be 0 or 1");
     if (o.spmv_format == 2 && (o.batch_blocks > 0 || o.spmv_lanes != 0))
         return bad("the sliced SpMV format serves single programs with spmv_lanes = 0");
+    if (o.n_primal_cones < 0 || (o.n_primal_cones > 0 && !o.primal_cones)) return bad("bad primal cone list");
+    if (o.n_primal_cones > 0) {
+        if (o.precision != PDCS_PRECISION_FP64 || o.batch_blocks > 0 || o.fuse_primal)
+            return bad("primal cones need FP64 iterates, a single program and separate primal updates");
+        long long pt = 0;
+        for (int64_t k = 0; k < o.n_primal_cones; ++k) {
+            const int t = o.primal_cones[k].type;
+            const long long d = o.primal_cones[k].dim;
+            if ((t != PDCS_CONE_SOC && t != PDCS_CONE_RSOC) || d < (t == PDCS_CONE_RSOC ? 2 : 1))
+                return bad("primal cones are SOC (dim >= 1) or RSOC (dim >= 2)");
+            pt += d;
+        }
+        if (o.primal_cone_start < 0 || o.primal_cone_start + pt > K->n) return bad("primal cones exceed n");
+        for (long long j = o.primal_cone_start; j < o.primal_cone_start + pt; ++j)
+            if (!lb || !ub || lb[j] != -INFINITY || ub[j] != INFINITY)
+                return bad("primal cone variables must have lb = -inf and ub = +inf");
+    }
 
     pdcs_ctx* ctx = new (std::nothrow) pdcs_ctx();
     if (!ctx) return bad("host allocation failed");
     ctx->opt = o;
+    if (o.n_primal_cones > 0) ctx->pcones.assign(o.primal_cones, o.primal_cones + o.n_primal_cones);
+    ctx->pc_start = o.primal_cone_start;
+    ctx->opt.primal_cones = nullptr;  // copied; the caller's array need not outlive this call
     ctx->m = (int)K->m;
     ctx->n = (int)K->n;
     ctx->nnz = K->nnz;

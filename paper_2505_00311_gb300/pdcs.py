@@ -47,7 +47,9 @@ class pdcs_options(ctypes.Structure):
                 ("spmv_lanes", ctypes.c_int32), ("time_limit", ctypes.c_double),
                 ("exp_mlp", ctypes.c_void_p), ("spmv_autotune", ctypes.c_int32), ("batch_blocks", ctypes.c_int32),
                 ("spmv_format", ctypes.c_int32), ("soc_lane_entries", ctypes.c_int32),
-                ("soc_grid_dim", ctypes.c_int32), ("fuse_primal", ctypes.c_int32)]
+                ("soc_grid_dim", ctypes.c_int32), ("fuse_primal", ctypes.c_int32),
+                ("primal_cones", ctypes.c_void_p), ("n_primal_cones", ctypes.c_int64),
+                ("primal_cone_start", ctypes.c_int64)]
 
 
 class pdcs_info(ctypes.Structure):
@@ -193,7 +195,8 @@ def pdcs_last_error(ctx=None):
 
 def pdcs_create(prob, options=None, stream=None):
     """Creates a solver for ``prob`` (dict with m, n, row_ptr, col, val, c, h, lb, ub,
-    cone_types, cone_dims; host arrays).  Returns the opaque context handle."""
+    cone_types, cone_dims and optionally the primal cone blocks pcone_types, pcone_dims,
+    pcone_start; host arrays).  Returns the opaque context handle."""
     rp = np.ascontiguousarray(prob["row_ptr"], dtype=np.int64)
     ci = np.ascontiguousarray(prob["col"], dtype=np.int32)
     val = _f64(prob["val"])
@@ -204,6 +207,13 @@ def pdcs_create(prob, options=None, stream=None):
     K = pdcs_csr(int(prob["m"]), int(prob["n"]), int(rp[-1]), _ptr(rp, _i64p), _ptr(ci, _i32p), _ptr(val))
     cones = _cones(prob["cone_types"], prob["cone_dims"])
     opt = options if options is not None else pdcs_default_options()
+    pcones = None
+    if len(prob.get("pcone_types", [])):  # copied by pdcs_create
+        pcones = _cones(prob["pcone_types"], prob["pcone_dims"])
+        opt = pdcs_options.from_buffer_copy(opt)
+        opt.primal_cones = ctypes.addressof(pcones)
+        opt.n_primal_cones = len(pcones)
+        opt.primal_cone_start = int(prob.get("pcone_start", 0))
     out = ctypes.c_void_p()
     st = lib().pdcs_create(ctypes.byref(K), _ptr(c), _ptr(h), _ptr(lb), _ptr(ub), cones, len(cones),
                            ctypes.byref(opt), stream, ctypes.byref(out))

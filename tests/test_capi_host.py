@@ -97,6 +97,18 @@ def test_validation_rejects_bad_input(lib):
     _bad(q)
 
 
+def test_validation_rejects_bad_primal_cones(lib):
+    p = I.primal_cone_program(seed=7, n_before=6, pcone_dims=(4, 5), n_after=3, m=16, row_nnz=4)
+    assert "lb = -inf" in _bad(dict(p, lb=np.zeros(p["n"])))
+    assert "SOC" in _bad(dict(p, pcone_types=np.array([P.CONE_SOC, P.CONE_EXP], np.int32)))
+    assert "SOC" in _bad(dict(p, pcone_types=np.array([P.CONE_SOC, P.CONE_RSOC], np.int32),
+                              pcone_dims=np.array([4, 1], np.int64)))
+    assert "exceed" in _bad(dict(p, pcone_start=p["n"] - 3))
+    assert "FP64" in _bad(p, precision=P.PRECISION_FP32)
+    assert "FP64" in _bad(p, fuse_primal=1)
+    assert "FP64" in _bad(p, batch_blocks=64)
+
+
 def test_missing_library_fails_loudly():
     """No CPU fallback: without the CUDA library every entry point raises."""
     import subprocess

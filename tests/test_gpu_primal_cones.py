@@ -1,0 +1,135 @@
+"""Primal cone blocks x2 in K_p (Sec. 2, eq. prob_cp with n2 > 0; SOC / RSOC cones over
+variables) against the FP64 oracle: tied column scales, one PDHG evaluation from the oracle's
+states, windows of evaluations with checks, the check errors against the oracle's KKT
+evaluator, a solve to the known optimum, and the App. B.2 Lasso in the appendix's own form
+(the cone on (w, r, y)) against the same Lasso with the cone as rows."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_00311_gb300 import build as B
+from paper_2505_00311_gb300 import instances as I
+from paper_2505_00311_gb300 import pdcs as P
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    oracle.build()
+
+
+def rel_inf(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
+
+
+# a cone of 2,500 variables spans three blocks of the projection kernels (1,024 each)
+PROGRAMS = {
+    "small": dict(seed=4),
+    "chunked": dict(seed=8, n_before=200, pcone_dims=(3, 2500, 7, 1, 40), n_after=100, m=600, row_nnz=10),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PROGRAMS))
+def test_scaling_is_tied_per_block_and_matches_the_oracle(name):
+    p = I.primal_cone_program(**PROGRAMS[name])
+    g, o = P.Solver(p), oracle.Solver(p)
+    gdr, gdc = g.scaling()
+    odr, odc = o.scaling()
+    assert rel_inf(gdr, odr) <= 1e-13 and rel_inf(gdc, odc) <= 1e-13
+    s = p["pcone_start"]
+    for d in p["pcone_dims"]:
+        assert np.all(gdc[s:s + int(d)] == gdc[s])
+        s += int(d)
+    g.close()
+
+
+@pytest.mark.parametrize("name", sorted(PROGRAMS))
+@pytest.mark.parametrize("beta", [1.0, 0.5])
+def test_one_evaluation_with_primal_cones(name, beta):
+    """From the oracle's states after 0, 64 and 500 evaluations: x-hat (the cone blocks
+    projected onto K_p), y-hat per role, the next Halpern iterate and eta within 1e-12."""
+    from parity_helpers import one_evaluation
+    p = I.primal_cone_program(**PROGRAMS[name])
+    o = oracle.Solver(p, check_period=64, beta=beta)
+    g = P.Solver(p, check_period=64, beta=beta)
+    done = 0
+    for start in [0, 64, 500]:
+        o.run(start - done)
+        err, acc = one_evaluation(p, g, o)
+        done = start + 1
+        assert acc[0] == acc[1] and max(err.values()) <= RTOL, (start, err)
+    g.close()
+
+
+def test_window_with_primal_cones():
+    """32 evaluations with checks every 16 (candidates projected onto the cone blocks,
+    restarts): counters equal, iterates within 1e-12 over the first 16, 1e-11 after."""
+    p = I.primal_cone_program(**PROGRAMS["chunked"])
+    g = P.Solver(p, check_period=16, beta=0.5)
+    o = oracle.Solver(p, check_period=16, beta=0.5)
+    done = 0
+    for target in [1, 2, 3, 8, 15, 16, 17, 24, 32]:
+        g.run(target - done)
+        o.run(target - done)
+        done = target
+        gs, os_ = g.info(), o.scalars()
+        assert gs["attempts"] == os_["attempts"] and gs["accepted"] == os_["accepted"]
+        assert gs["restarts"] == os_["restarts"]
+        gx, gy, gxh, gyh = g.iterate()
+        ox, oy, oxh, oyh = o.iterate()
+        err = max(rel_inf(gx, ox), rel_inf(gy, oy), rel_inf(gxh, oxh), rel_inf(gyh, oyh))
+        assert err <= (RTOL if target <= 16 else 10 * RTOL), (target, err)
+    g.close()
+
+
+def test_checks_agree_with_the_oracle_evaluator():
+    """The device's check (reduced costs of the cone variables projected onto K_p^*, no bound
+    term for them) gives the oracle evaluator's errors for the returned solution."""
+    p = I.primal_cone_program(**PROGRAMS["chunked"])
+    g = P.Solver(p, beta=0.5)
+    for n in (64, 640, 3200):
+        g.run(n)
+        inf = g.info()
+        x, y = g.solution()
+        k = oracle.kkt(p, x, y)
+        for key in ("err_p", "err_d", "err_gap", "pobj", "dobj"):
+            assert abs(inf[key] - k[key]) <= 1e-7 * max(abs(k[key]), 1e-12) + 1e-15, (n, key, inf[key], k[key])
+    g.close()
+
+
+@pytest.mark.parametrize("name", sorted(PROGRAMS))
+def test_solve_with_primal_cones_reaches_the_known_optimum(name):
+    p = I.primal_cone_program(**PROGRAMS[name])
+    g = P.Solver(p, beta=0.5)
+    st, info = g.solve(1e-6, 400_000)
+    assert st == P.OK, info
+    x, y = g.solution()
+    k = oracle.kkt(p, x, y)
+    assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1e-6, k
+    assert k["pobj"] == pytest.approx(p["obj_star"], rel=1e-5)
+    g.close()
+
+
+def test_paper_lasso_with_a_primal_cone_matches_the_row_form():
+    """The App. B.2 Lasso (1,000 x 10,000, density 1e-4) with (w, r, y) in K_rsoc as a primal
+    cone block and with the cone as m + 2 rows: both reach 1e-6 at the same Lasso objective,
+    both judged by the oracle's KKT evaluator."""
+    objs = {}
+    for f in (I.lasso_paper, I.lasso_paper_kp):
+        q = f(0, 1000, 10000, 1e-4)
+        g = P.Solver(q)
+        st, info = g.solve(1e-6, 400_000)
+        assert st == P.OK, (q["name"], info)
+        x, y = g.solution()
+        k = oracle.kkt(q, x, y)
+        assert max(k["err_p"], k["err_d"], k["err_gap"]) <= 1e-6, (q["name"], k)
+        A, b, lam = q["lasso"]["A"], q["lasso"]["b"], q["lasso"]["lam"]
+        m, n = A.shape
+        w = x[2 + m:2 + m + n] - x[2 + m + n:]
+        objs[q["name"]] = float(np.sum((A @ w - b) ** 2) + lam * np.abs(w).sum())
+        g.close()
+    assert objs["lasso_paper_kp"] == pytest.approx(objs["lasso_paper"], rel=1e-5)
