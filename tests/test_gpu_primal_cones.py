@@ -29,7 +29,7 @@ def rel_inf(a, b):
 # a cone of 2,500 variables spans three blocks of the projection kernels (1,024 each)
 PROGRAMS = {
     "small": dict(seed=4),
-    "chunked": dict(seed=8, n_before=200, pcone_dims=(3, 2500, 7, 1, 40), n_after=100, m=600, row_nnz=10),
+    "chunked": dict(seed=8, n_before=200, pcone_dims=(1, 2500, 7, 2, 40), n_after=100, m=600, row_nnz=10),
 }
 
 
@@ -89,7 +89,7 @@ def test_window_with_primal_cones():
 def test_checks_agree_with_the_oracle_evaluator():
     """The device's check (reduced costs of the cone variables projected onto K_p^*, no bound
     term for them) gives the oracle evaluator's errors for the returned solution."""
-    p = I.primal_cone_program(**PROGRAMS["chunked"])
+    p = I.primal_cone_program(**PROGRAMS["small"])
     g = P.Solver(p, beta=0.5)
     for n in (64, 640, 3200):
         g.run(n)
