@@ -597,6 +597,27 @@ def main():
             if st != P.OK:
                 break
         sl.close()
+        # the same Lasso in the appendix's own form: (w, r, y) in K_rsoc as a primal cone block,
+        # the m + 1 zero rows only (each solve call limited to half the time-to-tolerance limit)
+        qk = I.lasso_paper_kp(0, 70_000, 700_000, 1e-4)
+        sk = P.Solver(qk, stream=stream.cuda_stream, time_limit=args.ttt_limit / 2)
+        kp = {"form": "primal cone block of %d variables, %d rows, nnz = %d" %
+                      (int(qk["pcone_dims"][0]), qk["m"], int(qk["row_ptr"][-1])),
+              "setup_seconds": sk.info()["setup_seconds"], "time_to_tol": []}
+        total_s = 0.0
+        for tol in (1e-3, 1e-6):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, inf = sk.solve(tol, 10_000_000)
+            torch.cuda.synchronize()
+            total_s += time.perf_counter() - t0
+            kp["time_to_tol"].append({"tol": tol, "seconds": total_s, "status": P.STATUS_NAMES.get(st, st),
+                                      "evaluations": inf["attempts"],
+                                      "err": [inf["err_p"], inf["err_d"], inf["err_gap"]]})
+            if st != P.OK:
+                break
+        sk.close()
+        lasso["primal_cone_form"] = kp
 
     # the exp-cone-heavy program (l1 logistic regression, 400k exp cones), plain exp root
     # search against the learned starting point: the first evaluation (no cached roots), the
