@@ -249,6 +249,8 @@ def primal_cone_program(seed: int = 4, n_before: int = 300, pcone_dims=(5, 40, 2
     pcone_dims = [int(d) for d in pcone_dims]
     if pcone_types is None:
         pcone_types = [SOC if k % 2 == 0 else RSOC for k in range(len(pcone_dims))]
+    if any(d < (2 if t == RSOC else 1) for t, d in zip(pcone_types, pcone_dims)):
+        raise ValueError("an SOC block needs at least 1 variable, an RSOC block at least 2")
     n_pc = sum(pcone_dims)
     n = n_before + n_pc + n_after
     row_ptr = np.arange(m + 1, dtype=np.int64) * row_nnz
